@@ -1,0 +1,125 @@
+"""Seeded synthetic workloads: parameter sets and initial fields.
+
+This module is the only code shared by the CUDA path's tests/benchmark and
+the CPU oracle.  It holds no arithmetic of the method itself: it converts the
+dimensionless groups of the paper's test cases into lattice parameters and
+draws initial fields (a circular / spherical droplet or bubble, uniform bulk
+surfactant outside it, optional seeded perturbations).
+
+Parameter keys (lattice units, delta_x = delta_t = 1):
+  nx, ny, nz            grid (nz = 1: D2Q9, nz > 1: D3Q19)
+  wall[3]               0 periodic / 1 half-way bounce-back walls per axis
+  uw_lo, uw_hi          3x3 wall velocities (row = axis of the wall)
+  rhoR0, rhoB0          pure-phase densities (red = droplet/bubble)
+  muR0, muB0            pure-phase dynamic viscosities
+  alphaR, alphaB        sound-speed parameters (light phase standard,
+                        heavy phase from the density ratio, Eq. 42)
+  sigma0, sigma_min_ratio, E0, psi_inf, beta
+  eos (0 Langmuir, 1 linear), source (0 Eq. 22, 1 r_a psi_inf C),
+  transport (1 solve the surfactant equations, 0 hold psi, C fixed)
+  Ds, Db, ra, rd, g[3], sor_omega, eps_w, eps_n
+  geometry: center[3], R, width, C0, psi0
+"""
+import math
+
+import numpy as np
+
+ALPHA_STD = {2: 4.0 / 9.0, 3: 1.0 / 3.0}
+
+
+def _alphas(D, rhoR0, rhoB0):
+    """Light phase standard; heavy phase alpha from Eq. 42 (equal pressure
+    of the two pure phases at rest)."""
+    a_std = ALPHA_STD[D]
+    if rhoR0 <= rhoB0:
+        gamma = rhoR0 / rhoB0
+        return a_std, 1.0 - gamma * (1.0 - a_std)
+    gamma = rhoB0 / rhoR0
+    return 1.0 - gamma * (1.0 - a_std), a_std
+
+
+def base(nx, ny, nz=1):
+    D = 2 if nz == 1 else 3
+    a = ALPHA_STD[D]
+    return dict(
+        nx=nx, ny=ny, nz=nz, wall=[0, 0, 0],
+        uw_lo=[[0.0] * 3 for _ in range(3)], uw_hi=[[0.0] * 3 for _ in range(3)],
+        rhoR0=1.0, rhoB0=1.0, muR0=0.1, muB0=0.1, alphaR=a, alphaB=a,
+        sigma0=0.1, sigma_min_ratio=0.1, E0=0.5, psi_inf=1.0, beta=0.7,
+        eos=0, source=0, transport=1,
+        Ds=0.1, Db=0.1, ra=0.0, rd=0.0, g=[0.0, 0.0, 0.0],
+        sor_omega=1.2, eps_w=1e-6, eps_n=1e-6,
+        center=[(nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0],
+        R=min(nx, ny) / 4.0, width=3.0, C0=0.0, psi0=0.0,
+    )
+
+
+def droplet_adsorption_2d(n=128, R=25.0, C0=0.5):
+    """2D stationary droplet adsorbing bulk surfactant (the 2D analogue of
+    the paper's Sec. 3.1 test): D2Q9 n x n periodic, density and viscosity
+    ratio 1 (rho = 1, mu = 0.1), sigma = 0.1, D_s = D_b = 0.1, E0 = 0.5,
+    simple source j = r_a psi_inf C with r_a = 0.2, psi = 0 initially, bulk
+    C0 outside the droplet, 0 inside."""
+    c = base(n, n)
+    c.update(R=float(R), C0=float(C0), ra=0.2, source=1, name="droplet_adsorption_2d")
+    return c
+
+
+def bubble_rise_2d(nx=256, ny=1024, D_b=64.0, Eo=10.0, Mo=0.1, Bi=1.0, Pe=10.0,
+                   k=1.0, h=0.5, E0=0.5, C0=0.5, sigma0=0.004, rho_ratio=10.0,
+                   mu_ratio=10.0, y0=None):
+    """2D buoyant bubble in a walled channel (2D version of Sec. 3.4):
+    D2Q9 nx x ny, bounce-back walls at x = -1/2 and nx - 1/2, periodic in y,
+    gravity along -y.  Lattice parameters from the dimensionless groups:
+      g   = Eo sigma0 / (drho (2R)^2)                  (Eotvos number)
+      muB = (Mo rhoB0^2 sigma0^3 / (drho g))^(1/4)     (Morton number)
+      U_ref = sqrt(2 R g), t_ref = 2R / U_ref          (tau of Sec. 3.4)
+      r_d = Bi / t_ref, D_s = D_b = U_ref 2R / Pe, r_a = k r_d / C0
+      psi_inf = h C0 R (1 + k) / k   (h of Sec. 3.3 with psi0 taken as the
+                                      equilibrium coverage psi_inf k/(1+k))."""
+    R = D_b / 2.0
+    rhoB0, rhoR0 = 1.0, 1.0 / rho_ratio
+    drho = rhoB0 - rhoR0
+    g = Eo * sigma0 / (drho * (2 * R) ** 2)
+    muB = (Mo * rhoB0 ** 2 * sigma0 ** 3 / (drho * g)) ** 0.25
+    U = math.sqrt(2 * R * g)
+    t_ref = 2 * R / U
+    rd = Bi / t_ref
+    Dd = U * 2 * R / Pe
+    c = base(nx, ny)
+    aR, aB = _alphas(2, rhoR0, rhoB0)
+    c.update(
+        name="bubble_rise_2d", wall=[1, 0, 0], rhoR0=rhoR0, rhoB0=rhoB0,
+        muB0=muB, muR0=muB / mu_ratio, alphaR=aR, alphaB=aB,
+        sigma0=sigma0, E0=E0, psi_inf=h * C0 * R * (1 + k) / k,
+        Ds=Dd, Db=Dd, rd=rd, ra=k * rd / C0, source=0,
+        g=[0.0, -g, 0.0], R=R, C0=C0, psi0=0.0,
+        center=[(nx - 1) / 2.0, (2.0 * R if y0 is None else y0), 0.0],
+        Eo=Eo, Mo=Mo, Bi=Bi, Pe=Pe, U_ref=U, t_ref=t_ref,
+    )
+    return c
+
+
+def initial_fields(cfg, seed=None, noise=0.0, u0=None):
+    """Colour field phi = tanh((R - r)/width) (red inside), psi = psi0 times
+    the interface indicator (1 - phi^2), C = C0 (1 - phi)/2 (bulk surfactant
+    in the blue fluid only).  With a seed, psi and C receive multiplicative
+    uniform noise of relative amplitude `noise` and u gets an additive field
+    of amplitude `u0` (both break mirror symmetry for parity tests)."""
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg.get("nz", 1)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cx, cy, cz = cfg["center"]
+    r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + ((z - cz) ** 2 if nz > 1 else 0.0))
+    phi = np.tanh((cfg["R"] - r) / cfg["width"])
+    psi = cfg["psi0"] * (1.0 - phi ** 2)
+    C = cfg["C0"] * 0.5 * (1.0 - phi)
+    u = np.zeros((3, nz, ny, nx))
+    if seed is not None:
+        rng = np.random.default_rng(seed)
+        if noise:
+            psi = psi * (1.0 + noise * rng.uniform(-1, 1, psi.shape))
+            C = C * (1.0 + noise * rng.uniform(-1, 1, C.shape))
+        if u0:
+            D = 2 if nz == 1 else 3
+            u[:D] = u0 * rng.uniform(-1, 1, (D, nz, ny, nx))
+    return dict(phi=phi, psi=psi, C=C, u=u)
