@@ -1,0 +1,298 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled LB-FD time step (arXiv 2311.15242) on GB300.
+
+Workload: the 2D buoyant bubble rise in a walled channel, D2Q9 256 x 1024,
+bubble diameter 64, density ratio 10, viscosity ratio 10, Eo = 10, Mo = 0.1,
+Bi = 1, bulk C0 = 0.5, psi = 0 initially (seeded synthetic initial state).
+A step is one full coupled update (LB step + surfactant FD step with its SOR
+solve and rescale) of the whole grid.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lbs|reference]
+
+Timing: W untimed warm-up steps, then K steps, each timed with CUDA events on
+the solver's stream; L2 (126 MB) is flushed by a 256 MiB write before every
+timed step, outside the events.  With N > 1 (torchrun) every rank runs an
+independent replica (weak scaling); the slowest rank's time is reported.
+The reference arm (--impl reference) times the FP64 CPU oracle on the same
+workload on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "coupled-step MLUPS and % of HBM roofline (1 GB300), mixed/batched vs plain FP32"
+UNIT = "MLUPS"
+
+# Algorithmic bytes per cell of each kernel group in FP32 (each input and
+# output field of the group read or written once; derivation in the design doc).
+ALG_BYTES_F32 = {"force": 44, "fd": 48, "collide": 176, "stream": 172, "grad": 28,
+                 "surf": 40}
+SOR_BYTES_PER_SWEEP_F32 = 32
+
+# DRAM bytes per launch of the collide kernel group from one ncu capture of
+# the source tree with this hash (scaled to the 256 x 1024 grid); None when
+# not captured for the current kernels.
+TRAFFIC = {"kernel": "collide", "src_sha": None, "bytes_per_launch": None}
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2311_15242_gb300", "csrc")
+    for n in sorted(os.listdir(d)):
+        if n.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def workload():
+    cfg = W.bubble_rise_2d()
+    name = ("bubble_rise_2d D2Q9 256x1024 walls-x periodic-y, D=64, rho 0.1/1, "
+            "mu ratio 10, Eo=10, Mo=0.1, Bi=1, Pe=10, C0=0.5")
+    return cfg, name
+
+
+def reference_arm(args, rank):
+    """FP64 CPU oracle on the host cores, same workload and metric."""
+    if rank != 0:
+        return 0
+    from oracle.ora import Oracle
+    cfg, name = workload()
+    f = W.initial_fields(cfg, seed=0)
+    o = Oracle(cfg)
+    o.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    cells = cfg["nx"] * cfg["ny"]
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = cells * args.steps / dt / 1e6
+    sample = f"{name}: steps {args.warmup + 1}..{args.warmup + args.steps} of the seeded run"
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": name, "cells": cells},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def cpu_baseline(cfg, name, budget_s=15.0):
+    """The oracle as it stands, single-threaded, on a bounded sample."""
+    from oracle.ora import Oracle
+    f = W.initial_fields(cfg, seed=0)
+    o = Oracle(cfg)
+    o.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    cells = cfg["nx"] * cfg["ny"]
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    n = int(max(2, min(60, budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    return {"value": cells * n / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{name}: steps 2..{n + 1} of the seeded run on the full grid"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lbs", choices=["lbs", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2311_15242_gb300 import Solver
+
+    cfg, name = workload()
+    cells = cfg["nx"] * cfg["ny"]
+    f = W.initial_fields(cfg, seed=0)
+    s = Solver(cfg, storage=args.storage)
+    s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    s.profile(True)
+    stream = s.stream
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def one_step(timed):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)  # evict L2 (outside the events)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.step(1)
+            b.record(stream)
+        b.synchronize()
+        kt = s.kernel_times() if timed else None
+        return a.elapsed_time(b), kt
+
+    for _ in range(args.warmup):
+        one_step(False)
+    s.sync()
+
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times, ktimes = [], []
+    for _ in range(args.steps):
+        t, kt = one_step(True)
+        times.append(t)
+        ktimes.append(kt)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    s.sync()
+    total_ms = float(sum(times))
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * cells * args.steps / (total_ms / 1e3) / 1e6
+
+    # per-group device time (mean over the timed steps)
+    groups = list(ktimes[0].keys())
+    kmean = {g: float(np.mean([k[g] for k in ktimes])) for g in groups}
+    sweeps = s.diagnostics()["sor_iters_psi"]
+    dom = max((g for g in groups if g in ALG_BYTES_F32), key=lambda g: kmean[g])
+    scale = 2 if args.storage == "f64" else 1
+    alg = ALG_BYTES_F32[dom] * scale * cells
+    hbm, src = peaks()
+    achieved = alg / (kmean[dom] / 1e3) / 1e9
+    sha = src_hash()
+    traffic = TRAFFIC["bytes_per_launch"] if (TRAFFIC["src_sha"] == sha and dom == TRAFFIC["kernel"]) else None
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+            "peak_source": src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+            "alg_bytes_per_launch": alg, "avg_launch_ms": kmean[dom]}
+
+    # end to end through the C ABI with host buffers
+    pin = {k: torch.from_numpy(np.ascontiguousarray(f[k])).pin_memory().numpy()
+           for k in ("phi", "psi", "C")}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.init_fields(pin["phi"], pin["psi"], pin["C"], None)
+    d2h = 0
+    for _ in range(args.steps):
+        s.step(1)
+        s.diagnostics()
+        d2h += 2352 + 4  # control block and status word read by lbs_diagnostics
+    s.fields()
+    e2e_dt = time.perf_counter() - t0
+    N = cells
+    e2e = {"value": cells * args.steps / e2e_dt / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": 3 * N * 8 / args.steps,
+           "d2h_bytes_per_step": (d2h + 7 * N * 8) / args.steps}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
+           "data": "synthetic",
+           "config": {"workload": name, "cells": cells, "storage": args.storage,
+                      "l2": "flushed before every timed step (256 MiB write)",
+                      "parallelism": f"replicas x{world}" if world > 1 else "single"},
+           "roofline": roof, "kernel_ms": kmean, "sor_sweeps": sweeps,
+           "gpu_launches": args.steps * s.kernel_count(),
+           "clocks": clk, "e2e": e2e, "impl": "lbs", "src_sha": sha}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, name)
+    s.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * lbs.h — C ABI of the GB300 hybrid lattice Boltzmann / finite-difference
+ * solver for two-phase flow with soluble surfactants (Ba, Liu, Li & Yang,
+ * arXiv 2311.15242).
+ *
+ * One call of lbs_step advances the coupled update of the paper by one time
+ * step on the GPU:
+ *   Sec. 2.1   colour-gradient LB step: MRT collision with the correction
+ *              term and the forcing term (Eqs. 1-4, App. A Eqs. 36-43), the
+ *              interfacial force from the modified Langmuir equation of state
+ *              with the Marangoni term (Eqs. 5-9), the velocity of Eq. 10,
+ *              recolouring (Eqs. 11-12), streaming with half-way bounce-back
+ *              (Eq. 13);
+ *   Sec. 2.2   finite-difference update of the interface and bulk surfactant
+ *              equations (Eqs. 20-22): WENO3 convection (Eqs. 25-27),
+ *              Crank-Nicolson diffusion (Eqs. 23-24, 28) solved by red-black
+ *              SOR with omega = 1.2, rescaling of the total surfactant.
+ *
+ * Conventions (all entry points):
+ *   - every function returns an lbs_status (0 = success) unless noted; no
+ *     exception or abort crosses the ABI; lbs_last_error() describes the
+ *     last failure of a context;
+ *   - host arrays are caller-owned, double precision, row-major [z][y][x]
+ *     (x fastest) with N = nx*ny*nz entries per scalar field and 3*N for a
+ *     vector field (component-major: [3][z][y][x]); the library copies them
+ *     and keeps no reference;
+ *   - device memory of a context is either allocated by the library or
+ *     supplied by the caller as one workspace (lbs_workspace_bytes); a
+ *     supplied workspace stays owned by the caller and must outlive the
+ *     context;
+ *   - a context is used by one host thread at a time; work is queued on the
+ *     context's CUDA stream (borrowed when given, never destroyed);
+ *   - lattice units: delta_x = delta_t = 1.
+ */
+#ifndef LBS_H
+#define LBS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBS_OK = 0,
+    LBS_EINVAL = -1,    /* invalid argument or parameter set */
+    LBS_ENOMEM = -2,    /* device allocation failed or workspace too small */
+    LBS_ECUDA = -3,     /* a CUDA runtime call failed */
+    LBS_ENOCONV = -4,   /* SOR did not reach sor_tol within sor_max_iter sweeps */
+    LBS_EDIVERGED = -5, /* NaN/Inf in the conserved totals */
+    LBS_ETIMEOUT = -6,  /* a bounded device-side wait gave up */
+    LBS_EBOUNDS = -7    /* an index check of a debug build failed */
+} lbs_status;
+
+/* arithmetic / storage form of the populations and fields */
+typedef enum {
+    LBS_F64 = 0, /* everything in double (reference-grade, slow on GB300) */
+    LBS_F32 = 1  /* FP32 storage and arithmetic, FP64 conservation sums */
+} lbs_storage;
+
+/* Physical and numerical parameters (one instance).  Names follow the paper:
+ * red = droplet/bubble (rho^N = +1), blue = surfactant-laden liquid. */
+typedef struct {
+    int nx, ny, nz;           /* grid; nz == 1 selects D2Q9 (2D) */
+    int wall[3];              /* per axis: 0 periodic, 1 half-way bounce-back
+                                 walls at both ends (Secs. 3.2-3.4, ref. [57]) */
+    double uw_lo[3][3];       /* velocity of the low wall of each axis (Sec. 3.3) */
+    double uw_hi[3][3];       /* velocity of the high wall of each axis */
+    double rhoR0, rhoB0;      /* pure-phase densities (Eq. 6) */
+    double muR0, muB0;        /* pure-phase dynamic viscosities (Eq. 43) */
+    double alphaR, alphaB;    /* sound-speed parameters (App. A, Eq. 42) */
+    double sigma0;            /* clean interfacial tension (Eq. 8) */
+    double sigma_min_ratio;   /* sigma_min / sigma0, 0.1 in the paper */
+    double E0;                /* elasticity number (Eq. 8) */
+    double psi_inf;           /* interface capacity psi_infinity (Eq. 8) */
+    double beta;              /* recolouring parameter, 0.7 (Eq. 11) */
+    int eos;                  /* 0: modified Langmuir (Eq. 8); 1: linear (Sec. 3.2) */
+    int source;               /* 0: j of Eq. 22; 1: j = r_a psi_inf C (Sec. 3.1) */
+    int transport;            /* 1: solve Eqs. 20-21; 0: hold psi and C fixed */
+    double Ds, Db;            /* interface / bulk surfactant diffusivities */
+    double ra, rd;            /* adsorption / desorption coefficients (Eq. 22) */
+    double g[3];              /* gravity: F_b = (rho - rhoB0) g (Sec. 3.4) */
+    double sor_omega;         /* SOR relaxation factor, 1.2 (Sec. 2.2) */
+    double sor_tol;           /* stop when max|update| <= sor_tol * max|x| */
+    int sor_max_iter;         /* SOR sweeps per solve at most */
+    double eps_w;             /* regularisation of the Crank-Nicolson weights */
+    double eps_n;             /* regularisation of the interface normal */
+} lbs_params;
+
+/* Diagnostics of the current state (Eqs. 33-34 and Sec. 3.4). */
+typedef struct {
+    double mass_R, mass_B;      /* sum rho^R, sum rho^B (FP64) */
+    double surf_total;          /* sum (|grad rhoN|+eps) psi + (1-rhoN+eps) C */
+    double surf_pre_rescale;    /* the same total before the last rescale */
+    double rescale_factor;      /* factor applied by the last rescale */
+    double U[3];                /* mean velocity over rhoN >= 0 (Eqs. 33-34) */
+    double centroid[3];         /* centroid of rhoN >= 0 */
+    double aspect_ratio;        /* sqrt(I_hh / I_vv), second moments of rhoN >= 0 */
+    double psi_av, psi_min, psi_max; /* over cells with |rhoN| < 0.5 */
+    double umax;                /* max |u| */
+    double Re;                  /* 2 rhoB0 |U_v| R / muB0, R from the red area/volume */
+    int sor_iters_psi, sor_iters_C; /* sweeps used by the last solve */
+    long long step;             /* time steps taken since lbs_init_fields */
+} lbs_diag;
+
+typedef struct lbs_ctx lbs_ctx;
+
+/* Fill p with the defaults of the paper (rho 1/1, mu 0.1/0.1, standard
+ * alpha, sigma0 0.1, sigma_min 0.1 sigma0, E0 0.5, psi_inf 1, beta 0.7,
+ * omega 1.2, D 0.1, periodic walls) for an nx x ny x nz grid. */
+int lbs_params_default(lbs_params *p, int nx, int ny, int nz);
+
+/* Device bytes a context needs for p and storage (0 on invalid input). */
+size_t lbs_workspace_bytes(const lbs_params *p, int storage);
+
+/* Create a context.  stream: a cudaStream_t to queue work on (borrowed) or
+ * NULL for a library-owned stream.  workspace: device memory of at least
+ * lbs_workspace_bytes() bytes (caller-owned, 256-byte aligned) or NULL to let
+ * the library allocate.  The current CUDA device is used.  Errors:
+ * LBS_EINVAL (bad parameters: grid < 3 on a walled axis, non-positive
+ * densities or viscosities, ...), LBS_ENOMEM, LBS_ECUDA. */
+int lbs_create(const lbs_params *p, int storage, void *stream, void *workspace,
+               size_t workspace_bytes, lbs_ctx **out);
+
+/* Initial state from host fields (reading of the paper's initial
+ * conditions): colour field phi in [-1, 1] gives rho^R = rhoR0 (1+phi)/2 and
+ * rho^B = rhoB0 (1-phi)/2 (so that Eq. 6 returns phi), populations at the
+ * equilibrium of App. A with velocity u (NULL = 0); psi, C as given (NULL =
+ * 0).  Resets the step counter and the conserved surfactant total. */
+int lbs_init_fields(lbs_ctx *c, const double *phi, const double *psi,
+                    const double *C, const double *u);
+
+/* Queue n coupled time steps on the context's stream (asynchronous; device
+ * errors are reported by the next lbs_sync / lbs_get_fields /
+ * lbs_diagnostics).  n >= 0. */
+int lbs_step(lbs_ctx *c, int n);
+
+/* Wait for queued work; return the first device-side error (LBS_ENOCONV,
+ * LBS_EDIVERGED, LBS_ETIMEOUT) raised since the last check, else LBS_OK. */
+int lbs_sync(lbs_ctx *c);
+
+/* Copy the current macroscopic fields to caller-owned host arrays (any may
+ * be NULL): density rho = rho^R + rho^B, velocity u of Eq. 10 (3*N),
+ * colour field phi = rho^N of Eq. 6, psi, C.  Synchronises. */
+int lbs_get_fields(lbs_ctx *c, double *rho, double *u, double *phi,
+                   double *psi, double *C);
+
+/* Fill *d with the diagnostics of the current state.  Synchronises. */
+int lbs_diagnostics(lbs_ctx *c, lbs_diag *d);
+
+/* ---- measurement ----------------------------------------------------- */
+
+/* Kernel groups of one time step, in launch order. */
+typedef enum {
+    LBS_K_FORCE = 0,   /* force and velocity, Eqs. 5-10 */
+    LBS_K_FD = 1,      /* explicit surfactant terms and CN right-hand sides */
+    LBS_K_COLLIDE = 2, /* collision and recolouring, Eqs. 1-4, 11-12 */
+    LBS_K_STREAM = 3,  /* streaming and bounce-back, Eq. 13 */
+    LBS_K_GRAD = 4,    /* colour gradient and CN weights at t+1 */
+    LBS_K_SOR = 5,     /* all red-black SOR sweeps of the step */
+    LBS_K_SURF = 6,    /* total surfactant, rescale, bookkeeping */
+    LBS_K_NGROUPS = 7
+} lbs_kernel_group;
+
+/* Enable (1) or disable (0) CUDA-event timing of the kernel groups inside
+ * the captured step graph (event-record nodes on the context's stream). */
+int lbs_profile(lbs_ctx *c, int enable);
+
+/* Synchronise and write, for the most recent step, the device time in
+ * milliseconds of each kernel group (ms[LBS_K_NGROUPS]); requires
+ * lbs_profile(c, 1) before the steps.  Groups that did not run read 0. */
+int lbs_kernel_times(lbs_ctx *c, double *ms, int n);
+
+/* Number of kernel launches one step queues (graph kernel nodes). */
+int lbs_step_kernel_count(const lbs_ctx *c);
+
+/* Release the context (and its device memory unless caller-supplied). */
+void lbs_destroy(lbs_ctx *c);
+
+/* Human-readable description of the last error of c (never NULL). */
+const char *lbs_last_error(const lbs_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBS_H */

@@ -1,0 +1,614 @@
+// lbs_api.cu — C ABI of the coupled LB-FD solver (include/lbs.h): context
+// lifecycle, device workspace layout, CUDA-graph capture of one time step,
+// field import/export and diagnostics.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/lbs.h"
+#include "lbs_k2d.cuh"
+
+using namespace lbs;
+
+namespace {
+
+constexpr int BX = 32, BY = 8, BS = BX * BY;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// host-side equilibrium of one colour at rest for the shift (App. A, Eq. 37)
+void rest_eq9(double rho, double al, double *f) {
+    double m[Q9] = {rho, rho * (-3.6 * al - 0.4), rho * (5.4 * al - 1.4), 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < Q9; i++) {
+        double s = 0;
+        for (int j = 0; j < Q9; j++) s += double(m9(j, i)) * m[j] / double(mnorm9(j));
+        f[i] = s;
+    }
+}
+
+struct Base {
+    virtual ~Base() {}
+    virtual int init(const double *, const double *, const double *, const double *) = 0;
+    virtual int step(int n) = 0;
+    virtual int sync() = 0;
+    virtual int get(double *, double *, double *, double *, double *) = 0;
+    virtual int diag(lbs_diag *) = 0;
+    virtual int profile(int on) = 0;
+    virtual int kernel_times(double *ms, int n) = 0;
+    virtual int kernel_count() const = 0;
+};
+
+}  // namespace
+
+struct lbs_ctx {
+    lbs_params p;
+    int storage;
+    cudaStream_t stream;
+    bool own_stream;
+    void *ws;
+    size_t ws_bytes;
+    bool own_ws;
+    Base *impl;
+    char err[512];
+};
+
+namespace {
+
+void set_err(lbs_ctx *c, const char *fmt, ...) {
+    if (!c) return;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            set_err(ctx, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                    __LINE__);                                                          \
+            return LBS_ECUDA;                                                           \
+        }                                                                               \
+    } while (0)
+
+// layout of the device workspace
+struct Layout {
+    int pitch;
+    long long plane;
+    size_t pops_off, scal_off, ctl_off, part_off, stage_off, total;
+    int nblocks;
+};
+
+template <typename R>
+Layout layout_of(const lbs_params *p) {
+    Layout L;
+    L.pitch = (int)align_up(p->nx, 32);
+    L.plane = (long long)align_up((size_t)L.pitch * p->ny * p->nz, 64);
+    size_t pb = (size_t)L.plane * sizeof(R);
+    L.pops_off = 0;
+    size_t pops = 4 * (size_t)Q9 * pb;
+    L.scal_off = pops;
+    size_t scal = 19 * pb;
+    L.ctl_off = align_up(L.scal_off + scal, 256);
+    L.part_off = align_up(L.ctl_off + sizeof(Ctl), 256);
+    L.nblocks = ((p->nx + BX - 1) / BX) * ((p->ny + BY - 1) / BY) * p->nz;
+    L.stage_off = align_up(L.part_off + (size_t)L.nblocks * (NDIAG + 3) * sizeof(double), 256);
+    size_t N = (size_t)p->nx * p->ny * p->nz;
+    L.total = align_up(L.stage_off + 7 * N * sizeof(double), 256);
+    return L;
+}
+
+template <typename R>
+struct Solver : Base {
+    lbs_ctx *ctx;
+    Inst<R> I;
+    Layout L;
+    char *ws;
+    double *stage;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    dim3 grid, block;
+    bool prof = false;
+    cudaEvent_t ev[LBS_K_NGROUPS + 1] = {};
+    bool ran[LBS_K_NGROUPS] = {};
+
+    Solver(lbs_ctx *c) : ctx(c) {
+        const lbs_params *p = &c->p;
+        L = layout_of<R>(p);
+        ws = (char *)c->ws;
+        std::memset(&I, 0, sizeof(I));
+        I.nx = p->nx;
+        I.ny = p->ny;
+        I.nz = p->nz;
+        I.pitch = L.pitch;
+        I.plane = L.plane;
+        for (int a = 0; a < 3; a++) {
+            I.wall[a] = p->wall[a];
+            for (int b = 0; b < 3; b++) {
+                I.uw_lo[a][b] = R(p->uw_lo[a][b]);
+                I.uw_hi[a][b] = R(p->uw_hi[a][b]);
+            }
+            I.g[a] = R(p->g[a]);
+        }
+        I.rhoR0 = R(p->rhoR0);
+        I.rhoB0 = R(p->rhoB0);
+        I.alphaR = R(p->alphaR);
+        I.alphaB = R(p->alphaB);
+        I.cs2R = R(0.6 * (1.0 - p->alphaR));
+        I.cs2B = R(0.6 * (1.0 - p->alphaB));
+        I.muR0 = R(p->muR0);
+        I.muB0 = R(p->muB0);
+        I.beta = R(p->beta);
+        I.eps_n = R(p->eps_n);
+        I.eps_w = R(p->eps_w);
+        I.sigma0 = R(p->sigma0);
+        I.sigma_min = R(p->sigma_min_ratio * p->sigma0);
+        I.E0 = R(p->E0);
+        I.psi_inf = R(p->psi_inf);
+        double cmc = (p->eos == 0 && p->E0 > 0)
+                         ? p->psi_inf * (1.0 - std::exp(-(1.0 - p->sigma_min_ratio) / p->E0))
+                         : (sizeof(R) == 4 ? (double)FLT_MAX : DBL_MAX);
+        I.cmc = R(cmc);
+        I.eos = p->eos;
+        I.source = p->source;
+        I.transport = p->transport;
+        I.Ds = R(p->Ds);
+        I.Db = R(p->Db);
+        I.ra = R(p->ra);
+        I.rd = R(p->rd);
+        I.omega = R(p->sor_omega);
+        I.sor_tol = R(p->sor_tol);
+        I.sor_max_iter = p->sor_max_iter;
+        double s[Q9];
+        rest_eq9(p->rhoB0, p->alphaB, s);
+        double rs = 0;
+        for (int i = 0; i < Q9; i++) {
+            I.shift[i] = R(s[i]);
+            rs += double(I.shift[i]);
+        }
+        I.rho_s = R(rs);
+        size_t pb = (size_t)L.plane;
+        R *pops = (R *)(ws + L.pops_off);
+        I.fT = pops;
+        I.fR = pops + 1 * Q9 * pb;
+        I.gT = pops + 2 * Q9 * pb;
+        I.gR = pops + 3 * Q9 * pb;
+        R *sc = (R *)(ws + L.scal_off);
+        R **fields[] = {&I.rhoR, &I.rhoB, &I.rhoN, &I.jx,  &I.jy, &I.gx,  &I.gy,
+                        &I.a,    &I.chi,  &I.ux,   &I.uy,  &I.Fx, &I.Fy,  &I.psi,
+                        &I.C,    &I.S,    &I.B,    &I.rpsi, &I.rC};
+        for (int k = 0; k < 19; k++) *fields[k] = sc + k * pb;
+        I.ctl = (Ctl *)(ws + L.ctl_off);
+        I.part = (double *)(ws + L.part_off);
+        stage = (double *)(ws + L.stage_off);
+        block = dim3(BX, BY, 1);
+        grid = dim3((p->nx + BX - 1) / BX, (p->ny + BY - 1) / BY, 1);
+    }
+
+    ~Solver() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+
+    void mark(cudaStream_t s, int g) {
+        if (prof) cudaEventRecord(ev[g], s);
+    }
+
+    int launch_check() {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_err(ctx, "kernel launch failed: %s", cudaGetErrorString(e));
+            return LBS_ECUDA;
+        }
+        return LBS_OK;
+    }
+
+    // the launches of one time step, in order (also captured into the graph);
+    // with profiling on, an event is recorded at every group boundary
+    void enqueue_step(cudaStream_t s) {
+        for (bool &r : ran) r = false;
+        mark(s, LBS_K_FORCE);
+        k_force2<R><<<grid, block, 0, s>>>(I);
+        ran[LBS_K_FORCE] = true;
+        mark(s, LBS_K_FD);
+        if (I.transport) {
+            k_fd2<R><<<grid, block, 0, s>>>(I);
+            ran[LBS_K_FD] = true;
+        }
+        mark(s, LBS_K_COLLIDE);
+        k_collide2<R><<<grid, block, 0, s>>>(I);
+        ran[LBS_K_COLLIDE] = true;
+        mark(s, LBS_K_STREAM);
+        k_stream2<R><<<grid, block, 0, s>>>(I);
+        ran[LBS_K_STREAM] = true;
+        mark(s, LBS_K_GRAD);
+        k_grad2<R><<<grid, block, 0, s>>>(I);
+        ran[LBS_K_GRAD] = true;
+        mark(s, LBS_K_SOR);
+        if (I.transport) {
+            for (int k = 0; k < I.sor_max_iter; k++) {
+                k_sor2<R, BS><<<grid, block, 0, s>>>(I, 0, k);
+                k_sor2<R, BS><<<grid, block, 0, s>>>(I, 1, k);
+            }
+            ran[LBS_K_SOR] = true;
+        }
+        mark(s, LBS_K_SURF);
+        if (I.transport) {
+            k_surf2<R, BS><<<grid, block, 0, s>>>(I, 1, L.nblocks);
+            k_scale2<R><<<grid, block, 0, s>>>(I);
+        } else {
+            k_tick<R><<<1, 32, 0, s>>>(I);
+        }
+        ran[LBS_K_SURF] = true;
+        mark(s, LBS_K_NGROUPS);
+    }
+
+    int kernel_count() const override {
+        return I.transport ? 7 + 2 * I.sor_max_iter : 4;
+    }
+
+    int profile(int on) override {
+        if (bool(on) == prof) return LBS_OK;
+        if (on)
+            for (auto &e : ev)
+                if (!e) CK(cudaEventCreate(&e));
+        prof = bool(on);
+        if (gexec) {  // rebuild with / without the event nodes
+            CK(cudaGraphExecDestroy(gexec));
+            CK(cudaGraphDestroy(graph));
+            gexec = nullptr;
+            graph = nullptr;
+        }
+        return LBS_OK;
+    }
+
+    int kernel_times(double *ms, int n) override {
+        if (!prof) {
+            set_err(ctx, "profiling is off (lbs_profile)");
+            return LBS_EINVAL;
+        }
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (int g = 0; g < n && g < LBS_K_NGROUPS; g++) {
+            float t = 0;
+            if (ran[g]) CK(cudaEventElapsedTime(&t, ev[g], ev[g + 1]));
+            ms[g] = t;
+        }
+        return LBS_OK;
+    }
+
+    int init(const double *phi, const double *psi, const double *C, const double *u) override {
+        size_t N = (size_t)I.nx * I.ny * I.nz;
+        cudaStream_t s = ctx->stream;
+        double *dphi = stage, *dpsi = stage + N, *dC = stage + 2 * N, *du = stage + 3 * N;
+        CK(cudaMemcpyAsync(dphi, phi, N * sizeof(double), cudaMemcpyHostToDevice, s));
+        if (psi) CK(cudaMemcpyAsync(dpsi, psi, N * sizeof(double), cudaMemcpyHostToDevice, s));
+        if (C) CK(cudaMemcpyAsync(dC, C, N * sizeof(double), cudaMemcpyHostToDevice, s));
+        if (u) CK(cudaMemcpyAsync(du, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(ws + L.pops_off, 0, L.ctl_off - L.pops_off, s));
+        CK(cudaMemsetAsync(I.ctl, 0, sizeof(Ctl), s));
+        k_init2<R><<<grid, block, 0, s>>>(I, dphi, psi ? dpsi : nullptr, C ? dC : nullptr,
+                                          u ? du : nullptr);
+        k_moments2<R><<<grid, block, 0, s>>>(I);
+        k_grad2<R><<<grid, block, 0, s>>>(I);
+        k_surf2<R, BS><<<grid, block, 0, s>>>(I, 0, L.nblocks);
+        int r = launch_check();
+        if (r) return r;
+        CK(cudaStreamSynchronize(s));
+        return LBS_OK;
+    }
+
+    int build_graph() {
+        cudaStream_t s = ctx->stream;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        enqueue_step(s);
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (e != cudaSuccess) {
+            set_err(ctx, "graph capture failed: %s", cudaGetErrorString(e));
+            return LBS_ECUDA;
+        }
+        CK(cudaGraphInstantiate(&gexec, graph, 0));
+        return LBS_OK;
+    }
+
+    int step(int n) override {
+        if (n <= 0) return LBS_OK;
+        if (!gexec) {
+            int r = build_graph();
+            if (r) return r;
+        }
+        for (int k = 0; k < n; k++) CK(cudaGraphLaunch(gexec, ctx->stream));
+        return LBS_OK;
+    }
+
+    int sync() override {
+        CK(cudaStreamSynchronize(ctx->stream));
+        int st = 0;
+        CK(cudaMemcpy(&st, &I.ctl->status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st) {
+            int zero = 0;
+            CK(cudaMemcpy(&I.ctl->status, &zero, sizeof(int), cudaMemcpyHostToDevice));
+            if (st & ST_DIVERGED) {
+                set_err(ctx, "non-finite total surfactant (diverged)");
+                return LBS_EDIVERGED;
+            }
+            if (st & ST_TIMEOUT) {
+                set_err(ctx, "a bounded device wait gave up");
+                return LBS_ETIMEOUT;
+            }
+            if (st & ST_NOCONV) {
+                set_err(ctx, "SOR did not converge within %d sweeps", I.sor_max_iter);
+                return LBS_ENOCONV;
+            }
+        }
+        return LBS_OK;
+    }
+
+    int get(double *rho, double *u, double *phi, double *psi, double *C) override {
+        int r = sync();
+        if (r) return r;
+        size_t N = (size_t)I.nx * I.ny * I.nz;
+        cudaStream_t s = ctx->stream;
+        k_force2<R><<<grid, block, 0, s>>>(I);
+        k_export2<R><<<grid, block, 0, s>>>(I, stage, stage + N, stage + 4 * N, stage + 5 * N,
+                                            stage + 6 * N);
+        r = launch_check();
+        if (r) return r;
+        if (rho) CK(cudaMemcpyAsync(rho, stage, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (u) CK(cudaMemcpyAsync(u, stage + N, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (phi) CK(cudaMemcpyAsync(phi, stage + 4 * N, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (psi) CK(cudaMemcpyAsync(psi, stage + 5 * N, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (C) CK(cudaMemcpyAsync(C, stage + 6 * N, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return LBS_OK;
+    }
+
+    int diag(lbs_diag *d) override {
+        int r = sync();
+        if (r) return r;
+        cudaStream_t s = ctx->stream;
+        k_force2<R><<<grid, block, 0, s>>>(I);
+        k_diag2<R, BS><<<grid, block, 0, s>>>(I, L.nblocks);
+        r = launch_check();
+        if (r) return r;
+        Ctl h;
+        CK(cudaMemcpyAsync(&h, I.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const double *v = h.diag;
+        std::memset(d, 0, sizeof(*d));
+        d->mass_R = v[0];
+        d->mass_B = v[1];
+        d->surf_total = v[2];
+        d->surf_pre_rescale = h.pre;
+        d->rescale_factor = h.scale;
+        const lbs_params *p = &ctx->p;
+        int D = p->nz == 1 ? 2 : 3;
+        int vert = D - 1;
+        double gmax = 0;
+        for (int a = 0; a < D; a++)
+            if (std::fabs(p->g[a]) > gmax) {
+                gmax = std::fabs(p->g[a]);
+                vert = a;
+            }
+        double cnt = v[3];
+        if (cnt > 0) {
+            d->U[0] = v[4] / cnt;
+            d->U[1] = v[5] / cnt;
+            d->U[2] = v[15] / cnt;
+            d->centroid[0] = v[6] / cnt;
+            d->centroid[1] = v[7] / cnt;
+            d->centroid[2] = v[16] / cnt;
+            double I2[3] = {v[8] - cnt * d->centroid[0] * d->centroid[0],
+                            v[9] - cnt * d->centroid[1] * d->centroid[1], 0};
+            int hor = vert == 0 ? 1 : 0;
+            d->aspect_ratio = I2[vert] > 0 ? std::sqrt(I2[hor] / I2[vert]) : 0.0;
+            double rad = D == 2 ? std::sqrt(cnt / M_PI) : std::cbrt(3 * cnt / (4 * M_PI));
+            d->Re = 2 * p->rhoB0 * std::fabs(d->U[vert]) * rad / p->muB0;
+        }
+        if (v[11] > 0) {
+            d->psi_av = v[10] / v[11];
+            d->psi_min = -v[NDIAG + 0];
+            d->psi_max = v[NDIAG + 1];
+        }
+        d->umax = v[NDIAG + 2];
+        d->sor_iters_psi = d->sor_iters_C = h.sor_iters;
+        d->step = h.step;
+        return LBS_OK;
+    }
+};
+
+int validate(const lbs_params *p, char *err, size_t n) {
+    if (p->nx < 1 || p->ny < 1 || p->nz != 1) {
+        snprintf(err, n, "grid %dx%dx%d: only 2D (nz == 1) grids are supported", p->nx, p->ny, p->nz);
+        return LBS_EINVAL;
+    }
+    int dims[3] = {p->nx, p->ny, p->nz};
+    for (int a = 0; a < 3; a++) {
+        if (p->wall[a] && dims[a] < 3) {
+            snprintf(err, n, "walled axis %d needs at least 3 nodes", a);
+            return LBS_EINVAL;
+        }
+        if (p->uw_lo[a][a] != 0 || p->uw_hi[a][a] != 0) {
+            snprintf(err, n, "walls move tangentially only (axis %d)", a);
+            return LBS_EINVAL;
+        }
+    }
+    if (!(p->rhoR0 > 0 && p->rhoB0 > 0 && p->muR0 > 0 && p->muB0 > 0)) {
+        snprintf(err, n, "densities and viscosities must be positive");
+        return LBS_EINVAL;
+    }
+    if (!(p->alphaR < 1 && p->alphaB < 1)) {
+        snprintf(err, n, "alpha must be below 1");
+        return LBS_EINVAL;
+    }
+    if (p->sor_max_iter < 1 || p->sor_max_iter > KMAX_SWEEPS) {
+        snprintf(err, n, "sor_max_iter must be in [1, %d]", KMAX_SWEEPS);
+        return LBS_EINVAL;
+    }
+    if (!(p->psi_inf > 0) || p->sor_omega <= 0 || p->sor_omega >= 2) {
+        snprintf(err, n, "psi_inf > 0 and 0 < omega < 2 required");
+        return LBS_EINVAL;
+    }
+    return LBS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbs_params_default(lbs_params *p, int nx, int ny, int nz) {
+    if (!p) return LBS_EINVAL;
+    std::memset(p, 0, sizeof(*p));
+    p->nx = nx;
+    p->ny = ny;
+    p->nz = nz;
+    p->rhoR0 = p->rhoB0 = 1.0;
+    p->muR0 = p->muB0 = 0.1;
+    p->alphaR = p->alphaB = nz == 1 ? 4.0 / 9.0 : 1.0 / 3.0;
+    p->sigma0 = 0.1;
+    p->sigma_min_ratio = 0.1;
+    p->E0 = 0.5;
+    p->psi_inf = 1.0;
+    p->beta = 0.7;
+    p->transport = 1;
+    p->Ds = p->Db = 0.1;
+    p->sor_omega = 1.2;
+    p->sor_tol = 1e-6;
+    p->sor_max_iter = 40;
+    p->eps_w = 1e-6;
+    p->eps_n = 1e-6;
+    return LBS_OK;
+}
+
+size_t lbs_workspace_bytes(const lbs_params *p, int storage) {
+    if (!p) return 0;
+    char e[256];
+    if (validate(p, e, sizeof(e))) return 0;
+    if (storage == LBS_F64) return layout_of<double>(p).total;
+    if (storage == LBS_F32) return layout_of<float>(p).total;
+    return 0;
+}
+
+int lbs_create(const lbs_params *p, int storage, void *stream, void *workspace,
+               size_t workspace_bytes, lbs_ctx **out) {
+    if (!p || !out) return LBS_EINVAL;
+    *out = nullptr;
+    lbs_ctx *ctx = new (std::nothrow) lbs_ctx();
+    if (!ctx) return LBS_ENOMEM;
+    std::memset(ctx, 0, sizeof(*ctx));
+    ctx->p = *p;
+    ctx->storage = storage;
+    int r = validate(p, ctx->err, sizeof(ctx->err));
+    if (!r && storage != LBS_F64 && storage != LBS_F32) {
+        set_err(ctx, "unsupported storage %d", storage);
+        r = LBS_EINVAL;
+    }
+    if (r) {
+        *out = ctx;  // carries the message; lbs_destroy releases it
+        return r;
+    }
+    size_t need = lbs_workspace_bytes(p, storage);
+    if (workspace) {
+        if (workspace_bytes < need || ((uintptr_t)workspace & 255)) {
+            set_err(ctx, "workspace of %zu bytes (need %zu, 256-byte aligned)", workspace_bytes,
+                    need);
+            *out = ctx;
+            return LBS_ENOMEM;
+        }
+        ctx->ws = workspace;
+        ctx->ws_bytes = workspace_bytes;
+    } else {
+        cudaError_t e = cudaMalloc(&ctx->ws, need);
+        if (e != cudaSuccess) {
+            set_err(ctx, "cudaMalloc(%zu) failed: %s", need, cudaGetErrorString(e));
+            ctx->ws = nullptr;
+            *out = ctx;
+            return LBS_ENOMEM;
+        }
+        ctx->own_ws = true;
+        ctx->ws_bytes = need;
+    }
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            set_err(ctx, "cudaStreamCreate failed");
+            *out = ctx;
+            return LBS_ECUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (storage == LBS_F64)
+        ctx->impl = new (std::nothrow) Solver<double>(ctx);
+    else
+        ctx->impl = new (std::nothrow) Solver<float>(ctx);
+    *out = ctx;
+    if (!ctx->impl) return LBS_ENOMEM;
+    return LBS_OK;
+}
+
+int lbs_init_fields(lbs_ctx *c, const double *phi, const double *psi, const double *C,
+                    const double *u) {
+    if (!c || !c->impl || !phi) return LBS_EINVAL;
+    return c->impl->init(phi, psi, C, u);
+}
+
+int lbs_step(lbs_ctx *c, int n) {
+    if (!c || !c->impl || n < 0) return LBS_EINVAL;
+    return c->impl->step(n);
+}
+
+int lbs_sync(lbs_ctx *c) {
+    if (!c || !c->impl) return LBS_EINVAL;
+    return c->impl->sync();
+}
+
+int lbs_get_fields(lbs_ctx *c, double *rho, double *u, double *phi, double *psi, double *C) {
+    if (!c || !c->impl) return LBS_EINVAL;
+    return c->impl->get(rho, u, phi, psi, C);
+}
+
+int lbs_diagnostics(lbs_ctx *c, lbs_diag *d) {
+    if (!c || !c->impl || !d) return LBS_EINVAL;
+    return c->impl->diag(d);
+}
+
+void lbs_destroy(lbs_ctx *c) {
+    if (!c) return;
+    if (c->impl) {
+        cudaStreamSynchronize(c->stream);
+        delete c->impl;
+    }
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int lbs_profile(lbs_ctx *c, int enable) {
+    if (!c || !c->impl) return LBS_EINVAL;
+    return c->impl->profile(enable);
+}
+
+int lbs_kernel_times(lbs_ctx *c, double *ms, int n) {
+    if (!c || !c->impl || !ms || n < 0) return LBS_EINVAL;
+    return c->impl->kernel_times(ms, n);
+}
+
+int lbs_step_kernel_count(const lbs_ctx *c) {
+    if (!c || !c->impl) return 0;
+    return c->impl->kernel_count();
+}
+
+const char *lbs_last_error(const lbs_ctx *c) {
+    if (!c) return "null context";
+    return c->err[0] ? c->err : "no error";
+}
+
+}  // extern "C"

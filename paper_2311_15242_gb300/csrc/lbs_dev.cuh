@@ -1,0 +1,177 @@
+// lbs_dev.cuh — device-side definitions shared by the kernels of the coupled
+// LB-FD step (arXiv 2311.15242): lattice tables, the instance descriptor,
+// boundary mapping and the equation of state.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace lbs {
+
+// ---------------------------------------------------------------------------
+// D2Q9 lattice.  Velocity order: the one carried by the momentum rows of the
+// transformation matrix of Eq. 36 (rows j_x, j_y), so that M below is the
+// printed matrix.  Weights 4/9, 1/9, 1/36.
+// ---------------------------------------------------------------------------
+constexpr int Q9 = 9;
+
+__host__ __device__ constexpr int ex9(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey9(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp9(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+}
+template <typename R>
+__host__ __device__ constexpr R w9(int i) {
+    return i == 0 ? R(4.0 / 9.0) : (i <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0));
+}
+// Rows of M (Eq. 36) as the moment polynomials of e_i:
+// rho, e, epsilon, j_x, q_x, j_y, q_y, p_xx, p_xy.
+__host__ __device__ constexpr int m9(int j, int i) {
+    // (integer arithmetic; every entry of Eq. 36 is an integer)
+    return j == 0   ? 1
+           : j == 1 ? -4 + 3 * (ex9(i) * ex9(i) + ey9(i) * ey9(i))
+           : j == 2 ? (8 - 21 * (ex9(i) * ex9(i) + ey9(i) * ey9(i)) +
+                       9 * (ex9(i) * ex9(i) + ey9(i) * ey9(i)) *
+                           (ex9(i) * ex9(i) + ey9(i) * ey9(i))) / 2
+           : j == 3 ? ex9(i)
+           : j == 4 ? (-5 + 3 * (ex9(i) * ex9(i) + ey9(i) * ey9(i))) * ex9(i)
+           : j == 5 ? ey9(i)
+           : j == 6 ? (-5 + 3 * (ex9(i) * ex9(i) + ey9(i) * ey9(i))) * ey9(i)
+           : j == 7 ? ex9(i) * ex9(i) - ey9(i) * ey9(i)
+                    : ex9(i) * ey9(i);
+}
+// squared norms of the (orthogonal) rows: M^{-1} = M^T diag(1/norm)
+__host__ __device__ constexpr int mnorm9(int j) {
+    return j == 0 ? 9 : (j <= 2 ? 36 : (j == 3 || j == 5 ? 6 : (j == 4 || j == 6 ? 12 : 4)));
+}
+
+// ---------------------------------------------------------------------------
+// Per-step control block in device memory (dynamic state read by kernels of
+// a captured graph: step counter, SOR progress, conserved total, status).
+// ---------------------------------------------------------------------------
+constexpr int KMAX_SWEEPS = 64;
+enum : int { ST_NOCONV = 1, ST_DIVERGED = 2, ST_TIMEOUT = 4 };
+
+struct Ctl {
+    long long step;         // time steps taken
+    double M0;              // conserved total surfactant
+    double pre;             // total before the last rescale
+    double scale;           // last rescale factor
+    int status;             // ST_* bits, sticky until read by the host
+    int sor_iters;          // sweeps used by the last solve
+    unsigned int ticket;    // arrival counter of the last-block reductions
+    int pad;
+    // per sweep: max |d psi|, max |d C|, max |psi|, max |C| (bits of
+    // non-negative doubles, compared as unsigned integers)
+    unsigned long long sweep[KMAX_SWEEPS][4];
+    double diag[32];        // finalised diagnostics sums
+};
+
+// ---------------------------------------------------------------------------
+// Instance descriptor passed by value to every kernel.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Inst {
+    int nx, ny, nz, pitch;   // pitch: elements per row (>= nx)
+    long long plane;         // elements per scalar plane (pitch * ny * nz)
+    int wall[3];
+    R uw_lo[3][3], uw_hi[3][3];
+    R rhoR0, rhoB0, alphaR, alphaB, cs2R, cs2B, muR0, muB0;
+    R beta, eps_n, eps_w;
+    R sigma0, sigma_min, E0, psi_inf, cmc;
+    int eos, source, transport;
+    R Ds, Db, ra, rd, g[3], omega, sor_tol;
+    int sor_max_iter;
+    // shift of the stored total populations: the rest equilibrium of the pure
+    // blue phase, and its first three moments (rho, e, epsilon of Eq. 36)
+    R shift[Q9];
+    R rho_s, e_s, eps_s;
+    // state (device pointers; every field is `plane` elements, populations Q planes)
+    R *fT, *fR;               // total populations minus shift, red populations
+    R *gT, *gR;               // post-collision buffers
+    R *rhoR, *rhoB, *rhoN, *jx, *jy;
+    R *gx, *gy, *a, *chi;     // grad rhoN, |grad rhoN|, 1 - rhoN
+    R *ux, *uy, *Fx, *Fy;
+    R *psi, *C, *S, *B, *rpsi, *rC;
+    Ctl *ctl;
+    double *part;             // per-block partial sums of reductions
+};
+
+// ---------------------------------------------------------------------------
+// Boundary mapping.  Periodic axes wrap; on a walled axis the coordinate is
+// mirrored about the half-way wall (-1 -> 0, -2 -> 1, n -> n-1, ...).
+// refl: bit a set when axis a was reflected; side: -1 low wall, +1 high wall.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int map_axis(int c, int n, int wall, int bit, int &refl,
+                                        int &side) {
+    side = 0;
+    if (c >= 0 && c < n) return c;
+    if (!wall) return ((c % n) + n) % n;
+    refl |= bit;
+    if (c < 0) {
+        side = -1;
+        return -1 - c;
+    }
+    side = 1;
+    return 2 * n - 1 - c;
+}
+
+template <typename R>
+__device__ __forceinline__ long long nb2(const Inst<R> &I, int x, int y, int dx, int dy,
+                                         int &refl, int &sx, int &sy) {
+    refl = 0;
+    int X = map_axis(x + dx, I.nx, I.wall[0], 1, refl, sx);
+    int Y = map_axis(y + dy, I.ny, I.wall[1], 2, refl, sy);
+    return (long long)Y * I.pitch + X;
+}
+
+// velocity at a ghost node: u -> 2 u_wall - u for each wall crossed
+template <typename R>
+__device__ __forceinline__ void ghost_u2(const Inst<R> &I, int refl, int sx, int sy,
+                                         R &u0, R &u1) {
+    if (refl & 1) {
+        const R *w = sx < 0 ? I.uw_lo[0] : I.uw_hi[0];
+        u0 = R(2) * w[0] - u0;
+        u1 = R(2) * w[1] - u1;
+    }
+    if (refl & 2) {
+        const R *w = sy < 0 ? I.uw_lo[1] : I.uw_hi[1];
+        u0 = R(2) * w[0] - u0;
+        u1 = R(2) * w[1] - u1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Equation of state (Eq. 8) and the Marangoni coefficient -d sigma/d psi of
+// Eq. 9.  Above the CMC sigma = sigma_min and the coefficient is 0.  The
+// logarithm is taken in double precision near saturation (psi/psi_inf > 1/2).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ bool eos(const Inst<R> &I, R psi, R &sigma, R &mcoef) {
+    if (I.eos == 1) {
+        sigma = I.sigma0 * (R(1) - I.E0 * psi / I.psi_inf);
+        mcoef = I.sigma0 * I.E0 / I.psi_inf;
+        return true;
+    }
+    if (psi < I.cmc) {
+        R x = -psi / I.psi_inf;
+        R lg;
+        if (x < R(-0.5))
+            lg = R(log1p(double(x)));
+        else
+            lg = log1p(x);
+        sigma = I.sigma0 * (R(1) + I.E0 * lg);
+        mcoef = I.sigma0 * I.E0 / (I.psi_inf - psi);
+        return true;
+    }
+    sigma = I.sigma_min;
+    mcoef = R(0);
+    return false;
+}
+
+}  // namespace lbs

@@ -1,0 +1,747 @@
+// lbs_k2d.cuh — D2Q9 kernels of the coupled LB-FD time step (arXiv 2311.15242).
+//
+// Storage form of the populations: the total f_i = f_i^R + f_i^B is kept
+// shifted by a constant rest state s_i (the rest equilibrium of the pure blue
+// phase; for the alpha-model of App. A both pure phases share the moving
+// components of that state), and the red populations f_i^R are kept as they
+// are.  The momentum sum_i f_i e_i and every non-conserved moment are then
+// formed from small numbers, which keeps FP32 cancellation out of the
+// velocity; f_i^B = s_i + fT_i - f_i^R.
+//
+// One time step (t -> t+1) is the kernel sequence
+//   k_force    u, F at t                   (Eqs. 5-10)
+//   k_fd       S^t, B^t, CN right-hand sides (Eqs. 22-28)
+//   k_collide  collision + recolouring      (Eqs. 1-4, 11-12, App. A)
+//   k_stream   streaming, bounce-back, moments at t+1 (Eq. 13)
+//   k_grad     grad rhoN, |grad rhoN|, 1 - rhoN at t+1
+//   k_sor      red-black SOR sweeps        (Sec. 2.2)
+//   k_surf     total surfactant, rescale factor (Sec. 2.2)
+//   k_scale    psi, C *= factor
+#pragma once
+
+#include "lbs_dev.cuh"
+
+namespace lbs {
+
+template <typename R>
+__device__ __forceinline__ R cs2_lattice() { return R(1) / R(3); }
+
+// sum over the red and total-shifted populations of one cell
+template <typename R>
+struct Mom2 {
+    R rR, drho, jx, jy;  // rho^R, rho - rho_s, momentum (without the force)
+};
+
+template <typename R>
+__device__ __forceinline__ Mom2<R> moments9(const R *fT, const R *fR) {
+    Mom2<R> m{R(0), R(0), R(0), R(0)};
+#pragma unroll
+    for (int i = 0; i < Q9; i++) {
+        m.rR += fR[i];
+        m.drho += fT[i];
+        m.jx += R(ex9(i)) * fT[i];
+        m.jy += R(ey9(i)) * fT[i];
+    }
+    return m;
+}
+
+// colour function, Eq. 6
+template <typename R>
+__device__ __forceinline__ R colour_fn(const Inst<R> &I, R rR, R rB) {
+    R xr = rR / I.rhoR0, xb = rB / I.rhoB0;
+    return (xr - xb) / (xr + xb);
+}
+
+// ---------------------------------------------------------------------------
+// Initial populations: f^k = M^{-1} m^{k,eq}(rho^k, u) (App. A), rho^R and
+// rho^B from the colour field.  Inputs are dense double arrays [ny][nx].
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void meq9(R rho, R ux, R uy, R al, R *m) {
+    R u2 = ux * ux + uy * uy;
+    m[0] = rho;
+    m[1] = rho * (R(-3.6) * al - R(0.4) + R(3) * u2);
+    m[2] = rho * (R(5.4) * al - R(1.4) - R(3) * u2);
+    m[3] = rho * ux;
+    m[4] = rho * (R(-1.8) * al - R(0.2)) * ux;
+    m[5] = rho * uy;
+    m[6] = rho * (R(-1.8) * al - R(0.2)) * uy;
+    m[7] = rho * (ux * ux - uy * uy);
+    m[8] = rho * ux * uy;
+}
+
+template <typename R>
+__device__ __forceinline__ void minv9(const R *m, R *f) {
+#pragma unroll
+    for (int i = 0; i < Q9; i++) {
+        R s = R(0);
+#pragma unroll
+        for (int j = 0; j < Q9; j++)
+            if (m9(j, i) != 0) s += R(m9(j, i)) * m[j] / R(mnorm9(j));
+        f[i] = s;
+    }
+}
+
+template <typename R>
+__global__ void k_init2(Inst<R> I, const double *phi, const double *psi, const double *C,
+                        const double *u) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= I.nx || y >= I.ny) return;
+    long long d = (long long)y * I.nx + x;
+    long long c = (long long)y * I.pitch + x;
+    long long N = (long long)I.nx * I.ny;
+    double ph = phi[d];
+    ph = ph > 1.0 ? 1.0 : (ph < -1.0 ? -1.0 : ph);
+    R ux = u ? R(u[d]) : R(0), uy = u ? R(u[N + d]) : R(0);
+    R mR[Q9], mB[Q9], fR[Q9], fB[Q9];
+    meq9(R(I.rhoR0 * R(0.5 * (1.0 + ph))), ux, uy, I.alphaR, mR);
+    meq9(R(I.rhoB0 * R(0.5 * (1.0 - ph))), ux, uy, I.alphaB, mB);
+    minv9(mR, fR);
+    minv9(mB, fB);
+#pragma unroll
+    for (int i = 0; i < Q9; i++) {
+        I.fT[i * I.plane + c] = (fR[i] + fB[i]) - I.shift[i];
+        I.fR[i * I.plane + c] = fR[i];
+    }
+    I.psi[c] = psi ? R(psi[d]) : R(0);
+    I.C[c] = C ? R(C[d]) : R(0);
+    I.S[c] = R(0);
+    I.B[c] = R(0);
+}
+
+// moments of the stored populations -> rho^R, rho^B, rho^N, momentum
+template <typename R>
+__device__ __forceinline__ void store_moments(const Inst<R> &I, long long c, const R *fT,
+                                              const R *fR) {
+    Mom2<R> m = moments9(fT, fR);
+    R rB = (I.rho_s - m.rR) + m.drho;
+    I.rhoR[c] = m.rR;
+    I.rhoB[c] = rB;
+    I.rhoN[c] = colour_fn(I, m.rR, rB);
+    I.jx[c] = m.jx;
+    I.jy[c] = m.jy;
+}
+
+template <typename R>
+__global__ void k_moments2(Inst<R> I) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= I.nx || y >= I.ny) return;
+    long long c = (long long)y * I.pitch + x;
+    R fT[Q9], fR[Q9];
+#pragma unroll
+    for (int i = 0; i < Q9; i++) {
+        fT[i] = I.fT[i * I.plane + c];
+        fR[i] = I.fR[i * I.plane + c];
+    }
+    store_moments(I, c, fT, fR);
+}
+
+// ---------------------------------------------------------------------------
+// k_grad: colour gradient by the isotropic stencil (Sec. 2.1 after Eq. 9):
+// d_a X = (1/c_s^2) sum_i w_i X(x + e_i) e_ia, rho^N mirrored at walls;
+// a = |grad rho^N| and chi = 1 - rho^N (formed as 2 x_B / (x_R + x_B)).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_grad2(Inst<R> I) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= I.nx || y >= I.ny) return;
+    long long c = (long long)y * I.pitch + x;
+    R gx = R(0), gy = R(0);
+#pragma unroll
+    for (int i = 1; i < Q9; i++) {
+        int refl, sx, sy;
+        long long j = nb2(I, x, y, ex9(i), ey9(i), refl, sx, sy);
+        R v = I.rhoN[j];
+        gx += w9<R>(i) * R(ex9(i)) * v;
+        gy += w9<R>(i) * R(ey9(i)) * v;
+    }
+    gx *= R(3);
+    gy *= R(3);
+    I.gx[c] = gx;
+    I.gy[c] = gy;
+    I.a[c] = sqrt(gx * gx + gy * gy);
+    R xr = I.rhoR[c] / I.rhoR0, xb = I.rhoB[c] / I.rhoB0;
+    I.chi[c] = R(2) * xb / (xr + xb);
+}
+
+// ---------------------------------------------------------------------------
+// k_force: n = -grad rhoN / |grad rhoN| (regularised by eps_n), curvature
+// kappa = -div n (Eq. 7), grad psi, sigma(psi) (Eq. 8), interfacial force
+// (Eq. 9) plus buoyancy (rho - rhoB0) g (Sec. 3.4), velocity of Eq. 10.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_force2(Inst<R> I) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= I.nx || y >= I.ny) return;
+    long long c = (long long)y * I.pitch + x;
+    const R e2 = I.eps_n * I.eps_n;
+    R divn = R(0), dpx = R(0), dpy = R(0);
+#pragma unroll
+    for (int i = 1; i < Q9; i++) {
+        int refl, sx, sy;
+        long long j = nb2(I, x, y, ex9(i), ey9(i), refl, sx, sy);
+        R gx = I.gx[j], gy = I.gy[j];
+        if (refl & 1) gx = -gx;  // normal component mirrored with a sign change
+        if (refl & 2) gy = -gy;
+        R inv = R(1) / sqrt(gx * gx + gy * gy + e2);
+        R nx = -gx * inv, ny = -gy * inv;
+        divn += w9<R>(i) * (R(ex9(i)) * nx + R(ey9(i)) * ny);
+        R p = I.psi[j];
+        dpx += w9<R>(i) * R(ex9(i)) * p;
+        dpy += w9<R>(i) * R(ey9(i)) * p;
+    }
+    R kappa = -R(3) * divn;
+    dpx *= R(3);
+    dpy *= R(3);
+    R gx = I.gx[c], gy = I.gy[c], a = I.a[c];
+    R sigma, mco;
+    R Fx, Fy;
+    if (eos(I, I.psi[c], sigma, mco)) {
+        R inv = R(1) / sqrt(gx * gx + gy * gy + e2);
+        R nx = -gx * inv, ny = -gy * inv;
+        R ndp = nx * dpx + ny * dpy;
+        Fx = -R(0.5) * sigma * kappa * gx - R(0.5) * a * mco * (dpx - ndp * nx);
+        Fy = -R(0.5) * sigma * kappa * gy - R(0.5) * a * mco * (dpy - ndp * ny);
+    } else {
+        Fx = -R(0.5) * I.sigma_min * kappa * gx;
+        Fy = -R(0.5) * I.sigma_min * kappa * gy;
+    }
+    R rR = I.rhoR[c], rB = I.rhoB[c];
+    R rho = rR + rB;
+    // (rho - rhoB0) = rho^R + (rho^B - rhoB0)
+    R drb = rR + (rB - I.rhoB0);
+    Fx += drb * I.g[0];
+    Fy += drb * I.g[1];
+    I.Fx[c] = Fx;
+    I.Fy[c] = Fy;
+    I.ux[c] = (I.jx[c] + R(0.5) * Fx) / rho;
+    I.uy[c] = (I.jy[c] + R(0.5) * Fy) / rho;
+}
+
+// ---------------------------------------------------------------------------
+// k_fd: explicit terms of Eqs. 23-24 at time t and the Crank-Nicolson
+// right-hand sides.
+//   S = -div(psi a u) + a j,  B = -div(C chi u) - a j   (Eq. 22 for j)
+//   div by the WENO3 one-sided differences of Eqs. 25-27, upwinded by the sign
+//   of the local velocity component (mean of both sides where it is zero)
+//   rhs_psi = w psi + (Ds/2) L_w psi + {S (t = 0) | 3/2 S - 1/2 S_prev}
+//   with w = a + eps_w and L_w the flux-form operator of Eq. 28.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R weno_m(const R *v) {  // v points at node i, v[-2..1]
+    const R eps = R(1e-6);
+    R d2m = v[0] - R(2) * v[-1] + v[-2];
+    R d20 = v[1] - R(2) * v[0] + v[-1];
+    R r = (eps + d2m * d2m) / (eps + d20 * d20);
+    R w = R(1) / (R(1) + R(2) * r * r);
+    R dpm2 = v[-1] - v[-2], dpm1 = v[0] - v[-1], dp0 = v[1] - v[0];
+    return R(0.5) * ((dpm1 + dp0) - w * (dpm2 - R(2) * dpm1 + dp0));
+}
+template <typename R>
+__device__ __forceinline__ R weno_p(const R *v) {  // v[-1..2]
+    const R eps = R(1e-6);
+    R d2p = v[2] - R(2) * v[1] + v[0];
+    R d20 = v[1] - R(2) * v[0] + v[-1];
+    R r = (eps + d2p * d2p) / (eps + d20 * d20);
+    R w = R(1) / (R(1) + R(2) * r * r);
+    R dpm1 = v[0] - v[-1], dp0 = v[1] - v[0], dp1 = v[2] - v[1];
+    return R(0.5) * ((dpm1 + dp0) - w * (dp1 - R(2) * dp0 + dpm1));
+}
+template <typename R>
+__device__ __forceinline__ R upwind(const R *v, R u) {
+    if (u > R(0)) return weno_m(v);
+    if (u < R(0)) return weno_p(v);
+    return R(0.5) * (weno_m(v) + weno_p(v));
+}
+
+template <typename R>
+__global__ void k_fd2(Inst<R> I) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= I.nx || y >= I.ny) return;
+    long long c = (long long)y * I.pitch + x;
+    // line values of Psi_x, Phi_x along x and Psi_y, Phi_y along y
+    R Px[5], Cx[5], Py[5], Cy[5];
+#pragma unroll
+    for (int k = -2; k <= 2; k++) {
+        int refl, sx, sy;
+        long long j = nb2(I, x, y, k, 0, refl, sx, sy);
+        R sgn = (refl & 1) ? R(-1) : R(1);
+        R u = I.ux[j];
+        Px[k + 2] = sgn * I.psi[j] * I.a[j] * u;
+        Cx[k + 2] = sgn * I.C[j] * I.chi[j] * u;
+        j = nb2(I, x, y, 0, k, refl, sx, sy);
+        sgn = (refl & 2) ? R(-1) : R(1);
+        u = I.uy[j];
+        Py[k + 2] = sgn * I.psi[j] * I.a[j] * u;
+        Cy[k + 2] = sgn * I.C[j] * I.chi[j] * u;
+    }
+    R ux = I.ux[c], uy = I.uy[c];
+    R divP = upwind(Px + 2, ux) + upwind(Py + 2, uy);
+    R divC = upwind(Cx + 2, ux) + upwind(Cy + 2, uy);
+    R psi = I.psi[c], Cc = I.C[c], a = I.a[c];
+    R j = I.source == 1 ? I.ra * I.psi_inf * Cc
+                        : I.ra * Cc * (I.psi_inf - psi) - I.rd * psi;
+    R S = -divP + a * j;
+    R B = -divC - a * j;
+    // diffusion operator of Eq. 28 with the weights of time t
+    R wp = a + I.eps_w, wc = I.chi[c] + I.eps_w;
+    R Lp = R(0), Lc = R(0);
+#pragma unroll
+    for (int f = 0; f < 4; f++) {
+        int dx = f == 0 ? -1 : (f == 1 ? 1 : 0);
+        int dy = f == 2 ? -1 : (f == 3 ? 1 : 0);
+        int refl, sx, sy;
+        long long j2 = nb2(I, x, y, dx, dy, refl, sx, sy);
+        if (refl) continue;
+        Lp += R(0.5) * (wp + (I.a[j2] + I.eps_w)) * (I.psi[j2] - psi);
+        Lc += R(0.5) * (wc + (I.chi[j2] + I.eps_w)) * (I.C[j2] - Cc);
+    }
+    const bool first = I.ctl->step == 0;
+    R Sp = I.S[c], Bp = I.B[c];
+    R abS = first ? S : R(1.5) * S - R(0.5) * Sp;
+    R abB = first ? B : R(1.5) * B - R(0.5) * Bp;
+    I.rpsi[c] = wp * psi + R(0.5) * I.Ds * Lp + abS;
+    I.rC[c] = wc * Cc + R(0.5) * I.Db * Lc + abB;
+    I.S[c] = S;
+    I.B[c] = B;
+}
+
+// ---------------------------------------------------------------------------
+// k_collide: MRT collision with correction and forcing in moment space
+// (Eqs. 1-4, App. A Eqs. 36-38, 43) on the total populations, then
+// recolouring (Eqs. 11-12).  Output: post-collision buffers gT, gR.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_collide2(Inst<R> I) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= I.nx || y >= I.ny) return;
+    long long c = (long long)y * I.pitch + x;
+    R fT[Q9], fR[Q9];
+#pragma unroll
+    for (int i = 0; i < Q9; i++) {
+        fT[i] = I.fT[i * I.plane + c];
+        fR[i] = I.fR[i * I.plane + c];
+    }
+    Mom2<R> mo = moments9(fT, fR);
+    const R rR = mo.rR;
+    const R dB = mo.drho - mo.rR;  // rho^B - rhoB0 (the shift carries rhoB0)
+    const R rB = I.rho_s + dB;
+    const R rho = rR + rB;
+    const R ux = I.ux[c], uy = I.uy[c], Fx = I.Fx[c], Fy = I.Fy[c];
+
+    // d_a(rho^k u_a) by the isotropic stencil, u at walls as the ghost velocity
+    R dRx = R(0), dRy = R(0), dBx = R(0), dBy = R(0);
+#pragma unroll
+    for (int i = 1; i < Q9; i++) {
+        int refl, sx, sy;
+        long long j = nb2(I, x, y, ex9(i), ey9(i), refl, sx, sy);
+        R vx = I.ux[j], vy = I.uy[j];
+        ghost_u2(I, refl, sx, sy, vx, vy);
+        R r1 = I.rhoR[j], r2 = I.rhoB[j];
+        R wx = w9<R>(i) * R(ex9(i)), wy = w9<R>(i) * R(ey9(i));
+        dRx += wx * r1 * vx;
+        dRy += wy * r1 * vy;
+        dBx += wx * r2 * vx;
+        dBy += wy * r2 * vy;
+    }
+    // Q^k = (1.8 alpha^k - 0.8) d(rho^k u); correction C (Eq. 37), summed over k
+    const R cR = R(1.8) * I.alphaR - R(0.8), cB = R(1.8) * I.alphaB - R(0.8);
+    const R Qx = R(3) * (cR * dRx + cB * dBx), Qy = R(3) * (cR * dRy + cB * dBy);
+
+    // moments of the shifted total populations
+    R mT[Q9];
+#pragma unroll
+    for (int j = 0; j < Q9; j++) {
+        R s = R(0);
+#pragma unroll
+        for (int i = 0; i < Q9; i++)
+            if (m9(j, i) != 0) s += R(m9(j, i)) * fT[i];
+        mT[j] = s;
+    }
+    // non-equilibrium part m - m^eq (rows e, epsilon in deviation form:
+    // m = mT + moments of the shift; m^eq summed over the two colours)
+    const R u2 = ux * ux + uy * uy;
+    const R aBm = R(3.6) * I.alphaB + R(0.4), aRm = R(3.6) * I.alphaR + R(0.4);
+    const R bBm = R(5.4) * I.alphaB - R(1.4), bRm = R(5.4) * I.alphaR - R(1.4);
+    const R qco = R(-1.8) * (I.alphaR * rR + I.alphaB * rB) - R(0.2) * rho;
+    R neq[Q9];
+    neq[0] = R(0);
+    neq[1] = mT[1] + dB * aBm + rR * aRm - R(3) * rho * u2;
+    neq[2] = mT[2] - dB * bBm - rR * bRm + R(3) * rho * u2;
+    neq[3] = R(0);
+    neq[4] = mT[4] - qco * ux;
+    neq[5] = R(0);
+    neq[6] = mT[6] - qco * uy;
+    neq[7] = mT[7] - rho * (ux * ux - uy * uy);
+    neq[8] = mT[8] - rho * ux * uy;
+
+    // relaxation (Eq. 38) with s_v from the mixture viscosity (Eq. 43)
+    const R rN = colour_fn(I, rR, rB);
+    const R inv_mu = (R(1) + rN) / (R(2) * I.muR0) + (R(1) - rN) / (R(2) * I.muB0);
+    const R pk = rR * I.cs2R + rB * I.cs2B;
+    const R sv = R(1) / (R(0.5) + R(1) / (inv_mu * pk));
+    const R Sd[Q9] = {R(0), R(1.25), R(1.14), R(0), R(1.6), R(0), R(1.6), sv, sv};
+    // forcing moments of Eq. 4 (closed form for D2Q9)
+    const R uF = ux * Fx + uy * Fy;
+    const R Fh[Q9] = {R(0), R(6) * uF, R(-6) * uF, Fx, -Fx, Fy, -Fy,
+                      R(2) * (ux * Fx - uy * Fy), ux * Fy + uy * Fx};
+    const R Cm[Q9] = {R(0), R(3) * (Qx + Qy), R(0), R(0), R(0), R(0), R(0), Qx - Qy, R(0)};
+    R dm[Q9];
+#pragma unroll
+    for (int j = 0; j < Q9; j++)
+        dm[j] = (-Sd[j] * neq[j] + (R(1) - R(0.5) * Sd[j]) * (Cm[j] + Fh[j])) / R(mnorm9(j));
+
+    // recolouring: segregation weight f_i^eq(rho, 0)/rho; for the alpha-model
+    // its moving components are w_i * 3 p / rho with p = sum_k rho^k (c_s^k)^2
+    const R ggx = I.gx[c], ggy = I.gy[c];
+    const R gn = sqrt(ggx * ggx + ggy * ggy + I.eps_n * I.eps_n);
+    const R seg = I.beta * rR * rB / (rho * rho) * R(3) * pk / gn;
+    const R fr = rR / rho;
+#pragma unroll
+    for (int i = 0; i < Q9; i++) {
+        R s = fT[i];
+#pragma unroll
+        for (int j = 0; j < Q9; j++)
+            if (m9(j, i) != 0) s += R(m9(j, i)) * dm[j];
+        // s = post-collision total minus shift
+        R segi = i == 0 ? R(0) : seg * w9<R>(i) * (R(ex9(i)) * ggx + R(ey9(i)) * ggy);
+        I.gT[i * I.plane + c] = s;
+        I.gR[i * I.plane + c] = fr * (I.shift[i] + s) + segi;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_stream: f_i(x, t+1) = f_i^post(x - e_i) (Eq. 13, pull form); a link that
+// crosses a wall is reflected (half-way bounce-back), a moving wall adds
+// 2 w_i rho^k (e_i . u_w) / c_s^2.  Stores the moments at t+1.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_stream2(Inst<R> I) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= I.nx || y >= I.ny) return;
+    long long c = (long long)y * I.pitch + x;
+    R fT[Q9], fR[Q9];
+    const R rRc = I.rhoR[c], rBc = I.rhoB[c];
+#pragma unroll
+    for (int i = 0; i < Q9; i++) {
+        int refl, sx, sy;
+        long long j = nb2(I, x, y, -ex9(i), -ey9(i), refl, sx, sy);
+        if (!refl) {
+            fT[i] = I.gT[i * I.plane + j];
+            fR[i] = I.gR[i * I.plane + j];
+        } else {
+            R uwx = R(0), uwy = R(0);
+            int nw = 0;
+            if (refl & 1) {
+                const R *w = sx < 0 ? I.uw_lo[0] : I.uw_hi[0];
+                uwx += w[0];
+                uwy += w[1];
+                nw++;
+            }
+            if (refl & 2) {
+                const R *w = sy < 0 ? I.uw_lo[1] : I.uw_hi[1];
+                uwx += w[0];
+                uwy += w[1];
+                nw++;
+            }
+            R eu = (R(ex9(i)) * uwx + R(ey9(i)) * uwy) / R(nw);
+            R mw = R(2) * w9<R>(i) * eu * R(3);
+            fT[i] = I.gT[opp9(i) * I.plane + c] + mw * (rRc + rBc);
+            fR[i] = I.gR[opp9(i) * I.plane + c] + mw * rRc;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q9; i++) {
+        I.fT[i * I.plane + c] = fT[i];
+        I.fR[i * I.plane + c] = fR[i];
+    }
+    store_moments(I, c, fT, fR);
+}
+
+// ---------------------------------------------------------------------------
+// k_sor: one half-sweep of red-black SOR (Sec. 2.2: relaxation factor 1.2) for
+// (w - h L_w) x = rhs on psi (w = a + eps_w, h = Ds/2) and C (w = chi + eps_w,
+// h = Db/2).  Sweep k returns at once if sweep k-1 already met the tolerance.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void atomic_max_pos(unsigned long long *p, double v) {
+    atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename R>
+__device__ __forceinline__ bool sweep_converged(const Ctl *ctl, int k, double tol) {
+    double dp = __longlong_as_double((long long)ctl->sweep[k][0]);
+    double dc = __longlong_as_double((long long)ctl->sweep[k][1]);
+    double xp = __longlong_as_double((long long)ctl->sweep[k][2]);
+    double xc = __longlong_as_double((long long)ctl->sweep[k][3]);
+    return dp <= tol * xp && dc <= tol * xc;
+}
+
+template <typename R, int BS>
+__device__ __forceinline__ void block_max4(double v[4], unsigned long long *dst) {
+    __shared__ double sh[4][BS / 32];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
+    }
+    int t = threadIdx.x + threadIdx.y * blockDim.x;
+    if ((t & 31) == 0)
+        for (int q = 0; q < 4; q++) sh[q][t >> 5] = v[q];
+    __syncthreads();
+    if (t == 0) {
+        for (int q = 0; q < 4; q++) {
+            double m = 0;
+            for (int w = 0; w < BS / 32; w++) m = fmax(m, sh[q][w]);
+            atomic_max_pos(&dst[q], m);
+        }
+    }
+}
+
+template <typename R, int BS>
+__global__ void k_sor2(Inst<R> I, int colour, int k) {
+    if (k > 0 && sweep_converged<R>(I.ctl, k - 1, double(I.sor_tol))) return;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    double v[4] = {0, 0, 0, 0};
+    if (x < I.nx && y < I.ny && ((x + y) & 1) == colour) {
+        long long c = (long long)y * I.pitch + x;
+        const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
+        R wp = I.a[c] + I.eps_w, wc = I.chi[c] + I.eps_w;
+        R dgp = wp, dgc = wc, op = R(0), oc = R(0);
+#pragma unroll
+        for (int f = 0; f < 4; f++) {
+            int dx = f == 0 ? -1 : (f == 1 ? 1 : 0);
+            int dy = f == 2 ? -1 : (f == 3 ? 1 : 0);
+            int refl, sx, sy;
+            long long j = nb2(I, x, y, dx, dy, refl, sx, sy);
+            if (refl) continue;
+            R fp = hp * R(0.5) * (wp + (I.a[j] + I.eps_w));
+            R fc = hc * R(0.5) * (wc + (I.chi[j] + I.eps_w));
+            dgp += fp;
+            dgc += fc;
+            op += fp * I.psi[j];
+            oc += fc * I.C[j];
+        }
+        R p0 = I.psi[c], c0 = I.C[c];
+        R dp = I.omega * ((I.rpsi[c] + op) / dgp - p0);
+        R dc = I.omega * ((I.rC[c] + oc) / dgc - c0);
+        R p1 = p0 + dp, c1 = c0 + dc;
+        I.psi[c] = p1;
+        I.C[c] = c1;
+        v[0] = fabs(double(dp));
+        v[1] = fabs(double(dc));
+        v[2] = fabs(double(p1));
+        v[3] = fabs(double(c1));
+    }
+    block_max4<R, BS>(v, I.ctl->sweep[k]);
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic FP64 reductions: per-block partials, the last block to arrive
+// sums them in block order.
+// ---------------------------------------------------------------------------
+template <int BS, int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double *out /* K, thread 0 */) {
+    __shared__ double sh[K][BS / 32];
+#pragma unroll
+    for (int q = 0; q < K; q++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    }
+    int t = threadIdx.x + threadIdx.y * blockDim.x;
+    if ((t & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < K; q++) sh[q][t >> 5] = v[q];
+    __syncthreads();
+    if (t == 0)
+        for (int q = 0; q < K; q++) {
+            double s = 0;
+            for (int w = 0; w < BS / 32; w++) s += sh[q][w];
+            out[q] = s;
+        }
+}
+
+// returns true in thread 0 of the last block to finish; its partials are then
+// all visible
+__device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned int nblocks) {
+    __shared__ bool last;
+    int t = threadIdx.x + threadIdx.y * blockDim.x;
+    __syncthreads();
+    if (t == 0) {
+        __threadfence();
+        unsigned int prev = atomicAdd(ticket, 1u);
+        last = prev == nblocks - 1;
+    }
+    __syncthreads();
+    return last;
+}
+
+// k_surf: total surfactant sum (a+eps) psi + (chi+eps) C in FP64.
+// mode 0: set the conserved total M0 (after initialisation);
+// mode 1: end of a step: rescale factor M0/total (Sec. 2.2), SOR bookkeeping,
+//         step counter, divergence check.
+template <typename R, int BS>
+__global__ void k_surf2(Inst<R> I, int mode, int nblocks) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    double v[1] = {0};
+    if (x < I.nx && y < I.ny) {
+        long long c = (long long)y * I.pitch + x;
+        v[0] = double(I.a[c] + I.eps_w) * double(I.psi[c]) +
+               double(I.chi[c] + I.eps_w) * double(I.C[c]);
+    }
+    int b = blockIdx.x + blockIdx.y * gridDim.x;
+    block_sum<BS, 1>(v, I.part + b);
+    if (!last_block(&I.ctl->ticket, nblocks)) return;
+    int t = threadIdx.x + threadIdx.y * blockDim.x;
+    if (t != 0) return;
+    double tot = 0;
+    for (int k = 0; k < nblocks; k++) tot += I.part[k];
+    Ctl *ctl = I.ctl;
+    ctl->ticket = 0;
+    if (mode == 0) {
+        ctl->M0 = tot;
+        ctl->pre = tot;
+        ctl->scale = 1.0;
+        return;
+    }
+    ctl->pre = tot;
+    ctl->scale = tot > 0 ? ctl->M0 / tot : 1.0;
+    if (!isfinite(tot)) ctl->status |= ST_DIVERGED;
+    int used = I.sor_max_iter;
+    bool conv = false;
+    for (int k = 0; k < I.sor_max_iter; k++)
+        if (sweep_converged<R>(ctl, k, double(I.sor_tol))) {
+            used = k + 1;
+            conv = true;
+            break;
+        }
+    if (!conv) ctl->status |= ST_NOCONV;
+    ctl->sor_iters = used;
+    for (int k = 0; k < KMAX_SWEEPS; k++)
+        for (int q = 0; q < 4; q++) ctl->sweep[k][q] = 0ull;
+    ctl->step += 1;
+}
+
+template <typename R>
+__global__ void k_scale2(Inst<R> I) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= I.nx || y >= I.ny) return;
+    long long c = (long long)y * I.pitch + x;
+    R s = R(I.ctl->scale);
+    I.psi[c] *= s;
+    I.C[c] *= s;
+}
+
+// step counter for runs without surfactant transport
+template <typename R>
+__global__ void k_tick(Inst<R> I) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) I.ctl->step += 1;
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics (FP64): masses, total surfactant, indicator N = [rhoN >= 0]
+// sums for U (Eqs. 33-34), centroid and second moments, interface psi stats.
+// ---------------------------------------------------------------------------
+constexpr int NDIAG = 17;
+template <typename R, int BS>
+__global__ void k_diag2(Inst<R> I, int nblocks) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    // 0 mR, 1 mB, 2 surf, 3 cnt, 4 sux, 5 suy, 6 sx, 7 sy, 8 sxx, 9 syy,
+    // 10 psum, 11 pcnt, 12 pmin(-), 13 pmax, 14 umax, 15 suz, 16 sz (2D: 0)
+    double v[NDIAG] = {0};
+    double pmin = 1e300, pmax = -1e300, umax = 0;
+    if (x < I.nx && y < I.ny) {
+        long long c = (long long)y * I.pitch + x;
+        double rR = I.rhoR[c], rB = I.rhoB[c], rN = I.rhoN[c];
+        v[0] = rR;
+        v[1] = rB;
+        v[2] = double(I.a[c] + I.eps_w) * double(I.psi[c]) +
+               double(I.chi[c] + I.eps_w) * double(I.C[c]);
+        double ux = I.ux[c], uy = I.uy[c];
+        if (rN >= 0) {
+            v[3] = 1;
+            v[4] = ux;
+            v[5] = uy;
+            v[6] = x;
+            v[7] = y;
+            v[8] = double(x) * x;
+            v[9] = double(y) * y;
+        }
+        if (fabs(rN) < 0.5) {
+            double p = I.psi[c];
+            v[10] = p;
+            v[11] = 1;
+            pmin = p;
+            pmax = p;
+        }
+        umax = sqrt(ux * ux + uy * uy);
+    }
+    int b = blockIdx.x + blockIdx.y * gridDim.x;
+    double s[NDIAG];
+    block_sum<BS, NDIAG>(v, s);
+    // min / max through a second pass on the same shared scheme
+    double mm[4] = {-pmin, pmax, umax, 0};
+    __shared__ double shm[3][BS / 32];
+#pragma unroll
+    for (int q = 0; q < 3; q++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mm[q] = fmax(mm[q], __shfl_down_sync(0xffffffffu, mm[q], o));
+    int t = threadIdx.x + threadIdx.y * blockDim.x;
+    if ((t & 31) == 0)
+        for (int q = 0; q < 3; q++) shm[q][t >> 5] = mm[q];
+    __syncthreads();
+    if (t == 0) {
+        for (int q = 0; q < 3; q++) {
+            double m = -1e300;
+            for (int w = 0; w < BS / 32; w++) m = fmax(m, shm[q][w]);
+            mm[q] = m;
+        }
+        for (int q = 0; q < NDIAG; q++) I.part[(long long)b * (NDIAG + 3) + q] = s[q];
+        I.part[(long long)b * (NDIAG + 3) + NDIAG + 0] = mm[0];
+        I.part[(long long)b * (NDIAG + 3) + NDIAG + 1] = mm[1];
+        I.part[(long long)b * (NDIAG + 3) + NDIAG + 2] = mm[2];
+    }
+    if (!last_block(&I.ctl->ticket, nblocks)) return;
+    if (t != 0) return;
+    double tot[NDIAG + 3];
+    for (int q = 0; q < NDIAG; q++) tot[q] = 0;
+    for (int q = NDIAG; q < NDIAG + 3; q++) tot[q] = -1e300;
+    for (int k = 0; k < nblocks; k++) {
+        for (int q = 0; q < NDIAG; q++) tot[q] += I.part[(long long)k * (NDIAG + 3) + q];
+        for (int q = NDIAG; q < NDIAG + 3; q++)
+            tot[q] = fmax(tot[q], I.part[(long long)k * (NDIAG + 3) + q]);
+    }
+    for (int q = 0; q < NDIAG + 3; q++) I.ctl->diag[q] = tot[q];
+    I.ctl->ticket = 0;
+}
+
+// dense double copies of the macroscopic fields for the host
+template <typename R>
+__global__ void k_export2(Inst<R> I, double *rho, double *u, double *phi, double *psi,
+                          double *C) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= I.nx || y >= I.ny) return;
+    long long c = (long long)y * I.pitch + x;
+    long long d = (long long)y * I.nx + x;
+    long long N = (long long)I.nx * I.ny;
+    rho[d] = double(I.rhoR[c]) + double(I.rhoB[c]);
+    u[d] = I.ux[c];
+    u[N + d] = I.uy[c];
+    u[2 * N + d] = 0.0;
+    phi[d] = I.rhoN[c];
+    psi[d] = I.psi[c];
+    C[d] = I.C[c];
+}
+
+}  // namespace lbs

@@ -1,0 +1,214 @@
+"""Python binding of the C ABI in ``include/lbs.h`` (``liblbs.so``).
+
+Argument marshalling only: every step of the coupled update runs in the CUDA
+kernels of the library.  PyTorch supplies the device workspace and the CUDA
+stream.  There is no CPU fallback: loading fails loudly when the library or
+a CUDA device is missing.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBS_OK, LBS_EINVAL, LBS_ENOMEM, LBS_ECUDA = 0, -1, -2, -3
+LBS_ENOCONV, LBS_EDIVERGED, LBS_ETIMEOUT, LBS_EBOUNDS = -4, -5, -6, -7
+LBS_F64, LBS_F32 = 0, 1
+STORAGE = {"f64": LBS_F64, "f32": LBS_F32}
+
+EXPORTS = ("lbs_params_default", "lbs_workspace_bytes", "lbs_create",
+           "lbs_init_fields", "lbs_step", "lbs_sync", "lbs_get_fields",
+           "lbs_diagnostics", "lbs_profile", "lbs_kernel_times",
+           "lbs_step_kernel_count", "lbs_destroy", "lbs_last_error")
+KERNEL_GROUPS = ("force", "fd", "collide", "stream", "grad", "sor", "surf")
+
+
+class LbsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbs error {code}: {msg}")
+        self.code = code
+
+
+class LbsParams(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("wall", C.c_int * 3),
+        ("uw_lo", (C.c_double * 3) * 3), ("uw_hi", (C.c_double * 3) * 3),
+        ("rhoR0", C.c_double), ("rhoB0", C.c_double),
+        ("muR0", C.c_double), ("muB0", C.c_double),
+        ("alphaR", C.c_double), ("alphaB", C.c_double),
+        ("sigma0", C.c_double), ("sigma_min_ratio", C.c_double),
+        ("E0", C.c_double), ("psi_inf", C.c_double), ("beta", C.c_double),
+        ("eos", C.c_int), ("source", C.c_int), ("transport", C.c_int),
+        ("Ds", C.c_double), ("Db", C.c_double), ("ra", C.c_double), ("rd", C.c_double),
+        ("g", C.c_double * 3),
+        ("sor_omega", C.c_double), ("sor_tol", C.c_double), ("sor_max_iter", C.c_int),
+        ("eps_w", C.c_double), ("eps_n", C.c_double),
+    ]
+
+
+class LbsDiag(C.Structure):
+    _fields_ = [
+        ("mass_R", C.c_double), ("mass_B", C.c_double),
+        ("surf_total", C.c_double), ("surf_pre_rescale", C.c_double),
+        ("rescale_factor", C.c_double),
+        ("U", C.c_double * 3), ("centroid", C.c_double * 3),
+        ("aspect_ratio", C.c_double),
+        ("psi_av", C.c_double), ("psi_min", C.c_double), ("psi_max", C.c_double),
+        ("umax", C.c_double), ("Re", C.c_double),
+        ("sor_iters_psi", C.c_int), ("sor_iters_C", C.c_int),
+        ("step", C.c_longlong),
+    ]
+
+
+_lib = None
+_DP = C.POINTER(C.c_double)
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblbs.so (building it in-tree if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library missing: {path}")
+    L = C.CDLL(path)
+    L.lbs_params_default.argtypes = [C.POINTER(LbsParams), C.c_int, C.c_int, C.c_int]
+    L.lbs_workspace_bytes.restype = C.c_size_t
+    L.lbs_workspace_bytes.argtypes = [C.POINTER(LbsParams), C.c_int]
+    L.lbs_create.argtypes = [C.POINTER(LbsParams), C.c_int, C.c_void_p, C.c_void_p,
+                             C.c_size_t, C.POINTER(C.c_void_p)]
+    L.lbs_init_fields.argtypes = [C.c_void_p, _DP, _DP, _DP, _DP]
+    L.lbs_step.argtypes = [C.c_void_p, C.c_int]
+    L.lbs_sync.argtypes = [C.c_void_p]
+    L.lbs_get_fields.argtypes = [C.c_void_p, _DP, _DP, _DP, _DP, _DP]
+    L.lbs_diagnostics.argtypes = [C.c_void_p, C.POINTER(LbsDiag)]
+    L.lbs_profile.argtypes = [C.c_void_p, C.c_int]
+    L.lbs_kernel_times.argtypes = [C.c_void_p, _DP, C.c_int]
+    L.lbs_step_kernel_count.argtypes = [C.c_void_p]
+    L.lbs_destroy.argtypes = [C.c_void_p]
+    L.lbs_last_error.restype = C.c_char_p
+    L.lbs_last_error.argtypes = [C.c_void_p]
+    _lib = L
+    return L
+
+
+def params_from(cfg: dict, storage: int) -> LbsParams:
+    """Marshal a workload parameter dict into the ABI's parameter struct."""
+    p = LbsParams()
+    load().lbs_params_default(C.byref(p), int(cfg["nx"]), int(cfg["ny"]), int(cfg.get("nz", 1)))
+    for a in range(3):
+        p.wall[a] = int(cfg.get("wall", (0, 0, 0))[a])
+        for b in range(3):
+            p.uw_lo[a][b] = float(cfg.get("uw_lo", [[0] * 3] * 3)[a][b])
+            p.uw_hi[a][b] = float(cfg.get("uw_hi", [[0] * 3] * 3)[a][b])
+        p.g[a] = float(cfg.get("g", (0, 0, 0))[a])
+    for k in ("rhoR0", "rhoB0", "muR0", "muB0", "alphaR", "alphaB", "sigma0",
+              "sigma_min_ratio", "E0", "psi_inf", "beta", "Ds", "Db", "ra", "rd",
+              "sor_omega", "eps_w", "eps_n"):
+        if k in cfg:
+            setattr(p, k, float(cfg[k]))
+    for k in ("eos", "source", "transport"):
+        if k in cfg:
+            setattr(p, k, int(cfg[k]))
+    p.sor_tol = float(cfg.get("sor_tol", 1e-13 if storage == LBS_F64 else 1e-6))
+    p.sor_max_iter = int(cfg.get("sor_max_iter", 64 if storage == LBS_F64 else 40))
+    return p
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_DP)
+
+
+class Solver:
+    """One solver context on the current CUDA device.
+
+    The device workspace is a torch uint8 tensor and the work is queued on a
+    torch CUDA stream (both borrowed by the library)."""
+
+    def __init__(self, cfg: dict, storage="f32", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.L = load()
+        self.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        self.p = params_from(cfg, self.storage)
+        self.shape = (self.p.nz, self.p.ny, self.p.nx)
+        self.N = int(np.prod(self.shape))
+        nbytes = self.L.lbs_workspace_bytes(C.byref(self.p), self.storage)
+        if nbytes == 0:
+            raise LbsError(LBS_EINVAL, "invalid parameters")
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        # a stream of its own: the step graph is captured on it, which the
+        # legacy default stream does not allow
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = C.c_void_p()
+        r = self.L.lbs_create(C.byref(self.p), self.storage, C.c_void_p(self.stream.cuda_stream),
+                              C.c_void_p(aligned), nbytes, C.byref(h))
+        self.h = h
+        self._check(r)
+
+    def _check(self, r):
+        if r != LBS_OK:
+            msg = self.L.lbs_last_error(self.h).decode() if self.h else "?"
+            raise LbsError(r, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.lbs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _f(self, x, comps=None):
+        if x is None:
+            return None
+        shape = self.shape if comps is None else (comps,) + self.shape
+        return np.ascontiguousarray(np.broadcast_to(np.asarray(x, np.float64), shape))
+
+    def init_fields(self, phi, psi=None, C_=None, u=None):
+        arrs = [self._f(phi), self._f(psi), self._f(C_), self._f(u, 3)]
+        self._check(self.L.lbs_init_fields(self.h, *[_dp(a) for a in arrs]))
+
+    def step(self, n=1):
+        self._check(self.L.lbs_step(self.h, int(n)))
+
+    def sync(self):
+        self._check(self.L.lbs_sync(self.h))
+
+    def fields(self):
+        rho = np.empty(self.shape)
+        u = np.empty((3,) + self.shape)
+        phi, psi, C_ = (np.empty(self.shape) for _ in range(3))
+        self._check(self.L.lbs_get_fields(self.h, _dp(rho), _dp(u), _dp(phi), _dp(psi), _dp(C_)))
+        return dict(rho=rho, u=u, phi=phi, psi=psi, C=C_)
+
+    def profile(self, on=True):
+        self._check(self.L.lbs_profile(self.h, int(bool(on))))
+
+    def kernel_times(self):
+        """Device milliseconds of each kernel group in the last step."""
+        ms = np.zeros(len(KERNEL_GROUPS))
+        self._check(self.L.lbs_kernel_times(self.h, _dp(ms), len(KERNEL_GROUPS)))
+        return dict(zip(KERNEL_GROUPS, ms.tolist()))
+
+    def kernel_count(self):
+        return int(self.L.lbs_step_kernel_count(self.h))
+
+    def diagnostics(self):
+        d = LbsDiag()
+        self._check(self.L.lbs_diagnostics(self.h, C.byref(d)))
+        return {k: (list(getattr(d, k)) if k in ("U", "centroid") else getattr(d, k))
+                for k, _ in LbsDiag._fields_}

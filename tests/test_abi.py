@@ -1,0 +1,58 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/lbs.h declares (no GPU needed: nothing is called that computes)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2311_15242_gb300 as P
+from paper_2311_15242_gb300 import lbs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    txt = open(os.path.join(ROOT, "include", "lbs.h")).read()
+    pat = r"^(?:int|void|size_t|const char)\s*\*?\s*(lbs_[a-z_0-9]+)\s*\("
+    return sorted(set(re.findall(pat, txt, flags=re.M)))
+
+
+def test_header_and_binding_agree():
+    assert declared() == sorted(lbs.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    L = P.load()
+    for name in declared():
+        assert hasattr(L, name), name
+
+
+def test_param_struct_layout_matches_header():
+    """ctypes mirror of lbs_params: size equals the C struct (sizeof via the
+    defaults call writing every field) and defaults are the paper's values."""
+    p = lbs.LbsParams()
+    assert P.load().lbs_params_default(ctypes.byref(p), 64, 32, 1) == 0
+    assert (p.nx, p.ny, p.nz) == (64, 32, 1)
+    assert p.beta == 0.7 and p.sor_omega == 1.2 and p.sigma_min_ratio == 0.1
+    assert abs(p.alphaR - 4 / 9) < 1e-15
+
+
+def test_workspace_and_validation_on_host():
+    L = P.load()
+    p = lbs.LbsParams()
+    L.lbs_params_default(ctypes.byref(p), 64, 32, 1)
+    assert L.lbs_workspace_bytes(ctypes.byref(p), lbs.LBS_F32) > 0
+    assert L.lbs_workspace_bytes(ctypes.byref(p), lbs.LBS_F64) > L.lbs_workspace_bytes(ctypes.byref(p), lbs.LBS_F32)
+    bad = lbs.LbsParams()
+    L.lbs_params_default(ctypes.byref(bad), 64, 32, 1)
+    bad.rhoR0 = -1.0
+    assert L.lbs_workspace_bytes(ctypes.byref(bad), lbs.LBS_F32) == 0
+    bad.rhoR0 = 1.0
+    bad.wall[0] = 1
+    bad.nx = 2
+    assert L.lbs_workspace_bytes(ctypes.byref(bad), lbs.LBS_F32) == 0
+    h = ctypes.c_void_p()
+    assert L.lbs_create(ctypes.byref(bad), lbs.LBS_F32, None, None, 0, ctypes.byref(h)) == lbs.LBS_EINVAL
+    assert b"3 nodes" in L.lbs_last_error(h)
+    L.lbs_destroy(h)

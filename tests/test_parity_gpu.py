@@ -1,0 +1,125 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Error metric (per field): max |x_gpu - x_oracle| / max|x_oracle|, the velocity
+normalised by its own maximum.  Tolerances:
+  - FP64 storage: 1e-9 after tens of steps (both sides converge SOR to a
+    relative update of 1e-13; what remains is rounding order);
+  - FP32 storage: 1e-5 after 1000 steps on rho, u, phi, psi, C (the FP32
+    accuracy target of the method's GPU form).
+Grids span several 32 x 8 thread blocks and end in ragged tails."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.ora import Oracle
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("rho", "u", "phi", "psi", "C")
+
+
+def solver(cfg, storage):
+    from paper_2311_15242_gb300 import Solver
+    return Solver(cfg, storage=storage)
+
+
+def run_both(cfg, steps, storage, seed=7, noise=0.02, u0=0.0, gpu_steps_chunk=None):
+    f = W.initial_fields(cfg, seed=seed, noise=noise, u0=u0)
+    o = Oracle(cfg)
+    o.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    s = solver(cfg, storage)
+    s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    o.step(steps)
+    s.step(steps)
+    return o, s
+
+
+def errors(ref, got):
+    out = {}
+    for k in FIELDS:
+        scale = max(np.abs(ref[k]).max(), 1e-30)
+        out[k] = float(np.abs(got[k] - ref[k]).max() / scale)
+    return out
+
+
+def droplet(nx=72, ny=44, R=12.0):
+    c = W.droplet_adsorption_2d(n=nx, R=R, C0=0.5)
+    c["ny"] = ny
+    c["center"] = [(nx - 1) / 2 - 3.3, (ny - 1) / 2 + 1.7, 0.0]
+    return c
+
+
+def bubble(nx=40, ny=72):
+    return W.bubble_rise_2d(nx=nx, ny=ny, D_b=16.0, Eo=2.0)
+
+
+@pytest.mark.parametrize("make", [droplet, bubble], ids=["droplet", "bubble"])
+def test_f64_matches_oracle(make):
+    cfg = make()
+    o, s = run_both(cfg, 40, "f64", u0=1e-3)
+    err = errors(o.fields(), s.fields())
+    assert max(err.values()) < 1e-9, err
+    d_o, d_s = o.diagnostics(), s.diagnostics()
+    for k in ("mass_R", "mass_B", "surf_total"):
+        assert d_s[k] == pytest.approx(d_o[k], rel=1e-12), k
+    assert d_s["step"] == d_o["step"] == 40
+
+
+@pytest.mark.parametrize("make", [droplet, bubble], ids=["droplet", "bubble"])
+def test_f32_matches_oracle_1000_steps(make):
+    cfg = make()
+    o, s = run_both(cfg, 1000, "f32")
+    err = errors(o.fields(), s.fields())
+    assert max(err.values()) <= 1e-5, err
+
+
+def test_f32_conservation_per_step():
+    """Colour masses: FP32 storage, FP64 sums; drift <= 1e-10 relative per
+    step.  Total surfactant held by the rescale."""
+    cfg = bubble(64, 128)
+    f = W.initial_fields(cfg)
+    s = solver(cfg, "f32")
+    s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    d0 = s.diagnostics()
+    n = 200
+    s.step(n)
+    d = s.diagnostics()
+    for k in ("mass_R", "mass_B"):
+        assert abs(d[k] - d0[k]) / d0[k] <= 1e-10 * n, (k, d[k], d0[k])
+    assert abs(d["surf_total"] - d0["surf_total"]) / d0["surf_total"] <= 1e-6
+
+
+def test_edge_cases_small_and_ragged():
+    """Tiny walled grid (3 nodes across), ragged tails in x and y, zero steps,
+    no surfactant transport, E0 = 0 (no Marangoni) and psi above the CMC."""
+    cases = []
+    c = bubble(nx=5, ny=9)
+    c["R"] = 1.5
+    cases.append(c)
+    c = droplet(nx=33, ny=9, R=3.0)
+    c["transport"] = 0
+    cases.append(c)
+    c = droplet(nx=35, ny=17, R=5.0)
+    c["E0"] = 0.0
+    cases.append(c)
+    c = droplet(nx=31, ny=23, R=6.0)
+    c["psi0"] = 2.0  # above the CMC (psi_inf = 1)
+    cases.append(c)
+    for cfg in cases:
+        o, s = run_both(cfg, 0, "f64")
+        err0 = errors(o.fields(), s.fields())
+        assert max(err0.values()) < 1e-12, (cfg["nx"], err0)
+        o.step(15)
+        s.step(15)
+        err = errors(o.fields(), s.fields())
+        assert max(err.values()) < 1e-9, (cfg["nx"], cfg["ny"], err)
+
+
+def test_full_size_bubble_rise_sampled():
+    """The 256 x 1024 walled bubble rise (D = 64, density ratio 10, Eo = 10,
+    Bi = 1) in the launch configuration the benchmark times (FP32 storage,
+    one CUDA graph per step), against the oracle after a few steps."""
+    cfg = W.bubble_rise_2d()
+    o, s = run_both(cfg, 3, "f32", noise=0.0)
+    err = errors(o.fields(), s.fields())
+    assert max(err.values()) <= 1e-5, err
