@@ -260,6 +260,11 @@ void ora_eos(const ora_params *p, double psi, double *sigma, double *mcoef) {
         *mcoef = p->sigma0 * p->E0 / p->psi_inf;
         return;
     }
+    if (p->E0 == 0.0) { /* Eq. 8 with E0 = 0: sigma = sigma0 for every psi */
+        *sigma = p->sigma0;
+        *mcoef = 0.0;
+        return;
+    }
     if (psi < ora_cmc(p)) {
         *sigma = p->sigma0 * (1.0 + p->E0 * log1p(-psi / p->psi_inf));
         *mcoef = p->sigma0 * p->E0 / (p->psi_inf - psi);

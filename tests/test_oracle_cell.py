@@ -201,6 +201,9 @@ def test_eos_langmuir_closed_forms():
         h = 1e-6
         ds = (ora.eos(cfg, psi + h)[0] - ora.eos(cfg, psi - h)[0]) / (2 * h)
         assert np.isclose(-ds, ora.eos(cfg, psi)[1], rtol=1e-7)
+    clean = _cfg(sigma0=0.1, E0=0.0, psi_inf=1.0)
+    for psi in (0.0, 0.5, 3.0):  # E0 = 0: constant tension, no Marangoni stress
+        assert ora.eos(clean, psi) == (0.1, 0.0)
     lin = _cfg(sigma0=0.001, E0=0.5, psi_inf=1.0, eos=1)
     assert ora.eos(lin, 0.4) == pytest.approx((0.001 * 0.8, 0.001 * 0.5))
 
