@@ -81,7 +81,7 @@ void set_err(lbs_ctx *c, const char *fmt, ...) {
 struct Layout {
     int pitch;
     long long plane;
-    size_t pops_off, scal_off, ctl_off, part_off, stage_off, total;
+    size_t pops_off, scal_off, flag_off, ctl_off, part_off, stage_off, total;
     int nblocks;
 };
 
@@ -95,7 +95,8 @@ Layout layout_of(const lbs_params *p) {
     size_t pops = 4 * (size_t)Q9 * pb;
     L.scal_off = pops;
     size_t scal = 19 * pb;
-    L.ctl_off = align_up(L.scal_off + scal, 256);
+    L.flag_off = align_up(L.scal_off + scal, 256);
+    L.ctl_off = align_up(L.flag_off + 2 * (size_t)L.plane, 256);
     L.part_off = align_up(L.ctl_off + sizeof(Ctl), 256);
     L.nblocks = ((p->nx + BX - 1) / BX) * ((p->ny + BY - 1) / BY) * p->nz;
     L.stage_off = align_up(L.part_off + (size_t)L.nblocks * (NDIAG + 3) * sizeof(double), 256);
@@ -176,9 +177,11 @@ struct Solver : Base {
         size_t pb = (size_t)L.plane;
         R *pops = (R *)(ws + L.pops_off);
         I.fT = pops;
-        I.fR = pops + 1 * Q9 * pb;
+        I.fM = pops + 1 * Q9 * pb;
         I.gT = pops + 2 * Q9 * pb;
-        I.gR = pops + 3 * Q9 * pb;
+        I.gM = pops + 3 * Q9 * pb;
+        I.flag = (uint8_t *)(ws + L.flag_off);
+        I.gflag = I.flag + L.plane;
         R *sc = (R *)(ws + L.scal_off);
         R **fields[] = {&I.rhoR, &I.rhoB, &I.rhoN, &I.jx,  &I.jy, &I.gx,  &I.gy,
                         &I.a,    &I.chi,  &I.ux,   &I.uy,  &I.Fx, &I.Fy,  &I.psi,
@@ -198,8 +201,9 @@ struct Solver : Base {
             if (e) cudaEventDestroy(e);
     }
 
+    // (recorded as an event node when captured into the step graph)
     void mark(cudaStream_t s, int g) {
-        if (prof) cudaEventRecord(ev[g], s);
+        if (prof) cudaEventRecordWithFlags(ev[g], s, cudaEventRecordExternal);
     }
 
     int launch_check() {
@@ -480,7 +484,7 @@ int lbs_params_default(lbs_params *p, int nx, int ny, int nz) {
     p->transport = 1;
     p->Ds = p->Db = 0.1;
     p->sor_omega = 1.2;
-    p->sor_tol = 1e-6;
+    p->sor_tol = 2e-7;
     p->sor_max_iter = 40;
     p->eps_w = 1e-6;
     p->eps_n = 1e-6;

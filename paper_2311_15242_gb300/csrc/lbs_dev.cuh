@@ -90,10 +90,11 @@ struct Inst {
     // shift of the stored total populations: the rest equilibrium of the pure
     // blue phase, and its first three moments (rho, e, epsilon of Eq. 36)
     R shift[Q9];
-    R rho_s, e_s, eps_s;
+    R rho_s;
     // state (device pointers; every field is `plane` elements, populations Q planes)
-    R *fT, *fR;               // total populations minus shift, red populations
-    R *gT, *gR;               // post-collision buffers
+    R *fT, *fM;               // total populations minus shift, minority colour
+    R *gT, *gM;               // post-collision buffers
+    uint8_t *flag, *gflag;    // minority colour of a cell: 0 red, 1 blue
     R *rhoR, *rhoB, *rhoN, *jx, *jy;
     R *gx, *gy, *a, *chi;     // grad rhoN, |grad rhoN|, 1 - rhoN
     R *ux, *uy, *Fx, *Fy;
@@ -153,6 +154,11 @@ __device__ __forceinline__ void ghost_u2(const Inst<R> &I, int refl, int sx, int
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ bool eos(const Inst<R> &I, R psi, R &sigma, R &mcoef) {
+    if (I.E0 == R(0)) {  // Eq. 8 with E0 = 0: constant tension
+        sigma = I.sigma0;
+        mcoef = R(0);
+        return true;
+    }
     if (I.eos == 1) {
         sigma = I.sigma0 * (R(1) - I.E0 * psi / I.psi_inf);
         mcoef = I.sigma0 * I.E0 / I.psi_inf;

@@ -1,12 +1,15 @@
 // lbs_k2d.cuh — D2Q9 kernels of the coupled LB-FD time step (arXiv 2311.15242).
 //
-// Storage form of the populations: the total f_i = f_i^R + f_i^B is kept
-// shifted by a constant rest state s_i (the rest equilibrium of the pure blue
-// phase; for the alpha-model of App. A both pure phases share the moving
-// components of that state), and the red populations f_i^R are kept as they
-// are.  The momentum sum_i f_i e_i and every non-conserved moment are then
-// formed from small numbers, which keeps FP32 cancellation out of the
-// velocity; f_i^B = s_i + fT_i - f_i^R.
+// Storage form of the populations.  For every cell and direction the library
+// keeps fT_i = f_i - s_i, the total f_i = f_i^R + f_i^B minus a constant rest
+// state s_i (the rest equilibrium of the pure blue phase; for the alpha-model
+// of App. A both pure phases share its moving components), and fM_i, the
+// population of the cell's minority colour (a per-cell flag says which).  The
+// majority colour is s_i + fT_i - fM_i.  Momentum and every non-conserved
+// moment are formed from small numbers, and the colour that is nearly absent
+// keeps its full relative precision; both matter in FP32: the interface
+// weights |grad rho^N| and 1 - rho^N of the surfactant equations are divided
+// by a regularisation of 1e-6 where they vanish.
 //
 // One time step (t -> t+1) is the kernel sequence
 //   k_force    u, F at t                   (Eqs. 5-10)
@@ -26,23 +29,43 @@ namespace lbs {
 template <typename R>
 __device__ __forceinline__ R cs2_lattice() { return R(1) / R(3); }
 
-// sum over the red and total-shifted populations of one cell
+// both colours of one direction from (fT, fM, flag)
+template <typename R>
+__device__ __forceinline__ void split(R shift, R t, R m, int flag, R &fr, R &fb) {
+    R other = (shift + t) - m;
+    fr = flag ? other : m;
+    fb = flag ? m : other;
+}
+
+// colour densities and momentum (without the force) of one cell
 template <typename R>
 struct Mom2 {
-    R rR, drho, jx, jy;  // rho^R, rho - rho_s, momentum (without the force)
+    R rR, rB, drho, jx, jy;  // rho^R, rho^B, rho - rho_s, sum_i f_i e_i
 };
 
 template <typename R>
-__device__ __forceinline__ Mom2<R> moments9(const R *fT, const R *fR) {
-    Mom2<R> m{R(0), R(0), R(0), R(0)};
+__device__ __forceinline__ Mom2<R> moments9(const Inst<R> &I, const R *fT, const R *fM,
+                                           int flag) {
+    Mom2<R> m{R(0), R(0), R(0), R(0), R(0)};
+    R rm = R(0);
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
-        m.rR += fR[i];
+        rm += fM[i];
         m.drho += fT[i];
         m.jx += R(ex9(i)) * fT[i];
         m.jy += R(ey9(i)) * fT[i];
     }
+    // majority colour = total - minority
+    R rmaj = (I.rho_s - rm) + m.drho;
+    m.rR = flag ? rmaj : rm;
+    m.rB = flag ? rm : rmaj;
     return m;
+}
+
+// minority colour of a cell by colour fraction (0: red, 1: blue)
+template <typename R>
+__device__ __forceinline__ int minority(const Inst<R> &I, R rR, R rB) {
+    return (rR / I.rhoR0 <= rB / I.rhoB0) ? 0 : 1;
 }
 
 // colour function, Eq. 6
@@ -95,15 +118,18 @@ __global__ void k_init2(Inst<R> I, const double *phi, const double *psi, const d
     ph = ph > 1.0 ? 1.0 : (ph < -1.0 ? -1.0 : ph);
     R ux = u ? R(u[d]) : R(0), uy = u ? R(u[N + d]) : R(0);
     R mR[Q9], mB[Q9], fR[Q9], fB[Q9];
-    meq9(R(I.rhoR0 * R(0.5 * (1.0 + ph))), ux, uy, I.alphaR, mR);
-    meq9(R(I.rhoB0 * R(0.5 * (1.0 - ph))), ux, uy, I.alphaB, mB);
+    const R rR = R(I.rhoR0 * R(0.5 * (1.0 + ph))), rB = R(I.rhoB0 * R(0.5 * (1.0 - ph)));
+    meq9(rR, ux, uy, I.alphaR, mR);
+    meq9(rB, ux, uy, I.alphaB, mB);
     minv9(mR, fR);
     minv9(mB, fB);
+    const int fl = minority(I, rR, rB);
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         I.fT[i * I.plane + c] = (fR[i] + fB[i]) - I.shift[i];
-        I.fR[i * I.plane + c] = fR[i];
+        I.fM[i * I.plane + c] = fl ? fB[i] : fR[i];
     }
+    I.flag[c] = (uint8_t)fl;
     I.psi[c] = psi ? R(psi[d]) : R(0);
     I.C[c] = C ? R(C[d]) : R(0);
     I.S[c] = R(0);
@@ -113,12 +139,11 @@ __global__ void k_init2(Inst<R> I, const double *phi, const double *psi, const d
 // moments of the stored populations -> rho^R, rho^B, rho^N, momentum
 template <typename R>
 __device__ __forceinline__ void store_moments(const Inst<R> &I, long long c, const R *fT,
-                                              const R *fR) {
-    Mom2<R> m = moments9(fT, fR);
-    R rB = (I.rho_s - m.rR) + m.drho;
+                                              const R *fM, int flag) {
+    Mom2<R> m = moments9(I, fT, fM, flag);
     I.rhoR[c] = m.rR;
-    I.rhoB[c] = rB;
-    I.rhoN[c] = colour_fn(I, m.rR, rB);
+    I.rhoB[c] = m.rB;
+    I.rhoN[c] = colour_fn(I, m.rR, m.rB);
     I.jx[c] = m.jx;
     I.jy[c] = m.jy;
 }
@@ -129,42 +154,53 @@ __global__ void k_moments2(Inst<R> I) {
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= I.nx || y >= I.ny) return;
     long long c = (long long)y * I.pitch + x;
-    R fT[Q9], fR[Q9];
+    R fT[Q9], fM[Q9];
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         fT[i] = I.fT[i * I.plane + c];
-        fR[i] = I.fR[i * I.plane + c];
+        fM[i] = I.fM[i * I.plane + c];
     }
-    store_moments(I, c, fT, fR);
+    store_moments(I, c, fT, fM, I.flag[c]);
 }
 
 // ---------------------------------------------------------------------------
 // k_grad: colour gradient by the isotropic stencil (Sec. 2.1 after Eq. 9):
 // d_a X = (1/c_s^2) sum_i w_i X(x + e_i) e_ia, rho^N mirrored at walls;
-// a = |grad rho^N| and chi = 1 - rho^N (formed as 2 x_B / (x_R + x_B)).
+// a = |grad rho^N| and chi = 1 - rho^N.  Since rho^N = 2 phi_R - 1 = 1 - 2 phi_B
+// with the colour fractions phi_k = x_k / (x_R + x_B), x_k = rho^k / rho^k0,
+// the gradient is taken as 2 grad phi_R on the blue side and -2 grad phi_B on
+// the red side (the same number, formed from the colour that is small there),
+// and chi = 2 phi_B.
 // ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R frac(const Inst<R> &I, long long j, bool red) {
+    R xr = I.rhoR[j] / I.rhoR0, xb = I.rhoB[j] / I.rhoB0;
+    return (red ? xr : xb) / (xr + xb);
+}
+
 template <typename R>
 __global__ void k_grad2(Inst<R> I) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= I.nx || y >= I.ny) return;
     long long c = (long long)y * I.pitch + x;
+    const bool blue_side = I.rhoN[c] <= R(0);
     R gx = R(0), gy = R(0);
 #pragma unroll
     for (int i = 1; i < Q9; i++) {
         int refl, sx, sy;
         long long j = nb2(I, x, y, ex9(i), ey9(i), refl, sx, sy);
-        R v = I.rhoN[j];
+        R v = frac(I, j, blue_side);
         gx += w9<R>(i) * R(ex9(i)) * v;
         gy += w9<R>(i) * R(ey9(i)) * v;
     }
-    gx *= R(3);
-    gy *= R(3);
+    const R f = blue_side ? R(6) : R(-6);  // 2 / c_s^2
+    gx *= f;
+    gy *= f;
     I.gx[c] = gx;
     I.gy[c] = gy;
     I.a[c] = sqrt(gx * gx + gy * gy);
-    R xr = I.rhoR[c] / I.rhoR0, xb = I.rhoB[c] / I.rhoB0;
-    I.chi[c] = R(2) * xb / (xr + xb);
+    I.chi[c] = R(2) * frac(I, c, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -322,16 +358,16 @@ __global__ void k_collide2(Inst<R> I) {
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= I.nx || y >= I.ny) return;
     long long c = (long long)y * I.pitch + x;
-    R fT[Q9], fR[Q9];
+    R fT[Q9], fM[Q9];
+    const int fl = I.flag[c];
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         fT[i] = I.fT[i * I.plane + c];
-        fR[i] = I.fR[i * I.plane + c];
+        fM[i] = I.fM[i * I.plane + c];
     }
-    Mom2<R> mo = moments9(fT, fR);
-    const R rR = mo.rR;
-    const R dB = mo.drho - mo.rR;  // rho^B - rhoB0 (the shift carries rhoB0)
-    const R rB = I.rho_s + dB;
+    Mom2<R> mo = moments9(I, fT, fM, fl);
+    const R rR = mo.rR, rB = mo.rB;
+    const R dB = mo.drho - rR;  // rho^B - rhoB0 (the shift carries rhoB0)
     const R rho = rR + rB;
     const R ux = I.ux[c], uy = I.uy[c], Fx = I.Fx[c], Fy = I.Fy[c];
 
@@ -397,23 +433,37 @@ __global__ void k_collide2(Inst<R> I) {
     for (int j = 0; j < Q9; j++)
         dm[j] = (-Sd[j] * neq[j] + (R(1) - R(0.5) * Sd[j]) * (Cm[j] + Fh[j])) / R(mnorm9(j));
 
-    // recolouring: segregation weight f_i^eq(rho, 0)/rho; for the alpha-model
-    // its moving components are w_i * 3 p / rho with p = sum_k rho^k (c_s^k)^2
-    const R ggx = I.gx[c], ggy = I.gy[c];
-    const R gn = sqrt(ggx * ggx + ggy * ggy + I.eps_n * I.eps_n);
-    const R seg = I.beta * rR * rB / (rho * rho) * R(3) * pk / gn;
-    const R fr = rR / rho;
+    // post-collision total minus shift
+    R post[Q9];
+    R rdag = R(0);
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         R s = fT[i];
 #pragma unroll
         for (int j = 0; j < Q9; j++)
             if (m9(j, i) != 0) s += R(m9(j, i)) * dm[j];
-        // s = post-collision total minus shift
-        R segi = i == 0 ? R(0) : seg * w9<R>(i) * (R(ex9(i)) * ggx + R(ey9(i)) * ggy);
-        I.gT[i * I.plane + c] = s;
-        I.gR[i * I.plane + c] = fr * (I.shift[i] + s) + segi;
+        post[i] = s;
+        rdag += I.shift[i] + s;
     }
+    // recolouring (Eqs. 11-12) of the minority colour; the majority is the
+    // total minus it.  Segregation weight f_i^eq(rho, 0)/rho: for the
+    // alpha-model its moving components are w_i * 3 p / rho with
+    // p = sum_k rho^k (c_s^k)^2.  The split uses the post-collision total
+    // rdag = sum_i f_i^dagger (= rho up to rounding) so that the colour mass
+    // is conserved without a systematic rounding bias.
+    const R ggx = I.gx[c], ggy = I.gy[c];
+    const R gn = sqrt(ggx * ggx + ggy * ggy + I.eps_n * I.eps_n);
+    const R seg = I.beta * rR * rB / (rho * rho) * R(3) * pk / gn;
+    const R rmin = fl ? rB : rR;
+    const R fr = rmin / rdag;
+    const R sg = fl ? R(-1) : R(1);
+#pragma unroll
+    for (int i = 0; i < Q9; i++) {
+        R segi = i == 0 ? R(0) : seg * w9<R>(i) * (R(ex9(i)) * ggx + R(ey9(i)) * ggy);
+        I.gT[i * I.plane + c] = post[i];
+        I.gM[i * I.plane + c] = fr * (I.shift[i] + post[i]) + sg * segi;
+    }
+    I.gflag[c] = (uint8_t)fl;
 }
 
 // ---------------------------------------------------------------------------
@@ -427,15 +477,16 @@ __global__ void k_stream2(Inst<R> I) {
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= I.nx || y >= I.ny) return;
     long long c = (long long)y * I.pitch + x;
-    R fT[Q9], fR[Q9];
+    R fT[Q9], fR[Q9], fB[Q9];
     const R rRc = I.rhoR[c], rBc = I.rhoB[c];
+    const int flc = I.gflag[c];
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         int refl, sx, sy;
         long long j = nb2(I, x, y, -ex9(i), -ey9(i), refl, sx, sy);
         if (!refl) {
             fT[i] = I.gT[i * I.plane + j];
-            fR[i] = I.gR[i * I.plane + j];
+            split(I.shift[i], fT[i], I.gM[i * I.plane + j], int(I.gflag[j]), fR[i], fB[i]);
         } else {
             R uwx = R(0), uwy = R(0);
             int nw = 0;
@@ -453,16 +504,28 @@ __global__ void k_stream2(Inst<R> I) {
             }
             R eu = (R(ex9(i)) * uwx + R(ey9(i)) * uwy) / R(nw);
             R mw = R(2) * w9<R>(i) * eu * R(3);
-            fT[i] = I.gT[opp9(i) * I.plane + c] + mw * (rRc + rBc);
-            fR[i] = I.gR[opp9(i) * I.plane + c] + mw * rRc;
+            const int io = opp9(i);
+            fT[i] = I.gT[io * I.plane + c] + mw * (rRc + rBc);
+            const R mmin = I.gM[io * I.plane + c] + mw * (flc ? rBc : rRc);
+            split(I.shift[i], fT[i], mmin, flc, fR[i], fB[i]);
         }
     }
+    R rR = R(0), rB = R(0);
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
-        I.fT[i * I.plane + c] = fT[i];
-        I.fR[i * I.plane + c] = fR[i];
+        rR += fR[i];
+        rB += fB[i];
     }
-    store_moments(I, c, fT, fR);
+    const int fl = minority(I, rR, rB);
+    R fM[Q9];
+#pragma unroll
+    for (int i = 0; i < Q9; i++) {
+        fM[i] = fl ? fB[i] : fR[i];
+        I.fT[i * I.plane + c] = fT[i];
+        I.fM[i * I.plane + c] = fM[i];
+    }
+    I.flag[c] = (uint8_t)fl;
+    store_moments(I, c, fT, fM, fl);
 }
 
 // ---------------------------------------------------------------------------

@@ -117,7 +117,7 @@ def params_from(cfg: dict, storage: int) -> LbsParams:
     for k in ("eos", "source", "transport"):
         if k in cfg:
             setattr(p, k, int(cfg[k]))
-    p.sor_tol = float(cfg.get("sor_tol", 1e-13 if storage == LBS_F64 else 1e-6))
+    p.sor_tol = float(cfg.get("sor_tol", 1e-13 if storage == LBS_F64 else 2e-7))
     p.sor_max_iter = int(cfg.get("sor_max_iter", 64 if storage == LBS_F64 else 40))
     return p
 

@@ -95,6 +95,7 @@ def test_edge_cases_small_and_ragged():
     cases = []
     c = bubble(nx=5, ny=9)
     c["R"] = 1.5
+    c["center"] = [2.0, 4.0, 0.0]
     cases.append(c)
     c = droplet(nx=33, ny=9, R=3.0)
     c["transport"] = 0
