@@ -166,14 +166,32 @@ struct Solver : Base {
         I.omega = R(p->sor_omega);
         I.sor_tol = R(p->sor_tol);
         I.sor_max_iter = p->sor_max_iter;
-        double s[Q9];
-        rest_eq9(p->rhoB0, p->alphaB, s);
-        double rs = 0;
+        // rest states of the pure phases; their moving components agree when
+        // rhoR0 (1 - alphaR) = rhoB0 (1 - alphaB) (Eq. 42); the blue ones are used
+        double sB[Q9], sR[Q9];
+        rest_eq9(p->rhoB0, p->alphaB, sB);
+        rest_eq9(p->rhoR0, p->alphaR, sR);
+        double mov = 0;
         for (int i = 0; i < Q9; i++) {
-            I.shift[i] = R(s[i]);
-            rs += double(I.shift[i]);
+            I.shift[i] = R(sB[i]);
+            if (i) mov += double(I.shift[i]);
         }
-        I.rho_s = R(rs);
+        I.shift0[0] = R(sB[0]);
+        I.shift0[1] = R(sR[0]);
+        for (int f = 0; f < 2; f++) {
+            double tot = mov + double(I.shift0[f]);
+            I.rho_s[f] = R(tot);
+            double rk = f ? p->rhoR0 : p->rhoB0, ak = f ? p->alphaR : p->alphaB;
+            I.dsh[f] = R(tot - rk);
+            double e1 = 0, e2 = 0;
+            for (int i = 0; i < Q9; i++) {
+                double si = i ? double(I.shift[i]) : double(I.shift0[f]);
+                e1 += double(m9(1, i)) * si;
+                e2 += double(m9(2, i)) * si;
+            }
+            I.mcor1[f] = R(e1 - rk * (-3.6 * ak - 0.4));
+            I.mcor2[f] = R(e2 - rk * (5.4 * ak - 1.4));
+        }
         size_t pb = (size_t)L.plane;
         R *pops = (R *)(ws + L.pops_off);
         I.fT = pops;

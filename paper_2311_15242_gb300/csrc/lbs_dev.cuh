@@ -55,6 +55,10 @@ __host__ __device__ constexpr int mnorm9(int j) {
 // a captured graph: step counter, SOR progress, conserved total, status).
 // ---------------------------------------------------------------------------
 constexpr int KMAX_SWEEPS = 64;
+// sweeps run after the first one that meets the tolerance: the iteration
+// approaches the solution from one side, and stopping at once would leave a
+// remainder of the same sign every time step
+constexpr int SOR_EXTRA = 2;
 enum : int { ST_NOCONV = 1, ST_DIVERGED = 2, ST_TIMEOUT = 4 };
 
 struct Ctl {
@@ -65,7 +69,7 @@ struct Ctl {
     int status;             // ST_* bits, sticky until read by the host
     int sor_iters;          // sweeps used by the last solve
     unsigned int ticket;    // arrival counter of the last-block reductions
-    int pad;
+    int sor_exec;           // sweeps executed in the current solve
     // per sweep: max |d psi|, max |d C|, max |psi|, max |C| (bits of
     // non-negative doubles, compared as unsigned integers)
     unsigned long long sweep[KMAX_SWEEPS][4];
@@ -88,9 +92,15 @@ struct Inst {
     R Ds, Db, ra, rd, g[3], omega, sor_tol;
     int sor_max_iter;
     // shift of the stored total populations: the rest equilibrium of the pure
-    // blue phase, and its first three moments (rho, e, epsilon of Eq. 36)
+    // majority phase of a cell.  Its moving components are common to both
+    // phases (equal pure-phase pressures, Eq. 42): shift[1..8]; the rest
+    // component depends on the cell's flag: shift0[flag].  rho_s[flag] is the
+    // sum of the shift, dsh[flag] = rho_s[flag] - rho^k0 of the majority phase.
     R shift[Q9];
-    R rho_s;
+    R shift0[2], rho_s[2], dsh[2];
+    // e and epsilon moments (Eq. 36) of the shift minus those of the pure
+    // majority phase at rest: rounding only, unless alpha breaks Eq. 42
+    R mcor1[2], mcor2[2];
     // state (device pointers; every field is `plane` elements, populations Q planes)
     R *fT, *fM;               // total populations minus shift, minority colour
     R *gT, *gM;               // post-collision buffers

@@ -29,6 +29,12 @@ namespace lbs {
 template <typename R>
 __device__ __forceinline__ R cs2_lattice() { return R(1) / R(3); }
 
+// shift of direction i for a cell with the given flag
+template <typename R>
+__device__ __forceinline__ R shift_of(const Inst<R> &I, int i, int flag) {
+    return i == 0 ? I.shift0[flag] : I.shift[i];
+}
+
 // both colours of one direction from (fT, fM, flag)
 template <typename R>
 __device__ __forceinline__ void split(R shift, R t, R m, int flag, R &fr, R &fb) {
@@ -40,7 +46,7 @@ __device__ __forceinline__ void split(R shift, R t, R m, int flag, R &fr, R &fb)
 // colour densities and momentum (without the force) of one cell
 template <typename R>
 struct Mom2 {
-    R rR, rB, drho, jx, jy;  // rho^R, rho^B, rho - rho_s, sum_i f_i e_i
+    R rR, rB, drho, jx, jy;  // rho^R, rho^B, rho - rho_s[flag], sum_i f_i e_i
 };
 
 template <typename R>
@@ -56,7 +62,7 @@ __device__ __forceinline__ Mom2<R> moments9(const Inst<R> &I, const R *fT, const
         m.jy += R(ey9(i)) * fT[i];
     }
     // majority colour = total - minority
-    R rmaj = (I.rho_s - rm) + m.drho;
+    R rmaj = (I.rho_s[flag] - rm) + m.drho;
     m.rR = flag ? rmaj : rm;
     m.rB = flag ? rm : rmaj;
     return m;
@@ -116,18 +122,20 @@ __global__ void k_init2(Inst<R> I, const double *phi, const double *psi, const d
     long long N = (long long)I.nx * I.ny;
     double ph = phi[d];
     ph = ph > 1.0 ? 1.0 : (ph < -1.0 ? -1.0 : ph);
-    R ux = u ? R(u[d]) : R(0), uy = u ? R(u[N + d]) : R(0);
-    R mR[Q9], mB[Q9], fR[Q9], fB[Q9];
-    const R rR = R(I.rhoR0 * R(0.5 * (1.0 + ph))), rB = R(I.rhoB0 * R(0.5 * (1.0 - ph)));
-    meq9(rR, ux, uy, I.alphaR, mR);
-    meq9(rB, ux, uy, I.alphaB, mB);
-    minv9(mR, fR);
-    minv9(mB, fB);
-    const int fl = minority(I, rR, rB);
+    // built in double precision and rounded once, so that the stored
+    // deviations carry no direction-dependent rounding of the equilibrium
+    double ux = u ? u[d] : 0.0, uy = u ? u[N + d] : 0.0;
+    double mR[Q9], mB[Q9], fR[Q9], fB[Q9];
+    const double rR = double(I.rhoR0) * 0.5 * (1.0 + ph), rB = double(I.rhoB0) * 0.5 * (1.0 - ph);
+    meq9<double>(rR, ux, uy, double(I.alphaR), mR);
+    meq9<double>(rB, ux, uy, double(I.alphaB), mB);
+    minv9<double>(mR, fR);
+    minv9<double>(mB, fB);
+    const int fl = (rR / double(I.rhoR0) <= rB / double(I.rhoB0)) ? 0 : 1;
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
-        I.fT[i * I.plane + c] = (fR[i] + fB[i]) - I.shift[i];
-        I.fM[i * I.plane + c] = fl ? fB[i] : fR[i];
+        I.fT[i * I.plane + c] = R((fR[i] + fB[i]) - double(shift_of(I, i, fl)));
+        I.fM[i * I.plane + c] = R(fl ? fB[i] : fR[i]);
     }
     I.flag[c] = (uint8_t)fl;
     I.psi[c] = psi ? R(psi[d]) : R(0);
@@ -367,7 +375,9 @@ __global__ void k_collide2(Inst<R> I) {
     }
     Mom2<R> mo = moments9(I, fT, fM, fl);
     const R rR = mo.rR, rB = mo.rB;
-    const R dB = mo.drho - rR;  // rho^B - rhoB0 (the shift carries rhoB0)
+    const R rmin = fl ? rB : rR;
+    // deviation of the majority colour from its pure-phase density
+    const R devmaj = I.dsh[fl] + (mo.drho - rmin);
     const R rho = rR + rB;
     const R ux = I.ux[c], uy = I.uy[c], Fx = I.Fx[c], Fy = I.Fy[c];
 
@@ -408,8 +418,17 @@ __global__ void k_collide2(Inst<R> I) {
     const R qco = R(-1.8) * (I.alphaR * rR + I.alphaB * rB) - R(0.2) * rho;
     R neq[Q9];
     neq[0] = R(0);
-    neq[1] = mT[1] + dB * aBm + rR * aRm - R(3) * rho * u2;
-    neq[2] = mT[2] - dB * bBm - rR * bRm + R(3) * rho * u2;
+    // the shift of a flag-0 cell is the pure blue rest state, of a flag-1 cell
+    // the pure red one, whose e and epsilon moments cancel the majority term
+    if (fl == 0) {
+        neq[1] = mT[1] + devmaj * aBm + rR * aRm - R(3) * rho * u2;
+        neq[2] = mT[2] - devmaj * bBm - rR * bRm + R(3) * rho * u2;
+    } else {
+        neq[1] = mT[1] + devmaj * aRm + rB * aBm - R(3) * rho * u2;
+        neq[2] = mT[2] - devmaj * bRm - rB * bBm + R(3) * rho * u2;
+    }
+    neq[1] += I.mcor1[fl];
+    neq[2] += I.mcor2[fl];
     neq[3] = R(0);
     neq[4] = mT[4] - qco * ux;
     neq[5] = R(0);
@@ -443,7 +462,7 @@ __global__ void k_collide2(Inst<R> I) {
         for (int j = 0; j < Q9; j++)
             if (m9(j, i) != 0) s += R(m9(j, i)) * dm[j];
         post[i] = s;
-        rdag += I.shift[i] + s;
+        rdag += shift_of(I, i, fl) + s;
     }
     // recolouring (Eqs. 11-12) of the minority colour; the majority is the
     // total minus it.  Segregation weight f_i^eq(rho, 0)/rho: for the
@@ -454,14 +473,13 @@ __global__ void k_collide2(Inst<R> I) {
     const R ggx = I.gx[c], ggy = I.gy[c];
     const R gn = sqrt(ggx * ggx + ggy * ggy + I.eps_n * I.eps_n);
     const R seg = I.beta * rR * rB / (rho * rho) * R(3) * pk / gn;
-    const R rmin = fl ? rB : rR;
     const R fr = rmin / rdag;
     const R sg = fl ? R(-1) : R(1);
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         R segi = i == 0 ? R(0) : seg * w9<R>(i) * (R(ex9(i)) * ggx + R(ey9(i)) * ggy);
         I.gT[i * I.plane + c] = post[i];
-        I.gM[i * I.plane + c] = fr * (I.shift[i] + post[i]) + sg * segi;
+        I.gM[i * I.plane + c] = fr * (shift_of(I, i, fl) + post[i]) + sg * segi;
     }
     I.gflag[c] = (uint8_t)fl;
 }
@@ -485,8 +503,10 @@ __global__ void k_stream2(Inst<R> I) {
         int refl, sx, sy;
         long long j = nb2(I, x, y, -ex9(i), -ey9(i), refl, sx, sy);
         if (!refl) {
+            // (i = 0 stays in its own cell, j = c: shift of the cell's old flag)
             fT[i] = I.gT[i * I.plane + j];
-            split(I.shift[i], fT[i], I.gM[i * I.plane + j], int(I.gflag[j]), fR[i], fB[i]);
+            const int fj = I.gflag[j];
+            split(shift_of(I, i, fj), fT[i], I.gM[i * I.plane + j], fj, fR[i], fB[i]);
         } else {
             R uwx = R(0), uwy = R(0);
             int nw = 0;
@@ -507,7 +527,7 @@ __global__ void k_stream2(Inst<R> I) {
             const int io = opp9(i);
             fT[i] = I.gT[io * I.plane + c] + mw * (rRc + rBc);
             const R mmin = I.gM[io * I.plane + c] + mw * (flc ? rBc : rRc);
-            split(I.shift[i], fT[i], mmin, flc, fR[i], fB[i]);
+            split(I.shift[i], fT[i], mmin, flc, fR[i], fB[i]);  // i != 0 here
         }
     }
     R rR = R(0), rB = R(0);
@@ -517,6 +537,9 @@ __global__ void k_stream2(Inst<R> I) {
         rB += fB[i];
     }
     const int fl = minority(I, rR, rB);
+    // a change of flag re-expresses the rest population against the new
+    // rest shift (the moving shifts are common to both flags)
+    if (fl != flc) fT[0] = (I.shift0[flc] - I.shift0[fl]) + fT[0];
     R fM[Q9];
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
@@ -569,7 +592,13 @@ __device__ __forceinline__ void block_max4(double v[4], unsigned long long *dst)
 
 template <typename R, int BS>
 __global__ void k_sor2(Inst<R> I, int colour, int k) {
-    if (k > 0 && sweep_converged<R>(I.ctl, k - 1, double(I.sor_tol))) return;
+    // skip once a sweep at least SOR_EXTRA + 1 sweeps back met the tolerance
+    // (skipped sweeps leave zero slots, which read as converged)
+    const int kc = k - 1 - SOR_EXTRA;
+    if (kc >= 0 && sweep_converged<R>(I.ctl, kc, double(I.sor_tol))) return;
+    if (colour == 1 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 &&
+        threadIdx.y == 0)
+        atomicAdd(&I.ctl->sor_exec, 1);
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     double v[4] = {0, 0, 0, 0};
@@ -631,8 +660,26 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double *out /* K, thre
         }
 }
 
-// returns true in thread 0 of the last block to finish; its partials are then
-// all visible
+// sum of nblocks partials (stride apart, offset q) by the whole block, in a
+// fixed order: thread t adds partials t, t + BS, ...; then a fixed tree
+template <int BS>
+__device__ __forceinline__ double block_final_sum(const double *part, int stride, int q,
+                                                  int nblocks) {
+    int t = threadIdx.x + threadIdx.y * blockDim.x;
+    double v[1] = {0};
+    for (int k = t; k < nblocks; k += BS) v[0] += part[(long long)k * stride + q];
+    double out[1];
+    block_sum<BS, 1>(v, out);
+    __shared__ double res;
+    if (t == 0) res = out[0];
+    __syncthreads();
+    double r = res;
+    __syncthreads();
+    return r;
+}
+
+// returns true in every thread of the last block to finish; the partials of
+// all blocks are then visible
 __device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned int nblocks) {
     __shared__ bool last;
     int t = threadIdx.x + threadIdx.y * blockDim.x;
@@ -663,10 +710,9 @@ __global__ void k_surf2(Inst<R> I, int mode, int nblocks) {
     int b = blockIdx.x + blockIdx.y * gridDim.x;
     block_sum<BS, 1>(v, I.part + b);
     if (!last_block(&I.ctl->ticket, nblocks)) return;
+    const double tot = block_final_sum<BS>(I.part, 1, 0, nblocks);
     int t = threadIdx.x + threadIdx.y * blockDim.x;
     if (t != 0) return;
-    double tot = 0;
-    for (int k = 0; k < nblocks; k++) tot += I.part[k];
     Ctl *ctl = I.ctl;
     ctl->ticket = 0;
     if (mode == 0) {
@@ -678,16 +724,15 @@ __global__ void k_surf2(Inst<R> I, int mode, int nblocks) {
     ctl->pre = tot;
     ctl->scale = tot > 0 ? ctl->M0 / tot : 1.0;
     if (!isfinite(tot)) ctl->status |= ST_DIVERGED;
-    int used = I.sor_max_iter;
     bool conv = false;
     for (int k = 0; k < I.sor_max_iter; k++)
         if (sweep_converged<R>(ctl, k, double(I.sor_tol))) {
-            used = k + 1;
             conv = true;
             break;
         }
     if (!conv) ctl->status |= ST_NOCONV;
-    ctl->sor_iters = used;
+    ctl->sor_iters = ctl->sor_exec;
+    ctl->sor_exec = 0;
     for (int k = 0; k < KMAX_SWEEPS; k++)
         for (int q = 0; q < 4; q++) ctl->sweep[k][q] = 0ull;
     ctl->step += 1;
@@ -699,9 +744,12 @@ __global__ void k_scale2(Inst<R> I) {
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= I.nx || y >= I.ny) return;
     long long c = (long long)y * I.pitch + x;
-    R s = R(I.ctl->scale);
-    I.psi[c] *= s;
-    I.C[c] *= s;
+    // the factor is 1 + O(1e-6): multiplying by it rounded to R would apply a
+    // quantised correction with the same bias every step; x + x d with
+    // d = s - 1 formed in double and one fused rounding is unbiased
+    const R d = R(I.ctl->scale - 1.0);
+    I.psi[c] = fma(I.psi[c], d, I.psi[c]);
+    I.C[c] = fma(I.C[c], d, I.C[c]);
 }
 
 // step counter for runs without surfactant transport
@@ -775,16 +823,16 @@ __global__ void k_diag2(Inst<R> I, int nblocks) {
         I.part[(long long)b * (NDIAG + 3) + NDIAG + 2] = mm[2];
     }
     if (!last_block(&I.ctl->ticket, nblocks)) return;
-    if (t != 0) return;
-    double tot[NDIAG + 3];
-    for (int q = 0; q < NDIAG; q++) tot[q] = 0;
-    for (int q = NDIAG; q < NDIAG + 3; q++) tot[q] = -1e300;
-    for (int k = 0; k < nblocks; k++) {
-        for (int q = 0; q < NDIAG; q++) tot[q] += I.part[(long long)k * (NDIAG + 3) + q];
-        for (int q = NDIAG; q < NDIAG + 3; q++)
-            tot[q] = fmax(tot[q], I.part[(long long)k * (NDIAG + 3) + q]);
+    for (int q = 0; q < NDIAG; q++) {
+        double tq = block_final_sum<BS>(I.part, NDIAG + 3, q, nblocks);
+        if (t == 0) I.ctl->diag[q] = tq;
     }
-    for (int q = 0; q < NDIAG + 3; q++) I.ctl->diag[q] = tot[q];
+    if (t != 0) return;
+    for (int q = NDIAG; q < NDIAG + 3; q++) {
+        double m = -1e300;
+        for (int k = 0; k < nblocks; k++) m = fmax(m, I.part[(long long)k * (NDIAG + 3) + q]);
+        I.ctl->diag[q] = m;
+    }
     I.ctl->ticket = 0;
 }
 
