@@ -18,6 +18,8 @@ using namespace lbs;
 namespace {
 
 constexpr int BX = 32, BY = 8, BS = BX * BY;
+// blocked SOR: tile, sweeps per launch, threads
+constexpr int STX = 64, STY = 32, SK = 3, SBS = 256;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -94,7 +96,7 @@ Layout layout_of(const lbs_params *p) {
     L.pops_off = 0;
     size_t pops = 4 * (size_t)Q9 * pb;
     L.scal_off = pops;
-    size_t scal = 19 * pb;
+    size_t scal = 21 * pb;
     L.flag_off = align_up(L.scal_off + scal, 256);
     L.ctl_off = align_up(L.flag_off + 2 * (size_t)L.plane, 256);
     L.part_off = align_up(L.ctl_off + sizeof(Ctl), 256);
@@ -114,7 +116,7 @@ struct Solver : Base {
     double *stage;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
-    dim3 grid, block;
+    dim3 grid, block, sor_grid;
     bool prof = false;
     cudaEvent_t ev[LBS_K_NGROUPS + 1] = {};
     bool ran[LBS_K_NGROUPS] = {};
@@ -201,15 +203,19 @@ struct Solver : Base {
         I.flag = (uint8_t *)(ws + L.flag_off);
         I.gflag = I.flag + L.plane;
         R *sc = (R *)(ws + L.scal_off);
-        R **fields[] = {&I.rhoR, &I.rhoB, &I.rhoN, &I.jx,  &I.jy, &I.gx,  &I.gy,
-                        &I.a,    &I.chi,  &I.ux,   &I.uy,  &I.Fx, &I.Fy,  &I.psi,
-                        &I.C,    &I.S,    &I.B,    &I.rpsi, &I.rC};
-        for (int k = 0; k < 19; k++) *fields[k] = sc + k * pb;
+        R **fields[] = {&I.rhoR, &I.rhoB, &I.rhoN, &I.jx,  &I.jy,  &I.gx,  &I.gy,
+                        &I.a,    &I.chi,  &I.ux,   &I.uy,  &I.Fx,  &I.Fy,  &I.psi,
+                        &I.C,    &I.S,    &I.B,    &I.rpsi, &I.rC, &I.psi2, &I.C2};
+        for (int k = 0; k < 21; k++) *fields[k] = sc + k * pb;
         I.ctl = (Ctl *)(ws + L.ctl_off);
         I.part = (double *)(ws + L.part_off);
         stage = (double *)(ws + L.stage_off);
         block = dim3(BX, BY, 1);
         grid = dim3((p->nx + BX - 1) / BX, (p->ny + BY - 1) / BY, 1);
+        sor_grid = dim3((p->nx + STX - 1) / STX, (p->ny + STY - 1) / STY, 1);
+        using T = SorTile<R, STX, STY, SK, SBS>;
+        cudaFuncSetAttribute(k_sor_tb2<R, STX, STY, SK, SBS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes());
     }
 
     ~Solver() {
@@ -256,15 +262,14 @@ struct Solver : Base {
         ran[LBS_K_GRAD] = true;
         mark(s, LBS_K_SOR);
         if (I.transport) {
-            for (int k = 0; k < I.sor_max_iter; k++) {
-                k_sor2<R, BS><<<grid, block, 0, s>>>(I, 0, k);
-                k_sor2<R, BS><<<grid, block, 0, s>>>(I, 1, k);
-            }
+            using T = SorTile<R, STX, STY, SK, SBS>;
+            for (int r = 0; r < sor_rounds(); r++)
+                k_sor_tb2<R, STX, STY, SK, SBS><<<sor_grid, SBS, T::smem_bytes(), s>>>(I, r);
             ran[LBS_K_SOR] = true;
         }
         mark(s, LBS_K_SURF);
         if (I.transport) {
-            k_surf2<R, BS><<<grid, block, 0, s>>>(I, 1, L.nblocks);
+            k_surf2<R, BS><<<grid, block, 0, s>>>(I, 1, L.nblocks, SK);
             k_scale2<R><<<grid, block, 0, s>>>(I);
         } else {
             k_tick<R><<<1, 32, 0, s>>>(I);
@@ -273,8 +278,10 @@ struct Solver : Base {
         mark(s, LBS_K_NGROUPS);
     }
 
+    int sor_rounds() const { return (I.sor_max_iter + SK - 1) / SK; }
+
     int kernel_count() const override {
-        return I.transport ? 7 + 2 * I.sor_max_iter : 4;
+        return I.transport ? 7 + sor_rounds() : 4;
     }
 
     int profile(int on) override {
@@ -320,7 +327,7 @@ struct Solver : Base {
                                           u ? du : nullptr);
         k_moments2<R><<<grid, block, 0, s>>>(I);
         k_grad2<R><<<grid, block, 0, s>>>(I);
-        k_surf2<R, BS><<<grid, block, 0, s>>>(I, 0, L.nblocks);
+        k_surf2<R, BS><<<grid, block, 0, s>>>(I, 0, L.nblocks, SK);
         int r = launch_check();
         if (r) return r;
         CK(cudaStreamSynchronize(s));

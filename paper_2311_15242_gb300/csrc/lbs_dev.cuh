@@ -69,7 +69,9 @@ struct Ctl {
     int status;             // ST_* bits, sticky until read by the host
     int sor_iters;          // sweeps used by the last solve
     unsigned int ticket;    // arrival counter of the last-block reductions
-    int sor_exec;           // sweeps executed in the current solve
+    int sor_exec;           // sweeps (rounds) executed in the current solve
+    int sor_iters_parity;   // rounds of the last solve were odd: result in psi2, C2
+    int pad2;
     // per sweep: max |d psi|, max |d C|, max |psi|, max |C| (bits of
     // non-negative doubles, compared as unsigned integers)
     unsigned long long sweep[KMAX_SWEEPS][4];
@@ -109,6 +111,7 @@ struct Inst {
     R *gx, *gy, *a, *chi;     // grad rhoN, |grad rhoN|, 1 - rhoN
     R *ux, *uy, *Fx, *Fy;
     R *psi, *C, *S, *B, *rpsi, *rC;
+    R *psi2, *C2;             // second buffers of the blocked SOR rounds
     Ctl *ctl;
     double *part;             // per-block partial sums of reductions
 };

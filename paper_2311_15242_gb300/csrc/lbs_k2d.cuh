@@ -552,9 +552,8 @@ __global__ void k_stream2(Inst<R> I) {
 }
 
 // ---------------------------------------------------------------------------
-// k_sor: one half-sweep of red-black SOR (Sec. 2.2: relaxation factor 1.2) for
-// (w - h L_w) x = rhs on psi (w = a + eps_w, h = Ds/2) and C (w = chi + eps_w,
-// h = Db/2).  Sweep k returns at once if sweep k-1 already met the tolerance.
+// SOR (Sec. 2.2: relaxation factor 1.2) for (w - h L_w) x = rhs on psi
+// (w = a + eps_w, h = Ds/2) and C (w = chi + eps_w, h = Db/2).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void atomic_max_pos(unsigned long long *p, double v) {
     atomicMax(p, (unsigned long long)__double_as_longlong(v));
@@ -569,70 +568,167 @@ __device__ __forceinline__ bool sweep_converged(const Ctl *ctl, int k, double to
     return dp <= tol * xp && dc <= tol * xc;
 }
 
-template <typename R, int BS>
-__device__ __forceinline__ void block_max4(double v[4], unsigned long long *dst) {
+// ---------------------------------------------------------------------------
+// k_sor_tb2: K red-black SOR sweeps per launch with temporal blocking.  A block
+// loads its TX x TY tile plus a halo of H = 2K cells into shared memory and
+// sweeps there; a red or black half-sweep spreads the error of the stale
+// region border by one cell, so after K sweeps the tile interior holds exactly
+// the values global red-black SOR would have.  psi and C are read from one
+// global buffer and the interior is written to the other (rounds alternate),
+// so no block reads values written by the same round.  The updates of a
+// half-sweep are staged in registers and written after a barrier, which keeps
+// same-colour neighbours across an odd periodic seam deterministic.
+// Round r skips when round r-1 met the tolerance on its last sweep.
+// ---------------------------------------------------------------------------
+template <typename R, int TX, int TY, int K, int BS>
+struct SorTile {
+    static constexpr int H = 2 * K, RX = TX + 2 * H, RY = TY + 2 * H, NR = RX * RY;
+    static constexpr int PER = (NR + BS - 1) / BS;
+    static constexpr size_t smem_bytes() { return (size_t)NR * (6 * sizeof(R) + 1); }
+};
+
+template <typename R, int TX, int TY, int K, int BS>
+__global__ void __launch_bounds__(BS) k_sor_tb2(Inst<R> I, int round) {
+    using T = SorTile<R, TX, TY, K, BS>;
+    constexpr int RX = T::RX, RY = T::RY, NR = T::NR, H = T::H, PER = T::PER;
+    if (round > 0 && sweep_converged<R>(I.ctl, round - 1, double(I.sor_tol))) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sp = (R *)smem_raw, *sc = sp + NR, *wp = sc + NR, *wc = wp + NR, *bp = wc + NR,
+      *bc = bp + NR;
+    uint8_t *fl = (uint8_t *)(bc + NR);
+    const int tid = threadIdx.x;
+    if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0) atomicAdd(&I.ctl->sor_exec, 1);
+    const int x0 = blockIdx.x * TX - H, y0 = blockIdx.y * TY - H;
+    const R *pin = (round & 1) ? I.psi2 : I.psi;
+    const R *cin = (round & 1) ? I.C2 : I.C;
+    R *pout = (round & 1) ? I.psi : I.psi2;
+    R *cout = (round & 1) ? I.C : I.C2;
+    // flags: bit0 in the domain, bit1 colour, bits 2-5 faces -x,+x,-y,+y usable,
+    // bit6 tile interior owned by this block
+    for (int k = 0; k < PER; k++) {
+        int q = tid + k * BS;
+        if (q >= NR) break;
+        int rx = q % RX, ry = q / RX;
+        int gx = x0 + rx, gy = y0 + ry;
+        int refl = 0, sx, sy;
+        int X = map_axis(gx, I.nx, I.wall[0], 1, refl, sx);
+        int Y = map_axis(gy, I.ny, I.wall[1], 2, refl, sy);
+        uint8_t f = 0;
+        if (!refl) {
+            long long c = (long long)Y * I.pitch + X;
+            f = 1 | (((X + Y) & 1) << 1);
+            sp[q] = pin[c];
+            sc[q] = cin[c];
+            wp[q] = I.a[c] + I.eps_w;
+            wc[q] = I.chi[c] + I.eps_w;
+            bp[q] = I.rpsi[c];
+            bc[q] = I.rC[c];
+            if (rx >= H && rx < H + TX && ry >= H && ry < H + TY && gx >= 0 && gx < I.nx &&
+                gy >= 0 && gy < I.ny)
+                f |= 64;
+        }
+        fl[q] = f;
+    }
+    __syncthreads();
+    // usable faces (neighbour inside the region and in the domain)
+    for (int k = 0; k < PER; k++) {
+        int q = tid + k * BS;
+        if (q >= NR) break;
+        if (!(fl[q] & 1)) continue;
+        int rx = q % RX, ry = q / RX;
+        uint8_t f = fl[q];
+        if (rx > 0 && (fl[q - 1] & 1)) f |= 4;
+        if (rx < RX - 1 && (fl[q + 1] & 1)) f |= 8;
+        if (ry > 0 && (fl[q - RX] & 1)) f |= 16;
+        if (ry < RY - 1 && (fl[q + RX] & 1)) f |= 32;
+        fl[q] = f;
+    }
+    __syncthreads();
+    // region-border cells are never updated (a neighbour is missing); walls
+    // are the faces whose neighbour is outside the domain: they carry no flux
+    const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
+    double v[4] = {0, 0, 0, 0};
+    for (int s = 0; s < K; s++) {
+        for (int colour = 0; colour < 2; colour++) {
+            R np[PER], nc[PER];
+#pragma unroll
+            for (int k = 0; k < PER; k++) {
+                int q = tid + k * BS;
+                np[k] = R(0);
+                nc[k] = R(0);
+                if (q >= NR) continue;
+                uint8_t f = fl[q];
+                int rx = q % RX, ry = q / RX;
+                if (!(f & 1) || ((f >> 1) & 1) != colour || rx == 0 || rx == RX - 1 || ry == 0 ||
+                    ry == RY - 1)
+                    continue;
+                const R wpc = wp[q], wcc = wc[q];
+                R dgp = wpc, dgc = wcc, op = R(0), oc = R(0);
+                const int nbq[4] = {q - 1, q + 1, q - RX, q + RX};
+#pragma unroll
+                for (int d = 0; d < 4; d++) {
+                    if (!(f & (4 << d))) continue;
+                    int j = nbq[d];
+                    R fp = hp * R(0.5) * (wpc + wp[j]);
+                    R fc = hc * R(0.5) * (wcc + wc[j]);
+                    dgp += fp;
+                    dgc += fc;
+                    op += fp * sp[j];
+                    oc += fc * sc[j];
+                }
+                R p0 = sp[q], c0 = sc[q];
+                R dp = I.omega * ((bp[q] + op) / dgp - p0);
+                R dc = I.omega * ((bc[q] + oc) / dgc - c0);
+                np[k] = p0 + dp;
+                nc[k] = c0 + dc;
+                if (s == K - 1 && (f & 64)) {
+                    v[0] = fmax(v[0], fabs(double(dp)));
+                    v[1] = fmax(v[1], fabs(double(dc)));
+                    v[2] = fmax(v[2], fabs(double(np[k])));
+                    v[3] = fmax(v[3], fabs(double(nc[k])));
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < PER; k++) {
+                int q = tid + k * BS;
+                if (q >= NR) continue;
+                uint8_t f = fl[q];
+                int rx = q % RX, ry = q / RX;
+                if (!(f & 1) || ((f >> 1) & 1) != colour || rx == 0 || rx == RX - 1 || ry == 0 ||
+                    ry == RY - 1)
+                    continue;
+                sp[q] = np[k];
+                sc[q] = nc[k];
+            }
+            __syncthreads();
+        }
+    }
+    // interior cells back to the other buffer
+    for (int k = 0; k < PER; k++) {
+        int q = tid + k * BS;
+        if (q >= NR) break;
+        if (!(fl[q] & 64)) continue;
+        int rx = q % RX, ry = q / RX;
+        long long c = (long long)(y0 + ry) * I.pitch + (x0 + rx);
+        pout[c] = sp[q];
+        cout[c] = sc[q];
+    }
+    // block maxima of the last sweep -> round slot
     __shared__ double sh[4][BS / 32];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < 4; q++)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
-    }
-    int t = threadIdx.x + threadIdx.y * blockDim.x;
-    if ((t & 31) == 0)
-        for (int q = 0; q < 4; q++) sh[q][t >> 5] = v[q];
+    if ((tid & 31) == 0)
+        for (int q = 0; q < 4; q++) sh[q][tid >> 5] = v[q];
     __syncthreads();
-    if (t == 0) {
+    if (tid == 0)
         for (int q = 0; q < 4; q++) {
             double m = 0;
             for (int w = 0; w < BS / 32; w++) m = fmax(m, sh[q][w]);
-            atomic_max_pos(&dst[q], m);
+            atomic_max_pos(&I.ctl->sweep[round][q], m);
         }
-    }
-}
-
-template <typename R, int BS>
-__global__ void k_sor2(Inst<R> I, int colour, int k) {
-    // skip once a sweep at least SOR_EXTRA + 1 sweeps back met the tolerance
-    // (skipped sweeps leave zero slots, which read as converged)
-    const int kc = k - 1 - SOR_EXTRA;
-    if (kc >= 0 && sweep_converged<R>(I.ctl, kc, double(I.sor_tol))) return;
-    if (colour == 1 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 &&
-        threadIdx.y == 0)
-        atomicAdd(&I.ctl->sor_exec, 1);
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
-    double v[4] = {0, 0, 0, 0};
-    if (x < I.nx && y < I.ny && ((x + y) & 1) == colour) {
-        long long c = (long long)y * I.pitch + x;
-        const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
-        R wp = I.a[c] + I.eps_w, wc = I.chi[c] + I.eps_w;
-        R dgp = wp, dgc = wc, op = R(0), oc = R(0);
-#pragma unroll
-        for (int f = 0; f < 4; f++) {
-            int dx = f == 0 ? -1 : (f == 1 ? 1 : 0);
-            int dy = f == 2 ? -1 : (f == 3 ? 1 : 0);
-            int refl, sx, sy;
-            long long j = nb2(I, x, y, dx, dy, refl, sx, sy);
-            if (refl) continue;
-            R fp = hp * R(0.5) * (wp + (I.a[j] + I.eps_w));
-            R fc = hc * R(0.5) * (wc + (I.chi[j] + I.eps_w));
-            dgp += fp;
-            dgc += fc;
-            op += fp * I.psi[j];
-            oc += fc * I.C[j];
-        }
-        R p0 = I.psi[c], c0 = I.C[c];
-        R dp = I.omega * ((I.rpsi[c] + op) / dgp - p0);
-        R dc = I.omega * ((I.rC[c] + oc) / dgc - c0);
-        R p1 = p0 + dp, c1 = c0 + dc;
-        I.psi[c] = p1;
-        I.C[c] = c1;
-        v[0] = fabs(double(dp));
-        v[1] = fabs(double(dc));
-        v[2] = fabs(double(p1));
-        v[3] = fabs(double(c1));
-    }
-    block_max4<R, BS>(v, I.ctl->sweep[k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -698,14 +794,16 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned int nb
 // mode 1: end of a step: rescale factor M0/total (Sec. 2.2), SOR bookkeeping,
 //         step counter, divergence check.
 template <typename R, int BS>
-__global__ void k_surf2(Inst<R> I, int mode, int nblocks) {
+__global__ void k_surf2(Inst<R> I, int mode, int nblocks, int sweeps_per_round) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
+    // after an odd number of blocked SOR rounds the solution is in psi2, C2
+    const bool alt = mode == 1 && (I.ctl->sor_exec & 1);
     double v[1] = {0};
     if (x < I.nx && y < I.ny) {
         long long c = (long long)y * I.pitch + x;
-        v[0] = double(I.a[c] + I.eps_w) * double(I.psi[c]) +
-               double(I.chi[c] + I.eps_w) * double(I.C[c]);
+        v[0] = double(I.a[c] + I.eps_w) * double(alt ? I.psi2[c] : I.psi[c]) +
+               double(I.chi[c] + I.eps_w) * double(alt ? I.C2[c] : I.C[c]);
     }
     int b = blockIdx.x + blockIdx.y * gridDim.x;
     block_sum<BS, 1>(v, I.part + b);
@@ -725,13 +823,15 @@ __global__ void k_surf2(Inst<R> I, int mode, int nblocks) {
     ctl->scale = tot > 0 ? ctl->M0 / tot : 1.0;
     if (!isfinite(tot)) ctl->status |= ST_DIVERGED;
     bool conv = false;
-    for (int k = 0; k < I.sor_max_iter; k++)
+    const int rounds = (I.sor_max_iter + sweeps_per_round - 1) / sweeps_per_round;
+    for (int k = 0; k < rounds; k++)
         if (sweep_converged<R>(ctl, k, double(I.sor_tol))) {
             conv = true;
             break;
         }
     if (!conv) ctl->status |= ST_NOCONV;
-    ctl->sor_iters = ctl->sor_exec;
+    ctl->sor_iters = ctl->sor_exec * sweeps_per_round;
+    ctl->sor_iters_parity = ctl->sor_exec & 1;
     ctl->sor_exec = 0;
     for (int k = 0; k < KMAX_SWEEPS; k++)
         for (int q = 0; q < 4; q++) ctl->sweep[k][q] = 0ull;
@@ -748,8 +848,13 @@ __global__ void k_scale2(Inst<R> I) {
     // quantised correction with the same bias every step; x + x d with
     // d = s - 1 formed in double and one fused rounding is unbiased
     const R d = R(I.ctl->scale - 1.0);
-    I.psi[c] = fma(I.psi[c], d, I.psi[c]);
-    I.C[c] = fma(I.C[c], d, I.C[c]);
+    // the blocked SOR leaves its result in the second buffer after an odd
+    // number of rounds
+    const bool alt = I.ctl->sor_iters_parity != 0;
+    const R p = alt ? I.psi2[c] : I.psi[c];
+    const R q = alt ? I.C2[c] : I.C[c];
+    I.psi[c] = fma(p, d, p);
+    I.C[c] = fma(q, d, q);
 }
 
 // step counter for runs without surfactant transport
