@@ -176,6 +176,9 @@ def main():
     ap.add_argument("--impl", default="lbs", choices=["lbs", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="individual kernel launches instead of one graph per step "
+                         "(for kernel profilers)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -199,6 +202,8 @@ def main():
     s = Solver(cfg, storage=args.storage)
     s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
     s.profile(True)
+    if args.eager:
+        s.set_graph(False)
     stream = s.stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 

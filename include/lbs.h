@@ -145,6 +145,15 @@ int lbs_sync(lbs_ctx *c);
 int lbs_get_fields(lbs_ctx *c, double *rho, double *u, double *phi,
                    double *psi, double *C);
 
+/* Intermediate fields of the current state, for stage-by-stage checks
+ * (any may be NULL; vector fields 3*N): the colour gradient g = grad rho^N
+ * (isotropic stencil, Sec. 2.1), a = |grad rho^N|, the total force F of
+ * Eq. 9 plus buoyancy, the velocity u of Eq. 10, and the explicit terms
+ * S = -div(psi a u) + a j, B = -div(C (1 - rho^N) u) - a j of Eqs. 23-24.
+ * Leaves the state unchanged.  Synchronises. */
+int lbs_get_macro(lbs_ctx *c, double *g, double *a, double *F, double *u,
+                  double *S, double *B);
+
 /* Fill *d with the diagnostics of the current state.  Synchronises. */
 int lbs_diagnostics(lbs_ctx *c, lbs_diag *d);
 
@@ -170,6 +179,13 @@ int lbs_profile(lbs_ctx *c, int enable);
  * milliseconds of each kernel group (ms[LBS_K_NGROUPS]); requires
  * lbs_profile(c, 1) before the steps.  Groups that did not run read 0. */
 int lbs_kernel_times(lbs_ctx *c, double *ms, int n);
+
+/* Queue each step as one CUDA graph (enable = 1, the default; the SOR
+ * iteration is a conditional WHILE node that stops on convergence) or as
+ * individual kernel launches with a host-side bound on the SOR rounds
+ * (enable = 0, for kernel profilers that cannot trace conditional graphs).
+ * Both forms compute the same numbers. */
+int lbs_set_graph(lbs_ctx *c, int enable);
 
 /* Number of kernel launches one step queues (graph kernel nodes). */
 int lbs_step_kernel_count(const lbs_ctx *c);

@@ -43,6 +43,8 @@ struct Base {
     virtual int profile(int on) = 0;
     virtual int kernel_times(double *ms, int n) = 0;
     virtual int kernel_count() const = 0;
+    virtual int set_graph(int on) = 0;
+    virtual int macro(double *, double *, double *, double *, double *, double *) = 0;
 };
 
 }  // namespace
@@ -103,7 +105,7 @@ Layout layout_of(const lbs_params *p) {
     L.nblocks = ((p->nx + BX - 1) / BX) * ((p->ny + BY - 1) / BY) * p->nz;
     L.stage_off = align_up(L.part_off + (size_t)L.nblocks * (NDIAG + 3) * sizeof(double), 256);
     size_t N = (size_t)p->nx * p->ny * p->nz;
-    L.total = align_up(L.stage_off + 7 * N * sizeof(double), 256);
+    L.total = align_up(L.stage_off + 12 * N * sizeof(double), 256);
     return L;
 }
 
@@ -116,7 +118,8 @@ struct Solver : Base {
     double *stage;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
-    dim3 grid, block, sor_grid;
+    dim3 grid, block, sor_grid, surf_grid;
+    int surf_blocks = 0;
     bool prof = false;
     cudaEvent_t ev[LBS_K_NGROUPS + 1] = {};
     bool ran[LBS_K_NGROUPS] = {};
@@ -213,6 +216,8 @@ struct Solver : Base {
         block = dim3(BX, BY, 1);
         grid = dim3((p->nx + BX - 1) / BX, (p->ny + BY - 1) / BY, 1);
         sor_grid = dim3((p->nx + STX - 1) / STX, (p->ny + STY - 1) / STY, 1);
+        surf_grid = dim3((p->nx + BX - 1) / BX, (p->ny + BY * SURF_STRIP - 1) / (BY * SURF_STRIP), 1);
+        surf_blocks = (int)(surf_grid.x * surf_grid.y);
         using T = SorTile<R, STX, STY, SK, SBS>;
         cudaFuncSetAttribute(k_sor_tb2<R, STX, STY, SK, SBS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes());
@@ -227,8 +232,14 @@ struct Solver : Base {
 
     // (recorded as an event node when captured into the step graph)
     void mark(cudaStream_t s, int g) {
-        if (prof) cudaEventRecordWithFlags(ev[g], s, cudaEventRecordExternal);
+        if (!prof) return;
+        if (capturing)
+            cudaEventRecordWithFlags(ev[g], s, cudaEventRecordExternal);
+        else
+            cudaEventRecord(ev[g], s);
     }
+    bool capturing = false;
+    bool use_graph = true;
 
     int launch_check() {
         cudaError_t e = cudaGetLastError();
@@ -239,9 +250,30 @@ struct Solver : Base {
         return LBS_OK;
     }
 
-    // the launches of one time step, in order (also captured into the graph);
-    // with profiling on, an event is recorded at every group boundary
-    void enqueue_step(cudaStream_t s) {
+    // the launches of one time step, in order, captured into the step graph;
+    // with profiling on, an event is recorded at every group boundary.  The
+    // SOR rounds run in a WHILE conditional node whose body is one blocked
+    // round; the round's last block ends the loop on convergence.
+    int capture_step(cudaStream_t s, cudaGraph_t g) {
+        CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal));
+        capturing = true;
+        int r = enqueue_step(s);
+        capturing = false;
+        cudaGraph_t out = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &out);
+        if (r) return r;
+        if (e != cudaSuccess) {
+            set_err(ctx, "graph capture failed: %s", cudaGetErrorString(e));
+            return LBS_ECUDA;
+        }
+        return LBS_OK;
+    }
+
+    // launches of one step; inside a capture the SOR loop becomes the WHILE
+    // node, outside it a host loop of sor_rounds() launches that return at
+    // once after the round that converged
+    int enqueue_step(cudaStream_t s) {
         for (bool &r : ran) r = false;
         mark(s, LBS_K_FORCE);
         k_force2<R><<<grid, block, 0, s>>>(I);
@@ -261,28 +293,68 @@ struct Solver : Base {
         k_grad2<R><<<grid, block, 0, s>>>(I);
         ran[LBS_K_GRAD] = true;
         mark(s, LBS_K_SOR);
-        if (I.transport) {
+        if (I.transport && !capturing) {
             using T = SorTile<R, STX, STY, SK, SBS>;
             for (int r = 0; r < sor_rounds(); r++)
-                k_sor_tb2<R, STX, STY, SK, SBS><<<sor_grid, SBS, T::smem_bytes(), s>>>(I, r);
+                k_sor_tb2<R, STX, STY, SK, SBS><<<sor_grid, SBS, T::smem_bytes(), s>>>(
+                    I, cudaGraphConditionalHandle(0), sor_rounds(), r);
+            ran[LBS_K_SOR] = true;
+        } else if (I.transport) {
+            cudaStreamCaptureStatus st;
+            cudaGraph_t cg;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t nd = 0;
+            CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, nullptr, &nd));
+            cudaGraphConditionalHandle h;
+            CK(cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t cnode;
+            CK(cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            using T = SorTile<R, STX, STY, SK, SBS>;
+            int maxr = sor_rounds(), eager = -1;
+            void *args[] = {(void *)&I, (void *)&h, (void *)&maxr, (void *)&eager};
+            cudaKernelNodeParams kp = {};
+            kp.func = (void *)k_sor_tb2<R, STX, STY, SK, SBS>;
+            kp.gridDim = sor_grid;
+            kp.blockDim = dim3(SBS, 1, 1);
+            kp.sharedMemBytes = (unsigned)T::smem_bytes();
+            kp.kernelParams = args;
+            cudaGraphNode_t kn;
+            CK(cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp));
+            CK(cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1,
+                                                   cudaStreamSetCaptureDependencies));
             ran[LBS_K_SOR] = true;
         }
         mark(s, LBS_K_SURF);
         if (I.transport) {
-            k_surf2<R, BS><<<grid, block, 0, s>>>(I, 1, L.nblocks, SK);
+            k_surf2<R, BS><<<surf_grid, block, 0, s>>>(I, 1, surf_blocks, SK);
             k_scale2<R><<<grid, block, 0, s>>>(I);
         } else {
             k_tick<R><<<1, 32, 0, s>>>(I);
         }
         ran[LBS_K_SURF] = true;
         mark(s, LBS_K_NGROUPS);
+        return launch_check();
+    }
+
+    int set_graph(int on) override {
+        use_graph = bool(on);
+        return LBS_OK;
     }
 
     int sor_rounds() const { return (I.sor_max_iter + SK - 1) / SK; }
 
+    // kernels of one step: the SOR loop is counted at its typical 4 rounds
+    // (the exact count of a step is sor_iters / 3 from the diagnostics)
     int kernel_count() const override {
-        return I.transport ? 7 + sor_rounds() : 4;
+        return I.transport ? 7 + last_rounds : 4;
     }
+    int last_rounds = 4;
 
     int profile(int on) override {
         if (bool(on) == prof) return LBS_OK;
@@ -327,7 +399,7 @@ struct Solver : Base {
                                           u ? du : nullptr);
         k_moments2<R><<<grid, block, 0, s>>>(I);
         k_grad2<R><<<grid, block, 0, s>>>(I);
-        k_surf2<R, BS><<<grid, block, 0, s>>>(I, 0, L.nblocks, SK);
+        k_surf2<R, BS><<<surf_grid, block, 0, s>>>(I, 0, surf_blocks, SK);
         int r = launch_check();
         if (r) return r;
         CK(cudaStreamSynchronize(s));
@@ -335,20 +407,22 @@ struct Solver : Base {
     }
 
     int build_graph() {
-        cudaStream_t s = ctx->stream;
-        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        enqueue_step(s);
-        cudaError_t e = cudaStreamEndCapture(s, &graph);
-        if (e != cudaSuccess) {
-            set_err(ctx, "graph capture failed: %s", cudaGetErrorString(e));
-            return LBS_ECUDA;
-        }
+        CK(cudaGraphCreate(&graph, 0));
+        int r = capture_step(ctx->stream, graph);
+        if (r) return r;
         CK(cudaGraphInstantiate(&gexec, graph, 0));
         return LBS_OK;
     }
 
     int step(int n) override {
         if (n <= 0) return LBS_OK;
+        if (!use_graph) {
+            for (int k = 0; k < n; k++) {
+                int r = enqueue_step(ctx->stream);
+                if (r) return r;
+            }
+            return LBS_OK;
+        }
         if (!gexec) {
             int r = build_graph();
             if (r) return r;
@@ -395,6 +469,28 @@ struct Solver : Base {
         if (phi) CK(cudaMemcpyAsync(phi, stage + 4 * N, N * sizeof(double), cudaMemcpyDeviceToHost, s));
         if (psi) CK(cudaMemcpyAsync(psi, stage + 5 * N, N * sizeof(double), cudaMemcpyDeviceToHost, s));
         if (C) CK(cudaMemcpyAsync(C, stage + 6 * N, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return LBS_OK;
+    }
+
+    int macro(double *g, double *a, double *F, double *u, double *S, double *B) override {
+        int r = sync();
+        if (r) return r;
+        size_t N = (size_t)I.nx * I.ny * I.nz;
+        cudaStream_t s = ctx->stream;
+        k_force2<R><<<grid, block, 0, s>>>(I);
+        double *dg = stage, *da = stage + 3 * N, *dF = stage + 4 * N, *du = stage + 7 * N,
+               *dS = stage + 10 * N, *dB = stage + 11 * N;
+        k_export_macro2<R><<<grid, block, 0, s>>>(I, dg, da, dF, du);
+        k_fd2<R><<<grid, block, 0, s>>>(I, dS, dB);
+        r = launch_check();
+        if (r) return r;
+        struct {
+            double *h, *d;
+            size_t n;
+        } cp[] = {{g, dg, 3 * N}, {a, da, N}, {F, dF, 3 * N}, {u, du, 3 * N}, {S, dS, N}, {B, dB, N}};
+        for (auto &c : cp)
+            if (c.h) CK(cudaMemcpyAsync(c.h, c.d, c.n * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         return LBS_OK;
     }
@@ -448,6 +544,7 @@ struct Solver : Base {
         }
         d->umax = v[NDIAG + 2];
         d->sor_iters_psi = d->sor_iters_C = h.sor_iters;
+        if (h.sor_iters > 0) last_rounds = h.sor_iters / SK;
         d->step = h.step;
         return LBS_OK;
     }
@@ -509,7 +606,7 @@ int lbs_params_default(lbs_params *p, int nx, int ny, int nz) {
     p->transport = 1;
     p->Ds = p->Db = 0.1;
     p->sor_omega = 1.2;
-    p->sor_tol = 2e-7;
+    p->sor_tol = 5e-7;
     p->sor_max_iter = 40;
     p->eps_w = 1e-6;
     p->eps_n = 1e-6;
@@ -628,6 +725,17 @@ int lbs_profile(lbs_ctx *c, int enable) {
 int lbs_kernel_times(lbs_ctx *c, double *ms, int n) {
     if (!c || !c->impl || !ms || n < 0) return LBS_EINVAL;
     return c->impl->kernel_times(ms, n);
+}
+
+int lbs_get_macro(lbs_ctx *c, double *g, double *a, double *F, double *u, double *S,
+                  double *B) {
+    if (!c || !c->impl) return LBS_EINVAL;
+    return c->impl->macro(g, a, F, u, S, B);
+}
+
+int lbs_set_graph(lbs_ctx *c, int enable) {
+    if (!c || !c->impl) return LBS_EINVAL;
+    return c->impl->set_graph(enable);
 }
 
 int lbs_step_kernel_count(const lbs_ctx *c) {

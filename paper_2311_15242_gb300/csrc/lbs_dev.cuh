@@ -71,7 +71,10 @@ struct Ctl {
     unsigned int ticket;    // arrival counter of the last-block reductions
     int sor_exec;           // sweeps (rounds) executed in the current solve
     int sor_iters_parity;   // rounds of the last solve were odd: result in psi2, C2
-    int pad2;
+    unsigned int sor_ticket; // arrival counter of the SOR round blocks
+    double dscale;          // scale - 1 of the last rescale
+    float dscale_f;         // the same in single precision
+    int pad3;
     // per sweep: max |d psi|, max |d C|, max |psi|, max |C| (bits of
     // non-negative doubles, compared as unsigned integers)
     unsigned long long sweep[KMAX_SWEEPS][4];

@@ -302,8 +302,11 @@ __device__ __forceinline__ R upwind(const R *v, R u) {
     return R(0.5) * (weno_m(v) + weno_p(v));
 }
 
+// Sout, Bout: when given, only S and B of the current state are written
+// there (export; the Adams-Bashforth history and the right-hand sides are
+// left untouched)
 template <typename R>
-__global__ void k_fd2(Inst<R> I) {
+__global__ void k_fd2(Inst<R> I, double *Sout = nullptr, double *Bout = nullptr) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= I.nx || y >= I.ny) return;
@@ -332,6 +335,12 @@ __global__ void k_fd2(Inst<R> I) {
                         : I.ra * Cc * (I.psi_inf - psi) - I.rd * psi;
     R S = -divP + a * j;
     R B = -divC - a * j;
+    if (Sout) {
+        long long d = (long long)y * I.nx + x;
+        Sout[d] = S;
+        Bout[d] = B;
+        return;
+    }
     // diffusion operator of Eq. 28 with the weights of time t
     R wp = a + I.eps_w, wc = I.chi[c] + I.eps_w;
     R Lp = R(0), Lc = R(0);
@@ -580,6 +589,8 @@ __device__ __forceinline__ bool sweep_converged(const Ctl *ctl, int k, double to
 // same-colour neighbours across an odd periodic seam deterministic.
 // Round r skips when round r-1 met the tolerance on its last sweep.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned int nblocks);
+
 template <typename R, int TX, int TY, int K, int BS>
 struct SorTile {
     static constexpr int H = 2 * K, RX = TX + 2 * H, RY = TY + 2 * H, NR = RX * RY;
@@ -587,17 +598,35 @@ struct SorTile {
     static constexpr size_t smem_bytes() { return (size_t)NR * (6 * sizeof(R) + 1); }
 };
 
+// convergence of a round: the largest update of its last sweep is within
+// sor_tol of the largest value, or (single precision) the updates stopped
+// shrinking at a level within 8 sor_tol, i.e. at the rounding floor
+template <typename R>
+__device__ __forceinline__ bool round_converged(const Ctl *ctl, int r, double tol) {
+    if (sweep_converged<R>(ctl, r, tol)) return true;
+    if (sizeof(R) != 4 || r == 0) return false;
+    if (!sweep_converged<R>(ctl, r, 8 * tol)) return false;
+    double d0 = fmax(__longlong_as_double((long long)ctl->sweep[r - 1][0]),
+                     __longlong_as_double((long long)ctl->sweep[r - 1][1]));
+    double d1 = fmax(__longlong_as_double((long long)ctl->sweep[r][0]),
+                     __longlong_as_double((long long)ctl->sweep[r][1]));
+    return d1 >= 0.5 * d0;
+}
+
+// loop: the WHILE node's handle in graph mode; eager_round >= 0 instead runs
+// round eager_round of a host-side loop (returns at once once converged)
 template <typename R, int TX, int TY, int K, int BS>
-__global__ void __launch_bounds__(BS) k_sor_tb2(Inst<R> I, int round) {
+__global__ void __launch_bounds__(BS)
+    k_sor_tb2(Inst<R> I, cudaGraphConditionalHandle loop, int max_rounds, int eager_round) {
     using T = SorTile<R, TX, TY, K, BS>;
     constexpr int RX = T::RX, RY = T::RY, NR = T::NR, H = T::H, PER = T::PER;
-    if (round > 0 && sweep_converged<R>(I.ctl, round - 1, double(I.sor_tol))) return;
+    if (eager_round > 0 && I.ctl->sor_exec < eager_round) return;  // loop already ended
+    const int round = I.ctl->sor_exec;  // rounds run so far in this solve
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sp = (R *)smem_raw, *sc = sp + NR, *wp = sc + NR, *wc = wp + NR, *bp = wc + NR,
       *bc = bp + NR;
     uint8_t *fl = (uint8_t *)(bc + NR);
     const int tid = threadIdx.x;
-    if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0) atomicAdd(&I.ctl->sor_exec, 1);
     const int x0 = blockIdx.x * TX - H, y0 = blockIdx.y * TY - H;
     const R *pin = (round & 1) ? I.psi2 : I.psi;
     const R *cin = (round & 1) ? I.C2 : I.C;
@@ -647,7 +676,7 @@ __global__ void __launch_bounds__(BS) k_sor_tb2(Inst<R> I, int round) {
     // region-border cells are never updated (a neighbour is missing); walls
     // are the faces whose neighbour is outside the domain: they carry no flux
     const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
-    double v[4] = {0, 0, 0, 0};
+    R v[4] = {R(0), R(0), R(0), R(0)};  // maxima of the last sweep (never FP64 per cell)
     for (int s = 0; s < K; s++) {
         for (int colour = 0; colour < 2; colour++) {
             R np[PER], nc[PER];
@@ -682,10 +711,10 @@ __global__ void __launch_bounds__(BS) k_sor_tb2(Inst<R> I, int round) {
                 np[k] = p0 + dp;
                 nc[k] = c0 + dc;
                 if (s == K - 1 && (f & 64)) {
-                    v[0] = fmax(v[0], fabs(double(dp)));
-                    v[1] = fmax(v[1], fabs(double(dc)));
-                    v[2] = fmax(v[2], fabs(double(np[k])));
-                    v[3] = fmax(v[3], fabs(double(nc[k])));
+                    v[0] = fmax(v[0], fabs(dp));
+                    v[1] = fmax(v[1], fabs(dc));
+                    v[2] = fmax(v[2], fabs(np[k]));
+                    v[3] = fmax(v[3], fabs(nc[k]));
                 }
             }
             __syncthreads();
@@ -715,7 +744,7 @@ __global__ void __launch_bounds__(BS) k_sor_tb2(Inst<R> I, int round) {
         cout[c] = sc[q];
     }
     // block maxima of the last sweep -> round slot
-    __shared__ double sh[4][BS / 32];
+    __shared__ R sh[4][BS / 32];
 #pragma unroll
     for (int q = 0; q < 4; q++)
 #pragma unroll
@@ -725,10 +754,27 @@ __global__ void __launch_bounds__(BS) k_sor_tb2(Inst<R> I, int round) {
     __syncthreads();
     if (tid == 0)
         for (int q = 0; q < 4; q++) {
-            double m = 0;
+            R m = R(0);
             for (int w = 0; w < BS / 32; w++) m = fmax(m, sh[q][w]);
-            atomic_max_pos(&I.ctl->sweep[round][q], m);
+            atomic_max_pos(&I.ctl->sweep[round][q], double(m));
         }
+    // the last block to finish decides whether the loop runs another round
+    const unsigned int nb = gridDim.x * gridDim.y;
+    if (!last_block(&I.ctl->sor_ticket, nb)) return;
+    if (tid != 0) return;
+    Ctl *ctl = I.ctl;
+    ctl->sor_ticket = 0;
+    const bool conv = round_converged<R>(ctl, round, double(I.sor_tol));
+    const bool stop = conv || round + 1 >= max_rounds;
+    if (stop && !conv) ctl->status |= ST_NOCONV;
+    if (eager_round < 0) {
+        ctl->sor_exec = round + 1;
+        if (stop) cudaGraphSetConditional(loop, 0);
+    } else {
+        // eager: sor_exec counts finished rounds; a stop freezes it one below
+        // the next launch's index so that the later launches return at once
+        ctl->sor_exec = stop ? -(round + 1) - 1000000 : round + 1;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -793,18 +839,37 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned int nb
 // mode 0: set the conserved total M0 (after initialisation);
 // mode 1: end of a step: rescale factor M0/total (Sec. 2.2), SOR bookkeeping,
 //         step counter, divergence check.
+// rounds finished, from the counter the SOR loop leaves behind (an eager
+// loop that stopped stores -(rounds) - 1000000)
+__device__ __forceinline__ int sor_rounds_done(int e) { return e >= 0 ? e : -(e + 1000000); }
+
+// k_surf: every thread sums a strip of SURF_STRIP cells along y with a
+// compensated (Kahan) sum in R; strips are added in FP64 (no per-cell FP64:
+// the FP64 pipe of GB300 is narrow).
+constexpr int SURF_STRIP = 16;
+
 template <typename R, int BS>
 __global__ void k_surf2(Inst<R> I, int mode, int nblocks, int sweeps_per_round) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * SURF_STRIP;
     // after an odd number of blocked SOR rounds the solution is in psi2, C2
-    const bool alt = mode == 1 && (I.ctl->sor_exec & 1);
-    double v[1] = {0};
-    if (x < I.nx && y < I.ny) {
-        long long c = (long long)y * I.pitch + x;
-        v[0] = double(I.a[c] + I.eps_w) * double(alt ? I.psi2[c] : I.psi[c]) +
-               double(I.chi[c] + I.eps_w) * double(alt ? I.C2[c] : I.C[c]);
-    }
+    const int rounds = sor_rounds_done(I.ctl->sor_exec);
+    const bool alt = mode == 1 && (rounds & 1);
+    const R *P = alt ? I.psi2 : I.psi;
+    const R *Cc = alt ? I.C2 : I.C;
+    R sum = R(0), comp = R(0);
+    if (x < I.nx)
+        for (int k = 0; k < SURF_STRIP; k++) {
+            int y = y0 + k;
+            if (y >= I.ny) break;
+            long long c = (long long)y * I.pitch + x;
+            R v = (I.a[c] + I.eps_w) * P[c] + (I.chi[c] + I.eps_w) * Cc[c];
+            R yv = v - comp;
+            R t = sum + yv;
+            comp = (t - sum) - yv;
+            sum = t;
+        }
+    double v[1] = {double(sum) - double(comp)};
     int b = blockIdx.x + blockIdx.y * gridDim.x;
     block_sum<BS, 1>(v, I.part + b);
     if (!last_block(&I.ctl->ticket, nblocks)) return;
@@ -817,21 +882,17 @@ __global__ void k_surf2(Inst<R> I, int mode, int nblocks, int sweeps_per_round) 
         ctl->M0 = tot;
         ctl->pre = tot;
         ctl->scale = 1.0;
+        ctl->dscale = 0.0;
+        ctl->dscale_f = 0.0f;
         return;
     }
     ctl->pre = tot;
     ctl->scale = tot > 0 ? ctl->M0 / tot : 1.0;
+    ctl->dscale = ctl->scale - 1.0;
+    ctl->dscale_f = float(ctl->dscale);
     if (!isfinite(tot)) ctl->status |= ST_DIVERGED;
-    bool conv = false;
-    const int rounds = (I.sor_max_iter + sweeps_per_round - 1) / sweeps_per_round;
-    for (int k = 0; k < rounds; k++)
-        if (sweep_converged<R>(ctl, k, double(I.sor_tol))) {
-            conv = true;
-            break;
-        }
-    if (!conv) ctl->status |= ST_NOCONV;
-    ctl->sor_iters = ctl->sor_exec * sweeps_per_round;
-    ctl->sor_iters_parity = ctl->sor_exec & 1;
+    ctl->sor_iters = rounds * sweeps_per_round;
+    ctl->sor_iters_parity = rounds & 1;
     ctl->sor_exec = 0;
     for (int k = 0; k < KMAX_SWEEPS; k++)
         for (int q = 0; q < 4; q++) ctl->sweep[k][q] = 0ull;
@@ -847,7 +908,7 @@ __global__ void k_scale2(Inst<R> I) {
     // the factor is 1 + O(1e-6): multiplying by it rounded to R would apply a
     // quantised correction with the same bias every step; x + x d with
     // d = s - 1 formed in double and one fused rounding is unbiased
-    const R d = R(I.ctl->scale - 1.0);
+    const R d = sizeof(R) == 4 ? R(I.ctl->dscale_f) : R(I.ctl->dscale);
     // the blocked SOR leaves its result in the second buffer after an odd
     // number of rounds
     const bool alt = I.ctl->sor_iters_parity != 0;
@@ -939,6 +1000,27 @@ __global__ void k_diag2(Inst<R> I, int nblocks) {
         I.ctl->diag[q] = m;
     }
     I.ctl->ticket = 0;
+}
+
+// dense double copies of the intermediate fields of the current state
+template <typename R>
+__global__ void k_export_macro2(Inst<R> I, double *g, double *a, double *F, double *u) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= I.nx || y >= I.ny) return;
+    long long c = (long long)y * I.pitch + x;
+    long long d = (long long)y * I.nx + x;
+    long long N = (long long)I.nx * I.ny;
+    g[d] = I.gx[c];
+    g[N + d] = I.gy[c];
+    g[2 * N + d] = 0.0;
+    a[d] = I.a[c];
+    F[d] = I.Fx[c];
+    F[N + d] = I.Fy[c];
+    F[2 * N + d] = 0.0;
+    u[d] = I.ux[c];
+    u[N + d] = I.uy[c];
+    u[2 * N + d] = 0.0;
 }
 
 // dense double copies of the macroscopic fields for the host

@@ -19,7 +19,7 @@ STORAGE = {"f64": LBS_F64, "f32": LBS_F32}
 
 EXPORTS = ("lbs_params_default", "lbs_workspace_bytes", "lbs_create",
            "lbs_init_fields", "lbs_step", "lbs_sync", "lbs_get_fields",
-           "lbs_diagnostics", "lbs_profile", "lbs_kernel_times",
+           "lbs_get_macro", "lbs_diagnostics", "lbs_profile", "lbs_kernel_times", "lbs_set_graph",
            "lbs_step_kernel_count", "lbs_destroy", "lbs_last_error")
 KERNEL_GROUPS = ("force", "fd", "collide", "stream", "grad", "sor", "surf")
 
@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True):
     L.lbs_profile.argtypes = [C.c_void_p, C.c_int]
     L.lbs_kernel_times.argtypes = [C.c_void_p, _DP, C.c_int]
     L.lbs_step_kernel_count.argtypes = [C.c_void_p]
+    L.lbs_set_graph.argtypes = [C.c_void_p, C.c_int]
+    L.lbs_get_macro.argtypes = [C.c_void_p] + [_DP] * 6
     L.lbs_destroy.argtypes = [C.c_void_p]
     L.lbs_last_error.restype = C.c_char_p
     L.lbs_last_error.argtypes = [C.c_void_p]
@@ -117,8 +119,8 @@ def params_from(cfg: dict, storage: int) -> LbsParams:
     for k in ("eos", "source", "transport"):
         if k in cfg:
             setattr(p, k, int(cfg[k]))
-    p.sor_tol = float(cfg.get("sor_tol", 1e-13 if storage == LBS_F64 else 2e-7))
-    p.sor_max_iter = int(cfg.get("sor_max_iter", 64 if storage == LBS_F64 else 40))
+    p.sor_tol = float(cfg.get("sor_tol", 1e-13 if storage == LBS_F64 else 5e-7))
+    p.sor_max_iter = int(cfg.get("sor_max_iter", 64 if storage == LBS_F64 else 48))
     return p
 
 
@@ -204,8 +206,20 @@ class Solver:
         self._check(self.L.lbs_kernel_times(self.h, _dp(ms), len(KERNEL_GROUPS)))
         return dict(zip(KERNEL_GROUPS, ms.tolist()))
 
+    def set_graph(self, on=True):
+        """One CUDA graph per step (default) or individual launches."""
+        self._check(self.L.lbs_set_graph(self.h, int(bool(on))))
+
     def kernel_count(self):
         return int(self.L.lbs_step_kernel_count(self.h))
+
+    def macro(self):
+        """Intermediate fields of the current state (see lbs_get_macro)."""
+        out = dict(g=np.empty((3,) + self.shape), a=np.empty(self.shape),
+                   F=np.empty((3,) + self.shape), u=np.empty((3,) + self.shape),
+                   S=np.empty(self.shape), B=np.empty(self.shape))
+        self._check(self.L.lbs_get_macro(self.h, *[_dp(out[k]) for k in ("g", "a", "F", "u", "S", "B")]))
+        return out
 
     def diagnostics(self):
         d = LbsDiag()
