@@ -17,8 +17,12 @@
  *             Eq. 25-27 WENO3 convection;  Eq. 28 diffusion operator
  *             SOR (omega = 1.2) and the rescaling of the total surfactant
  *
- * Readings of points the paper leaves open (numbered R1..R22 in the
- * design notes) are marked "reading:" where they are used.
+ * Readings of points the paper leaves open (numbered R1..R28) are marked
+ * "reading:" where they are used.
+ *
+ * Parity unpinned: the D3Q19 equilibrium rows 17-19 (Eq. 40, taken as
+ * printed) have no independent check; the 3D correction coefficient is
+ * checked only where it vanishes (standard alpha).
  */
 #include "ora.h"
 
