@@ -190,6 +190,37 @@ int lbs_set_graph(lbs_ctx *c, int enable);
 /* Number of kernel launches one step queues (graph kernel nodes). */
 int lbs_step_kernel_count(const lbs_ctx *c);
 
+/* ---- total surfactant without any device allocation --------------------
+ * (Not part of the paper's method: a service for callers that cannot call
+ * cudaMalloc, e.g. code whose device memory belongs to another allocator or
+ * a loop that must not stall on an allocation's device synchronisation.)
+ *
+ * Writes sum (a + eps_w) psi + (chi + eps_w) C over an nx x ny x nz grid to
+ * *total, the same conserved total that lbs_diagnostics reports as
+ * surf_total when a = |grad rho^N|, chi = 1 - rho^N.  a, chi, psi, C are
+ * caller-owned device arrays of float (storage = LBS_F32) or double
+ * (LBS_F64), row-major [z][y][x] with a row pitch of `pitch` elements
+ * (pitch >= nx); total points to one double the GPU can write (device
+ * memory, or mapped / managed host memory).  The work is queued on `stream`
+ * (NULL = the legacy default stream); read *total after the stream is
+ * synchronised.
+ *
+ * Nothing is allocated: the per-block partial sums live in a fixed scratch
+ * array in the library's device memory (64 KiB, held by every GPU that
+ * loads the library until the process exits).  Grids larger than that
+ * scratch can serve (more than 8192 thread blocks of 32 x 128 cells; at most
+ * LBS_STATIC_MAX_CELLS cells) are refused with LBS_EINVAL before anything is
+ * queued.  The first call on a device looks up the scratch's device address;
+ * make that first call before any stream capture.  All calls share the
+ * scratch: calls that may overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.
+ * Returns LBS_OK, LBS_EINVAL (bad arguments, grid too large) or LBS_ECUDA. */
+#define LBS_STATIC_MAX_CELLS 33554432LL
+int lbs_surfactant_total_static(int storage, const void *a, const void *chi,
+                                const void *psi, const void *C, int nx, int ny,
+                                int nz, int pitch, double eps_w, double *total,
+                                void *stream);
+
 /* Release the context (and its device memory unless caller-supplied). */
 void lbs_destroy(lbs_ctx *c);
 

@@ -20,7 +20,8 @@ STORAGE = {"f64": LBS_F64, "f32": LBS_F32}
 EXPORTS = ("lbs_params_default", "lbs_workspace_bytes", "lbs_create",
            "lbs_init_fields", "lbs_step", "lbs_sync", "lbs_get_fields",
            "lbs_get_macro", "lbs_diagnostics", "lbs_profile", "lbs_kernel_times", "lbs_set_graph",
-           "lbs_step_kernel_count", "lbs_destroy", "lbs_last_error")
+           "lbs_step_kernel_count", "lbs_surfactant_total_static", "lbs_destroy",
+           "lbs_last_error")
 KERNEL_GROUPS = ("force", "fd", "collide", "stream", "grad", "sor", "surf")
 
 
@@ -94,6 +95,8 @@ def load(build_if_missing: bool = True):
     L.lbs_step_kernel_count.argtypes = [C.c_void_p]
     L.lbs_set_graph.argtypes = [C.c_void_p, C.c_int]
     L.lbs_get_macro.argtypes = [C.c_void_p] + [_DP] * 6
+    L.lbs_surfactant_total_static.argtypes = [C.c_int] + [C.c_void_p] * 4 + [C.c_int] * 4 + [
+        C.c_double, C.c_void_p, C.c_void_p]
     L.lbs_destroy.argtypes = [C.c_void_p]
     L.lbs_last_error.restype = C.c_char_p
     L.lbs_last_error.argtypes = [C.c_void_p]
