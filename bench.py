@@ -41,12 +41,15 @@ UNIT = "MLUPS"
 # output field of the group read or written once; derivation in the design doc).
 ALG_BYTES_F32 = {"force": 44, "fd": 48, "collide": 176, "stream": 172, "grad": 28,
                  "surf": 40}
-SOR_BYTES_PER_SWEEP_F32 = 32
+# one blocked SOR launch (round): psi, C, a, chi and the two right-hand sides
+# read once, psi and C written once, whatever the sweeps it runs in shared memory
+SOR_BYTES_PER_ROUND_F32 = 32
 
-# DRAM bytes per launch of the collide kernel group from one ncu capture of
-# the source tree with this hash (scaled to the 256 x 1024 grid); None when
-# not captured for the current kernels.
-TRAFFIC = {"kernel": "collide", "src_sha": None, "bytes_per_launch": None}
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of the source tree with this hash on this workload
+# (profiles/step_bubble_rise_256x1024_f32.md); reported only while the
+# kernels are unchanged.
+TRAFFIC = {"kernel": "sor", "src_sha": "be4fac46d6f868c3", "bytes_per_launch": 6311680}
 
 
 def src_hash():
@@ -67,51 +70,83 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event reasons sampled during the timed region.
 
-    def __init__(self, gpu_index):
-        self.idx = gpu_index
-        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        self.p = None
+    Read-only NVML queries from a background thread every 5 ms (the timed
+    region can be shorter than nvidia-smi's sampling period); nvidia-smi is
+    the fallback when NVML cannot be loaded."""
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, gpu_index, pci_bus_id=None):
+        import ctypes
+        import threading
+        self.idx, self.rows, self.stop_ev = gpu_index, [], threading.Event()
+        self.nv = self.h = None
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit")
+            h = ctypes.c_void_p()
+            ok = False
+            if pci_bus_id:
+                ok = nv.nvmlDeviceGetHandleByPciBusId_v2(pci_bus_id.encode(), ctypes.byref(h)) == 0
+            if not ok and nv.nvmlDeviceGetHandleByIndex_v2(gpu_index, ctypes.byref(h)) != 0:
+                raise OSError("nvml handle")
+            self.nv, self.h = nv, h
+        except OSError:
+            self.nv = None
+        self.thread = threading.Thread(target=self._run, daemon=True)
+
+    def _sample(self):
+        import ctypes
+        nv, h = self.nv, self.h
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk))  # NVML_CLOCK_SM
+        nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))
+        fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        fn(h, ctypes.byref(rs))
+        self.rows.append((clk.value, mx.value, rs.value))
+
+    def _run(self):
+        while not self.stop_ev.is_set():
+            self._sample()
+            self.stop_ev.wait(0.005)
 
     def start(self):
+        if self.nv is not None:
+            self.thread.start()
+            return
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                ["nvidia-smi", f"--id={self.idx}", "--query-gpu=clocks.sm,clocks.max.sm,"
+                 "clocks_event_reasons.active", "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
+        except OSError:
             self.p = None
 
     def stop(self):
-        if self.p is None:
-            return None
-        self.p.terminate()
-        try:
+        if self.nv is not None:
+            self.stop_ev.set()
+            self.thread.join(timeout=2)
+            self._sample()
+        elif getattr(self, "p", None) is not None:
+            self.p.terminate()
             self.p.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.p.kill()
-        self.f.flush()
-        rows = []
-        for line in open(self.f.name):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
-            except ValueError:
-                continue
-        os.unlink(self.f.name)
-        if not rows:
+            for line in open(self.f.name):
+                parts = [x.strip() for x in line.split(",")]
+                try:
+                    self.rows.append((float(parts[0]), float(parts[1]), int(parts[2], 16)))
+                except (ValueError, IndexError):
+                    pass
+        if not self.rows:
             return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i] == "Active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows),
-                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
-                "samples": len(rows)}
+        reasons = sorted({name for _, _, r in self.rows for bit, name in self.BITS.items() if r & bit})
+        return {"sm_mhz": statistics.median(r[0] for r in self.rows),
+                "sm_max_mhz": max(r[1] for r in self.rows), "reasons": reasons,
+                "samples": len(self.rows), "source": "nvml" if self.nv is not None else "nvidia-smi"}
 
 
 def workload():
@@ -223,7 +258,11 @@ def main():
         one_step(False)
     s.sync()
 
-    clocks = Clocks(local)
+    props = torch.cuda.get_device_properties(local)
+    bus = getattr(props, "pci_bus_id", None)
+    dom = getattr(props, "pci_domain_id", 0)
+    pci = f"{dom:08x}:{bus:02x}:00.0" if isinstance(bus, int) else None
+    clocks = Clocks(local, pci)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -248,17 +287,23 @@ def main():
     # per-group device time (mean over the timed steps)
     groups = list(ktimes[0].keys())
     kmean = {g: float(np.mean([k[g] for k in ktimes])) for g in groups}
-    sweeps = s.diagnostics()["sor_iters_psi"]
-    dom = max((g for g in groups if g in ALG_BYTES_F32), key=lambda g: kmean[g])
+    dg = s.diagnostics()
+    sweeps, rounds = dg["sor_iters_psi"], max(dg["sor_rounds"], 1)
+    dom = max((g for g in groups if g in ALG_BYTES_F32 or g == "sor"), key=lambda g: kmean[g])
     scale = 2 if args.storage == "f64" else 1
-    alg = ALG_BYTES_F32[dom] * scale * cells
+    if dom == "sor":  # one launch = one round
+        alg = SOR_BYTES_PER_ROUND_F32 * scale * cells
+        launch_ms = kmean[dom] / rounds
+    else:
+        alg = ALG_BYTES_F32[dom] * scale * cells
+        launch_ms = kmean[dom]
     hbm, src = peaks()
-    achieved = alg / (kmean[dom] / 1e3) / 1e9
+    achieved = alg / (launch_ms / 1e3) / 1e9
     sha = src_hash()
     traffic = TRAFFIC["bytes_per_launch"] if (TRAFFIC["src_sha"] == sha and dom == TRAFFIC["kernel"]) else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
             "peak_source": src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-            "alg_bytes_per_launch": alg, "avg_launch_ms": kmean[dom]}
+            "alg_bytes_per_launch": alg, "avg_launch_ms": launch_ms}
 
     # end to end through the C ABI with host buffers
     pin = {k: torch.from_numpy(np.ascontiguousarray(f[k])).pin_memory().numpy()
@@ -286,7 +331,7 @@ def main():
            "config": {"workload": name, "cells": cells, "storage": args.storage,
                       "l2": "flushed before every timed step (256 MiB write)",
                       "parallelism": f"replicas x{world}" if world > 1 else "single"},
-           "roofline": roof, "kernel_ms": kmean, "sor_sweeps": sweeps,
+           "roofline": roof, "kernel_ms": kmean, "sor_sweeps": sweeps, "sor_rounds": rounds,
            "gpu_launches": args.steps * s.kernel_count(),
            "clocks": clk, "e2e": e2e, "impl": "lbs", "src_sha": sha}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -100,6 +100,7 @@ typedef struct {
     double umax;                /* max |u| */
     double Re;                  /* 2 rhoB0 |U_v| R / muB0, R from the red area/volume */
     int sor_iters_psi, sor_iters_C; /* sweeps used by the last solve */
+    int sor_rounds;             /* blocked SOR launches of the last solve */
     long long step;             /* time steps taken since lbs_init_fields */
 } lbs_diag;
 

@@ -19,7 +19,7 @@ namespace {
 
 constexpr int BX = 32, BY = 8, BS = BX * BY;
 // blocked SOR: tile, sweeps per launch, threads
-constexpr int STX = 64, STY = 32, SK = 3, SBS = 256;
+constexpr int STX = 32, STY = 16, SK = 2, SBS = 256;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -294,10 +294,17 @@ struct Solver : Base {
         ran[LBS_K_GRAD] = true;
         mark(s, LBS_K_SOR);
         if (I.transport && !capturing) {
+            // eager form (for profilers): the host reads the loop state after
+            // every round and launches no round beyond the converged one
             using T = SorTile<R, STX, STY, SK, SBS>;
-            for (int r = 0; r < sor_rounds(); r++)
+            for (int r = 0; r < sor_rounds(); r++) {
                 k_sor_tb2<R, STX, STY, SK, SBS><<<sor_grid, SBS, T::smem_bytes(), s>>>(
                     I, cudaGraphConditionalHandle(0), sor_rounds(), r);
+                int done = 0;
+                CK(cudaMemcpyAsync(&done, &I.ctl->sor_exec, sizeof(int), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                if (done < 0) break;
+            }
             ran[LBS_K_SOR] = true;
         } else if (I.transport) {
             cudaStreamCaptureStatus st;
@@ -544,6 +551,7 @@ struct Solver : Base {
         }
         d->umax = v[NDIAG + 2];
         d->sor_iters_psi = d->sor_iters_C = h.sor_iters;
+        d->sor_rounds = h.sor_iters / SK;
         if (h.sor_iters > 0) last_rounds = h.sor_iters / SK;
         d->step = h.step;
         return LBS_OK;

@@ -49,18 +49,37 @@ struct Mom2 {
     R rR, rB, drho, jx, jy;  // rho^R, rho^B, rho - rho_s[flag], sum_i f_i e_i
 };
 
+// compensated summation (Knuth's TwoSum): s + c carries the sum of the added
+// terms to about twice the working precision.  The colour masses of the
+// recolouring split are formed this way: a plainly rounded sum of nine
+// similar terms has nearly the same rounding error in neighbouring cells,
+// which biases the colour mass the same way every step.
+template <typename R>
+struct CSum {
+    R s = R(0), c = R(0);
+    __device__ __forceinline__ void add(R v) {
+        R t = s + v;
+        R bp = t - s;
+        c += (s - (t - bp)) + (v - bp);
+        s = t;
+    }
+    __device__ __forceinline__ R value() const { return s + c; }
+};
+
 template <typename R>
 __device__ __forceinline__ Mom2<R> moments9(const Inst<R> &I, const R *fT, const R *fM,
                                            int flag) {
     Mom2<R> m{R(0), R(0), R(0), R(0), R(0)};
-    R rm = R(0);
+    CSum<R> rmc, drc;
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
-        rm += fM[i];
-        m.drho += fT[i];
+        rmc.add(fM[i]);
+        drc.add(fT[i]);
         m.jx += R(ex9(i)) * fT[i];
         m.jy += R(ey9(i)) * fT[i];
     }
+    const R rm = rmc.value();
+    m.drho = drc.value();
     // majority colour = total - minority
     R rmaj = (I.rho_s[flag] - rm) + m.drho;
     m.rR = flag ? rmaj : rm;
@@ -463,7 +482,7 @@ __global__ void k_collide2(Inst<R> I) {
 
     // post-collision total minus shift
     R post[Q9];
-    R rdag = R(0);
+    CSum<R> rdc;
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         R s = fT[i];
@@ -471,8 +490,9 @@ __global__ void k_collide2(Inst<R> I) {
         for (int j = 0; j < Q9; j++)
             if (m9(j, i) != 0) s += R(m9(j, i)) * dm[j];
         post[i] = s;
-        rdag += shift_of(I, i, fl) + s;
+        rdc.add(shift_of(I, i, fl) + s);
     }
+    const R rdag = rdc.value();
     // recolouring (Eqs. 11-12) of the minority colour; the majority is the
     // total minus it.  Segregation weight f_i^eq(rho, 0)/rho: for the
     // alpha-model its moving components are w_i * 3 p / rho with
@@ -594,8 +614,12 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned int nb
 template <typename R, int TX, int TY, int K, int BS>
 struct SorTile {
     static constexpr int H = 2 * K, RX = TX + 2 * H, RY = TY + 2 * H, NR = RX * RY;
-    static constexpr int PER = (NR + BS - 1) / BS;
-    static constexpr size_t smem_bytes() { return (size_t)NR * (6 * sizeof(R) + 1); }
+    // per region cell: psi, C, rhs psi, rhs C, inverse diagonals (2), face
+    // coefficients to the +x and +y neighbours (2 fields x 2), one flag byte;
+    // and the cell lists of the two colours (2-byte indices)
+    static constexpr size_t smem_bytes() {
+        return (size_t)NR * (10 * sizeof(R) + 1 + 2 * 2) + 16;
+    }
 };
 
 // convergence of a round: the largest update of its last sweep is within
@@ -619,24 +643,26 @@ template <typename R, int TX, int TY, int K, int BS>
 __global__ void __launch_bounds__(BS)
     k_sor_tb2(Inst<R> I, cudaGraphConditionalHandle loop, int max_rounds, int eager_round) {
     using T = SorTile<R, TX, TY, K, BS>;
-    constexpr int RX = T::RX, RY = T::RY, NR = T::NR, H = T::H, PER = T::PER;
+    constexpr int RX = T::RX, RY = T::RY, NR = T::NR, H = T::H;
     if (eager_round > 0 && I.ctl->sor_exec < eager_round) return;  // loop already ended
     const int round = I.ctl->sor_exec;  // rounds run so far in this solve
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *sp = (R *)smem_raw, *sc = sp + NR, *wp = sc + NR, *wc = wp + NR, *bp = wc + NR,
-      *bc = bp + NR;
-    uint8_t *fl = (uint8_t *)(bc + NR);
+    R *sp = (R *)smem_raw, *sc = sp + NR, *bp = sc + NR, *bc = bp + NR;
+    R *ip = bc + NR, *ic = ip + NR;                    // 1 / diagonal
+    R *fpx = ic + NR, *fpy = fpx + NR, *fcx = fpy + NR, *fcy = fcx + NR;  // faces +x, +y
+    uint8_t *fl = (uint8_t *)(fcy + NR);
+    uint16_t *list = (uint16_t *)(((uintptr_t)(fl + NR) + 1) & ~(uintptr_t)1);
+    __shared__ int count[2];
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX - H, y0 = blockIdx.y * TY - H;
     const R *pin = (round & 1) ? I.psi2 : I.psi;
     const R *cin = (round & 1) ? I.C2 : I.C;
     R *pout = (round & 1) ? I.psi : I.psi2;
     R *cout = (round & 1) ? I.C : I.C2;
-    // flags: bit0 in the domain, bit1 colour, bits 2-5 faces -x,+x,-y,+y usable,
-    // bit6 tile interior owned by this block
-    for (int k = 0; k < PER; k++) {
-        int q = tid + k * BS;
-        if (q >= NR) break;
+    if (tid < 2) count[tid] = 0;
+    // 1. load.  flags: bit0 in the domain, bit1 colour, bit6 tile interior
+    //    owned here; ip / ic hold the weights a + eps, chi + eps for now
+    for (int q = tid; q < NR; q += BS) {
         int rx = q % RX, ry = q / RX;
         int gx = x0 + rx, gy = y0 + ry;
         int refl = 0, sx, sy;
@@ -648,69 +674,75 @@ __global__ void __launch_bounds__(BS)
             f = 1 | (((X + Y) & 1) << 1);
             sp[q] = pin[c];
             sc[q] = cin[c];
-            wp[q] = I.a[c] + I.eps_w;
-            wc[q] = I.chi[c] + I.eps_w;
             bp[q] = I.rpsi[c];
             bc[q] = I.rC[c];
+            ip[q] = I.a[c] + I.eps_w;
+            ic[q] = I.chi[c] + I.eps_w;
             if (rx >= H && rx < H + TX && ry >= H && ry < H + TY && gx >= 0 && gx < I.nx &&
                 gy >= 0 && gy < I.ny)
                 f |= 64;
+        } else {
+            sp[q] = sc[q] = bp[q] = bc[q] = ip[q] = ic[q] = R(0);
         }
         fl[q] = f;
     }
     __syncthreads();
-    // usable faces (neighbour inside the region and in the domain)
-    for (int k = 0; k < PER; k++) {
-        int q = tid + k * BS;
-        if (q >= NR) break;
-        if (!(fl[q] & 1)) continue;
+    // 2. face coefficients h (w_c + w_nb)/2 of Eq. 28 towards +x and +y; zero
+    //    across a wall or the region edge (no flux, no branch in the sweeps)
+    const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
+    for (int q = tid; q < NR; q += BS) {
         int rx = q % RX, ry = q / RX;
-        uint8_t f = fl[q];
-        if (rx > 0 && (fl[q - 1] & 1)) f |= 4;
-        if (rx < RX - 1 && (fl[q + 1] & 1)) f |= 8;
-        if (ry > 0 && (fl[q - RX] & 1)) f |= 16;
-        if (ry < RY - 1 && (fl[q + RX] & 1)) f |= 32;
-        fl[q] = f;
+        const bool in = fl[q] & 1;
+        const bool ex = in && rx < RX - 1 && (fl[q + 1] & 1);
+        const bool ny = in && ry < RY - 1 && (fl[q + RX] & 1);
+        fpx[q] = ex ? hp * R(0.5) * (ip[q] + ip[q + 1]) : R(0);
+        fcx[q] = ex ? hc * R(0.5) * (ic[q] + ic[q + 1]) : R(0);
+        fpy[q] = ny ? hp * R(0.5) * (ip[q] + ip[q + RX]) : R(0);
+        fcy[q] = ny ? hc * R(0.5) * (ic[q] + ic[q + RX]) : R(0);
     }
     __syncthreads();
-    // region-border cells are never updated (a neighbour is missing); walls
-    // are the faces whose neighbour is outside the domain: they carry no flux
-    const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
+    // 3. inverse diagonals w + sum of the four faces, and the lists of the
+    //    cells of each colour that can be updated (not on the region border)
+    for (int q = tid; q < NR; q += BS) {
+        int rx = q % RX, ry = q / RX;
+        uint8_t f = fl[q];
+        if (!(f & 1)) continue;
+        R sp_ = fpx[q] + fpy[q] + (rx > 0 ? fpx[q - 1] : R(0)) + (ry > 0 ? fpy[q - RX] : R(0));
+        R sc_ = fcx[q] + fcy[q] + (rx > 0 ? fcx[q - 1] : R(0)) + (ry > 0 ? fcy[q - RX] : R(0));
+        ip[q] = R(1) / (ip[q] + sp_);
+        ic[q] = R(1) / (ic[q] + sc_);
+        if (rx > 0 && rx < RX - 1 && ry > 0 && ry < RY - 1) {
+            int col = (f >> 1) & 1;
+            int slot = atomicAdd(&count[col], 1);
+            list[col * NR + slot] = (uint16_t)q;
+        }
+    }
+    __syncthreads();
+    // K red-black sweeps; a half-sweep stages its updates in registers
     R v[4] = {R(0), R(0), R(0), R(0)};  // maxima of the last sweep (never FP64 per cell)
+    constexpr int PER = (NR / 2 + BS) / BS + 1;
     for (int s = 0; s < K; s++) {
         for (int colour = 0; colour < 2; colour++) {
+            const int n = count[colour];
+            const uint16_t *L = list + colour * NR;
             R np[PER], nc[PER];
 #pragma unroll
             for (int k = 0; k < PER; k++) {
-                int q = tid + k * BS;
+                int idx = tid + k * BS;
                 np[k] = R(0);
                 nc[k] = R(0);
-                if (q >= NR) continue;
-                uint8_t f = fl[q];
-                int rx = q % RX, ry = q / RX;
-                if (!(f & 1) || ((f >> 1) & 1) != colour || rx == 0 || rx == RX - 1 || ry == 0 ||
-                    ry == RY - 1)
-                    continue;
-                const R wpc = wp[q], wcc = wc[q];
-                R dgp = wpc, dgc = wcc, op = R(0), oc = R(0);
-                const int nbq[4] = {q - 1, q + 1, q - RX, q + RX};
-#pragma unroll
-                for (int d = 0; d < 4; d++) {
-                    if (!(f & (4 << d))) continue;
-                    int j = nbq[d];
-                    R fp = hp * R(0.5) * (wpc + wp[j]);
-                    R fc = hc * R(0.5) * (wcc + wc[j]);
-                    dgp += fp;
-                    dgc += fc;
-                    op += fp * sp[j];
-                    oc += fc * sc[j];
-                }
+                if (idx >= n) continue;
+                int q = L[idx];
+                R op = bp[q] + fpx[q] * sp[q + 1] + fpy[q] * sp[q + RX] + fpx[q - 1] * sp[q - 1] +
+                       fpy[q - RX] * sp[q - RX];
+                R oc = bc[q] + fcx[q] * sc[q + 1] + fcy[q] * sc[q + RX] + fcx[q - 1] * sc[q - 1] +
+                       fcy[q - RX] * sc[q - RX];
                 R p0 = sp[q], c0 = sc[q];
-                R dp = I.omega * ((bp[q] + op) / dgp - p0);
-                R dc = I.omega * ((bc[q] + oc) / dgc - c0);
+                R dp = I.omega * (op * ip[q] - p0);
+                R dc = I.omega * (oc * ic[q] - c0);
                 np[k] = p0 + dp;
                 nc[k] = c0 + dc;
-                if (s == K - 1 && (f & 64)) {
+                if (s == K - 1 && (fl[q] & 64)) {
                     v[0] = fmax(v[0], fabs(dp));
                     v[1] = fmax(v[1], fabs(dc));
                     v[2] = fmax(v[2], fabs(np[k]));
@@ -720,13 +752,9 @@ __global__ void __launch_bounds__(BS)
             __syncthreads();
 #pragma unroll
             for (int k = 0; k < PER; k++) {
-                int q = tid + k * BS;
-                if (q >= NR) continue;
-                uint8_t f = fl[q];
-                int rx = q % RX, ry = q / RX;
-                if (!(f & 1) || ((f >> 1) & 1) != colour || rx == 0 || rx == RX - 1 || ry == 0 ||
-                    ry == RY - 1)
-                    continue;
+                int idx = tid + k * BS;
+                if (idx >= n) continue;
+                int q = L[idx];
                 sp[q] = np[k];
                 sc[q] = nc[k];
             }
@@ -734,9 +762,7 @@ __global__ void __launch_bounds__(BS)
         }
     }
     // interior cells back to the other buffer
-    for (int k = 0; k < PER; k++) {
-        int q = tid + k * BS;
-        if (q >= NR) break;
+    for (int q = tid; q < NR; q += BS) {
         if (!(fl[q] & 64)) continue;
         int rx = q % RX, ry = q / RX;
         long long c = (long long)(y0 + ry) * I.pitch + (x0 + rx);
@@ -939,9 +965,17 @@ __global__ void k_diag2(Inst<R> I, int nblocks) {
     double pmin = 1e300, pmax = -1e300, umax = 0;
     if (x < I.nx && y < I.ny) {
         long long c = (long long)y * I.pitch + x;
-        double rR = I.rhoR[c], rB = I.rhoB[c], rN = I.rhoN[c];
-        v[0] = rR;
-        v[1] = rB;
+        double rN = I.rhoN[c];
+        // colour masses: the exact FP64 sums of the stored populations
+        // (minority as stored, majority = shift + total deviation - minority)
+        const int fl = I.flag[c];
+        double rmin = 0, rtot = 0;
+        for (int i = 0; i < Q9; i++) {
+            rmin += double(I.fM[i * I.plane + c]);
+            rtot += double(shift_of(I, i, fl)) + double(I.fT[i * I.plane + c]);
+        }
+        v[0] = fl ? rtot - rmin : rmin;
+        v[1] = fl ? rmin : rtot - rmin;
         v[2] = double(I.a[c] + I.eps_w) * double(I.psi[c]) +
                double(I.chi[c] + I.eps_w) * double(I.C[c]);
         double ux = I.ux[c], uy = I.uy[c];

@@ -58,7 +58,7 @@ class LbsDiag(C.Structure):
         ("aspect_ratio", C.c_double),
         ("psi_av", C.c_double), ("psi_min", C.c_double), ("psi_max", C.c_double),
         ("umax", C.c_double), ("Re", C.c_double),
-        ("sor_iters_psi", C.c_int), ("sor_iters_C", C.c_int),
+        ("sor_iters_psi", C.c_int), ("sor_iters_C", C.c_int), ("sor_rounds", C.c_int),
         ("step", C.c_longlong),
     ]
 
