@@ -209,8 +209,10 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="lbs", choices=["lbs", "reference"])
-    ap.add_argument("--storage", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f64", "f16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip timing the other population storage forms")
     ap.add_argument("--eager", action="store_true",
                     help="individual kernel launches instead of one graph per step "
                          "(for kernel profilers)")
@@ -290,7 +292,7 @@ def main():
     dg = s.diagnostics()
     sweeps, rounds = dg["sor_iters_psi"], max(dg["sor_rounds"], 1)
     dom = max((g for g in groups if g in ALG_BYTES_F32 or g == "sor"), key=lambda g: kmean[g])
-    scale = 2 if args.storage == "f64" else 1
+    scale = 2 if args.storage == "f64" else 1  # (16-bit forms: fields stay FP32)
     if dom == "sor":  # one launch = one round
         alg = SOR_BYTES_PER_ROUND_F32 * scale * cells
         launch_ms = kmean[dom] / rounds
@@ -323,6 +325,30 @@ def main():
            "h2d_bytes_per_step": 3 * N * 8 / args.steps,
            "d2h_bytes_per_step": (d2h + 7 * N * 8) / args.steps}
 
+    # the other storage forms of the same step on the same workload and timing
+    forms = {args.storage: value}
+    if rank == 0 and not args.no_forms:
+        for st in ("f32", "f16", "bf16"):
+            if st in forms:
+                continue
+            s2 = Solver(cfg, storage=st, stream=stream)
+            s2.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+            tt = 0.0
+            for k in range(args.warmup + args.steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(1)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    s2.step(1)
+                    b.record(stream)
+                b.synchronize()
+                if k >= args.warmup:
+                    tt += a.elapsed_time(b)
+            s2.sync()
+            forms[st] = cells * args.steps / (tt / 1e3) / 1e6
+            s2.close()
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -333,6 +359,7 @@ def main():
                       "parallelism": f"replicas x{world}" if world > 1 else "single"},
            "roofline": roof, "kernel_ms": kmean, "sor_sweeps": sweeps, "sor_rounds": rounds,
            "gpu_launches": args.steps * s.kernel_count(),
+           "forms_mlups": forms,
            "clocks": clk, "e2e": e2e, "impl": "lbs", "src_sha": sha}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, name)

@@ -54,8 +54,12 @@ typedef enum {
 
 /* arithmetic / storage form of the populations and fields */
 typedef enum {
-    LBS_F64 = 0, /* everything in double (reference-grade, slow on GB300) */
-    LBS_F32 = 1  /* FP32 storage and arithmetic, FP64 conservation sums */
+    LBS_F64 = 0,  /* everything in double (reference-grade, slow on GB300) */
+    LBS_F32 = 1,  /* FP32 storage and arithmetic, FP64 conservation sums */
+    LBS_F16 = 2,  /* populations stored as IEEE FP16 in shifted form (total
+                     minus a rest state, and the minority colour), FP32
+                     arithmetic and fields, FP64 totals */
+    LBS_BF16 = 3  /* the same with bfloat16 population storage */
 } lbs_storage;
 
 /* Physical and numerical parameters (one instance).  Names follow the paper:

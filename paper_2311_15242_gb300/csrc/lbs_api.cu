@@ -89,14 +89,14 @@ struct Layout {
     int nblocks;
 };
 
-template <typename R>
+template <typename R, typename P>
 Layout layout_of(const lbs_params *p) {
     Layout L;
     L.pitch = (int)align_up(p->nx, 32);
-    L.plane = (long long)align_up((size_t)L.pitch * p->ny * p->nz, 64);
+    L.plane = (long long)align_up((size_t)L.pitch * p->ny * p->nz, 128);
     size_t pb = (size_t)L.plane * sizeof(R);
     L.pops_off = 0;
-    size_t pops = 4 * (size_t)Q9 * pb;
+    size_t pops = 4 * (size_t)Q9 * (size_t)L.plane * sizeof(P);
     L.scal_off = pops;
     size_t scal = 21 * pb;
     L.flag_off = align_up(L.scal_off + scal, 256);
@@ -109,7 +109,7 @@ Layout layout_of(const lbs_params *p) {
     return L;
 }
 
-template <typename R>
+template <typename R, typename P>
 struct Solver : Base {
     lbs_ctx *ctx;
     Inst<R> I;
@@ -126,7 +126,7 @@ struct Solver : Base {
 
     Solver(lbs_ctx *c) : ctx(c) {
         const lbs_params *p = &c->p;
-        L = layout_of<R>(p);
+        L = layout_of<R, P>(p);
         ws = (char *)c->ws;
         std::memset(&I, 0, sizeof(I));
         I.nx = p->nx;
@@ -171,6 +171,16 @@ struct Solver : Base {
         I.omega = R(p->sor_omega);
         I.sor_tol = R(p->sor_tol);
         I.sor_max_iter = p->sor_max_iter;
+        // FP16 population scale: 2^14 / (the power of two >= the heavier pure density)
+        {
+            double rmax = p->rhoR0 > p->rhoB0 ? p->rhoR0 : p->rhoB0, sc = 16384.0;
+            while (rmax > 1.0 && sc > 1.0) {
+                rmax *= 0.5;
+                sc *= 0.5;
+            }
+            I.pscale = R(sc);
+            I.pinv = R(1.0 / sc);
+        }
         // rest states of the pure phases; their moving components agree when
         // rhoR0 (1 - alphaR) = rhoB0 (1 - alphaB) (Eq. 42); the blue ones are used
         double sB[Q9], sR[Q9];
@@ -198,7 +208,7 @@ struct Solver : Base {
             I.mcor2[f] = R(e2 - rk * (5.4 * ak - 1.4));
         }
         size_t pb = (size_t)L.plane;
-        R *pops = (R *)(ws + L.pops_off);
+        P *pops = (P *)(ws + L.pops_off);
         I.fT = pops;
         I.fM = pops + 1 * Q9 * pb;
         I.gT = pops + 2 * Q9 * pb;
@@ -284,10 +294,10 @@ struct Solver : Base {
             ran[LBS_K_FD] = true;
         }
         mark(s, LBS_K_COLLIDE);
-        k_collide2<R><<<grid, block, 0, s>>>(I);
+        k_collide2<R, P><<<grid, block, 0, s>>>(I);
         ran[LBS_K_COLLIDE] = true;
         mark(s, LBS_K_STREAM);
-        k_stream2<R><<<grid, block, 0, s>>>(I);
+        k_stream2<R, P><<<grid, block, 0, s>>>(I);
         ran[LBS_K_STREAM] = true;
         mark(s, LBS_K_GRAD);
         k_grad2<R><<<grid, block, 0, s>>>(I);
@@ -402,9 +412,9 @@ struct Solver : Base {
         if (u) CK(cudaMemcpyAsync(du, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(ws + L.pops_off, 0, L.ctl_off - L.pops_off, s));
         CK(cudaMemsetAsync(I.ctl, 0, sizeof(Ctl), s));
-        k_init2<R><<<grid, block, 0, s>>>(I, dphi, psi ? dpsi : nullptr, C ? dC : nullptr,
+        k_init2<R, P><<<grid, block, 0, s>>>(I, dphi, psi ? dpsi : nullptr, C ? dC : nullptr,
                                           u ? du : nullptr);
-        k_moments2<R><<<grid, block, 0, s>>>(I);
+        k_moments2<R, P><<<grid, block, 0, s>>>(I);
         k_grad2<R><<<grid, block, 0, s>>>(I);
         k_surf2<R, BS><<<surf_grid, block, 0, s>>>(I, 0, surf_blocks, SK);
         int r = launch_check();
@@ -507,7 +517,7 @@ struct Solver : Base {
         if (r) return r;
         cudaStream_t s = ctx->stream;
         k_force2<R><<<grid, block, 0, s>>>(I);
-        k_diag2<R, BS><<<grid, block, 0, s>>>(I, L.nblocks);
+        k_diag2<R, P, BS><<<grid, block, 0, s>>>(I, L.nblocks);
         r = launch_check();
         if (r) return r;
         Ctl h;
@@ -625,8 +635,12 @@ size_t lbs_workspace_bytes(const lbs_params *p, int storage) {
     if (!p) return 0;
     char e[256];
     if (validate(p, e, sizeof(e))) return 0;
-    if (storage == LBS_F64) return layout_of<double>(p).total;
-    if (storage == LBS_F32) return layout_of<float>(p).total;
+    switch (storage) {
+    case LBS_F64: return layout_of<double, double>(p).total;
+    case LBS_F32: return layout_of<float, float>(p).total;
+    case LBS_F16: return layout_of<float, __half>(p).total;
+    case LBS_BF16: return layout_of<float, __nv_bfloat16>(p).total;
+    }
     return 0;
 }
 
@@ -640,7 +654,8 @@ int lbs_create(const lbs_params *p, int storage, void *stream, void *workspace,
     ctx->p = *p;
     ctx->storage = storage;
     int r = validate(p, ctx->err, sizeof(ctx->err));
-    if (!r && storage != LBS_F64 && storage != LBS_F32) {
+    if (!r && storage != LBS_F64 && storage != LBS_F32 && storage != LBS_F16 &&
+        storage != LBS_BF16) {
         set_err(ctx, "unsupported storage %d", storage);
         r = LBS_EINVAL;
     }
@@ -679,10 +694,12 @@ int lbs_create(const lbs_params *p, int storage, void *stream, void *workspace,
         }
         ctx->own_stream = true;
     }
-    if (storage == LBS_F64)
-        ctx->impl = new (std::nothrow) Solver<double>(ctx);
-    else
-        ctx->impl = new (std::nothrow) Solver<float>(ctx);
+    switch (storage) {
+    case LBS_F64: ctx->impl = new (std::nothrow) Solver<double, double>(ctx); break;
+    case LBS_F32: ctx->impl = new (std::nothrow) Solver<float, float>(ctx); break;
+    case LBS_F16: ctx->impl = new (std::nothrow) Solver<float, __half>(ctx); break;
+    default: ctx->impl = new (std::nothrow) Solver<float, __nv_bfloat16>(ctx); break;
+    }
     *out = ctx;
     if (!ctx->impl) return LBS_ENOMEM;
     return LBS_OK;

@@ -3,6 +3,8 @@
 // boundary mapping and the equation of state.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -96,6 +98,7 @@ struct Inst {
     int eos, source, transport;
     R Ds, Db, ra, rd, g[3], omega, sor_tol;
     int sor_max_iter;
+    R pscale, pinv;          // storage scale of FP16 populations (a power of 2) and 1/scale
     // shift of the stored total populations: the rest equilibrium of the pure
     // majority phase of a cell.  Its moving components are common to both
     // phases (equal pure-phase pressures, Eq. 42): shift[1..8]; the rest
@@ -107,8 +110,11 @@ struct Inst {
     // majority phase at rest: rounding only, unless alpha breaks Eq. 42
     R mcor1[2], mcor2[2];
     // state (device pointers; every field is `plane` elements, populations Q planes)
-    R *fT, *fM;               // total populations minus shift, minority colour
-    R *gT, *gM;               // post-collision buffers
+    // populations in the storage type P of the kernels that touch them
+    // (float / double, or __half / __nv_bfloat16 for the shifted
+    // low-precision forms): ldp / stp below convert
+    void *fT, *fM;            // total populations minus shift, minority colour
+    void *gT, *gM;            // post-collision buffers
     uint8_t *flag, *gflag;    // minority colour of a cell: 0 red, 1 blue
     R *rhoR, *rhoB, *rhoN, *jx, *jy;
     R *gx, *gy, *a, *chi;     // grad rhoN, |grad rhoN|, 1 - rhoN
@@ -118,6 +124,52 @@ struct Inst {
     Ctl *ctl;
     double *part;             // per-block partial sums of reductions
 };
+
+// ---------------------------------------------------------------------------
+// Population storage: arithmetic in R, storage in P.  The stored numbers are
+// deviations from a rest state or minority-colour populations, all small,
+// which is what makes 16-bit storage usable (rounded to nearest).
+// ---------------------------------------------------------------------------
+// FP16 populations are stored multiplied by a power of two (2^14 for pure-
+// phase densities <= 1, lower for heavier phases, set on the host): the
+// interface tails carry minority populations of 1e-7..1e-4, which unscaled
+// FP16 keeps only as subnormals; scaled, its normal range reaches ~4e-9.
+template <typename P>
+struct PopCvt;
+template <>
+struct PopCvt<float> {
+    static constexpr bool scaled = false;
+    static __device__ __forceinline__ float to(float v) { return v; }
+    static __device__ __forceinline__ float from(float v) { return v; }
+};
+template <>
+struct PopCvt<double> {
+    static constexpr bool scaled = false;
+    static __device__ __forceinline__ double to(double v) { return v; }
+    static __device__ __forceinline__ double from(double v) { return v; }
+};
+template <>
+struct PopCvt<__half> {
+    static constexpr bool scaled = true;
+    static __device__ __forceinline__ float to(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half from(float v) { return __float2half_rn(v); }
+};
+template <>
+struct PopCvt<__nv_bfloat16> {
+    static constexpr bool scaled = false;
+    static __device__ __forceinline__ float to(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+};
+
+template <typename R, typename P>
+__device__ __forceinline__ R ldp(const Inst<R> &I, const void *base, long long k) {
+    R v = R(PopCvt<P>::to(((const P *)base)[k]));
+    return PopCvt<P>::scaled ? v * I.pinv : v;
+}
+template <typename R, typename P>
+__device__ __forceinline__ void stp(const Inst<R> &I, void *base, long long k, R v) {
+    ((P *)base)[k] = PopCvt<P>::from(PopCvt<P>::scaled ? v * I.pscale : v);
+}
 
 // ---------------------------------------------------------------------------
 // Boundary mapping.  Periodic axes wrap; on a walled axis the coordinate is

@@ -130,7 +130,7 @@ __device__ __forceinline__ void minv9(const R *m, R *f) {
     }
 }
 
-template <typename R>
+template <typename R, typename P>
 __global__ void k_init2(Inst<R> I, const double *phi, const double *psi, const double *C,
                         const double *u) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,8 +153,8 @@ __global__ void k_init2(Inst<R> I, const double *phi, const double *psi, const d
     const int fl = (rR / double(I.rhoR0) <= rB / double(I.rhoB0)) ? 0 : 1;
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
-        I.fT[i * I.plane + c] = R((fR[i] + fB[i]) - double(shift_of(I, i, fl)));
-        I.fM[i * I.plane + c] = R(fl ? fB[i] : fR[i]);
+        stp<R, P>(I, I.fT, i * I.plane + c, R((fR[i] + fB[i]) - double(shift_of(I, i, fl))));
+        stp<R, P>(I, I.fM, i * I.plane + c, R(fl ? fB[i] : fR[i]));
     }
     I.flag[c] = (uint8_t)fl;
     I.psi[c] = psi ? R(psi[d]) : R(0);
@@ -175,7 +175,7 @@ __device__ __forceinline__ void store_moments(const Inst<R> &I, long long c, con
     I.jy[c] = m.jy;
 }
 
-template <typename R>
+template <typename R, typename P>
 __global__ void k_moments2(Inst<R> I) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -184,8 +184,8 @@ __global__ void k_moments2(Inst<R> I) {
     R fT[Q9], fM[Q9];
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
-        fT[i] = I.fT[i * I.plane + c];
-        fM[i] = I.fM[i * I.plane + c];
+        fT[i] = ldp<R, P>(I, I.fT, i * I.plane + c);
+        fM[i] = ldp<R, P>(I, I.fM, i * I.plane + c);
     }
     store_moments(I, c, fT, fM, I.flag[c]);
 }
@@ -388,7 +388,7 @@ __global__ void k_fd2(Inst<R> I, double *Sout = nullptr, double *Bout = nullptr)
 // (Eqs. 1-4, App. A Eqs. 36-38, 43) on the total populations, then
 // recolouring (Eqs. 11-12).  Output: post-collision buffers gT, gR.
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, typename P>
 __global__ void k_collide2(Inst<R> I) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -398,8 +398,8 @@ __global__ void k_collide2(Inst<R> I) {
     const int fl = I.flag[c];
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
-        fT[i] = I.fT[i * I.plane + c];
-        fM[i] = I.fM[i * I.plane + c];
+        fT[i] = ldp<R, P>(I, I.fT, i * I.plane + c);
+        fM[i] = ldp<R, P>(I, I.fM, i * I.plane + c);
     }
     Mom2<R> mo = moments9(I, fT, fM, fl);
     const R rR = mo.rR, rB = mo.rB;
@@ -507,8 +507,8 @@ __global__ void k_collide2(Inst<R> I) {
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         R segi = i == 0 ? R(0) : seg * w9<R>(i) * (R(ex9(i)) * ggx + R(ey9(i)) * ggy);
-        I.gT[i * I.plane + c] = post[i];
-        I.gM[i * I.plane + c] = fr * (shift_of(I, i, fl) + post[i]) + sg * segi;
+        stp<R, P>(I, I.gT, i * I.plane + c, post[i]);
+        stp<R, P>(I, I.gM, i * I.plane + c, fr * (shift_of(I, i, fl) + post[i]) + sg * segi);
     }
     I.gflag[c] = (uint8_t)fl;
 }
@@ -518,7 +518,7 @@ __global__ void k_collide2(Inst<R> I) {
 // crosses a wall is reflected (half-way bounce-back), a moving wall adds
 // 2 w_i rho^k (e_i . u_w) / c_s^2.  Stores the moments at t+1.
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, typename P>
 __global__ void k_stream2(Inst<R> I) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -533,9 +533,9 @@ __global__ void k_stream2(Inst<R> I) {
         long long j = nb2(I, x, y, -ex9(i), -ey9(i), refl, sx, sy);
         if (!refl) {
             // (i = 0 stays in its own cell, j = c: shift of the cell's old flag)
-            fT[i] = I.gT[i * I.plane + j];
+            fT[i] = ldp<R, P>(I, I.gT, i * I.plane + j);
             const int fj = I.gflag[j];
-            split(shift_of(I, i, fj), fT[i], I.gM[i * I.plane + j], fj, fR[i], fB[i]);
+            split(shift_of(I, i, fj), fT[i], ldp<R, P>(I, I.gM, i * I.plane + j), fj, fR[i], fB[i]);
         } else {
             R uwx = R(0), uwy = R(0);
             int nw = 0;
@@ -554,8 +554,8 @@ __global__ void k_stream2(Inst<R> I) {
             R eu = (R(ex9(i)) * uwx + R(ey9(i)) * uwy) / R(nw);
             R mw = R(2) * w9<R>(i) * eu * R(3);
             const int io = opp9(i);
-            fT[i] = I.gT[io * I.plane + c] + mw * (rRc + rBc);
-            const R mmin = I.gM[io * I.plane + c] + mw * (flc ? rBc : rRc);
+            fT[i] = ldp<R, P>(I, I.gT, io * I.plane + c) + mw * (rRc + rBc);
+            const R mmin = ldp<R, P>(I, I.gM, io * I.plane + c) + mw * (flc ? rBc : rRc);
             split(I.shift[i], fT[i], mmin, flc, fR[i], fB[i]);  // i != 0 here
         }
     }
@@ -573,8 +573,8 @@ __global__ void k_stream2(Inst<R> I) {
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         fM[i] = fl ? fB[i] : fR[i];
-        I.fT[i * I.plane + c] = fT[i];
-        I.fM[i * I.plane + c] = fM[i];
+        stp<R, P>(I, I.fT, i * I.plane + c, fT[i]);
+        stp<R, P>(I, I.fM, i * I.plane + c, fM[i]);
     }
     I.flag[c] = (uint8_t)fl;
     store_moments(I, c, fT, fM, fl);
@@ -955,7 +955,7 @@ __global__ void k_tick(Inst<R> I) {
 // sums for U (Eqs. 33-34), centroid and second moments, interface psi stats.
 // ---------------------------------------------------------------------------
 constexpr int NDIAG = 17;
-template <typename R, int BS>
+template <typename R, typename P, int BS>
 __global__ void k_diag2(Inst<R> I, int nblocks) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -971,8 +971,8 @@ __global__ void k_diag2(Inst<R> I, int nblocks) {
         const int fl = I.flag[c];
         double rmin = 0, rtot = 0;
         for (int i = 0; i < Q9; i++) {
-            rmin += double(I.fM[i * I.plane + c]);
-            rtot += double(shift_of(I, i, fl)) + double(I.fT[i * I.plane + c]);
+            rmin += double(ldp<R, P>(I, I.fM, i * I.plane + c));
+            rtot += double(shift_of(I, i, fl)) + double(ldp<R, P>(I, I.fT, i * I.plane + c));
         }
         v[0] = fl ? rtot - rmin : rmin;
         v[1] = fl ? rmin : rtot - rmin;

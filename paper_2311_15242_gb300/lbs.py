@@ -14,8 +14,8 @@ from . import build as _build
 
 LBS_OK, LBS_EINVAL, LBS_ENOMEM, LBS_ECUDA = 0, -1, -2, -3
 LBS_ENOCONV, LBS_EDIVERGED, LBS_ETIMEOUT, LBS_EBOUNDS = -4, -5, -6, -7
-LBS_F64, LBS_F32 = 0, 1
-STORAGE = {"f64": LBS_F64, "f32": LBS_F32}
+LBS_F64, LBS_F32, LBS_F16, LBS_BF16 = 0, 1, 2, 3
+STORAGE = {"f64": LBS_F64, "f32": LBS_F32, "f16": LBS_F16, "bf16": LBS_BF16}
 
 EXPORTS = ("lbs_params_default", "lbs_workspace_bytes", "lbs_create",
            "lbs_init_fields", "lbs_step", "lbs_sync", "lbs_get_fields",
