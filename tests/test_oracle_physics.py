@@ -241,3 +241,78 @@ def test_adsorption_first_step_uptake():
     assert total == pytest.approx(uptake, rel=1e-11)
     # geometry-free initial slope of Eq. 30: d(psi/psi_inf)/dt = r_a C at the interface
     assert uptake > 0
+
+
+# ---- D3Q19 (App. A, Eqs. 39-41) ---------------------------------------------
+
+def test_shear_wave_decay_3d_heavy_phase():
+    """3D single-phase limit: u_x = U sin(k y) decays at nu = mu/rho, for the
+    heavy phase of a density ratio 10 (alpha from Eq. 42, c_s^2 = 1/30 in 3D
+    with (c_s^k)^2 = (1/2)(1 - alpha^k))."""
+    n = 32
+    c, phi = _single_phase(2, n, red=False, rho_ratio=10.0, mu=0.05, nz=2)
+    y = np.arange(n)[None, :, None] * np.ones((2, 1, 2))
+    k = 2 * np.pi / n
+    u = np.zeros((3, 2, n, 2))
+    u[0] = 1e-4 * np.sin(k * y)
+    o = Oracle(c)
+    o.init_fields(phi, np.zeros_like(phi), np.zeros_like(phi), u)
+    amp = []
+    for t in (0, 100, 300):
+        o.step(t - o.step_count)
+        amp.append(2 * np.mean(o.fields()["u"][0, 0, :, 0] * np.sin(k * np.arange(n))))
+    nu = -np.log(amp[2] / amp[1]) / (200 * k * k)
+    assert nu == pytest.approx(0.05, rel=2e-2)
+
+
+def test_sound_speed_3d():
+    """3D: (c_s^k)^2 = (1/2)(1 - alpha^k); standing sound wave period."""
+    n = 48
+    c, phi = _single_phase(n, 2, red=False, rho_ratio=10.0, mu=0.02, nz=2)
+    o = Oracle(c)
+    x = np.arange(n)
+    k = 2 * np.pi / n
+    u = np.zeros((3, 2, 2, n))
+    u[0] = 1e-4 * np.sin(k * x)
+    o.init_fields(phi, np.zeros_like(phi), np.zeros_like(phi), u)
+    cs2 = 0.5 * (1 - c["alphaB"])
+    T = 2 * np.pi / (math.sqrt(cs2) * k)
+    amps = []
+    for t in range(int(0.9 * T)):
+        amps.append(np.mean(o.fields()["u"][0, 0, 0] * np.sin(k * x)))
+        o.step(1)
+    amps = np.array(amps)
+    z = [i + amps[i] / (amps[i] - amps[i + 1])
+         for i in range(len(amps) - 1) if amps[i] * amps[i + 1] < 0]
+    assert 2 * (z[1] - z[0]) == pytest.approx(T, rel=3e-3)
+
+
+def droplet_3d(n=(14, 12, 12), R=3.5, **kw):
+    c = W.droplet_adsorption_2d(n=n[0], R=R, C0=0.5)
+    c.update(ny=n[1], nz=n[2], alphaR=1 / 3, alphaB=1 / 3,
+             center=[(n[0] - 1) / 2, (n[1] - 1) / 2, (n[2] - 1) / 2])
+    c.update(kw)
+    return c
+
+
+def test_mirror_symmetry_and_conservation_3d():
+    """A droplet centred between walls moving with opposite velocities along
+    x (Sec. 3.3 set-up, 3D): the flow is symmetric under the point reflection
+    (x, z) -> (-x, -z) and under y -> -y; colour masses and the total
+    surfactant are conserved."""
+    cfg = droplet_3d(wall=[0, 0, 1], uw_lo=[[0] * 3, [0] * 3, [-0.01, 0, 0]],
+                     uw_hi=[[0] * 3, [0] * 3, [0.01, 0, 0]])
+    o = run(cfg)
+    d0 = o.diagnostics()
+    o.step(12)
+    d = o.diagnostics()
+    f = o.fields()
+    for k in ("rho", "phi", "psi", "C"):
+        a = f[k]
+        assert np.abs(a - a[::-1, :, ::-1]).max() <= 1e-11 * np.abs(a).max(), k
+        assert np.abs(a - a[:, ::-1, :]).max() <= 1e-11 * np.abs(a).max(), k
+    ux = f["u"][0]
+    assert np.abs(ux + ux[::-1, :, ::-1]).max() <= 1e-11 * np.abs(ux).max()
+    assert np.abs(ux).max() > 1e-3  # the walls drive a shear flow
+    for k in ("mass_R", "mass_B", "surf_total"):
+        assert abs(d[k] - d0[k]) <= 1e-12 * d0[k], k
