@@ -45,6 +45,15 @@ ALG_BYTES_F32 = {"force": 44, "fd": 48, "collide": 176, "stream": 172, "grad": 2
 # read once, psi and C written once, whatever the sweeps it runs in shared memory
 SOR_BYTES_PER_ROUND_F32 = 32
 
+# D3Q19: fixed bytes per cell of each group (FP32 fields, flags) and the
+# number of populations it reads plus writes (stored in the storage type)
+ALG3_FIXED = {"force": 60, "fd": 52, "collide": 46, "stream": 34, "grad": 32, "surf": 32}
+ALG3_POPS = {"collide": 76, "stream": 76}
+# one red or black half-sweep: psi, C, a, chi of every cell read, the two
+# right-hand sides read and psi, C written for half of the cells
+SOR3_BYTES_PER_HALF_SWEEP = 24
+POP_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture of the source tree with this hash on this workload
 # (profiles/step_bubble_rise_256x1024_f32.md); reported only while the
@@ -149,6 +158,56 @@ class Clocks:
                 "samples": len(self.rows), "source": "nvml" if self.nv is not None else "nvidia-smi"}
 
 
+def workload3d():
+    """The 3D sheared droplet: D3Q19 256 x 128 x 128, walls at z moving
+    along +-x, droplet radius 24, viscosity ratio 1, Ca = 0.2, C0 = 0.5, psi
+    at its Langmuir equilibrium; bfloat16 populations with FP32 collision is
+    the form this configuration names (FP32 and FP16 timed beside it)."""
+    cfg = W.shear_droplet_3d()
+    return cfg, "shear_droplet_3d_256x128x128_Ca0.2"
+
+
+def roofline3(kmean, cells, storage, rounds, hbm, src):
+    """Roofline of the dominant kernel group of the 3D step (bytes as above;
+    the SOR group's launch is one half-sweep, two per round)."""
+    sc = 2 if storage == "f64" else 1
+    pb = POP_BYTES[storage]
+    dom = max(kmean, key=lambda g: kmean[g])
+    if dom == "sor":
+        alg = SOR3_BYTES_PER_HALF_SWEEP * sc * cells
+        launch_ms = kmean[dom] / (2 * rounds)
+    else:
+        alg = (ALG3_FIXED[dom] * sc + ALG3_POPS.get(dom, 0) * pb) * cells
+        launch_ms = kmean[dom]
+    achieved = alg / (launch_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+            "peak_source": src, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+            "alg_bytes_per_launch": alg, "avg_launch_ms": launch_ms}
+
+
+def time_steps(s, stream, flush, warmup, steps, torch, profiled=True):
+    """Device time of `steps` steps of solver s (after `warmup`), each timed
+    with CUDA events on the solver's stream after an L2 flush outside them;
+    per-group times from the in-graph events when profiling is on."""
+    tt, kts = 0.0, []
+    for k in range(warmup + steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.step(1)
+            b.record(stream)
+        b.synchronize()
+        if k >= warmup:
+            tt += a.elapsed_time(b)
+            if profiled:
+                kts.append(s.kernel_times())
+    s.sync()
+    kmean = {g: float(np.mean([k[g] for k in kts])) for g in kts[0]} if kts else {}
+    return tt, kmean
+
+
 def workload():
     cfg = W.bubble_rise_2d()
     name = ("bubble_rise_2d D2Q9 256x1024 walls-x periodic-y, D=64, rho 0.1/1, "
@@ -213,6 +272,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip timing the other population storage forms")
+    ap.add_argument("--no-3d", action="store_true",
+                    help="skip the D3Q19 (3D sheared droplet) measurement")
+    ap.add_argument("--steps3", type=int, default=20,
+                    help="timed steps of each 3D storage form")
     ap.add_argument("--eager", action="store_true",
                     help="individual kernel launches instead of one graph per step "
                          "(for kernel profilers)")
@@ -333,21 +396,33 @@ def main():
                 continue
             s2 = Solver(cfg, storage=st, stream=stream)
             s2.init_fields(f["phi"], f["psi"], f["C"], f["u"])
-            tt = 0.0
-            for k in range(args.warmup + args.steps):
-                with torch.cuda.stream(stream):
-                    flush.fill_(1)
-                    a = torch.cuda.Event(enable_timing=True)
-                    b = torch.cuda.Event(enable_timing=True)
-                    a.record(stream)
-                    s2.step(1)
-                    b.record(stream)
-                b.synchronize()
-                if k >= args.warmup:
-                    tt += a.elapsed_time(b)
-            s2.sync()
+            tt, _ = time_steps(s2, stream, flush, args.warmup, args.steps, torch, profiled=False)
             forms[st] = cells * args.steps / (tt / 1e3) / 1e6
             s2.close()
+
+    # the D3Q19 configuration (3D sheared droplet), each storage form
+    d3 = None
+    if rank == 0 and not args.no_3d:
+        cfg3, name3 = workload3d()
+        cells3 = cfg3["nx"] * cfg3["ny"] * cfg3["nz"]
+        f3 = W.initial_fields(cfg3)
+        d3 = {"workload": name3, "cells": cells3, "storage": "bf16", "mlups": {},
+              "ms_per_step": {}, "steps": args.steps3, "warmup": args.warmup}
+        for st in ("bf16", "f32", "f16"):
+            s3 = Solver(cfg3, storage=st, stream=stream)
+            s3.init_fields(f3["phi"], f3["psi"], f3["C"], f3["u"])
+            s3.profile(True)
+            tt, km = time_steps(s3, stream, flush, args.warmup, args.steps3, torch)
+            d3["mlups"][st] = cells3 * args.steps3 / (tt / 1e3) / 1e6
+            d3["ms_per_step"][st] = tt / args.steps3
+            if st == "bf16":
+                dg3 = s3.diagnostics()
+                r3 = max(dg3["sor_rounds"], 1)
+                d3["kernel_ms"] = km
+                d3["sor_sweeps"] = dg3["sor_iters_psi"]
+                d3["roofline"] = roofline3(km, cells3, st, r3, hbm, src)
+                d3["gpu_launches_per_step"] = s3.kernel_count()
+            s3.close()
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
@@ -359,7 +434,7 @@ def main():
                       "parallelism": f"replicas x{world}" if world > 1 else "single"},
            "roofline": roof, "kernel_ms": kmean, "sor_sweeps": sweeps, "sor_rounds": rounds,
            "gpu_launches": args.steps * s.kernel_count(),
-           "forms_mlups": forms,
+           "forms_mlups": forms, "d3q19": d3,
            "clocks": clk, "e2e": e2e, "impl": "lbs", "src_sha": sha}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, name)

@@ -4,9 +4,10 @@
  * arXiv 2311.15242).
  *
  * One call of lbs_step advances the coupled update of the paper by one time
- * step on the GPU:
+ * step on the GPU, on a D2Q9 (nz == 1) or D3Q19 (nz > 1) lattice:
  *   Sec. 2.1   colour-gradient LB step: MRT collision with the correction
- *              term and the forcing term (Eqs. 1-4, App. A Eqs. 36-43), the
+ *              term and the forcing term (Eqs. 1-4, App. A Eqs. 36-43: D2Q9
+ *              Eqs. 36-38, D3Q19 Eqs. 39-41), the
  *              interfacial force from the modified Langmuir equation of state
  *              with the Marangoni term (Eqs. 5-9), the velocity of Eq. 10,
  *              recolouring (Eqs. 11-12), streaming with half-way bounce-back
@@ -65,7 +66,9 @@ typedef enum {
 /* Physical and numerical parameters (one instance).  Names follow the paper:
  * red = droplet/bubble (rho^N = +1), blue = surfactant-laden liquid. */
 typedef struct {
-    int nx, ny, nz;           /* grid; nz == 1 selects D2Q9 (2D) */
+    int nx, ny, nz;           /* grid; nz == 1 selects D2Q9 (2D), nz > 1 D3Q19;
+                                 3D: every periodic axis of even length (the
+                                 red-black SOR updates in place) */
     int wall[3];              /* per axis: 0 periodic, 1 half-way bounce-back
                                  walls at both ends (Secs. 3.2-3.4, ref. [57]) */
     double uw_lo[3][3];       /* velocity of the low wall of each axis (Sec. 3.3) */
@@ -104,8 +107,13 @@ typedef struct {
     double umax;                /* max |u| */
     double Re;                  /* 2 rhoB0 |U_v| R / muB0, R from the red area/volume */
     int sor_iters_psi, sor_iters_C; /* sweeps used by the last solve */
-    int sor_rounds;             /* blocked SOR launches of the last solve */
+    int sor_rounds;             /* SOR rounds of the last solve: 2D one blocked
+                                   launch of 2 sweeps, 3D one red-black sweep */
     long long step;             /* time steps taken since lbs_init_fields */
+    double deformation;         /* Taylor deformation (L-B)/(L+B) of rhoN >= 0 from
+                                   its principal second moments in the x-y plane
+                                   (2D) or x-z plane (3D; Sec. 3.3 shear set-up) */
+    double inclination;         /* angle of the major axis from x in that plane (rad) */
 } lbs_diag;
 
 typedef struct lbs_ctx lbs_ctx;

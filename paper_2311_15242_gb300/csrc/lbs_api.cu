@@ -11,7 +11,9 @@
 #include <new>
 
 #include "../../include/lbs.h"
+#include "lbs_d3q19.cuh"
 #include "lbs_k2d.cuh"
+#include "lbs_launch3.h"
 
 using namespace lbs;
 
@@ -31,6 +33,13 @@ void rest_eq9(double rho, double al, double *f) {
         for (int j = 0; j < Q9; j++) s += double(m9(j, i)) * m[j] / double(mnorm9(j));
         f[i] = s;
     }
+}
+
+// the same for D3Q19 (Eq. 40 at u = 0 through the closed-form inverse)
+void rest_eq19(double rho, double al, double *f) {
+    double m[Q19];
+    meq19<double>(rho, 0.0, 0.0, 0.0, al, m);
+    minv19<double>(m, f);
 }
 
 struct Base {
@@ -89,16 +98,20 @@ struct Layout {
     int nblocks;
 };
 
+// scalar planes: 21 in 2D, 25 in 3D (z components of j, grad, u, F)
+constexpr int kScal2 = 21, kScal3 = 25;
+
 template <typename R, typename P>
 Layout layout_of(const lbs_params *p) {
     Layout L;
+    const bool d3 = p->nz > 1;
     L.pitch = (int)align_up(p->nx, 32);
     L.plane = (long long)align_up((size_t)L.pitch * p->ny * p->nz, 128);
     size_t pb = (size_t)L.plane * sizeof(R);
     L.pops_off = 0;
-    size_t pops = 4 * (size_t)Q9 * (size_t)L.plane * sizeof(P);
+    size_t pops = 4 * (size_t)(d3 ? Q19 : Q9) * (size_t)L.plane * sizeof(P);
     L.scal_off = pops;
-    size_t scal = 21 * pb;
+    size_t scal = (d3 ? kScal3 : kScal2) * pb;
     L.flag_off = align_up(L.scal_off + scal, 256);
     L.ctl_off = align_up(L.flag_off + 2 * (size_t)L.plane, 256);
     L.part_off = align_up(L.ctl_off + sizeof(Ctl), 256);
@@ -124,7 +137,9 @@ struct Solver : Base {
     cudaEvent_t ev[LBS_K_NGROUPS + 1] = {};
     bool ran[LBS_K_NGROUPS] = {};
 
-    Solver(lbs_ctx *c) : ctx(c) {
+    const int D, Q;
+
+    Solver(lbs_ctx *c) : ctx(c), D(c->p.nz > 1 ? 3 : 2), Q(c->p.nz > 1 ? Q19 : Q9) {
         const lbs_params *p = &c->p;
         L = layout_of<R, P>(p);
         ws = (char *)c->ws;
@@ -146,8 +161,10 @@ struct Solver : Base {
         I.rhoB0 = R(p->rhoB0);
         I.alphaR = R(p->alphaR);
         I.alphaB = R(p->alphaB);
-        I.cs2R = R(0.6 * (1.0 - p->alphaR));
-        I.cs2B = R(0.6 * (1.0 - p->alphaB));
+        // (c_s^k)^2 = (3/5)(1 - alpha^k) in 2D, (1/2)(1 - alpha^k) in 3D (App. A)
+        const double cf = D == 2 ? 0.6 : 0.5;
+        I.cs2R = R(cf * (1.0 - p->alphaR));
+        I.cs2B = R(cf * (1.0 - p->alphaB));
         I.muR0 = R(p->muR0);
         I.muB0 = R(p->muB0);
         I.beta = R(p->beta);
@@ -183,11 +200,16 @@ struct Solver : Base {
         }
         // rest states of the pure phases; their moving components agree when
         // rhoR0 (1 - alphaR) = rhoB0 (1 - alphaB) (Eq. 42); the blue ones are used
-        double sB[Q9], sR[Q9];
-        rest_eq9(p->rhoB0, p->alphaB, sB);
-        rest_eq9(p->rhoR0, p->alphaR, sR);
+        double sB[Q19], sR[Q19];
+        if (D == 2) {
+            rest_eq9(p->rhoB0, p->alphaB, sB);
+            rest_eq9(p->rhoR0, p->alphaR, sR);
+        } else {
+            rest_eq19(p->rhoB0, p->alphaB, sB);
+            rest_eq19(p->rhoR0, p->alphaR, sR);
+        }
         double mov = 0;
-        for (int i = 0; i < Q9; i++) {
+        for (int i = 0; i < Q; i++) {
             I.shift[i] = R(sB[i]);
             if (i) mov += double(I.shift[i]);
         }
@@ -199,34 +221,55 @@ struct Solver : Base {
             double rk = f ? p->rhoR0 : p->rhoB0, ak = f ? p->alphaR : p->alphaB;
             I.dsh[f] = R(tot - rk);
             double e1 = 0, e2 = 0;
-            for (int i = 0; i < Q9; i++) {
+            for (int i = 0; i < Q; i++) {
                 double si = i ? double(I.shift[i]) : double(I.shift0[f]);
-                e1 += double(m9(1, i)) * si;
-                e2 += double(m9(2, i)) * si;
+                e1 += double(D == 2 ? m9(1, i) : m19(4, i)) * si;
+                e2 += double(D == 2 ? m9(2, i) : m19(16, i)) * si;
             }
-            I.mcor1[f] = R(e1 - rk * (-3.6 * ak - 0.4));
-            I.mcor2[f] = R(e2 - rk * (5.4 * ak - 1.4));
+            if (D == 2) {
+                I.mcor1[f] = R(e1 - rk * (-3.6 * ak - 0.4));
+                I.mcor2[f] = R(e2 - rk * (5.4 * ak - 1.4));
+            } else {
+                const double pk = rk * 0.5 * (1.0 - ak);
+                I.mcor1[f] = R(e1 - 3.0 * pk);
+                I.mcor2[f] = R(e2 - pk / 3.0);
+            }
         }
+        I.sor_pingpong = D == 2;
         size_t pb = (size_t)L.plane;
         P *pops = (P *)(ws + L.pops_off);
         I.fT = pops;
-        I.fM = pops + 1 * Q9 * pb;
-        I.gT = pops + 2 * Q9 * pb;
-        I.gM = pops + 3 * Q9 * pb;
+        I.fM = pops + 1 * Q * pb;
+        I.gT = pops + 2 * Q * pb;
+        I.gM = pops + 3 * Q * pb;
         I.flag = (uint8_t *)(ws + L.flag_off);
         I.gflag = I.flag + L.plane;
         R *sc = (R *)(ws + L.scal_off);
         R **fields[] = {&I.rhoR, &I.rhoB, &I.rhoN, &I.jx,  &I.jy,  &I.gx,  &I.gy,
                         &I.a,    &I.chi,  &I.ux,   &I.uy,  &I.Fx,  &I.Fy,  &I.psi,
                         &I.C,    &I.S,    &I.B,    &I.rpsi, &I.rC, &I.psi2, &I.C2};
-        for (int k = 0; k < 21; k++) *fields[k] = sc + k * pb;
+        for (int k = 0; k < kScal2; k++) *fields[k] = sc + k * pb;
+        if (D == 3) {
+            R **f3[] = {&I.jz, &I.gz, &I.uz, &I.Fz};
+            for (int k = 0; k < kScal3 - kScal2; k++) *f3[k] = sc + (kScal2 + k) * pb;
+        }
         I.ctl = (Ctl *)(ws + L.ctl_off);
         I.part = (double *)(ws + L.part_off);
         stage = (double *)(ws + L.stage_off);
         block = dim3(BX, BY, 1);
-        grid = dim3((p->nx + BX - 1) / BX, (p->ny + BY - 1) / BY, 1);
-        sor_grid = dim3((p->nx + STX - 1) / STX, (p->ny + STY - 1) / STY, 1);
-        surf_grid = dim3((p->nx + BX - 1) / BX, (p->ny + BY * SURF_STRIP - 1) / (BY * SURF_STRIP), 1);
+        grid = dim3((p->nx + BX - 1) / BX, (p->ny + BY - 1) / BY, p->nz);
+        if (D == 2) {
+            sor_grid = dim3((p->nx + STX - 1) / STX, (p->ny + STY - 1) / STY, 1);
+        } else {
+            // red-black half-sweeps: one thread per cell pair along x
+            using L3 = Launch3<R, P>;
+            const int hx = (p->nx + 1) / 2;
+            sor_grid = dim3((hx + L3::kSorBX - 1) / L3::kSorBX,
+                            (p->ny + L3::kSorBY - 1) / L3::kSorBY, p->nz);
+        }
+        const long long rows = (long long)p->ny * p->nz;
+        surf_grid = dim3((p->nx + BX - 1) / BX,
+                         (unsigned)((rows + BY * SURF_STRIP - 1) / (BY * SURF_STRIP)), 1);
         surf_blocks = (int)(surf_grid.x * surf_grid.y);
         using T = SorTile<R, STX, STY, SK, SBS>;
         cudaFuncSetAttribute(k_sor_tb2<R, STX, STY, SK, SBS>,
@@ -283,33 +326,51 @@ struct Solver : Base {
     // launches of one step; inside a capture the SOR loop becomes the WHILE
     // node, outside it a host loop of sor_rounds() launches that return at
     // once after the round that converged
+    using L3 = Launch3<R, P>;
+    void k_force(cudaStream_t s) {
+        if (D == 2)
+            k_force2<R><<<grid, block, 0, s>>>(I);
+        else
+            L3::force(I, grid, block, s);
+    }
+
     int enqueue_step(cudaStream_t s) {
         for (bool &r : ran) r = false;
         mark(s, LBS_K_FORCE);
-        k_force2<R><<<grid, block, 0, s>>>(I);
+        k_force(s);
         ran[LBS_K_FORCE] = true;
         mark(s, LBS_K_FD);
         if (I.transport) {
-            k_fd2<R><<<grid, block, 0, s>>>(I);
+            if (D == 2)
+                k_fd2<R><<<grid, block, 0, s>>>(I);
+            else
+                L3::fd(I, grid, block, s, nullptr, nullptr);
             ran[LBS_K_FD] = true;
         }
         mark(s, LBS_K_COLLIDE);
-        k_collide2<R, P><<<grid, block, 0, s>>>(I);
+        if (D == 2)
+            k_collide2<R, P><<<grid, block, 0, s>>>(I);
+        else
+            L3::collide(I, grid, block, s);
         ran[LBS_K_COLLIDE] = true;
         mark(s, LBS_K_STREAM);
-        k_stream2<R, P><<<grid, block, 0, s>>>(I);
+        if (D == 2)
+            k_stream2<R, P><<<grid, block, 0, s>>>(I);
+        else
+            L3::stream(I, grid, block, s);
         ran[LBS_K_STREAM] = true;
         mark(s, LBS_K_GRAD);
-        k_grad2<R><<<grid, block, 0, s>>>(I);
+        if (D == 2)
+            k_grad2<R><<<grid, block, 0, s>>>(I);
+        else
+            L3::grad(I, grid, block, s);
         ran[LBS_K_GRAD] = true;
         mark(s, LBS_K_SOR);
         if (I.transport && !capturing) {
             // eager form (for profilers): the host reads the loop state after
             // every round and launches no round beyond the converged one
-            using T = SorTile<R, STX, STY, SK, SBS>;
             for (int r = 0; r < sor_rounds(); r++) {
-                k_sor_tb2<R, STX, STY, SK, SBS><<<sor_grid, SBS, T::smem_bytes(), s>>>(
-                    I, cudaGraphConditionalHandle(0), sor_rounds(), r);
+                launch_sor_round(s, cudaGraphConditionalHandle(0), r);
                 int done = 0;
                 CK(cudaMemcpyAsync(&done, &I.ctl->sor_exec, sizeof(int), cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
@@ -332,24 +393,42 @@ struct Solver : Base {
             cudaGraphNode_t cnode;
             CK(cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &cp));
             cudaGraph_t body = cp.conditional.phGraph_out[0];
-            using T = SorTile<R, STX, STY, SK, SBS>;
             int maxr = sor_rounds(), eager = -1;
-            void *args[] = {(void *)&I, (void *)&h, (void *)&maxr, (void *)&eager};
-            cudaKernelNodeParams kp = {};
-            kp.func = (void *)k_sor_tb2<R, STX, STY, SK, SBS>;
-            kp.gridDim = sor_grid;
-            kp.blockDim = dim3(SBS, 1, 1);
-            kp.sharedMemBytes = (unsigned)T::smem_bytes();
-            kp.kernelParams = args;
-            cudaGraphNode_t kn;
-            CK(cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp));
+            if (D == 2) {
+                using T = SorTile<R, STX, STY, SK, SBS>;
+                void *args[] = {(void *)&I, (void *)&h, (void *)&maxr, (void *)&eager};
+                cudaKernelNodeParams kp = {};
+                kp.func = (void *)k_sor_tb2<R, STX, STY, SK, SBS>;
+                kp.gridDim = sor_grid;
+                kp.blockDim = dim3(SBS, 1, 1);
+                kp.sharedMemBytes = (unsigned)T::smem_bytes();
+                kp.kernelParams = args;
+                cudaGraphNode_t kn;
+                CK(cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp));
+            } else {
+                // body: red half-sweep, then black half-sweep
+                cudaGraphNode_t kn[2];
+                for (int colour = 0; colour < 2; colour++) {
+                    int col = colour;
+                    void *args[] = {(void *)&I, (void *)&col, (void *)&h, (void *)&maxr,
+                                    (void *)&eager};
+                    cudaKernelNodeParams kp = {};
+                    kp.func = L3::sor_fn();
+                    kp.gridDim = sor_grid;
+                    kp.blockDim = dim3(L3::kSorBX, L3::kSorBY, 1);
+                    kp.sharedMemBytes = 0;
+                    kp.kernelParams = args;
+                    CK(cudaGraphAddKernelNode(&kn[colour], body, colour ? &kn[0] : nullptr,
+                                              colour ? 1 : 0, &kp));
+                }
+            }
             CK(cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1,
                                                    cudaStreamSetCaptureDependencies));
             ran[LBS_K_SOR] = true;
         }
         mark(s, LBS_K_SURF);
         if (I.transport) {
-            k_surf2<R, BS><<<surf_grid, block, 0, s>>>(I, 1, surf_blocks, SK);
+            k_surf2<R, BS><<<surf_grid, block, 0, s>>>(I, 1, surf_blocks, sweeps_per_round());
             k_scale2<R><<<grid, block, 0, s>>>(I);
         } else {
             k_tick<R><<<1, 32, 0, s>>>(I);
@@ -359,17 +438,36 @@ struct Solver : Base {
         return launch_check();
     }
 
+    // one SOR round outside a graph (eager mode): 2D one blocked launch of SK
+    // sweeps, 3D a red and a black half-sweep
+    void launch_sor_round(cudaStream_t s, cudaGraphConditionalHandle h, int r) {
+        if (D == 2) {
+            using T = SorTile<R, STX, STY, SK, SBS>;
+            k_sor_tb2<R, STX, STY, SK, SBS><<<sor_grid, SBS, T::smem_bytes(), s>>>(
+                I, h, sor_rounds(), r);
+        } else {
+            const dim3 b(L3::kSorBX, L3::kSorBY, 1);
+            L3::sor(I, sor_grid, b, s, 0, h, sor_rounds(), r);
+            L3::sor(I, sor_grid, b, s, 1, h, sor_rounds(), r);
+        }
+    }
+
+    int sweeps_per_round() const { return D == 2 ? SK : 1; }
+
     int set_graph(int on) override {
         use_graph = bool(on);
         return LBS_OK;
     }
 
-    int sor_rounds() const { return (I.sor_max_iter + SK - 1) / SK; }
+    int sor_rounds() const {
+        return (I.sor_max_iter + sweeps_per_round() - 1) / sweeps_per_round();
+    }
 
-    // kernels of one step: the SOR loop is counted at its typical 4 rounds
-    // (the exact count of a step is sor_iters / 3 from the diagnostics)
+    // kernels of one step with the SOR loop at the round count of the last
+    // diagnostics (4 before the first): 2D one launch a round, 3D two
     int kernel_count() const override {
-        return I.transport ? 7 + last_rounds : 4;
+        const int per_round = D == 2 ? 1 : 2;
+        return I.transport ? 7 + per_round * last_rounds : 4;
     }
     int last_rounds = 4;
 
@@ -412,11 +510,18 @@ struct Solver : Base {
         if (u) CK(cudaMemcpyAsync(du, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(ws + L.pops_off, 0, L.ctl_off - L.pops_off, s));
         CK(cudaMemsetAsync(I.ctl, 0, sizeof(Ctl), s));
-        k_init2<R, P><<<grid, block, 0, s>>>(I, dphi, psi ? dpsi : nullptr, C ? dC : nullptr,
-                                          u ? du : nullptr);
-        k_moments2<R, P><<<grid, block, 0, s>>>(I);
-        k_grad2<R><<<grid, block, 0, s>>>(I);
-        k_surf2<R, BS><<<surf_grid, block, 0, s>>>(I, 0, surf_blocks, SK);
+        if (D == 2) {
+            k_init2<R, P><<<grid, block, 0, s>>>(I, dphi, psi ? dpsi : nullptr,
+                                              C ? dC : nullptr, u ? du : nullptr);
+            k_moments2<R, P><<<grid, block, 0, s>>>(I);
+            k_grad2<R><<<grid, block, 0, s>>>(I);
+        } else {
+            L3::init(I, grid, block, s, dphi, psi ? dpsi : nullptr, C ? dC : nullptr,
+                     u ? du : nullptr);
+            L3::moments(I, grid, block, s);
+            L3::grad(I, grid, block, s);
+        }
+        k_surf2<R, BS><<<surf_grid, block, 0, s>>>(I, 0, surf_blocks, sweeps_per_round());
         int r = launch_check();
         if (r) return r;
         CK(cudaStreamSynchronize(s));
@@ -476,7 +581,7 @@ struct Solver : Base {
         if (r) return r;
         size_t N = (size_t)I.nx * I.ny * I.nz;
         cudaStream_t s = ctx->stream;
-        k_force2<R><<<grid, block, 0, s>>>(I);
+        k_force(s);
         k_export2<R><<<grid, block, 0, s>>>(I, stage, stage + N, stage + 4 * N, stage + 5 * N,
                                             stage + 6 * N);
         r = launch_check();
@@ -495,11 +600,14 @@ struct Solver : Base {
         if (r) return r;
         size_t N = (size_t)I.nx * I.ny * I.nz;
         cudaStream_t s = ctx->stream;
-        k_force2<R><<<grid, block, 0, s>>>(I);
+        k_force(s);
         double *dg = stage, *da = stage + 3 * N, *dF = stage + 4 * N, *du = stage + 7 * N,
                *dS = stage + 10 * N, *dB = stage + 11 * N;
         k_export_macro2<R><<<grid, block, 0, s>>>(I, dg, da, dF, du);
-        k_fd2<R><<<grid, block, 0, s>>>(I, dS, dB);
+        if (D == 2)
+            k_fd2<R><<<grid, block, 0, s>>>(I, dS, dB);
+        else
+            L3::fd(I, grid, block, s, dS, dB);
         r = launch_check();
         if (r) return r;
         struct {
@@ -516,8 +624,11 @@ struct Solver : Base {
         int r = sync();
         if (r) return r;
         cudaStream_t s = ctx->stream;
-        k_force2<R><<<grid, block, 0, s>>>(I);
-        k_diag2<R, P, BS><<<grid, block, 0, s>>>(I, L.nblocks);
+        k_force(s);
+        if (D == 2)
+            k_diag<R, P, BS, Q9><<<grid, block, 0, s>>>(I, L.nblocks);
+        else
+            L3::diag(I, grid, block, s, L.nblocks);
         r = launch_check();
         if (r) return r;
         Ctl h;
@@ -553,6 +664,21 @@ struct Solver : Base {
             d->aspect_ratio = I2[vert] > 0 ? std::sqrt(I2[hor] / I2[vert]) : 0.0;
             double rad = D == 2 ? std::sqrt(cnt / M_PI) : std::cbrt(3 * cnt / (4 * M_PI));
             d->Re = 2 * p->rhoB0 * std::fabs(d->U[vert]) * rad / p->muB0;
+            // Taylor deformation (L - B)/(L + B) and inclination of the major
+            // axis in the x-y plane (2D) or x-z plane (3D: walls at z moving
+            // along x), from the principal second moments of the red region
+            const double cx = d->centroid[0], cb = D == 2 ? d->centroid[1] : d->centroid[2];
+            const double Iaa = v[8] - cnt * cx * cx;
+            const double Ibb = (D == 2 ? v[9] : v[17]) - cnt * cb * cb;
+            const double Iab = (D == 2 ? v[19] : v[18]) - cnt * cx * cb;
+            const double tr = 0.5 * (Iaa + Ibb);
+            const double dd = std::sqrt(0.25 * (Iaa - Ibb) * (Iaa - Ibb) + Iab * Iab);
+            const double l1 = tr + dd, l2 = tr - dd;
+            if (l2 > 0) {
+                const double L = std::sqrt(l1), B = std::sqrt(l2);
+                d->deformation = (L - B) / (L + B);
+            }
+            d->inclination = 0.5 * std::atan2(2 * Iab, Iaa - Ibb);
         }
         if (v[11] > 0) {
             d->psi_av = v[10] / v[11];
@@ -561,20 +687,34 @@ struct Solver : Base {
         }
         d->umax = v[NDIAG + 2];
         d->sor_iters_psi = d->sor_iters_C = h.sor_iters;
-        d->sor_rounds = h.sor_iters / SK;
-        if (h.sor_iters > 0) last_rounds = h.sor_iters / SK;
+        d->sor_rounds = h.sor_iters / sweeps_per_round();
+        if (h.sor_iters > 0) last_rounds = h.sor_iters / sweeps_per_round();
         d->step = h.step;
         return LBS_OK;
     }
 };
 
 int validate(const lbs_params *p, char *err, size_t n) {
-    if (p->nx < 1 || p->ny < 1 || p->nz != 1) {
-        snprintf(err, n, "grid %dx%dx%d: only 2D (nz == 1) grids are supported", p->nx, p->ny, p->nz);
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) {
+        snprintf(err, n, "grid %dx%dx%d: every size must be positive", p->nx, p->ny, p->nz);
+        return LBS_EINVAL;
+    }
+    if ((long long)p->nx * p->ny * p->nz > (1LL << 31) - 1) {
+        snprintf(err, n, "grid %dx%dx%d: more than 2^31 - 1 cells", p->nx, p->ny, p->nz);
+        return LBS_EINVAL;
+    }
+    if (p->nz == 1 && p->wall[2]) {
+        snprintf(err, n, "a 2D grid (nz == 1) cannot have walls on z");
         return LBS_EINVAL;
     }
     int dims[3] = {p->nx, p->ny, p->nz};
     for (int a = 0; a < 3; a++) {
+        // 3D red-black SOR updates in place: a periodic axis of odd length
+        // would make cells of one colour neighbours across the seam
+        if (p->nz > 1 && !p->wall[a] && (dims[a] & 1)) {
+            snprintf(err, n, "3D grids need an even size on periodic axis %d (got %d)", a, dims[a]);
+            return LBS_EINVAL;
+        }
         if (p->wall[a] && dims[a] < 3) {
             snprintf(err, n, "walled axis %d needs at least 3 nodes", a);
             return LBS_EINVAL;

@@ -88,7 +88,8 @@ struct Ctl {
 // ---------------------------------------------------------------------------
 template <typename R>
 struct Inst {
-    int nx, ny, nz, pitch;   // pitch: elements per row (>= nx)
+    int nx, ny, nz, pitch;   // pitch: elements per row (>= nx); cell (x, y, z) at
+                             // (z ny + y) pitch + x
     long long plane;         // elements per scalar plane (pitch * ny * nz)
     int wall[3];
     R uw_lo[3][3], uw_hi[3][3];
@@ -101,14 +102,17 @@ struct Inst {
     R pscale, pinv;          // storage scale of FP16 populations (a power of 2) and 1/scale
     // shift of the stored total populations: the rest equilibrium of the pure
     // majority phase of a cell.  Its moving components are common to both
-    // phases (equal pure-phase pressures, Eq. 42): shift[1..8]; the rest
+    // phases (equal pure-phase pressures, Eq. 42): shift[1..Q-1]; the rest
     // component depends on the cell's flag: shift0[flag].  rho_s[flag] is the
     // sum of the shift, dsh[flag] = rho_s[flag] - rho^k0 of the majority phase.
-    R shift[Q9];
+    R shift[19];
     R shift0[2], rho_s[2], dsh[2];
-    // e and epsilon moments (Eq. 36) of the shift minus those of the pure
-    // majority phase at rest: rounding only, unless alpha breaks Eq. 42
+    // moments of the shift minus those of the pure majority phase at rest
+    // (rounding only, unless alpha breaks Eq. 42): D2Q9 rows e and epsilon of
+    // Eq. 36; D3Q19 row 4 (|e|^2) and rows 16-18 (x^2 y^2 type, all equal)
+    // of Eq. 39
     R mcor1[2], mcor2[2];
+    int sor_pingpong;         // SOR result alternates between psi/C and psi2/C2
     // state (device pointers; every field is `plane` elements, populations Q planes)
     // populations in the storage type P of the kernels that touch them
     // (float / double, or __half / __nv_bfloat16 for the shifted
@@ -116,9 +120,9 @@ struct Inst {
     void *fT, *fM;            // total populations minus shift, minority colour
     void *gT, *gM;            // post-collision buffers
     uint8_t *flag, *gflag;    // minority colour of a cell: 0 red, 1 blue
-    R *rhoR, *rhoB, *rhoN, *jx, *jy;
-    R *gx, *gy, *a, *chi;     // grad rhoN, |grad rhoN|, 1 - rhoN
-    R *ux, *uy, *Fx, *Fy;
+    R *rhoR, *rhoB, *rhoN, *jx, *jy, *jz;
+    R *gx, *gy, *gz, *a, *chi;  // grad rhoN, |grad rhoN|, 1 - rhoN
+    R *ux, *uy, *uz, *Fx, *Fy, *Fz;  // z components: D3Q19 only (null in 2D)
     R *psi, *C, *S, *B, *rpsi, *rC;
     R *psi2, *C2;             // second buffers of the blocked SOR rounds
     Ctl *ctl;
@@ -212,6 +216,37 @@ __device__ __forceinline__ void ghost_u2(const Inst<R> &I, int refl, int sx, int
         const R *w = sy < 0 ? I.uw_lo[1] : I.uw_hi[1];
         u0 = R(2) * w[0] - u0;
         u1 = R(2) * w[1] - u1;
+    }
+}
+
+// 3D neighbour (same wall mapping per axis; bit 4 for z)
+template <typename R>
+__device__ __forceinline__ long long nb3(const Inst<R> &I, int x, int y, int z, int dx, int dy,
+                                         int dz, int &refl, int &sx, int &sy, int &sz) {
+    refl = 0;
+    int X = map_axis(x + dx, I.nx, I.wall[0], 1, refl, sx);
+    int Y = map_axis(y + dy, I.ny, I.wall[1], 2, refl, sy);
+    int Z = map_axis(z + dz, I.nz, I.wall[2], 4, refl, sz);
+    return ((long long)Z * I.ny + Y) * I.pitch + X;
+}
+
+template <typename R>
+__device__ __forceinline__ long long cell3(const Inst<R> &I, int x, int y, int z) {
+    return ((long long)z * I.ny + y) * I.pitch + x;
+}
+
+// 3D ghost velocity: u -> 2 u_wall - u for each wall crossed
+template <typename R>
+__device__ __forceinline__ void ghost_u3(const Inst<R> &I, int refl, int sx, int sy, int sz,
+                                         R &u0, R &u1, R &u2) {
+    const int side[3] = {sx, sy, sz};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        if (!(refl & (1 << a))) continue;
+        const R *w = side[a] < 0 ? I.uw_lo[a] : I.uw_hi[a];
+        u0 = R(2) * w[0] - u0;
+        u1 = R(2) * w[1] - u1;
+        u2 = R(2) * w[2] - u2;
     }
 }
 

@@ -877,17 +877,19 @@ constexpr int SURF_STRIP = 16;
 template <typename R, int BS>
 __global__ void k_surf2(Inst<R> I, int mode, int nblocks, int sweeps_per_round) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
+    // rows of the grid: y in 2D, (z, y) pairs in 3D (row index z ny + y)
     int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * SURF_STRIP;
+    const int rows = I.ny * I.nz;
     // after an odd number of blocked SOR rounds the solution is in psi2, C2
     const int rounds = sor_rounds_done(I.ctl->sor_exec);
-    const bool alt = mode == 1 && (rounds & 1);
+    const bool alt = I.sor_pingpong && mode == 1 && (rounds & 1);
     const R *P = alt ? I.psi2 : I.psi;
     const R *Cc = alt ? I.C2 : I.C;
     R sum = R(0), comp = R(0);
     if (x < I.nx)
         for (int k = 0; k < SURF_STRIP; k++) {
             int y = y0 + k;
-            if (y >= I.ny) break;
+            if (y >= rows) break;
             long long c = (long long)y * I.pitch + x;
             R v = (I.a[c] + I.eps_w) * P[c] + (I.chi[c] + I.eps_w) * Cc[c];
             R yv = v - comp;
@@ -918,7 +920,7 @@ __global__ void k_surf2(Inst<R> I, int mode, int nblocks, int sweeps_per_round) 
     ctl->dscale_f = float(ctl->dscale);
     if (!isfinite(tot)) ctl->status |= ST_DIVERGED;
     ctl->sor_iters = rounds * sweeps_per_round;
-    ctl->sor_iters_parity = rounds & 1;
+    ctl->sor_iters_parity = I.sor_pingpong ? (rounds & 1) : 0;
     ctl->sor_exec = 0;
     for (int k = 0; k < KMAX_SWEEPS; k++)
         for (int q = 0; q < 4; q++) ctl->sweep[k][q] = 0ull;
@@ -930,7 +932,7 @@ __global__ void k_scale2(Inst<R> I) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= I.nx || y >= I.ny) return;
-    long long c = (long long)y * I.pitch + x;
+    long long c = ((long long)blockIdx.z * I.ny + y) * I.pitch + x;
     // the factor is 1 + O(1e-6): multiplying by it rounded to R would apply a
     // quantised correction with the same bias every step; x + x d with
     // d = s - 1 formed in double and one fused rounding is unbiased
@@ -953,32 +955,35 @@ __global__ void k_tick(Inst<R> I) {
 // ---------------------------------------------------------------------------
 // Diagnostics (FP64): masses, total surfactant, indicator N = [rhoN >= 0]
 // sums for U (Eqs. 33-34), centroid and second moments, interface psi stats.
+// Q = 9 (D2Q9) or 19 (D3Q19); the grid's z index is the cell's z.
 // ---------------------------------------------------------------------------
-constexpr int NDIAG = 17;
-template <typename R, typename P, int BS>
-__global__ void k_diag2(Inst<R> I, int nblocks) {
+constexpr int NDIAG = 20;
+template <typename R, typename P, int BS, int Q>
+__global__ void k_diag(Inst<R> I, int nblocks) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
     // 0 mR, 1 mB, 2 surf, 3 cnt, 4 sux, 5 suy, 6 sx, 7 sy, 8 sxx, 9 syy,
-    // 10 psum, 11 pcnt, 12 pmin(-), 13 pmax, 14 umax, 15 suz, 16 sz (2D: 0)
+    // 10 psum, 11 pcnt, 12-14 (unused), 15 suz, 16 sz, 17 szz, 18 sxz, 19 sxy
     double v[NDIAG] = {0};
     double pmin = 1e300, pmax = -1e300, umax = 0;
     if (x < I.nx && y < I.ny) {
-        long long c = (long long)y * I.pitch + x;
+        long long c = ((long long)z * I.ny + y) * I.pitch + x;
         double rN = I.rhoN[c];
         // colour masses: the exact FP64 sums of the stored populations
         // (minority as stored, majority = shift + total deviation - minority)
         const int fl = I.flag[c];
         double rmin = 0, rtot = 0;
-        for (int i = 0; i < Q9; i++) {
+        for (int i = 0; i < Q; i++) {
             rmin += double(ldp<R, P>(I, I.fM, i * I.plane + c));
-            rtot += double(shift_of(I, i, fl)) + double(ldp<R, P>(I, I.fT, i * I.plane + c));
+            rtot += double(i == 0 ? I.shift0[fl] : I.shift[i]) +
+                    double(ldp<R, P>(I, I.fT, i * I.plane + c));
         }
         v[0] = fl ? rtot - rmin : rmin;
         v[1] = fl ? rmin : rtot - rmin;
         v[2] = double(I.a[c] + I.eps_w) * double(I.psi[c]) +
                double(I.chi[c] + I.eps_w) * double(I.C[c]);
-        double ux = I.ux[c], uy = I.uy[c];
+        double ux = I.ux[c], uy = I.uy[c], uz = Q == 19 ? double(I.uz[c]) : 0.0;
         if (rN >= 0) {
             v[3] = 1;
             v[4] = ux;
@@ -987,6 +992,11 @@ __global__ void k_diag2(Inst<R> I, int nblocks) {
             v[7] = y;
             v[8] = double(x) * x;
             v[9] = double(y) * y;
+            v[15] = uz;
+            v[16] = z;
+            v[17] = double(z) * z;
+            v[18] = double(x) * z;
+            v[19] = double(x) * y;
         }
         if (fabs(rN) < 0.5) {
             double p = I.psi[c];
@@ -995,9 +1005,9 @@ __global__ void k_diag2(Inst<R> I, int nblocks) {
             pmin = p;
             pmax = p;
         }
-        umax = sqrt(ux * ux + uy * uy);
+        umax = sqrt(ux * ux + uy * uy + uz * uz);
     }
-    int b = blockIdx.x + blockIdx.y * gridDim.x;
+    int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     double s[NDIAG];
     block_sum<BS, NDIAG>(v, s);
     // min / max through a second pass on the same shared scheme
@@ -1037,24 +1047,26 @@ __global__ void k_diag2(Inst<R> I, int nblocks) {
 }
 
 // dense double copies of the intermediate fields of the current state
+// (2D and 3D: the z components are null in 2D and exported as 0)
 template <typename R>
 __global__ void k_export_macro2(Inst<R> I, double *g, double *a, double *F, double *u) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= I.nx || y >= I.ny) return;
-    long long c = (long long)y * I.pitch + x;
-    long long d = (long long)y * I.nx + x;
-    long long N = (long long)I.nx * I.ny;
+    const int z = blockIdx.z;
+    long long c = ((long long)z * I.ny + y) * I.pitch + x;
+    long long d = ((long long)z * I.ny + y) * I.nx + x;
+    long long N = (long long)I.nx * I.ny * I.nz;
     g[d] = I.gx[c];
     g[N + d] = I.gy[c];
-    g[2 * N + d] = 0.0;
+    g[2 * N + d] = I.gz ? double(I.gz[c]) : 0.0;
     a[d] = I.a[c];
     F[d] = I.Fx[c];
     F[N + d] = I.Fy[c];
-    F[2 * N + d] = 0.0;
+    F[2 * N + d] = I.Fz ? double(I.Fz[c]) : 0.0;
     u[d] = I.ux[c];
     u[N + d] = I.uy[c];
-    u[2 * N + d] = 0.0;
+    u[2 * N + d] = I.uz ? double(I.uz[c]) : 0.0;
 }
 
 // dense double copies of the macroscopic fields for the host
@@ -1064,13 +1076,14 @@ __global__ void k_export2(Inst<R> I, double *rho, double *u, double *phi, double
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= I.nx || y >= I.ny) return;
-    long long c = (long long)y * I.pitch + x;
-    long long d = (long long)y * I.nx + x;
-    long long N = (long long)I.nx * I.ny;
+    const int z = blockIdx.z;
+    long long c = ((long long)z * I.ny + y) * I.pitch + x;
+    long long d = ((long long)z * I.ny + y) * I.nx + x;
+    long long N = (long long)I.nx * I.ny * I.nz;
     rho[d] = double(I.rhoR[c]) + double(I.rhoB[c]);
     u[d] = I.ux[c];
     u[N + d] = I.uy[c];
-    u[2 * N + d] = 0.0;
+    u[2 * N + d] = I.uz ? double(I.uz[c]) : 0.0;
     phi[d] = I.rhoN[c];
     psi[d] = I.psi[c];
     C[d] = I.C[c];

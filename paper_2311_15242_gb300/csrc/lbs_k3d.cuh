@@ -1,0 +1,551 @@
+// lbs_k3d.cuh — D3Q19 kernels of the coupled LB-FD time step (arXiv
+// 2311.15242; lattice of App. A, Eqs. 39-41).
+//
+// Same storage form and kernel sequence as the D2Q9 path (lbs_k2d.cuh):
+// fT = total populations minus the rest state of the cell's majority phase,
+// fM = populations of the cell's minority colour, a flag byte per cell.  The
+// differences from 2D:
+//   - the raw-moment matrix of Eq. 39 is not orthogonal; its inverse is the
+//     closed form of lbs_d3q19.cuh;
+//   - relaxation (Eq. 41): s = 1 on every row but the five second-order
+//     shear rows 5-9, which take s_v of the mixture viscosity (Eq. 43);
+//   - the correction of Eq. 40 acts on rows 4-6 with Q^k_a =
+//     d_a{rho^k u_a [1 - 3 (c_s^k)^2]}, (c_s^k)^2 = (1 - alpha^k)/2;
+//   - the interface weights, curvature, WENO fluxes and the diffusion
+//     operator of Eq. 28 run over three axes (six faces);
+//   - SOR: red-black half-sweeps as separate launches updating psi and C in
+//     place (cells of one colour only read cells of the other colour when
+//     every periodic axis has even length, which the host checks).
+#pragma once
+
+#include "lbs_d3q19.cuh"
+#include "lbs_k2d.cuh"
+
+namespace lbs {
+
+template <typename R>
+struct Mom3 {
+    R rR, rB, drho, jx, jy, jz;
+};
+
+template <typename R>
+__device__ __forceinline__ Mom3<R> moments19(const Inst<R> &I, const R *fT, const R *fM,
+                                            int flag) {
+    Mom3<R> m{R(0), R(0), R(0), R(0), R(0), R(0)};
+    CSum<R> rmc, drc;
+#pragma unroll
+    for (int i = 0; i < Q19; i++) {
+        rmc.add(fM[i]);
+        drc.add(fT[i]);
+        if (ex19(i)) m.jx += R(ex19(i)) * fT[i];
+        if (ey19(i)) m.jy += R(ey19(i)) * fT[i];
+        if (ez19(i)) m.jz += R(ez19(i)) * fT[i];
+    }
+    const R rm = rmc.value();
+    m.drho = drc.value();
+    R rmaj = (I.rho_s[flag] - rm) + m.drho;
+    m.rR = flag ? rmaj : rm;
+    m.rB = flag ? rm : rmaj;
+    return m;
+}
+
+template <typename R>
+__device__ __forceinline__ void store_moments3(const Inst<R> &I, long long c, const R *fT,
+                                               const R *fM, int flag) {
+    Mom3<R> m = moments19(I, fT, fM, flag);
+    I.rhoR[c] = m.rR;
+    I.rhoB[c] = m.rB;
+    I.rhoN[c] = colour_fn(I, m.rR, m.rB);
+    I.jx[c] = m.jx;
+    I.jy[c] = m.jy;
+    I.jz[c] = m.jz;
+}
+
+#define LBS_CELL3                                               \
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;        \
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;        \
+    const int z = blockIdx.z;                                   \
+    if (x >= I.nx || y >= I.ny) return;                         \
+    const long long c = cell3(I, x, y, z);
+
+// initial populations f^k = M^{-1} m^{k,eq}(rho^k, u) (Eq. 40), in double
+// precision and rounded once.  Inputs: dense double arrays [nz][ny][nx].
+template <typename R, typename P>
+__global__ void k_init3(Inst<R> I, const double *phi, const double *psi, const double *C,
+                        const double *u) {
+    LBS_CELL3
+    const long long d = ((long long)z * I.ny + y) * I.nx + x;
+    const long long N = (long long)I.nx * I.ny * I.nz;
+    double ph = phi[d];
+    ph = ph > 1.0 ? 1.0 : (ph < -1.0 ? -1.0 : ph);
+    const double ux = u ? u[d] : 0.0, uy = u ? u[N + d] : 0.0, uz = u ? u[2 * N + d] : 0.0;
+    double m[Q19], fR[Q19], fB[Q19];
+    const double rR = double(I.rhoR0) * 0.5 * (1.0 + ph), rB = double(I.rhoB0) * 0.5 * (1.0 - ph);
+    meq19<double>(rR, ux, uy, uz, double(I.alphaR), m);
+    minv19<double>(m, fR);
+    meq19<double>(rB, ux, uy, uz, double(I.alphaB), m);
+    minv19<double>(m, fB);
+    const int fl = (rR / double(I.rhoR0) <= rB / double(I.rhoB0)) ? 0 : 1;
+#pragma unroll
+    for (int i = 0; i < Q19; i++) {
+        stp<R, P>(I, I.fT, i * I.plane + c, R((fR[i] + fB[i]) - double(shift_of(I, i, fl))));
+        stp<R, P>(I, I.fM, i * I.plane + c, R(fl ? fB[i] : fR[i]));
+    }
+    I.flag[c] = (uint8_t)fl;
+    I.psi[c] = psi ? R(psi[d]) : R(0);
+    I.C[c] = C ? R(C[d]) : R(0);
+    I.S[c] = R(0);
+    I.B[c] = R(0);
+}
+
+template <typename R, typename P>
+__global__ void k_moments3(Inst<R> I) {
+    LBS_CELL3
+    R fT[Q19], fM[Q19];
+#pragma unroll
+    for (int i = 0; i < Q19; i++) {
+        fT[i] = ldp<R, P>(I, I.fT, i * I.plane + c);
+        fM[i] = ldp<R, P>(I, I.fM, i * I.plane + c);
+    }
+    store_moments3(I, c, fT, fM, I.flag[c]);
+}
+
+// colour gradient by the isotropic stencil over the 18 neighbours, from the
+// colour fraction that is small on the cell's side (see k_grad2)
+template <typename R>
+__global__ void k_grad3(Inst<R> I) {
+    LBS_CELL3
+    const bool blue_side = I.rhoN[c] <= R(0);
+    R gx = R(0), gy = R(0), gz = R(0);
+#pragma unroll
+    for (int i = 1; i < Q19; i++) {
+        int refl, sx, sy, sz;
+        long long j = nb3(I, x, y, z, ex19(i), ey19(i), ez19(i), refl, sx, sy, sz);
+        R v = w19<R>(i) * frac(I, j, blue_side);
+        if (ex19(i)) gx += R(ex19(i)) * v;
+        if (ey19(i)) gy += R(ey19(i)) * v;
+        if (ez19(i)) gz += R(ez19(i)) * v;
+    }
+    const R f = blue_side ? R(6) : R(-6);  // 2 / c_s^2
+    gx *= f;
+    gy *= f;
+    gz *= f;
+    I.gx[c] = gx;
+    I.gy[c] = gy;
+    I.gz[c] = gz;
+    I.a[c] = sqrt(gx * gx + gy * gy + gz * gz);
+    I.chi[c] = R(2) * frac(I, c, false);
+}
+
+// normal, curvature (Eq. 7), grad psi, sigma (Eq. 8), interfacial force
+// (Eq. 9) plus buoyancy, velocity (Eq. 10)
+template <typename R>
+__global__ void k_force3(Inst<R> I) {
+    LBS_CELL3
+    const R e2 = I.eps_n * I.eps_n;
+    R divn = R(0), dpx = R(0), dpy = R(0), dpz = R(0);
+#pragma unroll
+    for (int i = 1; i < Q19; i++) {
+        int refl, sx, sy, sz;
+        long long j = nb3(I, x, y, z, ex19(i), ey19(i), ez19(i), refl, sx, sy, sz);
+        R gx = I.gx[j], gy = I.gy[j], gz = I.gz[j];
+        if (refl & 1) gx = -gx;  // normal component mirrored with a sign change
+        if (refl & 2) gy = -gy;
+        if (refl & 4) gz = -gz;
+        const R inv = R(1) / sqrt(gx * gx + gy * gy + gz * gz + e2);
+        R s = R(0);
+        if (ex19(i)) s += R(ex19(i)) * gx;
+        if (ey19(i)) s += R(ey19(i)) * gy;
+        if (ez19(i)) s += R(ez19(i)) * gz;
+        divn -= w19<R>(i) * s * inv;
+        const R p = w19<R>(i) * I.psi[j];
+        if (ex19(i)) dpx += R(ex19(i)) * p;
+        if (ey19(i)) dpy += R(ey19(i)) * p;
+        if (ez19(i)) dpz += R(ez19(i)) * p;
+    }
+    const R kappa = -R(3) * divn;
+    dpx *= R(3);
+    dpy *= R(3);
+    dpz *= R(3);
+    const R gx = I.gx[c], gy = I.gy[c], gz = I.gz[c], a = I.a[c];
+    R sigma, mco, Fx, Fy, Fz;
+    if (eos(I, I.psi[c], sigma, mco)) {
+        const R inv = R(1) / sqrt(gx * gx + gy * gy + gz * gz + e2);
+        const R nx = -gx * inv, ny = -gy * inv, nz = -gz * inv;
+        const R ndp = nx * dpx + ny * dpy + nz * dpz;
+        Fx = -R(0.5) * sigma * kappa * gx - R(0.5) * a * mco * (dpx - ndp * nx);
+        Fy = -R(0.5) * sigma * kappa * gy - R(0.5) * a * mco * (dpy - ndp * ny);
+        Fz = -R(0.5) * sigma * kappa * gz - R(0.5) * a * mco * (dpz - ndp * nz);
+    } else {
+        Fx = -R(0.5) * I.sigma_min * kappa * gx;
+        Fy = -R(0.5) * I.sigma_min * kappa * gy;
+        Fz = -R(0.5) * I.sigma_min * kappa * gz;
+    }
+    const R rR = I.rhoR[c], rB = I.rhoB[c];
+    const R rho = rR + rB;
+    const R drb = rR + (rB - I.rhoB0);
+    Fx += drb * I.g[0];
+    Fy += drb * I.g[1];
+    Fz += drb * I.g[2];
+    I.Fx[c] = Fx;
+    I.Fy[c] = Fy;
+    I.Fz[c] = Fz;
+    I.ux[c] = (I.jx[c] + R(0.5) * Fx) / rho;
+    I.uy[c] = (I.jy[c] + R(0.5) * Fy) / rho;
+    I.uz[c] = (I.jz[c] + R(0.5) * Fz) / rho;
+}
+
+// explicit surfactant terms (Eqs. 22-27) and Crank-Nicolson right-hand sides
+// with the six-face operator of Eq. 28; Sout / Bout: export only (see k_fd2)
+template <typename R>
+__global__ void k_fd3(Inst<R> I, double *Sout = nullptr, double *Bout = nullptr) {
+    LBS_CELL3
+    const R u[3] = {I.ux[c], I.uy[c], I.uz[c]};
+    const R *uax[3] = {I.ux, I.uy, I.uz};
+    R divP = R(0), divC = R(0);
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+        R Pl[5], Cl[5];
+#pragma unroll
+        for (int k = -2; k <= 2; k++) {
+            int refl, sx, sy, sz;
+            long long j = nb3(I, x, y, z, ax == 0 ? k : 0, ax == 1 ? k : 0, ax == 2 ? k : 0, refl,
+                              sx, sy, sz);
+            const R sgn = (refl & (1 << ax)) ? R(-1) : R(1);
+            const R uj = uax[ax][j];
+            Pl[k + 2] = sgn * I.psi[j] * I.a[j] * uj;
+            Cl[k + 2] = sgn * I.C[j] * I.chi[j] * uj;
+        }
+        divP += upwind(Pl + 2, u[ax]);
+        divC += upwind(Cl + 2, u[ax]);
+    }
+    const R psi = I.psi[c], Cc = I.C[c], a = I.a[c];
+    const R jj = I.source == 1 ? I.ra * I.psi_inf * Cc
+                               : I.ra * Cc * (I.psi_inf - psi) - I.rd * psi;
+    const R S = -divP + a * jj;
+    const R B = -divC - a * jj;
+    if (Sout) {
+        const long long d = ((long long)z * I.ny + y) * I.nx + x;
+        Sout[d] = S;
+        Bout[d] = B;
+        return;
+    }
+    const R wp = a + I.eps_w, wc = I.chi[c] + I.eps_w;
+    R Lp = R(0), Lc = R(0);
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+        const int s = (f & 1) ? 1 : -1, ax = f >> 1;
+        int refl, sx, sy, sz;
+        long long j2 = nb3(I, x, y, z, ax == 0 ? s : 0, ax == 1 ? s : 0, ax == 2 ? s : 0, refl,
+                           sx, sy, sz);
+        if (refl) continue;
+        Lp += R(0.5) * (wp + (I.a[j2] + I.eps_w)) * (I.psi[j2] - psi);
+        Lc += R(0.5) * (wc + (I.chi[j2] + I.eps_w)) * (I.C[j2] - Cc);
+    }
+    const bool first = I.ctl->step == 0;
+    const R Sp = I.S[c], Bp = I.B[c];
+    const R abS = first ? S : R(1.5) * S - R(0.5) * Sp;
+    const R abB = first ? B : R(1.5) * B - R(0.5) * Bp;
+    I.rpsi[c] = wp * psi + R(0.5) * I.Ds * Lp + abS;
+    I.rC[c] = wc * Cc + R(0.5) * I.Db * Lc + abB;
+    I.S[c] = S;
+    I.B[c] = B;
+}
+
+// ---------------------------------------------------------------------------
+// k_collide3: MRT collision in raw-moment space (Eqs. 1-4, 39-41, 43) on the
+// shifted total populations, then recolouring (Eqs. 11-12).
+//   m - m^eq per row, with P = sum_k rho^k (c_s^k)^2, dP = P minus the
+//   pressure of the shift (the pure majority phase at rest):
+//     row 0: 0;   rows 1-3: -F/2 exactly (u carries the half force)
+//     row 4: mT4 - 3 dP - rho u^2
+//     rows 5-9: mT - rho (2ux^2-uy^2-uz^2, uy^2-uz^2, ux uy, ux uz, uy uz)
+//     rows 10-15: mT - P (uy, ux, uz, ux, uz, uy)
+//     rows 16-18: mT - dP/3 - rho (ux^2+uy^2-uz^2, ux^2+uz^2-uy^2,
+//                                  uy^2+uz^2-ux^2) / 6
+//   forcing moments of Eq. 4 for D3Q19 in closed form (isotropy of the
+//   weights to fourth order; rows 16-18 from the sixth-order sums):
+//     F0 = 0, F1-3 = F, F4 = 2 u.F, F5 = 4uxFx - 2uyFy - 2uzFz,
+//     F6 = 2uyFy - 2uzFz, F7 = uxFy + uyFx, F8 = uxFz + uzFx, F9 = uyFz + uzFy,
+//     F10-15 = (Fy, Fx, Fz, Fx, Fz, Fy)/3,
+//     F16 = uxFx + uyFy - u.F/3, F17 = uxFx + uzFz - u.F/3, F18 = uyFy + uzFz - u.F/3
+//   change of the moments: dm = -S (m - m^eq) + (1 - S/2)(C + F); rows 1-3
+//   then give F.
+// ---------------------------------------------------------------------------
+template <typename R, typename P>
+__global__ void __launch_bounds__(256) k_collide3(Inst<R> I) {
+    LBS_CELL3
+    R fT[Q19], fM[Q19];
+    const int fl = I.flag[c];
+#pragma unroll
+    for (int i = 0; i < Q19; i++) {
+        fT[i] = ldp<R, P>(I, I.fT, i * I.plane + c);
+        fM[i] = ldp<R, P>(I, I.fM, i * I.plane + c);
+    }
+    const Mom3<R> mo = moments19(I, fT, fM, fl);
+    const R rR = mo.rR, rB = mo.rB;
+    const R rmin = fl ? rB : rR;
+    const R devmaj = I.dsh[fl] + (mo.drho - rmin);
+    const R rho = rR + rB;
+    const R ux = I.ux[c], uy = I.uy[c], uz = I.uz[c];
+    const R Fx = I.Fx[c], Fy = I.Fy[c], Fz = I.Fz[c];
+
+    // d_a(rho^k u_a), isotropic stencil, ghost velocities at walls
+    R dR[3] = {R(0), R(0), R(0)}, dB[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int i = 1; i < Q19; i++) {
+        int refl, sx, sy, sz;
+        long long j = nb3(I, x, y, z, ex19(i), ey19(i), ez19(i), refl, sx, sy, sz);
+        R vx = I.ux[j], vy = I.uy[j], vz = I.uz[j];
+        ghost_u3(I, refl, sx, sy, sz, vx, vy, vz);
+        const R r1 = w19<R>(i) * I.rhoR[j], r2 = w19<R>(i) * I.rhoB[j];
+        if (ex19(i)) {
+            dR[0] += R(ex19(i)) * r1 * vx;
+            dB[0] += R(ex19(i)) * r2 * vx;
+        }
+        if (ey19(i)) {
+            dR[1] += R(ey19(i)) * r1 * vy;
+            dB[1] += R(ey19(i)) * r2 * vy;
+        }
+        if (ez19(i)) {
+            dR[2] += R(ez19(i)) * r1 * vz;
+            dB[2] += R(ez19(i)) * r2 * vz;
+        }
+    }
+    const R cR = R(1) - R(1.5) * (R(1) - I.alphaR), cB = R(1) - R(1.5) * (R(1) - I.alphaB);
+    const R Qx = R(3) * (cR * dR[0] + cB * dB[0]);
+    const R Qy = R(3) * (cR * dR[1] + cB * dB[1]);
+    const R Qz = R(3) * (cR * dR[2] + cB * dB[2]);
+
+    // moments of the shifted total populations (rows 4-18)
+    R mT[Q19];
+#pragma unroll
+    for (int j = 4; j < Q19; j++) {
+        R s = R(0);
+#pragma unroll
+        for (int i = 0; i < Q19; i++)
+            if (m19(j, i) != 0) s += R(m19(j, i)) * fT[i];
+        mT[j] = s;
+    }
+    const R Pk = rR * I.cs2R + rB * I.cs2B;
+    const R dP = fl == 0 ? devmaj * I.cs2B + rR * I.cs2R : devmaj * I.cs2R + rB * I.cs2B;
+    const R xx = ux * ux, yy = uy * uy, zz = uz * uz, u2 = xx + yy + zz;
+    R neq[Q19];
+    neq[4] = mT[4] - R(3) * dP - rho * u2 + I.mcor1[fl];
+    neq[5] = mT[5] - rho * (R(2) * xx - yy - zz);
+    neq[6] = mT[6] - rho * (yy - zz);
+    neq[7] = mT[7] - rho * ux * uy;
+    neq[8] = mT[8] - rho * ux * uz;
+    neq[9] = mT[9] - rho * uy * uz;
+    neq[10] = mT[10] - Pk * uy;
+    neq[11] = mT[11] - Pk * ux;
+    neq[12] = mT[12] - Pk * uz;
+    neq[13] = mT[13] - Pk * ux;
+    neq[14] = mT[14] - Pk * uz;
+    neq[15] = mT[15] - Pk * uy;
+    const R d3 = dP / R(3) - I.mcor2[fl];
+    neq[16] = mT[16] - d3 - rho * (xx + yy - zz) / R(6);
+    neq[17] = mT[17] - d3 - rho * (xx + zz - yy) / R(6);
+    neq[18] = mT[18] - d3 - rho * (yy + zz - xx) / R(6);
+
+    // s_v from the mixture viscosity (Eq. 43)
+    const R rN = colour_fn(I, rR, rB);
+    const R inv_mu = (R(1) + rN) / (R(2) * I.muR0) + (R(1) - rN) / (R(2) * I.muB0);
+    const R sv = R(1) / (R(0.5) + R(1) / (inv_mu * Pk));
+    const R uF = ux * Fx + uy * Fy + uz * Fz;
+    const R xF = ux * Fx, yF = uy * Fy, zF = uz * Fz;
+    R dm[Q19];
+    dm[0] = R(0);
+    dm[1] = Fx;
+    dm[2] = Fy;
+    dm[3] = Fz;
+    dm[4] = -neq[4] + R(0.5) * ((Qx + Qy + Qz) + R(2) * uF);
+    const R hv = R(1) - R(0.5) * sv;
+    dm[5] = -sv * neq[5] + hv * ((R(2) * Qx - Qy - Qz) + (R(4) * xF - R(2) * yF - R(2) * zF));
+    dm[6] = -sv * neq[6] + hv * ((Qy - Qz) + (R(2) * yF - R(2) * zF));
+    dm[7] = -sv * neq[7] + hv * (ux * Fy + uy * Fx);
+    dm[8] = -sv * neq[8] + hv * (ux * Fz + uz * Fx);
+    dm[9] = -sv * neq[9] + hv * (uy * Fz + uz * Fy);
+    const R t3 = R(0.5) / R(3);
+    dm[10] = -neq[10] + t3 * Fy;
+    dm[11] = -neq[11] + t3 * Fx;
+    dm[12] = -neq[12] + t3 * Fz;
+    dm[13] = -neq[13] + t3 * Fx;
+    dm[14] = -neq[14] + t3 * Fz;
+    dm[15] = -neq[15] + t3 * Fy;
+    const R u3 = uF / R(3);
+    dm[16] = -neq[16] + R(0.5) * (xF + yF - u3);
+    dm[17] = -neq[17] + R(0.5) * (xF + zF - u3);
+    dm[18] = -neq[18] + R(0.5) * (yF + zF - u3);
+    R df[Q19];
+    minv19<R>(dm, df);
+
+    R post[Q19];
+    CSum<R> rdc;
+#pragma unroll
+    for (int i = 0; i < Q19; i++) {
+        post[i] = fT[i] + df[i];
+        rdc.add(shift_of(I, i, fl) + post[i]);
+    }
+    const R rdag = rdc.value();
+    // recolouring: segregation weight f_i^eq(rho, 0)/rho = w_i 3 P / rho for
+    // the moving directions (the rest equilibrium of Eq. 40: rho - 2P at rest,
+    // P/6 on the axes, P/12 on the diagonals)
+    const R ggx = I.gx[c], ggy = I.gy[c], ggz = I.gz[c];
+    const R gn = sqrt(ggx * ggx + ggy * ggy + ggz * ggz + I.eps_n * I.eps_n);
+    const R seg = I.beta * rR * rB / (rho * rho) * R(3) * Pk / gn;
+    const R fr = rmin / rdag;
+    const R sg = fl ? R(-1) : R(1);
+#pragma unroll
+    for (int i = 0; i < Q19; i++) {
+        R eg = R(0);
+        if (ex19(i)) eg += R(ex19(i)) * ggx;
+        if (ey19(i)) eg += R(ey19(i)) * ggy;
+        if (ez19(i)) eg += R(ez19(i)) * ggz;
+        const R segi = i == 0 ? R(0) : seg * w19<R>(i) * eg;
+        stp<R, P>(I, I.gT, i * I.plane + c, post[i]);
+        stp<R, P>(I, I.gM, i * I.plane + c, fr * (shift_of(I, i, fl) + post[i]) + sg * segi);
+    }
+    I.gflag[c] = (uint8_t)fl;
+}
+
+// streaming (Eq. 13, pull), half-way bounce-back with moving walls, moments
+// at t+1 (see k_stream2)
+template <typename R, typename P>
+__global__ void __launch_bounds__(256) k_stream3(Inst<R> I) {
+    LBS_CELL3
+    R fT[Q19], fR[Q19], fB[Q19];
+    const R rRc = I.rhoR[c], rBc = I.rhoB[c];
+    const int flc = I.gflag[c];
+#pragma unroll
+    for (int i = 0; i < Q19; i++) {
+        int refl, sx, sy, sz;
+        long long j = nb3(I, x, y, z, -ex19(i), -ey19(i), -ez19(i), refl, sx, sy, sz);
+        if (!refl) {
+            fT[i] = ldp<R, P>(I, I.gT, i * I.plane + j);
+            const int fj = I.gflag[j];
+            split(shift_of(I, i, fj), fT[i], ldp<R, P>(I, I.gM, i * I.plane + j), fj, fR[i],
+                  fB[i]);
+        } else {
+            R uw[3] = {R(0), R(0), R(0)};
+            int nw = 0;
+            const int side[3] = {sx, sy, sz};
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                if (!(refl & (1 << a))) continue;
+                const R *w = side[a] < 0 ? I.uw_lo[a] : I.uw_hi[a];
+                uw[0] += w[0];
+                uw[1] += w[1];
+                uw[2] += w[2];
+                nw++;
+            }
+            const R eu = (R(ex19(i)) * uw[0] + R(ey19(i)) * uw[1] + R(ez19(i)) * uw[2]) / R(nw);
+            const R mw = R(2) * w19<R>(i) * eu * R(3);
+            const int io = opp19(i);
+            fT[i] = ldp<R, P>(I, I.gT, io * I.plane + c) + mw * (rRc + rBc);
+            const R mmin = ldp<R, P>(I, I.gM, io * I.plane + c) + mw * (flc ? rBc : rRc);
+            split(I.shift[i], fT[i], mmin, flc, fR[i], fB[i]);
+        }
+    }
+    R rR = R(0), rB = R(0);
+#pragma unroll
+    for (int i = 0; i < Q19; i++) {
+        rR += fR[i];
+        rB += fB[i];
+    }
+    const int fl = minority(I, rR, rB);
+    if (fl != flc) fT[0] = (I.shift0[flc] - I.shift0[fl]) + fT[0];
+    R fM[Q19];
+#pragma unroll
+    for (int i = 0; i < Q19; i++) {
+        fM[i] = fl ? fB[i] : fR[i];
+        stp<R, P>(I, I.fT, i * I.plane + c, fT[i]);
+        stp<R, P>(I, I.fM, i * I.plane + c, fM[i]);
+    }
+    I.flag[c] = (uint8_t)fl;
+    store_moments3(I, c, fT, fM, fl);
+}
+
+// ---------------------------------------------------------------------------
+// k_sor_rb3: one half-sweep of red-black SOR (omega of Sec. 2.2) for
+// (w - h L_w) x = rhs on psi and C, updating the cells of one colour
+// ((x + y + z) mod 2) in place.  Thread (tx, y, z) takes the cell
+// x = 2 tx + ((y + z + colour) mod 2).  Both half-sweeps fold their largest
+// update and value into the round's slot; the black launch's last block
+// decides whether another round (sweep) runs.
+// ---------------------------------------------------------------------------
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS)
+    k_sor_rb3(Inst<R> I, int colour, cudaGraphConditionalHandle loop, int max_rounds,
+              int eager_round) {
+    if (eager_round > 0 && I.ctl->sor_exec < eager_round) return;  // loop already ended
+    const int round = I.ctl->sor_exec;
+    const int tx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const int x = 2 * tx + ((y + z + colour) & 1);
+    R v[4] = {R(0), R(0), R(0), R(0)};
+    if (x < I.nx && y < I.ny) {
+        const long long c = cell3(I, x, y, z);
+        const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
+        const R wp = I.a[c] + I.eps_w, wc = I.chi[c] + I.eps_w;
+        R dp = wp, dc = wc, op = I.rpsi[c], oc = I.rC[c];
+#pragma unroll
+        for (int f = 0; f < 6; f++) {
+            const int s = (f & 1) ? 1 : -1, ax = f >> 1;
+            int refl, sx, sy, sz;
+            long long j = nb3(I, x, y, z, ax == 0 ? s : 0, ax == 1 ? s : 0, ax == 2 ? s : 0, refl,
+                              sx, sy, sz);
+            if (refl) continue;  // no flux through a wall
+            const R fp = hp * (R(0.5) * (wp + (I.a[j] + I.eps_w)));
+            const R fc = hc * (R(0.5) * (wc + (I.chi[j] + I.eps_w)));
+            dp += fp;
+            dc += fc;
+            op += fp * I.psi[j];
+            oc += fc * I.C[j];
+        }
+        const R p0 = I.psi[c], c0 = I.C[c];
+        const R d1 = I.omega * (op / dp - p0), d2 = I.omega * (oc / dc - c0);
+        const R p1 = p0 + d1, c1 = c0 + d2;
+        I.psi[c] = p1;
+        I.C[c] = c1;
+        v[0] = fabs(d1);
+        v[1] = fabs(d2);
+        v[2] = fabs(p1);
+        v[3] = fabs(c1);
+    }
+    __shared__ R sh[4][BS / 32];
+    const int t = threadIdx.x + threadIdx.y * blockDim.x;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
+    if ((t & 31) == 0)
+        for (int q = 0; q < 4; q++) sh[q][t >> 5] = v[q];
+    __syncthreads();
+    if (t == 0)
+        for (int q = 0; q < 4; q++) {
+            R m = R(0);
+            for (int w = 0; w < BS / 32; w++) m = fmax(m, sh[q][w]);
+            atomic_max_pos(&I.ctl->sweep[round][q], double(m));
+        }
+    if (colour == 0) return;
+    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    if (!last_block(&I.ctl->sor_ticket, nb)) return;
+    if (t != 0) return;
+    Ctl *ctl = I.ctl;
+    ctl->sor_ticket = 0;
+    const bool conv = round_converged<R>(ctl, round, double(I.sor_tol));
+    const bool stop = conv || round + 1 >= max_rounds;
+    if (stop && !conv) ctl->status |= ST_NOCONV;
+    if (eager_round < 0) {
+        ctl->sor_exec = round + 1;
+        if (stop) cudaGraphSetConditional(loop, 0);
+    } else {
+        ctl->sor_exec = stop ? -(round + 1) - 1000000 : round + 1;
+    }
+}
+
+#undef LBS_CELL3
+
+}  // namespace lbs

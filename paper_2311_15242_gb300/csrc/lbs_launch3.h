@@ -1,0 +1,32 @@
+// lbs_launch3.h — host-side launchers of the D3Q19 kernels.  The kernels are
+// instantiated in their own translation unit (lbs_3d.cu) so that the D2Q9
+// and D3Q19 code compile in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbs_dev.cuh"
+
+namespace lbs {
+
+template <typename R, typename P>
+struct Launch3 {
+    static void init(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s, const double *phi,
+                     const double *psi, const double *C, const double *u);
+    static void moments(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s);
+    static void grad(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s);
+    static void force(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s);
+    static void fd(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s, double *Sout,
+                   double *Bout);
+    static void collide(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s);
+    static void stream(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s);
+    static void diag(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s, int nblocks);
+    // one red (colour 0) or black (colour 1) SOR half-sweep
+    static void sor(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s, int colour,
+                    cudaGraphConditionalHandle h, int max_rounds, int eager_round);
+    // the half-sweep kernel, for a kernel node of the SOR loop's body graph
+    static void *sor_fn();
+    static constexpr int kSorBX = 32, kSorBY = 8;
+};
+
+}  // namespace lbs

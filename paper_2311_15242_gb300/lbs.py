@@ -60,6 +60,7 @@ class LbsDiag(C.Structure):
         ("umax", C.c_double), ("Re", C.c_double),
         ("sor_iters_psi", C.c_int), ("sor_iters_C", C.c_int), ("sor_rounds", C.c_int),
         ("step", C.c_longlong),
+        ("deformation", C.c_double), ("inclination", C.c_double),
     ]
 
 

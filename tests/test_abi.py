@@ -56,3 +56,34 @@ def test_workspace_and_validation_on_host():
     assert L.lbs_create(ctypes.byref(bad), lbs.LBS_F32, None, None, 0, ctypes.byref(h)) == lbs.LBS_EINVAL
     assert b"3 nodes" in L.lbs_last_error(h)
     L.lbs_destroy(h)
+
+
+def test_3d_validation_on_host():
+    """D3Q19 grids: accepted with even periodic axes (any size on a walled
+    axis), refused with an odd periodic axis (the in-place red-black SOR
+    would couple cells of one colour across the seam); a 2D grid cannot
+    have walls on z.  The 3D workspace holds 19 population planes per set."""
+    L = P.load()
+    p = lbs.LbsParams()
+    L.lbs_params_default(ctypes.byref(p), 34, 20, 17)
+    p.wall[2] = 1
+    b3 = L.lbs_workspace_bytes(ctypes.byref(p), lbs.LBS_F32)
+    assert b3 > 0
+    assert abs(p.alphaR - 1 / 3) < 1e-15
+    p.nx = 33
+    assert L.lbs_workspace_bytes(ctypes.byref(p), lbs.LBS_F32) == 0
+    h = ctypes.c_void_p()
+    assert L.lbs_create(ctypes.byref(p), lbs.LBS_F32, None, None, 0, ctypes.byref(h)) == lbs.LBS_EINVAL
+    assert b"even size on periodic axis 0" in L.lbs_last_error(h)
+    L.lbs_destroy(h)
+    p.wall[0] = 1  # odd is fine on a walled axis
+    assert L.lbs_workspace_bytes(ctypes.byref(p), lbs.LBS_F32) > 0
+    q = lbs.LbsParams()
+    L.lbs_params_default(ctypes.byref(q), 34, 20, 1)
+    q.wall[2] = 1
+    assert L.lbs_workspace_bytes(ctypes.byref(q), lbs.LBS_F32) == 0
+    # populations: 4 sets x 19 planes (3D) against 4 x 9 (2D) of the same cells
+    q.wall[2] = 0
+    q.ny = 20 * 17
+    b2 = L.lbs_workspace_bytes(ctypes.byref(q), lbs.LBS_F32)
+    assert b3 > b2

@@ -100,9 +100,45 @@ def bubble_rise_2d(nx=256, ny=1024, D_b=64.0, Eo=10.0, Mo=0.1, Bi=1.0, Pe=10.0,
     return c
 
 
+def shear_droplet_3d(nx=256, ny=128, nz=128, R=24.0, Ca=0.2, Re=1.0, lam=1.0, C0=0.5,
+                     E0=0.3, sigma0=5e-4, x_in=0.5, h=0.5, Bi=1.0, Pe_s=10.0, Pe_b=10.0):
+    """3D surfactant-laden droplet in simple shear (the 3D analogue of the
+    paper's Sec. 3.3 set-up): D3Q19 nx x ny x nz, half-way bounce-back walls
+    at z = -1/2 and nz - 1/2 moving with -u_w and +u_w along x, periodic in
+    x and y; droplet of radius R at the centre, density ratio 1.
+    Dimensionless groups of Sec. 3.3 (L = R, U = u_w / 2, shear rate
+    2 u_w / H with H = nz):
+      Re = rho U R / mu and Ca = mu U / sigma0 give mu = sqrt(Ca Re sigma0 R)
+      (rho = 1) and U = Ca sigma0 / mu;
+      Pe_s = U R / D_s, Pe_b = U R / D_b;  Bi = r_d / shear rate;
+      x_in = psi0 / psi_inf;  h = psi0 / (C0 R);  k = r_a C0 / r_d, with
+      no initial mass transfer (j = 0 at psi0, C0) so that k = x_in/(1-x_in).
+    psi starts uniform at its Langmuir equilibrium psi0 (Eq. 22 with j = 0),
+    C = C0 in the liquid."""
+    mu = math.sqrt(Ca * Re * sigma0 * R)
+    U = Ca * sigma0 / mu
+    uw = 2.0 * U
+    rate = 2.0 * uw / nz
+    psi0 = h * C0 * R
+    k = x_in / (1.0 - x_in)
+    rd = Bi * rate
+    c = base(nx, ny, nz)
+    c.update(
+        name="shear_droplet_3d", wall=[0, 0, 1],
+        uw_lo=[[0.0] * 3, [0.0] * 3, [-uw, 0.0, 0.0]],
+        uw_hi=[[0.0] * 3, [0.0] * 3, [uw, 0.0, 0.0]],
+        muR0=lam * mu, muB0=mu, sigma0=sigma0, E0=E0, psi_inf=psi0 / x_in,
+        Ds=U * R / Pe_s, Db=U * R / Pe_b, rd=rd, ra=k * rd / C0, source=0,
+        R=float(R), C0=C0, psi0=psi0, psi_profile="uniform",
+        Ca=Ca, Re=Re, U_ref=U, shear_rate=rate,
+    )
+    return c
+
+
 def initial_fields(cfg, seed=None, noise=0.0, u0=None):
     """Colour field phi = tanh((R - r)/width) (red inside), psi = psi0 times
-    the interface indicator (1 - phi^2), C = C0 (1 - phi)/2 (bulk surfactant
+    the interface indicator (1 - phi^2) (or psi0 everywhere when
+    cfg["psi_profile"] == "uniform"), C = C0 (1 - phi)/2 (bulk surfactant
     in the blue fluid only).  With a seed, psi and C receive multiplicative
     uniform noise of relative amplitude `noise` and u gets an additive field
     of amplitude `u0` (both break mirror symmetry for parity tests)."""
@@ -111,7 +147,10 @@ def initial_fields(cfg, seed=None, noise=0.0, u0=None):
     cx, cy, cz = cfg["center"]
     r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + ((z - cz) ** 2 if nz > 1 else 0.0))
     phi = np.tanh((cfg["R"] - r) / cfg["width"])
-    psi = cfg["psi0"] * (1.0 - phi ** 2)
+    if cfg.get("psi_profile") == "uniform":
+        psi = np.full_like(phi, cfg["psi0"])
+    else:
+        psi = cfg["psi0"] * (1.0 - phi ** 2)
     C = cfg["C0"] * 0.5 * (1.0 - phi)
     u = np.zeros((3, nz, ny, nx))
     if seed is not None:
