@@ -208,6 +208,69 @@ def time_steps(s, stream, flush, warmup, steps, torch, profiled=True):
     return tt, kmean
 
 
+def bench_batch(args, stream, flush, torch):
+    """MLUPS of the 64-instance bubble-rise sweep (widths 64-256, heights
+    512-1024, D = 32, Eo, Bi, E0, C0 drawn from the seeded generator) as one
+    batch with autotuned tiles, and of the same instances stepped one
+    single-instance context after another (same steps, same timing: CUDA
+    events around each chunk of 8 steps, an L2 flush before each chunk)."""
+    from paper_2311_15242_gb300 import Batch, Solver, autotune
+    cfgs = W.bubble_sweep_2d(64, seed=0)
+    cells = sum(c["nx"] * c["ny"] for c in cfgs)
+    fs = [W.initial_fields(c, seed=k) for k, c in enumerate(cfgs)]
+    out = {"workload": "bubble_sweep_2d_64", "instances": len(cfgs), "cells": cells,
+           "steps": args.batch_steps, "l2": "flushed before every timed graph launch"}
+    chunk = 8
+    nchunks = max(1, args.batch_steps // chunk)
+    for st in ("f32", "f16"):
+        b = Batch(cfgs, storage=st, stream=stream)
+        for k, f in enumerate(fs):
+            b.init_fields(k, f["phi"], f["psi"], f["C"], f["u"])
+        tune = autotune.tune(b, [c["nx"] for c in cfgs], use_cache=False)
+        b.step(chunk)  # warm-up (builds the graph)
+        b.sync()
+        tt = 0.0
+        for _ in range(nchunks):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                b.step(chunk)
+                e1.record(stream)
+            e1.synchronize()
+            tt += e0.elapsed_time(e1)
+        b.sync()
+        d = b.diagnostics()
+        out[f"mlups_{st}"] = cells * chunk * nchunks / (tt / 1e3) / 1e6
+        out[f"tiles_{st}"] = {k: tune[k] for k in ("tx", "ty", "sor")}
+        out[f"sor_rounds_max_{st}"] = max(x["sor_rounds"] for x in d)
+        out[f"gpu_launches_per_step_{st}"] = b.kernel_count()
+        b.close()
+    # plain: each instance in its own context, one after another
+    tt = 0.0
+    for k, c in enumerate(cfgs):
+        s = Solver(c, storage="f32", stream=stream)
+        s.init_fields(fs[k]["phi"], fs[k]["psi"], fs[k]["C"], fs[k]["u"])
+        s.step(2)
+        s.sync()
+        for _ in range(nchunks):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.step(chunk)
+                e1.record(stream)
+            e1.synchronize()
+            tt += e0.elapsed_time(e1)
+        s.sync()
+        s.close()
+    out["plain_mlups_f32"] = cells * chunk * nchunks / (tt / 1e3) / 1e6
+    out["speedup_f32"] = out["mlups_f32"] / out["plain_mlups_f32"]
+    return out
+
+
 def workload():
     cfg = W.bubble_rise_2d()
     name = ("bubble_rise_2d D2Q9 256x1024 walls-x periodic-y, D=64, rho 0.1/1, "
@@ -274,6 +337,10 @@ def main():
                     help="skip timing the other population storage forms")
     ap.add_argument("--no-3d", action="store_true",
                     help="skip the D3Q19 (3D sheared droplet) measurement")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched sweep measurement")
+    ap.add_argument("--batch-steps", type=int, default=16,
+                    help="timed steps of the batched sweep (a multiple of 8)")
     ap.add_argument("--steps3", type=int, default=20,
                     help="timed steps of each 3D storage form")
     ap.add_argument("--eager", action="store_true",
@@ -400,6 +467,12 @@ def main():
             forms[st] = cells * args.steps / (tt / 1e3) / 1e6
             s2.close()
 
+    # the batched sweep (64 2D instances) against the same instances run one
+    # context at a time
+    batched = None
+    if rank == 0 and not args.no_batch:
+        batched = bench_batch(args, stream, flush, torch)
+
     # the D3Q19 configuration (3D sheared droplet), each storage form
     d3 = None
     if rank == 0 and not args.no_3d:
@@ -434,7 +507,7 @@ def main():
                       "parallelism": f"replicas x{world}" if world > 1 else "single"},
            "roofline": roof, "kernel_ms": kmean, "sor_sweeps": sweeps, "sor_rounds": rounds,
            "gpu_launches": args.steps * s.kernel_count(),
-           "forms_mlups": forms, "d3q19": d3,
+           "forms_mlups": forms, "d3q19": d3, "batched": batched,
            "clocks": clk, "e2e": e2e, "impl": "lbs", "src_sha": sha}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, name)

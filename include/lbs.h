@@ -240,6 +240,69 @@ void lbs_destroy(lbs_ctx *c);
 /* Human-readable description of the last error of c (never NULL). */
 const char *lbs_last_error(const lbs_ctx *c);
 
+/* ------------------------------------------------------------------------
+ * Batched sweep: n independent 2D instances (each its own lbs_params: grid,
+ * Eotvos / Biot numbers, confinement; transport on) advanced together.
+ * Each phase of the coupled step is one launch for the whole batch: a grid of
+ * (SM count x resident blocks) blocks walks a work list of (instance, tile)
+ * items.  The SOR rounds of all instances run in one CUDA-graph WHILE loop,
+ * each instance with its own round counter and convergence test (Sec. 2.2
+ * tolerance); a converged instance skips the remaining rounds.  One graph
+ * holds 8 steps.  Results agree with n single-instance contexts to the
+ * rounding of the storage type (the same per-cell bodies, compiled apart). */
+typedef struct lbs_batch lbs_batch;
+
+/* Device bytes of the instances' state for p[0..n-1] (0 on invalid input:
+ * an invalid instance, nz != 1 or transport == 0). */
+size_t lbs_batch_workspace_bytes(const lbs_params *p, int n, int storage);
+
+/* Create a batch of n instances (p: n parameter sets, copied).  stream and
+ * workspace as in lbs_create (workspace: lbs_batch_workspace_bytes bytes,
+ * caller-owned, 256-byte aligned, or NULL); the work lists and descriptors
+ * are allocated by the library.  On failure *out still receives a handle
+ * that carries the message (release with lbs_batch_destroy).  Errors:
+ * LBS_EINVAL, LBS_ENOMEM, LBS_ECUDA. */
+int lbs_batch_create(const lbs_params *p, int n, int storage, void *stream, void *workspace,
+                     size_t workspace_bytes, lbs_batch **out);
+
+/* Initial state of instance k (0 <= k < n) from host fields, as
+ * lbs_init_fields (arrays of that instance's nx*ny). */
+int lbs_batch_init_fields(lbs_batch *b, int k, const double *phi, const double *psi,
+                          const double *C, const double *u);
+
+/* Tile shapes: the cell phases run tx x ty thread blocks, one cell per
+ * thread (tx*ty a multiple of 32, at most 1024); sor_tile selects the
+ * blocked SOR tile: 0 = 32x16, 1 = 64x8, 2 = 16x16 (2 sweeps a round each).
+ * Default 32 x 8, 0.  Results do not depend on the choice. */
+int lbs_batch_set_tiles(lbs_batch *b, int tx, int ty, int sor_tile);
+
+/* Queue n steps of every instance. */
+int lbs_batch_step(lbs_batch *b, int n);
+
+/* Wait for queued work; status of every instance as lbs_sync (the first
+ * failing instance is named in the message). */
+int lbs_batch_sync(lbs_batch *b);
+
+/* Fields of instance k, as lbs_get_fields. */
+int lbs_batch_get_fields(lbs_batch *b, int k, double *rho, double *u, double *phi, double *psi,
+                         double *C);
+
+/* Diagnostics of every instance into d[0..n-1], as lbs_diagnostics. */
+int lbs_batch_diagnostics(lbs_batch *b, lbs_diag *d);
+
+/* 1 (default): graphs of 8 steps with the SOR WHILE node; 0: individual
+ * launches with a host-driven SOR loop (for kernel profilers). */
+int lbs_batch_set_graph(lbs_batch *b, int enable);
+
+/* Kernel launches of one batch step (SOR rounds as of the last diagnostics). */
+int lbs_batch_step_kernel_count(const lbs_batch *b);
+
+/* Release the batch (waits for its stream). */
+void lbs_batch_destroy(lbs_batch *b);
+
+/* Message of the last failure of a batch. */
+const char *lbs_batch_last_error(const lbs_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

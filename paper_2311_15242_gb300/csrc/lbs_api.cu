@@ -12,6 +12,7 @@
 
 #include "../../include/lbs.h"
 #include "lbs_d3q19.cuh"
+#include "lbs_internal.h"
 #include "lbs_k2d.cuh"
 #include "lbs_launch3.h"
 
@@ -42,35 +43,6 @@ void rest_eq19(double rho, double al, double *f) {
     minv19<double>(m, f);
 }
 
-struct Base {
-    virtual ~Base() {}
-    virtual int init(const double *, const double *, const double *, const double *) = 0;
-    virtual int step(int n) = 0;
-    virtual int sync() = 0;
-    virtual int get(double *, double *, double *, double *, double *) = 0;
-    virtual int diag(lbs_diag *) = 0;
-    virtual int profile(int on) = 0;
-    virtual int kernel_times(double *ms, int n) = 0;
-    virtual int kernel_count() const = 0;
-    virtual int set_graph(int on) = 0;
-    virtual int macro(double *, double *, double *, double *, double *, double *) = 0;
-};
-
-}  // namespace
-
-struct lbs_ctx {
-    lbs_params p;
-    int storage;
-    cudaStream_t stream;
-    bool own_stream;
-    void *ws;
-    size_t ws_bytes;
-    bool own_ws;
-    Base *impl;
-    char err[512];
-};
-
-namespace {
 
 void set_err(lbs_ctx *c, const char *fmt, ...) {
     if (!c) return;
@@ -454,6 +426,9 @@ struct Solver : Base {
 
     int sweeps_per_round() const { return D == 2 ? SK : 1; }
 
+    const void *inst() const override { return &I; }
+    size_t inst_bytes() const override { return sizeof(I); }
+
     int set_graph(int on) override {
         use_graph = bool(on);
         return LBS_OK;
@@ -745,6 +720,22 @@ int validate(const lbs_params *p, char *err, size_t n) {
 
 }  // namespace
 
+namespace lbs {
+
+int validate_params(const lbs_params *p, char *err, size_t n) { return validate(p, err, n); }
+
+Base *make_solver(lbs_ctx *ctx) {
+    switch (ctx->storage) {
+    case LBS_F64: return new (std::nothrow) Solver<double, double>(ctx);
+    case LBS_F32: return new (std::nothrow) Solver<float, float>(ctx);
+    case LBS_F16: return new (std::nothrow) Solver<float, __half>(ctx);
+    case LBS_BF16: return new (std::nothrow) Solver<float, __nv_bfloat16>(ctx);
+    }
+    return nullptr;
+}
+
+}  // namespace lbs
+
 extern "C" {
 
 int lbs_params_default(lbs_params *p, int nx, int ny, int nz) {
@@ -834,12 +825,7 @@ int lbs_create(const lbs_params *p, int storage, void *stream, void *workspace,
         }
         ctx->own_stream = true;
     }
-    switch (storage) {
-    case LBS_F64: ctx->impl = new (std::nothrow) Solver<double, double>(ctx); break;
-    case LBS_F32: ctx->impl = new (std::nothrow) Solver<float, float>(ctx); break;
-    case LBS_F16: ctx->impl = new (std::nothrow) Solver<float, __half>(ctx); break;
-    default: ctx->impl = new (std::nothrow) Solver<float, __nv_bfloat16>(ctx); break;
-    }
+    ctx->impl = make_solver(ctx);
     *out = ctx;
     if (!ctx->impl) return LBS_ENOMEM;
     return LBS_OK;

@@ -76,7 +76,7 @@ struct Ctl {
     unsigned int sor_ticket; // arrival counter of the SOR round blocks
     double dscale;          // scale - 1 of the last rescale
     float dscale_f;         // the same in single precision
-    int pad3;
+    int sor_active;         // batched sweep: 1 while this instance's solve iterates
     // per sweep: max |d psi|, max |d C|, max |psi|, max |C| (bits of
     // non-negative doubles, compared as unsigned integers)
     unsigned long long sweep[KMAX_SWEEPS][4];

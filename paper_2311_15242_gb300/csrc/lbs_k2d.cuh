@@ -206,9 +206,7 @@ __device__ __forceinline__ R frac(const Inst<R> &I, long long j, bool red) {
 }
 
 template <typename R>
-__global__ void k_grad2(Inst<R> I) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void grad2_cell(const Inst<R> &I, int x, int y) {
     if (x >= I.nx || y >= I.ny) return;
     long long c = (long long)y * I.pitch + x;
     const bool blue_side = I.rhoN[c] <= R(0);
@@ -230,15 +228,18 @@ __global__ void k_grad2(Inst<R> I) {
     I.chi[c] = R(2) * frac(I, c, false);
 }
 
+template <typename R>
+__global__ void k_grad2(Inst<R> I) {
+    grad2_cell(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // k_force: n = -grad rhoN / |grad rhoN| (regularised by eps_n), curvature
 // kappa = -div n (Eq. 7), grad psi, sigma(psi) (Eq. 8), interfacial force
 // (Eq. 9) plus buoyancy (rho - rhoB0) g (Sec. 3.4), velocity of Eq. 10.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void k_force2(Inst<R> I) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void force2_cell(const Inst<R> &I, int x, int y) {
     if (x >= I.nx || y >= I.ny) return;
     long long c = (long long)y * I.pitch + x;
     const R e2 = I.eps_n * I.eps_n;
@@ -285,6 +286,11 @@ __global__ void k_force2(Inst<R> I) {
     I.uy[c] = (I.jy[c] + R(0.5) * Fy) / rho;
 }
 
+template <typename R>
+__global__ void k_force2(Inst<R> I) {
+    force2_cell(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // k_fd: explicit terms of Eqs. 23-24 at time t and the Crank-Nicolson
 // right-hand sides.
@@ -325,9 +331,8 @@ __device__ __forceinline__ R upwind(const R *v, R u) {
 // there (export; the Adams-Bashforth history and the right-hand sides are
 // left untouched)
 template <typename R>
-__global__ void k_fd2(Inst<R> I, double *Sout = nullptr, double *Bout = nullptr) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void fd2_cell(const Inst<R> &I, int x, int y, double *Sout,
+                                         double *Bout) {
     if (x >= I.nx || y >= I.ny) return;
     long long c = (long long)y * I.pitch + x;
     // line values of Psi_x, Phi_x along x and Psi_y, Phi_y along y
@@ -383,15 +388,18 @@ __global__ void k_fd2(Inst<R> I, double *Sout = nullptr, double *Bout = nullptr)
     I.B[c] = B;
 }
 
+template <typename R>
+__global__ void k_fd2(Inst<R> I, double *Sout = nullptr, double *Bout = nullptr) {
+    fd2_cell(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y, Sout, Bout);
+}
+
 // ---------------------------------------------------------------------------
 // k_collide: MRT collision with correction and forcing in moment space
 // (Eqs. 1-4, App. A Eqs. 36-38, 43) on the total populations, then
 // recolouring (Eqs. 11-12).  Output: post-collision buffers gT, gR.
 // ---------------------------------------------------------------------------
 template <typename R, typename P>
-__global__ void k_collide2(Inst<R> I) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void collide2_cell(const Inst<R> &I, int x, int y) {
     if (x >= I.nx || y >= I.ny) return;
     long long c = (long long)y * I.pitch + x;
     R fT[Q9], fM[Q9];
@@ -513,15 +521,18 @@ __global__ void k_collide2(Inst<R> I) {
     I.gflag[c] = (uint8_t)fl;
 }
 
+template <typename R, typename P>
+__global__ void k_collide2(Inst<R> I) {
+    collide2_cell<R, P>(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // k_stream: f_i(x, t+1) = f_i^post(x - e_i) (Eq. 13, pull form); a link that
 // crosses a wall is reflected (half-way bounce-back), a moving wall adds
 // 2 w_i rho^k (e_i . u_w) / c_s^2.  Stores the moments at t+1.
 // ---------------------------------------------------------------------------
 template <typename R, typename P>
-__global__ void k_stream2(Inst<R> I) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void stream2_cell(const Inst<R> &I, int x, int y) {
     if (x >= I.nx || y >= I.ny) return;
     long long c = (long long)y * I.pitch + x;
     R fT[Q9], fR[Q9], fB[Q9];
@@ -578,6 +589,11 @@ __global__ void k_stream2(Inst<R> I) {
     }
     I.flag[c] = (uint8_t)fl;
     store_moments(I, c, fT, fM, fl);
+}
+
+template <typename R, typename P>
+__global__ void k_stream2(Inst<R> I) {
+    stream2_cell<R, P>(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -637,16 +653,13 @@ __device__ __forceinline__ bool round_converged(const Ctl *ctl, int r, double to
     return d1 >= 0.5 * d0;
 }
 
-// loop: the WHILE node's handle in graph mode; eager_round >= 0 instead runs
-// round eager_round of a host-side loop (returns at once once converged)
+// one tile (bx, by) of round `round` of instance I, in smem_raw
+// (SorTile::smem_bytes()); folds the tile's maxima into the round's slot
 template <typename R, int TX, int TY, int K, int BS>
-__global__ void __launch_bounds__(BS)
-    k_sor_tb2(Inst<R> I, cudaGraphConditionalHandle loop, int max_rounds, int eager_round) {
+__device__ __forceinline__ void sor_tile2(const Inst<R> &I, int round, int bx, int by,
+                                          unsigned char *smem_raw) {
     using T = SorTile<R, TX, TY, K, BS>;
     constexpr int RX = T::RX, RY = T::RY, NR = T::NR, H = T::H;
-    if (eager_round > 0 && I.ctl->sor_exec < eager_round) return;  // loop already ended
-    const int round = I.ctl->sor_exec;  // rounds run so far in this solve
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sp = (R *)smem_raw, *sc = sp + NR, *bp = sc + NR, *bc = bp + NR;
     R *ip = bc + NR, *ic = ip + NR;                    // 1 / diagonal
     R *fpx = ic + NR, *fpy = fpx + NR, *fcx = fpy + NR, *fcy = fcx + NR;  // faces +x, +y
@@ -654,7 +667,7 @@ __global__ void __launch_bounds__(BS)
     uint16_t *list = (uint16_t *)(((uintptr_t)(fl + NR) + 1) & ~(uintptr_t)1);
     __shared__ int count[2];
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX - H, y0 = blockIdx.y * TY - H;
+    const int x0 = bx * TX - H, y0 = by * TY - H;
     const R *pin = (round & 1) ? I.psi2 : I.psi;
     const R *cin = (round & 1) ? I.C2 : I.C;
     R *pout = (round & 1) ? I.psi : I.psi2;
@@ -784,15 +797,34 @@ __global__ void __launch_bounds__(BS)
             for (int w = 0; w < BS / 32; w++) m = fmax(m, sh[q][w]);
             atomic_max_pos(&I.ctl->sweep[round][q], double(m));
         }
+}
+
+// decision after a round of instance ctl: converged, or out of rounds
+template <typename R>
+__device__ __forceinline__ bool sor_round_stop(Ctl *ctl, int round, double tol, int max_rounds) {
+    const bool conv = round_converged<R>(ctl, round, tol);
+    const bool stop = conv || round + 1 >= max_rounds;
+    if (stop && !conv) ctl->status |= ST_NOCONV;
+    return stop;
+}
+
+// loop: the WHILE node's handle in graph mode; eager_round >= 0 instead runs
+// round eager_round of a host-side loop (returns at once once converged)
+template <typename R, int TX, int TY, int K, int BS>
+__global__ void __launch_bounds__(BS)
+    k_sor_tb2(Inst<R> I, cudaGraphConditionalHandle loop, int max_rounds, int eager_round) {
+    if (eager_round > 0 && I.ctl->sor_exec < eager_round) return;  // loop already ended
+    const int round = I.ctl->sor_exec;  // rounds run so far in this solve
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    sor_tile2<R, TX, TY, K, BS>(I, round, blockIdx.x, blockIdx.y, smem_raw);
+    const int tid = threadIdx.x;
     // the last block to finish decides whether the loop runs another round
     const unsigned int nb = gridDim.x * gridDim.y;
     if (!last_block(&I.ctl->sor_ticket, nb)) return;
     if (tid != 0) return;
     Ctl *ctl = I.ctl;
     ctl->sor_ticket = 0;
-    const bool conv = round_converged<R>(ctl, round, double(I.sor_tol));
-    const bool stop = conv || round + 1 >= max_rounds;
-    if (stop && !conv) ctl->status |= ST_NOCONV;
+    const bool stop = sor_round_stop<R>(ctl, round, double(I.sor_tol), max_rounds);
     if (eager_round < 0) {
         ctl->sor_exec = round + 1;
         if (stop) cudaGraphSetConditional(loop, 0);
@@ -874,11 +906,13 @@ __device__ __forceinline__ int sor_rounds_done(int e) { return e >= 0 ? e : -(e 
 // the FP64 pipe of GB300 is narrow).
 constexpr int SURF_STRIP = 16;
 
+// block (bx, by) of a (gdx x .) grid of blockDim-shaped blocks
 template <typename R, int BS>
-__global__ void k_surf2(Inst<R> I, int mode, int nblocks, int sweeps_per_round) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void surf2_block(const Inst<R> &I, int mode, int nblocks,
+                                            int sweeps_per_round, int bx, int by, int gdx) {
+    int x = bx * blockDim.x + threadIdx.x;
     // rows of the grid: y in 2D, (z, y) pairs in 3D (row index z ny + y)
-    int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * SURF_STRIP;
+    int y0 = (by * blockDim.y + threadIdx.y) * SURF_STRIP;
     const int rows = I.ny * I.nz;
     // after an odd number of blocked SOR rounds the solution is in psi2, C2
     const int rounds = sor_rounds_done(I.ctl->sor_exec);
@@ -898,7 +932,7 @@ __global__ void k_surf2(Inst<R> I, int mode, int nblocks, int sweeps_per_round) 
             sum = t;
         }
     double v[1] = {double(sum) - double(comp)};
-    int b = blockIdx.x + blockIdx.y * gridDim.x;
+    int b = bx + by * gdx;
     block_sum<BS, 1>(v, I.part + b);
     if (!last_block(&I.ctl->ticket, nblocks)) return;
     const double tot = block_final_sum<BS>(I.part, 1, 0, nblocks);
@@ -927,12 +961,15 @@ __global__ void k_surf2(Inst<R> I, int mode, int nblocks, int sweeps_per_round) 
     ctl->step += 1;
 }
 
+template <typename R, int BS>
+__global__ void k_surf2(Inst<R> I, int mode, int nblocks, int sweeps_per_round) {
+    surf2_block<R, BS>(I, mode, nblocks, sweeps_per_round, blockIdx.x, blockIdx.y, gridDim.x);
+}
+
 template <typename R>
-__global__ void k_scale2(Inst<R> I) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void scale2_cell(const Inst<R> &I, int x, int y, int z) {
     if (x >= I.nx || y >= I.ny) return;
-    long long c = ((long long)blockIdx.z * I.ny + y) * I.pitch + x;
+    long long c = ((long long)z * I.ny + y) * I.pitch + x;
     // the factor is 1 + O(1e-6): multiplying by it rounded to R would apply a
     // quantised correction with the same bias every step; x + x d with
     // d = s - 1 formed in double and one fused rounding is unbiased
@@ -944,6 +981,11 @@ __global__ void k_scale2(Inst<R> I) {
     const R q = alt ? I.C2[c] : I.C[c];
     I.psi[c] = fma(p, d, p);
     I.C[c] = fma(q, d, q);
+}
+
+template <typename R>
+__global__ void k_scale2(Inst<R> I) {
+    scale2_cell(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y, (int)blockIdx.z);
 }
 
 // step counter for runs without surfactant transport

@@ -21,7 +21,10 @@ EXPORTS = ("lbs_params_default", "lbs_workspace_bytes", "lbs_create",
            "lbs_init_fields", "lbs_step", "lbs_sync", "lbs_get_fields",
            "lbs_get_macro", "lbs_diagnostics", "lbs_profile", "lbs_kernel_times", "lbs_set_graph",
            "lbs_step_kernel_count", "lbs_surfactant_total_static", "lbs_destroy",
-           "lbs_last_error")
+           "lbs_last_error", "lbs_batch_workspace_bytes", "lbs_batch_create",
+           "lbs_batch_init_fields", "lbs_batch_set_tiles", "lbs_batch_step", "lbs_batch_sync",
+           "lbs_batch_get_fields", "lbs_batch_diagnostics", "lbs_batch_set_graph",
+           "lbs_batch_step_kernel_count", "lbs_batch_destroy", "lbs_batch_last_error")
 KERNEL_GROUPS = ("force", "fd", "collide", "stream", "grad", "sor", "surf")
 
 
@@ -101,6 +104,21 @@ def load(build_if_missing: bool = True):
     L.lbs_destroy.argtypes = [C.c_void_p]
     L.lbs_last_error.restype = C.c_char_p
     L.lbs_last_error.argtypes = [C.c_void_p]
+    L.lbs_batch_workspace_bytes.restype = C.c_size_t
+    L.lbs_batch_workspace_bytes.argtypes = [C.POINTER(LbsParams), C.c_int, C.c_int]
+    L.lbs_batch_create.argtypes = [C.POINTER(LbsParams), C.c_int, C.c_int, C.c_void_p,
+                                   C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]
+    L.lbs_batch_init_fields.argtypes = [C.c_void_p, C.c_int, _DP, _DP, _DP, _DP]
+    L.lbs_batch_set_tiles.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+    L.lbs_batch_step.argtypes = [C.c_void_p, C.c_int]
+    L.lbs_batch_sync.argtypes = [C.c_void_p]
+    L.lbs_batch_get_fields.argtypes = [C.c_void_p, C.c_int, _DP, _DP, _DP, _DP, _DP]
+    L.lbs_batch_diagnostics.argtypes = [C.c_void_p, C.POINTER(LbsDiag)]
+    L.lbs_batch_set_graph.argtypes = [C.c_void_p, C.c_int]
+    L.lbs_batch_step_kernel_count.argtypes = [C.c_void_p]
+    L.lbs_batch_destroy.argtypes = [C.c_void_p]
+    L.lbs_batch_last_error.restype = C.c_char_p
+    L.lbs_batch_last_error.argtypes = [C.c_void_p]
     _lib = L
     return L
 
@@ -228,5 +246,94 @@ class Solver:
     def diagnostics(self):
         d = LbsDiag()
         self._check(self.L.lbs_diagnostics(self.h, C.byref(d)))
-        return {k: (list(getattr(d, k)) if k in ("U", "centroid") else getattr(d, k))
-                for k, _ in LbsDiag._fields_}
+        return _diag_dict(d)
+
+
+def _diag_dict(d):
+    return {k: (list(getattr(d, k)) if k in ("U", "centroid") else getattr(d, k))
+            for k, _ in LbsDiag._fields_}
+
+
+class Batch:
+    """A batch of independent 2D instances advanced together (lbs_batch_*):
+    one launch per phase for all instances, one CUDA graph per 8 steps.
+    Workspace: a torch uint8 tensor; work on a torch CUDA stream."""
+
+    def __init__(self, cfgs, storage="f32", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.L = load()
+        self.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        self.n = len(cfgs)
+        arr = (LbsParams * self.n)()
+        for k, cfg in enumerate(cfgs):
+            arr[k] = params_from(cfg, self.storage)
+        self.params = arr
+        self.shapes = [(1, arr[k].ny, arr[k].nx) for k in range(self.n)]
+        nbytes = self.L.lbs_batch_workspace_bytes(arr, self.n, self.storage)
+        if nbytes == 0:
+            raise LbsError(LBS_EINVAL, "invalid batch parameters")
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        aligned = (self.ws.data_ptr() + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = C.c_void_p()
+        r = self.L.lbs_batch_create(arr, self.n, self.storage, C.c_void_p(self.stream.cuda_stream),
+                                    C.c_void_p(aligned), nbytes, C.byref(h))
+        self.h = h
+        self._check(r)
+
+    def _check(self, r):
+        if r != LBS_OK:
+            msg = self.L.lbs_batch_last_error(self.h).decode() if self.h else "?"
+            raise LbsError(r, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.lbs_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _f(self, k, x, comps=None):
+        if x is None:
+            return None
+        shape = self.shapes[k] if comps is None else (comps,) + self.shapes[k]
+        return np.ascontiguousarray(np.broadcast_to(np.asarray(x, np.float64), shape))
+
+    def init_fields(self, k, phi, psi=None, C_=None, u=None):
+        arrs = [self._f(k, phi), self._f(k, psi), self._f(k, C_), self._f(k, u, 3)]
+        self._check(self.L.lbs_batch_init_fields(self.h, int(k), *[_dp(a) for a in arrs]))
+
+    def set_tiles(self, tx, ty, sor_tile=0):
+        self._check(self.L.lbs_batch_set_tiles(self.h, int(tx), int(ty), int(sor_tile)))
+
+    def set_graph(self, on=True):
+        self._check(self.L.lbs_batch_set_graph(self.h, int(bool(on))))
+
+    def step(self, n=1):
+        self._check(self.L.lbs_batch_step(self.h, int(n)))
+
+    def sync(self):
+        self._check(self.L.lbs_batch_sync(self.h))
+
+    def fields(self, k):
+        shape = self.shapes[k]
+        rho = np.empty(shape)
+        u = np.empty((3,) + shape)
+        phi, psi, C_ = (np.empty(shape) for _ in range(3))
+        self._check(self.L.lbs_batch_get_fields(self.h, int(k), _dp(rho), _dp(u), _dp(phi),
+                                                _dp(psi), _dp(C_)))
+        return dict(rho=rho, u=u, phi=phi, psi=psi, C=C_)
+
+    def diagnostics(self):
+        d = (LbsDiag * self.n)()
+        self._check(self.L.lbs_batch_diagnostics(self.h, d))
+        return [_diag_dict(d[k]) for k in range(self.n)]
+
+    def kernel_count(self):
+        return int(self.L.lbs_batch_step_kernel_count(self.h))

@@ -1,0 +1,148 @@
+"""The batched sweep (lbs_batch_*) against the FP64 oracle and against
+single-instance contexts.
+
+The batch runs the same per-cell bodies and the same SOR iterates as a
+single-instance context, whatever its tile shapes.  FP64 results match the
+oracle to 1e-9 per instance.  In FP32 the batched kernels are separate
+compilations of those bodies (the compiler may fuse a different set of
+multiply-adds), so batch and single-instance results agree to FP32 rounding
+(1e-5 after 20 steps, the FP32 parity tolerance of rho and phi), not
+bitwise; the SOR round counts agree."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.ora import Oracle
+
+from test_parity_gpu import F32_TOL, errors, within
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("rho", "u", "phi", "psi", "C")
+
+
+def small_sweep(n=4, seed=5):
+    """Sweep instances at reduced size (D = 12, heights 90-160) with the
+    sweep's parameter ranges; widths 33-64 give ragged tiles."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        pt = W.sweep_point(rng)
+        pt["width"] = int(rng.choice([33, 40, 48, 64]))
+        pt["height"] = int(rng.integers(90, 161))
+        c = W.sweep_instance(pt, D_b=12.0)
+        c["center"][1] = 20.0 + 3.3 * k
+        out.append(c)
+    return out
+
+
+def make_batch(cfgs, storage, seed=3, u0=1e-4):
+    from paper_2311_15242_gb300 import Batch
+    b = Batch(cfgs, storage=storage)
+    fs = [W.initial_fields(c, seed=seed + k, noise=0.02, u0=u0) for k, c in enumerate(cfgs)]
+    for k, f in enumerate(fs):
+        b.init_fields(k, f["phi"], f["psi"], f["C"], f["u"])
+    return b, fs
+
+
+def test_batch_f64_matches_oracle():
+    cfgs = small_sweep(3)
+    b, fs = make_batch(cfgs, "f64")
+    b.step(25)
+    for k, (c, f) in enumerate(zip(cfgs, fs)):
+        o = Oracle(c)
+        o.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+        o.step(25)
+        err = errors(o.fields(), b.fields(k))
+        assert max(err.values()) < 1e-9, (k, err)
+    d = b.diagnostics()
+    assert all(x["step"] == 25 for x in d)
+
+
+@pytest.mark.parametrize("tiles", [(32, 8, 0), (64, 4, 1), (16, 16, 2), (128, 2, 0)])
+def test_batch_equals_single_instances(tiles):
+    from paper_2311_15242_gb300 import Solver
+    cfgs = small_sweep(4)
+    b, fs = make_batch(cfgs, "f32")
+    b.set_tiles(*tiles)
+    b.step(20)
+    db = b.diagnostics()
+    for k, (c, f) in enumerate(zip(cfgs, fs)):
+        s = Solver(c, storage="f32")
+        s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+        s.step(20)
+        err = errors(s.fields(), b.fields(k))
+        print(tiles, k, {key: "%.1e" % v for key, v in err.items()})
+        assert max(err.values()) <= 1e-5, (tiles, k, err)
+        ds = s.diagnostics()
+        assert ds["sor_rounds"] == db[k]["sor_rounds"]
+        assert ds["mass_R"] == pytest.approx(db[k]["mass_R"], rel=1e-9)
+        s.close()
+    b.close()
+
+
+def test_per_instance_sor_convergence():
+    """Instances whose Crank-Nicolson systems need different numbers of SOR
+    rounds (diffusivities 0.01 and 0.4) each stop at their own count; the
+    loop runs until the slowest has converged."""
+    from paper_2311_15242_gb300 import Solver
+    cfgs = small_sweep(2)
+    cfgs[0].update(Ds=0.01, Db=0.01)
+    cfgs[1].update(Ds=0.4, Db=0.4)
+    b, fs = make_batch(cfgs, "f32")
+    b.step(5)
+    d = b.diagnostics()
+    rounds = [x["sor_rounds"] for x in d]
+    assert rounds[0] < rounds[1], rounds
+    for k, (c, f) in enumerate(zip(cfgs, fs)):
+        s = Solver(c, storage="f32")
+        s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+        s.step(5)
+        assert s.diagnostics()["sor_rounds"] == rounds[k]
+        s.close()
+
+
+def test_autotuner_on_the_gpu(tmp_path):
+    from paper_2311_15242_gb300 import autotune
+    cfgs = small_sweep(4)
+    b, _ = make_batch(cfgs, "f32")
+    r = autotune.tune(b, [c["nx"] for c in cfgs], cache_path=str(tmp_path / "t.json"),
+                      cell_tiles=((32, 8), (64, 4)), sor_tiles=(0, 1))
+    assert r["source"] == "timed" and r["ms_per_step"] > 0
+    assert (r["tx"], r["ty"]) in ((32, 8), (64, 4)) and r["sor"] in (0, 1)
+    b.sync()
+
+
+def test_full_sweep_64_instances():
+    """The 64-instance sweep (widths 64-256, heights 512-1024, D = 32; 8.0 M
+    cells) in the launch configuration the benchmark times: every instance
+    advances, stays finite and keeps its colour masses and total surfactant;
+    the smallest instance matches the oracle after the same steps."""
+    from paper_2311_15242_gb300 import Batch
+    cfgs = W.bubble_sweep_2d(64, seed=0)
+    b = Batch(cfgs, storage="f32")
+    fs = [W.initial_fields(c, seed=k) for k, c in enumerate(cfgs)]
+    for k, f in enumerate(fs):
+        b.init_fields(k, f["phi"], f["psi"], f["C"], f["u"])
+    d0 = b.diagnostics()
+    n = 16
+    b.step(n)
+    d = b.diagnostics()
+    drift = {key: max(abs(d[k][key] - d0[k][key]) / d0[k][key] / n for k in range(64))
+             for key in ("mass_R", "mass_B")}
+    print("largest colour-mass drift per step", drift)
+    for k in range(64):
+        assert d[k]["step"] == n
+        for key in ("mass_R", "mass_B"):
+            assert abs(d[k][key] - d0[k][key]) / d0[k][key] / n <= 1e-8, (k, key, d[k][key], d0[k][key])
+        assert abs(d[k]["surf_total"] - d0[k]["surf_total"]) / d0[k]["surf_total"] <= 1e-6
+    k = min(range(64), key=lambda i: cfgs[i]["nx"] * cfgs[i]["ny"])
+    o = Oracle(cfgs[k])
+    o.init_fields(fs[k]["phi"], fs[k]["psi"], fs[k]["C"], fs[k]["u"])
+    o.step(n)
+    got = b.fields(k)
+    for key in got:
+        assert np.isfinite(got[key]).all()
+    err = errors(o.fields(), got)
+    assert within(err, F32_TOL), err
+    b.close()

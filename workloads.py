@@ -100,6 +100,42 @@ def bubble_rise_2d(nx=256, ny=1024, D_b=64.0, Eo=10.0, Mo=0.1, Bi=1.0, Pe=10.0,
     return c
 
 
+SWEEP_WIDTHS = (64, 96, 128, 192, 256)
+
+
+def sweep_point(rng, vary_surfactant=True):
+    """One point of the batched bubble-rise sweep: Eo log-uniform in [1, 50],
+    Bi log-uniform in [0.01, 10], channel width uniform in SWEEP_WIDTHS
+    (confinement D / width with D = 32), height uniform in [512, 1024];
+    with vary_surfactant the elasticity E0 (uniform [0.2, 0.8]) and the bulk
+    concentration C0 (uniform [0.25, 1]) vary too (the surrogate's inputs),
+    else they keep the bubble-rise values 0.5 / 0.5."""
+    Eo = float(np.exp(rng.uniform(np.log(1.0), np.log(50.0))))
+    Bi = float(np.exp(rng.uniform(np.log(0.01), np.log(10.0))))
+    width = int(rng.choice(SWEEP_WIDTHS))
+    height = int(rng.integers(512, 1025))
+    E0 = float(rng.uniform(0.2, 0.8)) if vary_surfactant else 0.5
+    C0 = float(rng.uniform(0.25, 1.0)) if vary_surfactant else 0.5
+    return dict(Eo=Eo, Bi=Bi, width=width, height=height, E0=E0, C0=C0)
+
+
+def sweep_instance(pt, D_b=32.0):
+    """The bubble-rise instance of a sweep point (density ratio 10,
+    viscosity ratio 10, Mo = 0.1, Pe = 10, k = 1, h = 0.5)."""
+    c = bubble_rise_2d(nx=pt["width"], ny=pt["height"], D_b=D_b, Eo=pt["Eo"], Bi=pt["Bi"],
+                       E0=pt["E0"], C0=pt["C0"])
+    c["name"] = "sweep_bubble_2d"
+    c["sweep_point"] = dict(pt)
+    return c
+
+
+def bubble_sweep_2d(n=64, seed=0, vary_surfactant=True):
+    """n seeded sweep instances (the batched configuration: 64 instances of
+    widths 64-256 and heights 512-1024, D = 32)."""
+    rng = np.random.default_rng(seed)
+    return [sweep_instance(sweep_point(rng, vary_surfactant)) for _ in range(n)]
+
+
 def shear_droplet_3d(nx=256, ny=128, nz=128, R=24.0, Ca=0.2, Re=1.0, lam=1.0, C0=0.5,
                      E0=0.3, sigma0=5e-4, x_in=0.5, h=0.5, Bi=1.0, Pe_s=10.0, Pe_b=10.0):
     """3D surfactant-laden droplet in simple shear (the 3D analogue of the
