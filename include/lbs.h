@@ -279,8 +279,8 @@ int lbs_batch_set_tiles(lbs_batch *b, int tx, int ty, int sor_tile);
 /* Queue n steps of every instance. */
 int lbs_batch_step(lbs_batch *b, int n);
 
-/* Wait for queued work; status of every instance as lbs_sync (the first
- * failing instance is named in the message). */
+/* Wait for queued work; fails with the status of the first instance in the
+ * work lists whose solve failed (named in the message). */
 int lbs_batch_sync(lbs_batch *b);
 
 /* Fields of instance k, as lbs_get_fields. */
@@ -297,11 +297,87 @@ int lbs_batch_set_graph(lbs_batch *b, int enable);
 /* Kernel launches of one batch step (SOR rounds as of the last diagnostics). */
 int lbs_batch_step_kernel_count(const lbs_batch *b);
 
+/* Status of every instance since the last call, status[0..n-1] (lbs_status
+ * codes: LBS_EDIVERGED, LBS_ENOCONV, ...), then cleared.  An instance whose
+ * total surfactant went non-finite is skipped by every later step (its
+ * state is frozen); the others go on.  lbs_batch_sync and
+ * lbs_batch_get_fields do not clear these codes; lbs_batch_diagnostics
+ * reports every instance and does not fail on them. */
+int lbs_batch_status(lbs_batch *b, int *status);
+
+/* Take instance k out of the work lists (active = 0) or back in (1). */
+int lbs_batch_set_active(lbs_batch *b, int k, int active);
+
 /* Release the batch (waits for its stream). */
 void lbs_batch_destroy(lbs_batch *b);
 
 /* Message of the last failure of a batch. */
 const char *lbs_batch_last_error(const lbs_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Surrogate network: an ensemble of `members` fully connected networks
+ * n_in -> width (depth hidden layers, SiLU) -> n_out (linear), trained by
+ * mean-squared error with Adam on the GPU, evaluated with FP32 or bfloat16
+ * weights (FP32 arithmetic).  Parameters of a member, FP32: for each layer
+ * W (d_out x d_in, row-major) then b (d_out); members follow each other
+ * (lbs_mlp_param_count values each).  Host arrays below are caller-owned
+ * FP32, row-major, copied in and out; widths are at most 128, depth at
+ * most 7.  Errors: LBS_EINVAL (shapes, batch > max_batch, no data set),
+ * LBS_ENOMEM, LBS_ECUDA.
+ * ---------------------------------------------------------------------- */
+typedef struct lbs_mlp lbs_mlp;
+
+/* Create an ensemble (parameters zero until lbs_mlp_init / set_params);
+ * max_batch bounds the rows of every call.  stream as in lbs_create. */
+int lbs_mlp_create(int members, int n_in, int width, int depth, int n_out, int max_batch,
+                   void *stream, lbs_mlp **out);
+
+/* Parameters per member. */
+int lbs_mlp_param_count(const lbs_mlp *m);
+
+/* Glorot-uniform weights, zero biases (SplitMix64 on seed and index); resets Adam. */
+int lbs_mlp_init(lbs_mlp *m, unsigned long long seed);
+
+/* Copy all members' parameters in / out (members x param_count floats). */
+int lbs_mlp_set_params(lbs_mlp *m, const float *params);
+int lbs_mlp_get_params(lbs_mlp *m, float *params);
+
+/* Outputs y [members][batch][n_out] of inputs x [members][batch][n_in]
+ * (each member its own rows); bf16 != 0: bfloat16 copies of the weights. */
+int lbs_mlp_forward(lbs_mlp *m, const float *x, int batch, int bf16, float *y);
+
+/* Loss (mean over rows and outputs of the squared error, per member, FP64
+ * out) and its gradient with respect to every parameter (members x
+ * param_count, FP32 out; either output may be NULL) for inputs x and
+ * targets t [members][batch][n_out].  The gradient is kept for
+ * lbs_mlp_adam_step. */
+int lbs_mlp_gradient(lbs_mlp *m, const float *x, const float *t, int batch, float *grad,
+                     double *loss);
+
+/* Replace the kept gradient (members x param_count floats). */
+int lbs_mlp_set_grad(lbs_mlp *m, const float *grad);
+
+/* One Adam step with the kept gradient (Kingma & Ba 2015; bias-corrected). */
+int lbs_mlp_adam_step(lbs_mlp *m, float lr, float beta1, float beta2, float eps);
+
+/* Training set X [n][n_in], Y [n][n_out] (copied to the device). */
+int lbs_mlp_set_data(lbs_mlp *m, const float *X, const float *Y, int n);
+
+/* iters Adam steps on minibatches of `batch` rows drawn with replacement
+ * (SplitMix64 on seed, step, member, row: each member its own rows);
+ * loss: the last minibatch's loss per member (may be NULL). */
+int lbs_mlp_train(lbs_mlp *m, int iters, int batch, float lr, float beta1, float beta2,
+                  float eps, unsigned long long seed, double *loss);
+
+/* Ensemble mean and standard deviation over the members, mean/sd [n][n_out],
+ * of the outputs for x [n][n_in] (the same rows for every member). */
+int lbs_mlp_predict(lbs_mlp *m, const float *x, int n, int bf16, float *mean, float *sd);
+
+/* Release the ensemble. */
+void lbs_mlp_destroy(lbs_mlp *m);
+
+/* Message of the last failure. */
+const char *lbs_mlp_last_error(const lbs_mlp *m);
 
 #ifdef __cplusplus
 }

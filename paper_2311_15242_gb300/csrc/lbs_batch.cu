@@ -38,18 +38,25 @@ struct BatchCtl {
 
 enum { OP_FORCE, OP_FD, OP_COLLIDE, OP_STREAM, OP_GRAD, OP_SCALE };
 
-// copy descriptor k into shared memory (all threads; uniform)
+// copy descriptor k into shared memory (all threads; uniform) and return
+// whether the instance is alive (an instance whose total went non-finite is
+// skipped from then on; the flag is read once per change of instance)
 template <typename R>
-__device__ __forceinline__ void load_inst(const Inst<R> *insts, int k, Inst<R> &sI, int &cur) {
-    if (k == cur) return;
+__device__ __forceinline__ bool load_inst(const Inst<R> *insts, int k, Inst<R> &sI, int &cur,
+                                          int &alive) {
+    if (k == cur) return alive;
     __syncthreads();
     const int n = (int)(sizeof(Inst<R>) / 4);
     const int *src = (const int *)(insts + k);
     int *dst = (int *)&sI;
     const int nt = blockDim.x * blockDim.y;
     for (int i = threadIdx.x + threadIdx.y * blockDim.x; i < n; i += nt) dst[i] = src[i];
+    __shared__ int s_alive;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_alive = !insts[k].ctl->dead;
     __syncthreads();
     cur = k;
+    alive = s_alive;
+    return alive;
 }
 
 // one per-cell phase over the batch; work item = tile origin (x0, y0) of
@@ -58,10 +65,10 @@ template <typename R, typename P, int OP>
 __global__ void kb_cells2(const Inst<R> *__restrict__ insts, const WorkItem *__restrict__ work,
                           int nwork) {
     __shared__ Inst<R> sI;
-    int cur = -1;
+    int cur = -1, alive = 0;
     for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
         const WorkItem it = work[w];
-        load_inst(insts, it.inst, sI, cur);
+        if (!load_inst(insts, it.inst, sI, cur, alive)) continue;
         const int x = it.x0 + threadIdx.x, y = it.y0 + threadIdx.y;
         if (OP == OP_FORCE)
             force2_cell(sI, x, y);
@@ -78,12 +85,21 @@ __global__ void kb_cells2(const Inst<R> *__restrict__ insts, const WorkItem *__r
     }
 }
 
-// opens the SOR solve of every instance
+// opens the SOR solve of every live instance in the work lists (act[k])
 template <typename R>
-__global__ void kb_sor_begin(const Inst<R> *insts, int n, BatchCtl *bc) {
-    for (int k = threadIdx.x; k < n; k += blockDim.x) insts[k].ctl->sor_active = 1;
+__global__ void kb_sor_begin(const Inst<R> *insts, const int *act, int n, BatchCtl *bc) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        Ctl *ctl = insts[k].ctl;
+        const int a = act[k] && !ctl->dead;
+        ctl->sor_active = a;
+        if (a) atomicAdd(&cnt, 1);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        bc->active = n;
+        bc->active = cnt;
         bc->ticket = 0;
     }
 }
@@ -99,11 +115,11 @@ __global__ void __launch_bounds__(BS)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Inst<R> sI;
     __shared__ int s_round;
-    int cur = -1;
+    int cur = -1, alive = 0;
     const int tid = threadIdx.x;
     for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
         const WorkItem it = work[w];
-        load_inst(insts, it.inst, sI, cur);
+        load_inst(insts, it.inst, sI, cur, alive);
         __syncthreads();
         if (tid == 0) s_round = sI.ctl->sor_active ? sI.ctl->sor_exec : -1;
         __syncthreads();
@@ -134,10 +150,10 @@ template <typename R, int BS>
 __global__ void kb_surf2(const Inst<R> *__restrict__ insts, const WorkItem *__restrict__ work,
                          int nwork, int sweeps_per_round) {
     __shared__ Inst<R> sI;
-    int cur = -1;
+    int cur = -1, alive = 0;
     for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
         const WorkItem it = work[w];
-        load_inst(insts, it.inst, sI, cur);
+        if (!load_inst(insts, it.inst, sI, cur, alive)) continue;
         surf2_block<R, BS>(sI, 1, it.a0, sweeps_per_round, it.x0, it.y0, it.a1);
         __syncthreads();
     }
@@ -197,6 +213,8 @@ struct lbs_batch {
     virtual int diag(lbs_diag *) = 0;
     virtual int kernel_count() const = 0;
     virtual int set_graph(int on) = 0;
+    virtual int status(int *st) = 0;
+    virtual int set_active(int k, int on) = 0;
     char err[512] = {0};
 };
 
@@ -231,6 +249,9 @@ struct Batch : lbs_batch {
     std::vector<lbs_ctx *> ctxs;
     Inst<R> *d_insts = nullptr;
     BatchCtl *d_bc = nullptr;
+    int *d_act = nullptr;      // instance in the work lists (device copy of act)
+    std::vector<int> act;      // host flags: instance in the work lists
+    std::vector<int> st;       // sticky per-instance status (lbs_status codes)
     WorkItem *d_cells = nullptr, *d_sor = nullptr, *d_surf = nullptr;
     int n_cells = 0, n_sor = 0, n_surf = 0;
     int tx = 32, ty = 8, sv = 0;
@@ -251,6 +272,7 @@ struct Batch : lbs_batch {
         }
         cudaFree(d_insts);
         cudaFree(d_bc);
+        cudaFree(d_act);
         cudaFree(d_cells);
         cudaFree(d_sor);
         cudaFree(d_surf);
@@ -316,6 +338,10 @@ struct Batch : lbs_batch {
         BCK(cudaMemcpy(d_insts, h.data(), n * sizeof(Inst<R>), cudaMemcpyHostToDevice));
         BCK(cudaMalloc(&d_bc, sizeof(BatchCtl)));
         BCK(cudaMemset(d_bc, 0, sizeof(BatchCtl)));
+        act.assign(n, 1);
+        st.assign(n, 0);
+        BCK(cudaMalloc(&d_act, n * sizeof(int)));
+        BCK(cudaMemcpy(d_act, act.data(), n * sizeof(int), cudaMemcpyHostToDevice));
         for (int v = 0; v < kSorVariants; v++) {
             void *f = sor_kernel(sizeof(R) == 8, v);
             BCK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -361,6 +387,7 @@ struct Batch : lbs_batch {
         sor_tile_shape(sv, stx, sty);
         std::vector<WorkItem> cells, sor, surf;
         for (int k = 0; k < n; k++) {
+            if (!act[k]) continue;
             const lbs_params &p = ctxs[k]->p;
             for (int y0 = 0; y0 < p.ny; y0 += ty)
                 for (int x0 = 0; x0 < p.nx; x0 += tx) cells.push_back({k, x0, y0, 0, 0, {0, 0, 0}});
@@ -378,6 +405,7 @@ struct Batch : lbs_batch {
         n_cells = (int)cells.size();
         n_sor = (int)sor.size();
         n_surf = (int)surf.size();
+        BCK(cudaMemcpy(d_act, act.data(), n * sizeof(int), cudaMemcpyHostToDevice));
         const int th = tx * ty;
         const void *fk[6] = {(void *)kb_cells2<R, P, OP_FORCE>, (void *)kb_cells2<R, P, OP_FD>,
                              (void *)kb_cells2<R, P, OP_COLLIDE>, (void *)kb_cells2<R, P, OP_STREAM>,
@@ -407,7 +435,7 @@ struct Batch : lbs_batch {
         kb_cells2<R, P, OP_COLLIDE><<<g_cells[2], blk, 0, s>>>(d_insts, d_cells, n_cells);
         kb_cells2<R, P, OP_STREAM><<<g_cells[3], blk, 0, s>>>(d_insts, d_cells, n_cells);
         kb_cells2<R, P, OP_GRAD><<<g_cells[4], blk, 0, s>>>(d_insts, d_cells, n_cells);
-        kb_sor_begin<R><<<1, 256, 0, s>>>(d_insts, n, d_bc);
+        kb_sor_begin<R><<<1, 256, 0, s>>>(d_insts, d_act, n, d_bc);
         void *fsor = sor_kernel(sizeof(R) == 8, sv);
         const size_t smem = sor_smem<R>(sv);
         if (capturing) {
@@ -503,16 +531,51 @@ struct Batch : lbs_batch {
         return LBS_OK;
     }
 
-    int sync() override {
+    // reads (and clears on the device) every instance's status into the
+    // sticky host copy; CUDA failures are returned
+    int collect() {
         BCK(cudaStreamSynchronize(stream));
         for (int k = 0; k < n; k++) {
             int r = ctxs[k]->impl->sync();
-            if (r) {
+            if (r == LBS_ECUDA) {
                 berr(this, "instance %d: %s", k, ctxs[k]->err);
                 return r;
             }
+            if (r && !st[k]) st[k] = r;
         }
         return LBS_OK;
+    }
+
+    // fails with the first instance (in the work lists) whose solve failed
+    int sync() override {
+        int r = collect();
+        if (r) return r;
+        for (int k = 0; k < n; k++)
+            if (act[k] && st[k]) {
+                berr(this, "instance %d: %s", k, ctxs[k]->err);
+                return st[k];
+            }
+        return LBS_OK;
+    }
+
+    int status(int *out) override {
+        int r = collect();
+        if (r) return r;
+        for (int k = 0; k < n; k++) {
+            out[k] = st[k];
+            st[k] = 0;
+        }
+        return LBS_OK;
+    }
+
+    int set_active(int k, int on) override {
+        if (k < 0 || k >= n) {
+            berr(this, "instance %d of %d", k, n);
+            return LBS_EINVAL;
+        }
+        if (act[k] == (on ? 1 : 0)) return LBS_OK;
+        act[k] = on ? 1 : 0;
+        return set_tiles(tx, ty, sv);
     }
 
     int get(int k, double *rho, double *u, double *phi, double *psi, double *C) override {
@@ -520,15 +583,17 @@ struct Batch : lbs_batch {
             berr(this, "instance %d of %d", k, n);
             return LBS_EINVAL;
         }
-        int r = sync();
+        int r = collect();
         if (r) return r;
         r = ctxs[k]->impl->get(rho, u, phi, psi, C);
         if (r) berr(this, "instance %d: %s", k, ctxs[k]->err);
         return r;
     }
 
+    // diagnostics of every instance; failed solves are reported through
+    // lbs_batch_status, not here
     int diag(lbs_diag *d) override {
-        int r = sync();
+        int r = collect();
         if (r) return r;
         int rounds = 0;
         for (int k = 0; k < n; k++) {
@@ -649,6 +714,16 @@ int lbs_batch_set_graph(lbs_batch *b, int enable) {
 }
 
 int lbs_batch_step_kernel_count(const lbs_batch *b) { return b ? b->kernel_count() : 0; }
+
+int lbs_batch_status(lbs_batch *b, int *status) {
+    if (!b || !status) return LBS_EINVAL;
+    return b->status(status);
+}
+
+int lbs_batch_set_active(lbs_batch *b, int k, int active) {
+    if (!b) return LBS_EINVAL;
+    return b->set_active(k, active);
+}
 
 void lbs_batch_destroy(lbs_batch *b) {
     if (!b) return;

@@ -77,6 +77,7 @@ struct Ctl {
     double dscale;          // scale - 1 of the last rescale
     float dscale_f;         // the same in single precision
     int sor_active;         // batched sweep: 1 while this instance's solve iterates
+    int dead;               // non-finite total seen: a batch skips this instance
     // per sweep: max |d psi|, max |d C|, max |psi|, max |C| (bits of
     // non-negative doubles, compared as unsigned integers)
     unsigned long long sweep[KMAX_SWEEPS][4];

@@ -952,7 +952,10 @@ __device__ __forceinline__ void surf2_block(const Inst<R> &I, int mode, int nblo
     ctl->scale = tot > 0 ? ctl->M0 / tot : 1.0;
     ctl->dscale = ctl->scale - 1.0;
     ctl->dscale_f = float(ctl->dscale);
-    if (!isfinite(tot)) ctl->status |= ST_DIVERGED;
+    if (!isfinite(tot)) {
+        ctl->status |= ST_DIVERGED;
+        ctl->dead = 1;
+    }
     ctl->sor_iters = rounds * sweeps_per_round;
     ctl->sor_iters_parity = I.sor_pingpong ? (rounds & 1) : 0;
     ctl->sor_exec = 0;

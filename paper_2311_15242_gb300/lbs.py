@@ -24,7 +24,12 @@ EXPORTS = ("lbs_params_default", "lbs_workspace_bytes", "lbs_create",
            "lbs_last_error", "lbs_batch_workspace_bytes", "lbs_batch_create",
            "lbs_batch_init_fields", "lbs_batch_set_tiles", "lbs_batch_step", "lbs_batch_sync",
            "lbs_batch_get_fields", "lbs_batch_diagnostics", "lbs_batch_set_graph",
-           "lbs_batch_step_kernel_count", "lbs_batch_destroy", "lbs_batch_last_error")
+           "lbs_batch_step_kernel_count", "lbs_batch_status", "lbs_batch_set_active",
+           "lbs_batch_destroy", "lbs_batch_last_error",
+           "lbs_mlp_create", "lbs_mlp_param_count", "lbs_mlp_init", "lbs_mlp_set_params",
+           "lbs_mlp_get_params", "lbs_mlp_forward", "lbs_mlp_gradient", "lbs_mlp_set_grad",
+           "lbs_mlp_adam_step", "lbs_mlp_set_data", "lbs_mlp_train", "lbs_mlp_predict",
+           "lbs_mlp_destroy", "lbs_mlp_last_error")
 KERNEL_GROUPS = ("force", "fd", "collide", "stream", "grad", "sor", "surf")
 
 
@@ -116,6 +121,25 @@ def load(build_if_missing: bool = True):
     L.lbs_batch_diagnostics.argtypes = [C.c_void_p, C.POINTER(LbsDiag)]
     L.lbs_batch_set_graph.argtypes = [C.c_void_p, C.c_int]
     L.lbs_batch_step_kernel_count.argtypes = [C.c_void_p]
+    L.lbs_batch_status.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+    _FP = C.POINTER(C.c_float)
+    L.lbs_mlp_create.argtypes = [C.c_int] * 6 + [C.c_void_p, C.POINTER(C.c_void_p)]
+    L.lbs_mlp_param_count.argtypes = [C.c_void_p]
+    L.lbs_mlp_init.argtypes = [C.c_void_p, C.c_ulonglong]
+    L.lbs_mlp_set_params.argtypes = [C.c_void_p, _FP]
+    L.lbs_mlp_get_params.argtypes = [C.c_void_p, _FP]
+    L.lbs_mlp_forward.argtypes = [C.c_void_p, _FP, C.c_int, C.c_int, _FP]
+    L.lbs_mlp_gradient.argtypes = [C.c_void_p, _FP, _FP, C.c_int, _FP, _DP]
+    L.lbs_mlp_set_grad.argtypes = [C.c_void_p, _FP]
+    L.lbs_mlp_adam_step.argtypes = [C.c_void_p, C.c_float, C.c_float, C.c_float, C.c_float]
+    L.lbs_mlp_set_data.argtypes = [C.c_void_p, _FP, _FP, C.c_int]
+    L.lbs_mlp_train.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float,
+                                C.c_float, C.c_ulonglong, _DP]
+    L.lbs_mlp_predict.argtypes = [C.c_void_p, _FP, C.c_int, C.c_int, _FP, _FP]
+    L.lbs_mlp_destroy.argtypes = [C.c_void_p]
+    L.lbs_mlp_last_error.restype = C.c_char_p
+    L.lbs_mlp_last_error.argtypes = [C.c_void_p]
+    L.lbs_batch_set_active.argtypes = [C.c_void_p, C.c_int, C.c_int]
     L.lbs_batch_destroy.argtypes = [C.c_void_p]
     L.lbs_batch_last_error.restype = C.c_char_p
     L.lbs_batch_last_error.argtypes = [C.c_void_p]
@@ -337,3 +361,110 @@ class Batch:
 
     def kernel_count(self):
         return int(self.L.lbs_batch_step_kernel_count(self.h))
+
+    def status(self):
+        """Per-instance status codes since the last call (0 = fine)."""
+        st = (C.c_int * self.n)()
+        self._check(self.L.lbs_batch_status(self.h, st))
+        return list(st)
+
+    def set_active(self, k, on=True):
+        self._check(self.L.lbs_batch_set_active(self.h, int(k), int(bool(on))))
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class Mlp:
+    """Ensemble of fully connected networks trained and evaluated by the
+    library's kernels (lbs_mlp_*).  Arrays are float32 numpy, row-major."""
+
+    def __init__(self, members, n_in, width, depth, n_out, max_batch=1024, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.L = load()
+        self.E, self.n_in, self.n_out, self.max_batch = members, n_in, n_out, max_batch
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = C.c_void_p()
+        r = self.L.lbs_mlp_create(members, n_in, width, depth, n_out, max_batch,
+                                  C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        self.h = h
+        self._check(r)
+        self.P = int(self.L.lbs_mlp_param_count(self.h))
+
+    def _check(self, r):
+        if r != LBS_OK:
+            msg = self.L.lbs_mlp_last_error(self.h).decode() if self.h else "?"
+            raise LbsError(r, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.lbs_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _f32(a, shape=None):
+        a = np.ascontiguousarray(np.asarray(a, np.float32))
+        return a.reshape(shape) if shape is not None else a
+
+    def init(self, seed):
+        self._check(self.L.lbs_mlp_init(self.h, C.c_ulonglong(seed)))
+
+    def set_params(self, theta):
+        t = self._f32(theta, (self.E * self.P,))
+        self._check(self.L.lbs_mlp_set_params(self.h, _fp(t)))
+
+    def params(self):
+        out = np.empty(self.E * self.P, np.float32)
+        self._check(self.L.lbs_mlp_get_params(self.h, _fp(out)))
+        return out.reshape(self.E, self.P)
+
+    def forward(self, x, bf16=False):
+        """x [E][B][n_in] -> y [E][B][n_out]."""
+        x = self._f32(x)
+        B = x.shape[1]
+        y = np.empty((self.E, B, self.n_out), np.float32)
+        self._check(self.L.lbs_mlp_forward(self.h, _fp(x), B, int(bool(bf16)), _fp(y)))
+        return y
+
+    def gradient(self, x, t):
+        """(loss [E], grad [E][P]) for x [E][B][n_in], t [E][B][n_out]."""
+        x, t = self._f32(x), self._f32(t)
+        g = np.empty(self.E * self.P, np.float32)
+        loss = np.empty(self.E)
+        self._check(self.L.lbs_mlp_gradient(self.h, _fp(x), _fp(t), x.shape[1], _fp(g), _dp(loss)))
+        return loss, g.reshape(self.E, self.P)
+
+    def set_grad(self, g):
+        g = self._f32(g, (self.E * self.P,))
+        self._check(self.L.lbs_mlp_set_grad(self.h, _fp(g)))
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(self.L.lbs_mlp_adam_step(self.h, lr, beta1, beta2, eps))
+
+    def set_data(self, X, Y):
+        X, Y = self._f32(X), self._f32(Y)
+        self._check(self.L.lbs_mlp_set_data(self.h, _fp(X), _fp(Y), X.shape[0]))
+
+    def train(self, iters, batch, lr, seed, beta1=0.9, beta2=0.999, eps=1e-8):
+        loss = np.empty(self.E)
+        self._check(self.L.lbs_mlp_train(self.h, int(iters), int(batch), lr, beta1, beta2, eps,
+                                         C.c_ulonglong(seed), _dp(loss)))
+        return loss
+
+    def predict(self, x, bf16=True):
+        """Ensemble mean and standard deviation [n][n_out] for x [n][n_in]."""
+        x = self._f32(x)
+        n = x.shape[0]
+        mean = np.empty((n, self.n_out), np.float32)
+        sd = np.empty((n, self.n_out), np.float32)
+        self._check(self.L.lbs_mlp_predict(self.h, _fp(x), n, int(bool(bf16)), _fp(mean), _fp(sd)))
+        return mean, sd

@@ -54,8 +54,11 @@ def summarise(history, window):
 
 def run_batch(cfgs, steps, sample_every, storage="f32", window=0.25, seed=0, log=None):
     """Step the instances as one batch; returns per-instance (Re, AR,
-    spreads) and the device throughput (MLUPS, excluding diagnostics)."""
+    spreads) and the device throughput (MLUPS, excluding diagnostics).  An
+    instance whose solve diverges is taken out of the batch and reported as
+    NaN."""
     from . import Batch, autotune
+    from .lbs import LBS_EDIVERGED
     import torch
     b = Batch(cfgs, storage=storage)
     for k, c in enumerate(cfgs):
@@ -63,6 +66,8 @@ def run_batch(cfgs, steps, sample_every, storage="f32", window=0.25, seed=0, log
         b.init_fields(k, f["phi"], f["psi"], f["C"], f["u"])
     autotune.tune(b, [c["nx"] for c in cfgs])
     hist = [[] for _ in cfgs]
+    failed = set()
+    noconv = 0
     cells = sum(c["nx"] * c["ny"] for c in cfgs)
     dev_ms = 0.0
     done = 0
@@ -76,29 +81,50 @@ def run_batch(cfgs, steps, sample_every, storage="f32", window=0.25, seed=0, log
         e1.synchronize()
         dev_ms += e0.elapsed_time(e1)
         done += n
+        for k, code in enumerate(b.status()):
+            if code == LBS_EDIVERGED and k not in failed:
+                failed.add(k)
+                b.set_active(k, False)
+            elif code:
+                noconv += 1  # a solve that hit the SOR round limit (kept)
         for k, d in enumerate(b.diagnostics()):
             hist[k].append(d)
         if log:
-            log(f"batch of {len(cfgs)}: step {done}/{steps}")
+            log(f"batch of {len(cfgs)}: step {done}/{steps}, {len(failed)} diverged, "
+                f"{noconv} SOR round limits")
     b.close()
-    out = [summarise(h, window) for h in hist]
+    nan = (float("nan"),) * 4
+    out = [nan if k in failed else summarise(h, window) for k, h in enumerate(hist)]
     return out, cells * steps / (dev_ms / 1e3) / 1e6
 
 
 def run_plain(cfg, steps, sample_every, storage="f32", window=0.25, seed=0):
     """One plain single-instance solve of a sweep point."""
     from . import Solver
+    from .lbs import LBS_EDIVERGED, LBS_ENOCONV, LbsError
     s = Solver(cfg, storage=storage)
     f = W.initial_fields(cfg, seed=seed)
     s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
     hist = []
     done = 0
-    while done < steps:
-        n = min(sample_every, steps - done)
-        s.step(n)
-        done += n
-        hist.append(s.diagnostics())
-    s.close()
+    try:
+        while done < steps:
+            n = min(sample_every, steps - done)
+            s.step(n)
+            done += n
+            try:
+                d = s.diagnostics()
+            except LbsError as e:
+                if e.code != LBS_ENOCONV:  # (SOR round limit: reported, state kept)
+                    raise
+                d = s.diagnostics()
+            hist.append(d)
+    except LbsError as e:
+        if e.code != LBS_EDIVERGED:
+            raise
+        return (float("nan"),) * 4
+    finally:
+        s.close()
     return summarise(hist, window)
 
 
@@ -121,13 +147,16 @@ def generate(n, seed, steps, sample_every=500, batch_size=64, plain=False, stora
     else:
         for i in range(0, n, batch_size):
             part = cfgs[i:i + batch_size]
-            res, m = run_batch(part, steps, sample_every, storage, window, seed=1000 + i)
+            res, m = run_batch(part, steps, sample_every, storage, window, seed=1000 + i,
+                               log=log if sample_every * 10 >= steps else None)
             mlups.append(m)
             for j, (re, ar, rs, as_) in enumerate(res):
                 Y[i + j] = (re, ar)
                 S[i + j] = (rs, as_)
             log(f"batch {i // batch_size + 1}: {m:.0f} MLUPS ({time.time() - t0:.0f} s)")
-    return dict(X=X, Y=Y, S=S, seed=seed, steps=steps, plain=plain,
+    ok = np.isfinite(Y).all(axis=1)
+    log(f"{int(ok.sum())} of {n} solves finished ({n - int(ok.sum())} diverged)")
+    return dict(X=X, Y=Y, S=S, ok=ok, seed=seed, steps=steps, plain=plain,
                 mlups=np.array(mlups), features=np.array(FEATURES), targets=np.array(TARGETS))
 
 

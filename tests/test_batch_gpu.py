@@ -59,7 +59,8 @@ def test_batch_f64_matches_oracle():
     assert all(x["step"] == 25 for x in d)
 
 
-@pytest.mark.parametrize("tiles", [(32, 8, 0), (64, 4, 1), (16, 16, 2), (128, 2, 0)])
+@pytest.mark.parametrize("tiles", [(32, 8, 0), (64, 4, 1), (16, 16, 2), (128, 2, 0), (32, 4, 0),
+                                   (64, 2, 1), (32, 16, 2), (256, 1, 0), (32, 4, 1), (32, 4, 2)])
 def test_batch_equals_single_instances(tiles):
     from paper_2311_15242_gb300 import Solver
     cfgs = small_sweep(4)
@@ -146,3 +147,32 @@ def test_full_sweep_64_instances():
     err = errors(o.fields(), got)
     assert within(err, F32_TOL), err
     b.close()
+
+
+def test_diverging_instance_is_isolated():
+    """An instance started far above the lattice sound speed (u = 0.8)
+    diverges; the batch reports it through the per-instance status, skips
+    it from then on, and the other instances go on unchanged."""
+    from paper_2311_15242_gb300 import Solver
+    from paper_2311_15242_gb300.lbs import LBS_EDIVERGED
+    cfgs = small_sweep(3)
+    b, fs = make_batch(cfgs, "f32")
+    f = fs[1]
+    u = np.zeros_like(f["u"])
+    u[1] = 0.8
+    b.init_fields(1, f["phi"], f["psi"], f["C"], u)
+    b.step(40)
+    st = b.status()
+    assert st[1] == LBS_EDIVERGED and st[0] == 0 and st[2] == 0, st
+    d = b.diagnostics()
+    assert d[1]["step"] < 40 and d[0]["step"] == d[2]["step"] == 40
+    for k in (0, 2):
+        s = Solver(cfgs[k], storage="f32")
+        s.init_fields(fs[k]["phi"], fs[k]["psi"], fs[k]["C"], fs[k]["u"])
+        s.step(40)
+        err = errors(s.fields(), b.fields(k))
+        assert within(err, F32_TOL), (k, err)
+        s.close()
+    b.set_active(1, False)
+    b.step(8)
+    assert b.status() == [0, 0, 0]
