@@ -17,8 +17,8 @@ void Launch3<R, P>::moments(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s) {
     k_moments3<R, P><<<g, b, 0, s>>>(I);
 }
 template <typename R, typename P>
-void Launch3<R, P>::grad(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s) {
-    k_grad3<R><<<g, b, 0, s>>>(I);
+void Launch3<R, P>::grad(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s, int guess) {
+    k_grad3<R><<<g, b, 0, s>>>(I, guess);
 }
 template <typename R, typename P>
 void Launch3<R, P>::force(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s) {

@@ -70,8 +70,10 @@ struct Layout {
     int nblocks;
 };
 
-// scalar planes: 21 in 2D, 25 in 3D (z components of j, grad, u, F)
-constexpr int kScal2 = 21, kScal3 = 25;
+// scalar planes: 21 in 2D, 25 in 3D (z components of j, grad, u, F), then
+// the 4 rest-population planes of fT, fM, gT, gM and the previous time
+// level of psi and C
+constexpr int kScal2 = 21, kScal3 = 25, kRest = 6;
 
 template <typename R, typename P>
 Layout layout_of(const lbs_params *p) {
@@ -83,7 +85,7 @@ Layout layout_of(const lbs_params *p) {
     L.pops_off = 0;
     size_t pops = 4 * (size_t)(d3 ? Q19 : Q9) * (size_t)L.plane * sizeof(P);
     L.scal_off = pops;
-    size_t scal = (d3 ? kScal3 : kScal2) * pb;
+    size_t scal = ((d3 ? kScal3 : kScal2) + kRest) * pb;
     L.flag_off = align_up(L.scal_off + scal, 256);
     L.ctl_off = align_up(L.flag_off + 2 * (size_t)L.plane, 256);
     L.part_off = align_up(L.ctl_off + sizeof(Ctl), 256);
@@ -131,6 +133,10 @@ struct Solver : Base {
         }
         I.rhoR0 = R(p->rhoR0);
         I.rhoB0 = R(p->rhoB0);
+        I.inv_rhoR0 = R(1.0 / p->rhoR0);
+        I.inv_rhoB0 = R(1.0 / p->rhoB0);
+        I.inv_2muR = R(0.5 / p->muR0);
+        I.inv_2muB = R(0.5 / p->muB0);
         I.alphaR = R(p->alphaR);
         I.alphaB = R(p->alphaB);
         // (c_s^k)^2 = (3/5)(1 - alpha^k) in 2D, (1/2)(1 - alpha^k) in 3D (App. A)
@@ -224,6 +230,11 @@ struct Solver : Base {
         if (D == 3) {
             R **f3[] = {&I.jz, &I.gz, &I.uz, &I.Fz};
             for (int k = 0; k < kScal3 - kScal2; k++) *f3[k] = sc + (kScal2 + k) * pb;
+        }
+        {
+            R **fr[] = {&I.fT0, &I.fM0, &I.gT0, &I.gM0, &I.psip, &I.Cp};
+            const int base = D == 3 ? kScal3 : kScal2;
+            for (int k = 0; k < kRest; k++) *fr[k] = sc + (base + k) * pb;
         }
         I.ctl = (Ctl *)(ws + L.ctl_off);
         I.part = (double *)(ws + L.part_off);
@@ -489,12 +500,12 @@ struct Solver : Base {
             k_init2<R, P><<<grid, block, 0, s>>>(I, dphi, psi ? dpsi : nullptr,
                                               C ? dC : nullptr, u ? du : nullptr);
             k_moments2<R, P><<<grid, block, 0, s>>>(I);
-            k_grad2<R><<<grid, block, 0, s>>>(I);
+            k_grad2<R><<<grid, block, 0, s>>>(I, 0);
         } else {
             L3::init(I, grid, block, s, dphi, psi ? dpsi : nullptr, C ? dC : nullptr,
                      u ? du : nullptr);
             L3::moments(I, grid, block, s);
-            L3::grad(I, grid, block, s);
+            L3::grad(I, grid, block, s, 0);
         }
         k_surf2<R, BS><<<surf_grid, block, 0, s>>>(I, 0, surf_blocks, sweeps_per_round());
         int r = launch_check();

@@ -95,6 +95,8 @@ struct Inst {
     int wall[3];
     R uw_lo[3][3], uw_hi[3][3];
     R rhoR0, rhoB0, alphaR, alphaB, cs2R, cs2B, muR0, muB0;
+    R inv_rhoR0, inv_rhoB0;  // 1 / rho^k0
+    R inv_2muR, inv_2muB;    // 1 / (2 mu^k0)
     R beta, eps_n, eps_w;
     R sigma0, sigma_min, E0, psi_inf, cmc;
     int eos, source, transport;
@@ -120,12 +122,17 @@ struct Inst {
     // low-precision forms): ldp / stp below convert
     void *fT, *fM;            // total populations minus shift, minority colour
     void *gT, *gM;            // post-collision buffers
+    // the rest populations (i = 0) of the four sets, in R for every storage
+    // form: they absorb the rounding residuals of the moving populations, so
+    // that the stored populations of a cell sum to its colour masses
+    R *fT0, *fM0, *gT0, *gM0;
     uint8_t *flag, *gflag;    // minority colour of a cell: 0 red, 1 blue
     R *rhoR, *rhoB, *rhoN, *jx, *jy, *jz;
     R *gx, *gy, *gz, *a, *chi;  // grad rhoN, |grad rhoN|, 1 - rhoN
     R *ux, *uy, *uz, *Fx, *Fy, *Fz;  // z components: D3Q19 only (null in 2D)
     R *psi, *C, *S, *B, *rpsi, *rC;
     R *psi2, *C2;             // second buffers of the blocked SOR rounds
+    R *psip, *Cp;             // psi, C of the previous time level (SOR initial guess)
     Ctl *ctl;
     double *part;             // per-block partial sums of reductions
 };
@@ -176,6 +183,30 @@ __device__ __forceinline__ void stp(const Inst<R> &I, void *base, long long k, R
     ((P *)base)[k] = PopCvt<P>::from(PopCvt<P>::scaled ? v * I.pscale : v);
 }
 
+// population i of cell c of a set (moving array mov, rest plane rest)
+template <typename R, typename P>
+__device__ __forceinline__ R ldq(const Inst<R> &I, const void *mov, const R *rest, int i,
+                                 long long c) {
+    return i == 0 ? rest[c] : ldp<R, P>(I, mov, (long long)i * I.plane + c);
+}
+// store moving population i (i >= 1); returns the value actually stored
+template <typename R, typename P>
+__device__ __forceinline__ R stq(const Inst<R> &I, void *mov, int i, long long c, R v) {
+    const P s = PopCvt<P>::from(PopCvt<P>::scaled ? v * I.pscale : v);
+    ((P *)mov)[(long long)i * I.plane + c] = s;
+    const R back = R(PopCvt<P>::to(s));
+    return PopCvt<P>::scaled ? back * I.pinv : back;
+}
+
+// error-free transformations (Knuth's TwoSum): a + b = s + e exactly
+template <typename R>
+__device__ __forceinline__ R two_sum(R a, R b, R &e) {
+    const R s = a + b;
+    const R bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+    return s;
+}
+
 // ---------------------------------------------------------------------------
 // Boundary mapping.  Periodic axes wrap; on a walled axis the coordinate is
 // mirrored about the half-way wall (-1 -> 0, -2 -> 1, n -> n-1, ...).
@@ -194,6 +225,53 @@ __device__ __forceinline__ int map_axis(int c, int n, int wall, int bit, int &re
     side = 1;
     return 2 * n - 1 - c;
 }
+
+// the mapped coordinates of offsets -2..2 along one axis, computed once per
+// thread: v (coordinate), r (reflection bit of the axis or 0), s (wall side)
+struct Ax {
+    int v[5];
+    unsigned char r[5];
+    signed char s[5];
+};
+__device__ __forceinline__ Ax make_ax(int c, int n, int wall, int bit) {
+    Ax a;
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        int refl = 0, side;
+        a.v[k] = map_axis(c + k - 2, n, wall, bit, refl, side);
+        a.r[k] = (unsigned char)refl;
+        a.s[k] = (signed char)side;
+    }
+    return a;
+}
+// neighbour (dx, dy) of a 2D cell from its axes (|d| <= 2)
+template <typename R>
+__device__ __forceinline__ long long nbx2(const Inst<R> &I, const Ax &X, const Ax &Y, int dx,
+                                          int dy, int &refl, int &sx, int &sy) {
+    refl = X.r[dx + 2] | Y.r[dy + 2];
+    sx = X.s[dx + 2];
+    sy = Y.s[dy + 2];
+    return (long long)Y.v[dy + 2] * I.pitch + X.v[dx + 2];
+}
+// neighbour (dx, dy, dz) of a 3D cell from its axes
+template <typename R>
+__device__ __forceinline__ long long nbx3(const Inst<R> &I, const Ax &X, const Ax &Y, const Ax &Z,
+                                          int dx, int dy, int dz, int &refl, int &sx, int &sy,
+                                          int &sz) {
+    refl = X.r[dx + 2] | Y.r[dy + 2] | Z.r[dz + 2];
+    sx = X.s[dx + 2];
+    sy = Y.s[dy + 2];
+    sz = Z.s[dz + 2];
+    return ((long long)Z.v[dz + 2] * I.ny + Y.v[dy + 2]) * I.pitch + X.v[dx + 2];
+}
+
+// division and inverse square root: IEEE in double precision; in single
+// precision the hardware approximations (about 2 ulp), whose errors are of
+// the order of the FP32 rounding of the stored fields
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double frsq(double a) { return 1.0 / sqrt(a); }
+__device__ __forceinline__ float frsq(float a) { return rsqrtf(a); }
 
 template <typename R>
 __device__ __forceinline__ long long nb2(const Inst<R> &I, int x, int y, int dx, int dy,

@@ -35,18 +35,12 @@ __device__ __forceinline__ R shift_of(const Inst<R> &I, int i, int flag) {
     return i == 0 ? I.shift0[flag] : I.shift[i];
 }
 
-// both colours of one direction from (fT, fM, flag)
-template <typename R>
-__device__ __forceinline__ void split(R shift, R t, R m, int flag, R &fr, R &fb) {
-    R other = (shift + t) - m;
-    fr = flag ? other : m;
-    fb = flag ? m : other;
-}
 
 // colour densities and momentum (without the force) of one cell
 template <typename R>
 struct Mom2 {
     R rR, rB, drho, jx, jy;  // rho^R, rho^B, rho - rho_s[flag], sum_i f_i e_i
+    R rm_s, rm_c, dr_s, dr_c;  // minority mass and drho as unevaluated sums s + c
 };
 
 // compensated summation (Knuth's TwoSum): s + c carries the sum of the added
@@ -69,7 +63,7 @@ struct CSum {
 template <typename R>
 __device__ __forceinline__ Mom2<R> moments9(const Inst<R> &I, const R *fT, const R *fM,
                                            int flag) {
-    Mom2<R> m{R(0), R(0), R(0), R(0), R(0)};
+    Mom2<R> m{R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     CSum<R> rmc, drc;
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
@@ -80,6 +74,10 @@ __device__ __forceinline__ Mom2<R> moments9(const Inst<R> &I, const R *fT, const
     }
     const R rm = rmc.value();
     m.drho = drc.value();
+    m.rm_s = rmc.s;
+    m.rm_c = rmc.c;
+    m.dr_s = drc.s;
+    m.dr_c = drc.c;
     // majority colour = total - minority
     R rmaj = (I.rho_s[flag] - rm) + m.drho;
     m.rR = flag ? rmaj : rm;
@@ -90,14 +88,14 @@ __device__ __forceinline__ Mom2<R> moments9(const Inst<R> &I, const R *fT, const
 // minority colour of a cell by colour fraction (0: red, 1: blue)
 template <typename R>
 __device__ __forceinline__ int minority(const Inst<R> &I, R rR, R rB) {
-    return (rR / I.rhoR0 <= rB / I.rhoB0) ? 0 : 1;
+    return (rR * I.inv_rhoR0 <= rB * I.inv_rhoB0) ? 0 : 1;
 }
 
 // colour function, Eq. 6
 template <typename R>
 __device__ __forceinline__ R colour_fn(const Inst<R> &I, R rR, R rB) {
-    R xr = rR / I.rhoR0, xb = rB / I.rhoB0;
-    return (xr - xb) / (xr + xb);
+    const R xr = rR * I.inv_rhoR0, xb = rB * I.inv_rhoB0;
+    return fdiv(xr - xb, xr + xb);
 }
 
 // ---------------------------------------------------------------------------
@@ -151,16 +149,42 @@ __global__ void k_init2(Inst<R> I, const double *phi, const double *psi, const d
     minv9<double>(mR, fR);
     minv9<double>(mB, fB);
     const int fl = (rR / double(I.rhoR0) <= rB / double(I.rhoB0)) ? 0 : 1;
+    // moving populations rounded to the storage type; the rest populations
+    // take what the rounding left out, so the stored masses are the intended ones
+    double tT = 0, tM = 0, sT = 0, sM = 0;
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
-        stp<R, P>(I, I.fT, i * I.plane + c, R((fR[i] + fB[i]) - double(shift_of(I, i, fl))));
-        stp<R, P>(I, I.fM, i * I.plane + c, R(fl ? fB[i] : fR[i]));
+        const double vT = (fR[i] + fB[i]) - double(shift_of(I, i, fl)), vM = fl ? fB[i] : fR[i];
+        tT += vT;
+        tM += vM;
+        if (i) {
+            sT += double(stq<R, P>(I, I.fT, i, c, R(vT)));
+            sM += double(stq<R, P>(I, I.fM, i, c, R(vM)));
+        }
     }
+    I.fT0[c] = R(tT - sT);
+    I.fM0[c] = R(tM - sM);
     I.flag[c] = (uint8_t)fl;
     I.psi[c] = psi ? R(psi[d]) : R(0);
     I.C[c] = C ? R(C[d]) : R(0);
+    I.psip[c] = I.psi[c];
+    I.Cp[c] = I.C[c];
     I.S[c] = R(0);
     I.B[c] = R(0);
+}
+
+// initial guess of the Crank-Nicolson solves (Sec. 2.2): the linear
+// extrapolation 2 x^n - x^(n-1) of the last two time levels instead of
+// x^n; SOR converges to the same solution within its tolerance in fewer
+// sweeps.  Elementwise (run where no kernel reads psi, C of neighbours).
+template <typename R>
+__device__ __forceinline__ void sor_guess(const Inst<R> &I, long long c) {
+    if (!I.transport) return;
+    const R p = I.psi[c], q = I.C[c];
+    I.psi[c] = R(2) * p - I.psip[c];
+    I.C[c] = R(2) * q - I.Cp[c];
+    I.psip[c] = p;
+    I.Cp[c] = q;
 }
 
 // moments of the stored populations -> rho^R, rho^B, rho^N, momentum
@@ -184,8 +208,8 @@ __global__ void k_moments2(Inst<R> I) {
     R fT[Q9], fM[Q9];
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
-        fT[i] = ldp<R, P>(I, I.fT, i * I.plane + c);
-        fM[i] = ldp<R, P>(I, I.fM, i * I.plane + c);
+        fT[i] = ldq<R, P>(I, I.fT, I.fT0, i, c);
+        fM[i] = ldq<R, P>(I, I.fM, I.fM0, i, c);
     }
     store_moments(I, c, fT, fM, I.flag[c]);
 }
@@ -201,20 +225,21 @@ __global__ void k_moments2(Inst<R> I) {
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ R frac(const Inst<R> &I, long long j, bool red) {
-    R xr = I.rhoR[j] / I.rhoR0, xb = I.rhoB[j] / I.rhoB0;
-    return (red ? xr : xb) / (xr + xb);
+    const R xr = I.rhoR[j] * I.inv_rhoR0, xb = I.rhoB[j] * I.inv_rhoB0;
+    return fdiv(red ? xr : xb, xr + xb);
 }
 
 template <typename R>
-__device__ __forceinline__ void grad2_cell(const Inst<R> &I, int x, int y) {
+__device__ __forceinline__ void grad2_cell(const Inst<R> &I, int x, int y, bool guess = true) {
     if (x >= I.nx || y >= I.ny) return;
     long long c = (long long)y * I.pitch + x;
     const bool blue_side = I.rhoN[c] <= R(0);
+    const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2);
     R gx = R(0), gy = R(0);
 #pragma unroll
     for (int i = 1; i < Q9; i++) {
         int refl, sx, sy;
-        long long j = nb2(I, x, y, ex9(i), ey9(i), refl, sx, sy);
+        long long j = nbx2(I, X, Y, ex9(i), ey9(i), refl, sx, sy);
         R v = frac(I, j, blue_side);
         gx += w9<R>(i) * R(ex9(i)) * v;
         gy += w9<R>(i) * R(ey9(i)) * v;
@@ -226,11 +251,14 @@ __device__ __forceinline__ void grad2_cell(const Inst<R> &I, int x, int y) {
     I.gy[c] = gy;
     I.a[c] = sqrt(gx * gx + gy * gy);
     I.chi[c] = R(2) * frac(I, c, false);
+    if (guess) sor_guess(I, c);
 }
 
+// guess: also form the SOR initial guess (every step; not at initialisation)
 template <typename R>
-__global__ void k_grad2(Inst<R> I) {
-    grad2_cell(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+__global__ void k_grad2(Inst<R> I, int guess = 1) {
+    grad2_cell(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
+               guess != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -243,15 +271,16 @@ __device__ __forceinline__ void force2_cell(const Inst<R> &I, int x, int y) {
     if (x >= I.nx || y >= I.ny) return;
     long long c = (long long)y * I.pitch + x;
     const R e2 = I.eps_n * I.eps_n;
+    const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2);
     R divn = R(0), dpx = R(0), dpy = R(0);
 #pragma unroll
     for (int i = 1; i < Q9; i++) {
         int refl, sx, sy;
-        long long j = nb2(I, x, y, ex9(i), ey9(i), refl, sx, sy);
+        long long j = nbx2(I, X, Y, ex9(i), ey9(i), refl, sx, sy);
         R gx = I.gx[j], gy = I.gy[j];
         if (refl & 1) gx = -gx;  // normal component mirrored with a sign change
         if (refl & 2) gy = -gy;
-        R inv = R(1) / sqrt(gx * gx + gy * gy + e2);
+        R inv = frsq(gx * gx + gy * gy + e2);
         R nx = -gx * inv, ny = -gy * inv;
         divn += w9<R>(i) * (R(ex9(i)) * nx + R(ey9(i)) * ny);
         R p = I.psi[j];
@@ -265,7 +294,7 @@ __device__ __forceinline__ void force2_cell(const Inst<R> &I, int x, int y) {
     R sigma, mco;
     R Fx, Fy;
     if (eos(I, I.psi[c], sigma, mco)) {
-        R inv = R(1) / sqrt(gx * gx + gy * gy + e2);
+        R inv = frsq(gx * gx + gy * gy + e2);
         R nx = -gx * inv, ny = -gy * inv;
         R ndp = nx * dpx + ny * dpy;
         Fx = -R(0.5) * sigma * kappa * gx - R(0.5) * a * mco * (dpx - ndp * nx);
@@ -282,8 +311,9 @@ __device__ __forceinline__ void force2_cell(const Inst<R> &I, int x, int y) {
     Fy += drb * I.g[1];
     I.Fx[c] = Fx;
     I.Fy[c] = Fy;
-    I.ux[c] = (I.jx[c] + R(0.5) * Fx) / rho;
-    I.uy[c] = (I.jy[c] + R(0.5) * Fy) / rho;
+    const R irho = fdiv(R(1), rho);
+    I.ux[c] = (I.jx[c] + R(0.5) * Fx) * irho;
+    I.uy[c] = (I.jy[c] + R(0.5) * Fy) * irho;
 }
 
 template <typename R>
@@ -305,8 +335,8 @@ __device__ __forceinline__ R weno_m(const R *v) {  // v points at node i, v[-2..
     const R eps = R(1e-6);
     R d2m = v[0] - R(2) * v[-1] + v[-2];
     R d20 = v[1] - R(2) * v[0] + v[-1];
-    R r = (eps + d2m * d2m) / (eps + d20 * d20);
-    R w = R(1) / (R(1) + R(2) * r * r);
+    R r = fdiv(eps + d2m * d2m, eps + d20 * d20);
+    R w = fdiv(R(1), R(1) + R(2) * r * r);
     R dpm2 = v[-1] - v[-2], dpm1 = v[0] - v[-1], dp0 = v[1] - v[0];
     return R(0.5) * ((dpm1 + dp0) - w * (dpm2 - R(2) * dpm1 + dp0));
 }
@@ -315,8 +345,8 @@ __device__ __forceinline__ R weno_p(const R *v) {  // v[-1..2]
     const R eps = R(1e-6);
     R d2p = v[2] - R(2) * v[1] + v[0];
     R d20 = v[1] - R(2) * v[0] + v[-1];
-    R r = (eps + d2p * d2p) / (eps + d20 * d20);
-    R w = R(1) / (R(1) + R(2) * r * r);
+    R r = fdiv(eps + d2p * d2p, eps + d20 * d20);
+    R w = fdiv(R(1), R(1) + R(2) * r * r);
     R dpm1 = v[0] - v[-1], dp0 = v[1] - v[0], dp1 = v[2] - v[1];
     return R(0.5) * ((dpm1 + dp0) - w * (dp1 - R(2) * dp0 + dpm1));
 }
@@ -337,15 +367,16 @@ __device__ __forceinline__ void fd2_cell(const Inst<R> &I, int x, int y, double 
     long long c = (long long)y * I.pitch + x;
     // line values of Psi_x, Phi_x along x and Psi_y, Phi_y along y
     R Px[5], Cx[5], Py[5], Cy[5];
+    const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2);
 #pragma unroll
     for (int k = -2; k <= 2; k++) {
         int refl, sx, sy;
-        long long j = nb2(I, x, y, k, 0, refl, sx, sy);
+        long long j = nbx2(I, X, Y, k, 0, refl, sx, sy);
         R sgn = (refl & 1) ? R(-1) : R(1);
         R u = I.ux[j];
         Px[k + 2] = sgn * I.psi[j] * I.a[j] * u;
         Cx[k + 2] = sgn * I.C[j] * I.chi[j] * u;
-        j = nb2(I, x, y, 0, k, refl, sx, sy);
+        j = nbx2(I, X, Y, 0, k, refl, sx, sy);
         sgn = (refl & 2) ? R(-1) : R(1);
         u = I.uy[j];
         Py[k + 2] = sgn * I.psi[j] * I.a[j] * u;
@@ -373,7 +404,7 @@ __device__ __forceinline__ void fd2_cell(const Inst<R> &I, int x, int y, double 
         int dx = f == 0 ? -1 : (f == 1 ? 1 : 0);
         int dy = f == 2 ? -1 : (f == 3 ? 1 : 0);
         int refl, sx, sy;
-        long long j2 = nb2(I, x, y, dx, dy, refl, sx, sy);
+        long long j2 = nbx2(I, X, Y, dx, dy, refl, sx, sy);
         if (refl) continue;
         Lp += R(0.5) * (wp + (I.a[j2] + I.eps_w)) * (I.psi[j2] - psi);
         Lc += R(0.5) * (wc + (I.chi[j2] + I.eps_w)) * (I.C[j2] - Cc);
@@ -406,8 +437,8 @@ __device__ __forceinline__ void collide2_cell(const Inst<R> &I, int x, int y) {
     const int fl = I.flag[c];
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
-        fT[i] = ldp<R, P>(I, I.fT, i * I.plane + c);
-        fM[i] = ldp<R, P>(I, I.fM, i * I.plane + c);
+        fT[i] = ldq<R, P>(I, I.fT, I.fT0, i, c);
+        fM[i] = ldq<R, P>(I, I.fM, I.fM0, i, c);
     }
     Mom2<R> mo = moments9(I, fT, fM, fl);
     const R rR = mo.rR, rB = mo.rB;
@@ -419,10 +450,11 @@ __device__ __forceinline__ void collide2_cell(const Inst<R> &I, int x, int y) {
 
     // d_a(rho^k u_a) by the isotropic stencil, u at walls as the ghost velocity
     R dRx = R(0), dRy = R(0), dBx = R(0), dBy = R(0);
+    const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2);
 #pragma unroll
     for (int i = 1; i < Q9; i++) {
         int refl, sx, sy;
-        long long j = nb2(I, x, y, ex9(i), ey9(i), refl, sx, sy);
+        long long j = nbx2(I, X, Y, ex9(i), ey9(i), refl, sx, sy);
         R vx = I.ux[j], vy = I.uy[j];
         ghost_u2(I, refl, sx, sy, vx, vy);
         R r1 = I.rhoR[j], r2 = I.rhoB[j];
@@ -474,9 +506,9 @@ __device__ __forceinline__ void collide2_cell(const Inst<R> &I, int x, int y) {
 
     // relaxation (Eq. 38) with s_v from the mixture viscosity (Eq. 43)
     const R rN = colour_fn(I, rR, rB);
-    const R inv_mu = (R(1) + rN) / (R(2) * I.muR0) + (R(1) - rN) / (R(2) * I.muB0);
+    const R inv_mu = (R(1) + rN) * I.inv_2muR + (R(1) - rN) * I.inv_2muB;
     const R pk = rR * I.cs2R + rB * I.cs2B;
-    const R sv = R(1) / (R(0.5) + R(1) / (inv_mu * pk));
+    const R sv = fdiv(R(1), R(0.5) + fdiv(R(1), inv_mu * pk));
     const R Sd[Q9] = {R(0), R(1.25), R(1.14), R(0), R(1.6), R(0), R(1.6), sv, sv};
     // forcing moments of Eq. 4 (closed form for D2Q9)
     const R uF = ux * Fx + uy * Fy;
@@ -486,7 +518,8 @@ __device__ __forceinline__ void collide2_cell(const Inst<R> &I, int x, int y) {
     R dm[Q9];
 #pragma unroll
     for (int j = 0; j < Q9; j++)
-        dm[j] = (-Sd[j] * neq[j] + (R(1) - R(0.5) * Sd[j]) * (Cm[j] + Fh[j])) / R(mnorm9(j));
+        dm[j] = (-Sd[j] * neq[j] + (R(1) - R(0.5) * Sd[j]) * (Cm[j] + Fh[j])) *
+                (R(1) / R(mnorm9(j)));
 
     // post-collision total minus shift
     R post[Q9];
@@ -508,16 +541,23 @@ __device__ __forceinline__ void collide2_cell(const Inst<R> &I, int x, int y) {
     // rdag = sum_i f_i^dagger (= rho up to rounding) so that the colour mass
     // is conserved without a systematic rounding bias.
     const R ggx = I.gx[c], ggy = I.gy[c];
-    const R gn = sqrt(ggx * ggx + ggy * ggy + I.eps_n * I.eps_n);
-    const R seg = I.beta * rR * rB / (rho * rho) * R(3) * pk / gn;
-    const R fr = rmin / rdag;
+    const R seg = I.beta * rR * rB * R(3) * pk *
+                  frsq(ggx * ggx + ggy * ggy + I.eps_n * I.eps_n) * fdiv(R(1), rho * rho);
+    const R fr = fdiv(rmin, rdag);
     const R sg = fl ? R(-1) : R(1);
+    // moving populations as stored; the rest populations close the cell's
+    // total and minority mass on the pre-collision values (collision keeps
+    // the total, recolouring each colour): every rounding residual of the
+    // step stays in the cell
+    CSum<R> sT, sM;
 #pragma unroll
-    for (int i = 0; i < Q9; i++) {
-        R segi = i == 0 ? R(0) : seg * w9<R>(i) * (R(ex9(i)) * ggx + R(ey9(i)) * ggy);
-        stp<R, P>(I, I.gT, i * I.plane + c, post[i]);
-        stp<R, P>(I, I.gM, i * I.plane + c, fr * (shift_of(I, i, fl) + post[i]) + sg * segi);
+    for (int i = 1; i < Q9; i++) {
+        const R segi = seg * w9<R>(i) * (R(ex9(i)) * ggx + R(ey9(i)) * ggy);
+        sT.add(stq<R, P>(I, I.gT, i, c, post[i]));
+        sM.add(stq<R, P>(I, I.gM, i, c, fr * (I.shift[i] + post[i]) + sg * segi));
     }
+    I.gT0[c] = (mo.dr_s - sT.s) + (mo.dr_c - sT.c);
+    I.gM0[c] = (mo.rm_s - sM.s) + (mo.rm_c - sM.c);
     I.gflag[c] = (uint8_t)fl;
 }
 
@@ -535,40 +575,107 @@ template <typename R, typename P>
 __device__ __forceinline__ void stream2_cell(const Inst<R> &I, int x, int y) {
     if (x >= I.nx || y >= I.ny) return;
     long long c = (long long)y * I.pitch + x;
-    R fT[Q9], fR[Q9], fB[Q9];
-    const R rRc = I.rhoR[c], rBc = I.rhoB[c];
     const int flc = I.gflag[c];
+    const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2);
+    // 1. the streamed (total, minority) pairs as stored at their sources
+    //    (i = 0 stays in its own cell); slow: bit i set where the source's
+    //    flag differs from the cell's or the link crosses a wall (then the
+    //    cell's own opposite population is reflected)
+    R t[Q9], m[Q9];
+    unsigned slow = 0, fbits = 0;
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         int refl, sx, sy;
-        long long j = nb2(I, x, y, -ex9(i), -ey9(i), refl, sx, sy);
+        const long long j = nbx2(I, X, Y, -ex9(i), -ey9(i), refl, sx, sy);
         if (!refl) {
-            // (i = 0 stays in its own cell, j = c: shift of the cell's old flag)
-            fT[i] = ldp<R, P>(I, I.gT, i * I.plane + j);
+            t[i] = ldq<R, P>(I, I.gT, I.gT0, i, j);
+            m[i] = ldq<R, P>(I, I.gM, I.gM0, i, j);
             const int fj = I.gflag[j];
-            split(shift_of(I, i, fj), fT[i], ldp<R, P>(I, I.gM, i * I.plane + j), fj, fR[i], fB[i]);
+            fbits |= (unsigned)fj << i;
+            if (fj != flc) slow |= 1u << i;
         } else {
-            R uwx = R(0), uwy = R(0);
-            int nw = 0;
-            if (refl & 1) {
-                const R *w = sx < 0 ? I.uw_lo[0] : I.uw_hi[0];
-                uwx += w[0];
-                uwy += w[1];
-                nw++;
-            }
-            if (refl & 2) {
-                const R *w = sy < 0 ? I.uw_lo[1] : I.uw_hi[1];
-                uwx += w[0];
-                uwy += w[1];
-                nw++;
-            }
-            R eu = (R(ex9(i)) * uwx + R(ey9(i)) * uwy) / R(nw);
-            R mw = R(2) * w9<R>(i) * eu * R(3);
-            const int io = opp9(i);
-            fT[i] = ldp<R, P>(I, I.gT, io * I.plane + c) + mw * (rRc + rBc);
-            const R mmin = ldp<R, P>(I, I.gM, io * I.plane + c) + mw * (flc ? rBc : rRc);
-            split(I.shift[i], fT[i], mmin, flc, fR[i], fB[i]);  // i != 0 here
+            t[i] = ldp<R, P>(I, I.gT, opp9(i) * I.plane + c);
+            m[i] = ldp<R, P>(I, I.gM, opp9(i) * I.plane + c);
+            fbits |= (unsigned)flc << i;
+            slow |= 1u << i;
         }
+    }
+    // 2. fast path: every population moves unchanged (no rounding anywhere);
+    //    the cell keeps its flag unless its minority has become the majority
+    if (!slow) {
+        CSum<R> tot, mn;
+        R jx = R(0), jy = R(0);
+#pragma unroll
+        for (int i = 0; i < Q9; i++) {
+            tot.add(t[i]);
+            mn.add(m[i]);
+            if (ex9(i)) jx += R(ex9(i)) * t[i];
+            if (ey9(i)) jy += R(ey9(i)) * t[i];
+        }
+        const R rmin = mn.value(), rmaj = (I.rho_s[flc] - rmin) + tot.value();
+        const R rR = flc ? rmaj : rmin, rB = flc ? rmin : rmaj;
+        if (minority(I, rR, rB) == flc) {
+#pragma unroll
+            for (int i = 1; i < Q9; i++) {
+                stp<R, P>(I, I.fT, (long long)i * I.plane + c, t[i]);
+                stp<R, P>(I, I.fM, (long long)i * I.plane + c, m[i]);
+            }
+            I.fT0[c] = t[0];
+            I.fM0[c] = m[0];
+            I.flag[c] = (uint8_t)flc;
+            I.rhoR[c] = rR;
+            I.rhoB[c] = rB;
+            I.rhoN[c] = colour_fn(I, rR, rB);
+            I.jx[c] = jx;
+            I.jy[c] = jy;
+            return;
+        }
+    }
+    // 3. general path: colours re-split where the flags differ, moving-wall
+    //    terms (2 w_i rho^k (e_i . u_w) / c_s^2) added; every value carried
+    //    as hi + lo (TwoSum errors), and the rest populations close the
+    //    cell's total and minority mass exactly
+    const R rRc = I.rhoR[c], rBc = I.rhoB[c];
+    R fR[Q9], fB[Q9];
+    R loT = R(0), loR = R(0), loB = R(0);
+#pragma unroll
+    for (int i = 0; i < Q9; i++) {
+        const int fj = (fbits >> i) & 1;
+        R tlo = R(0), mlo = R(0);
+        R sh = shift_of(I, i, fj);
+        if ((slow >> i) & 1) {
+            int refl, sx, sy;
+            nbx2(I, X, Y, -ex9(i), -ey9(i), refl, sx, sy);
+            if (refl) {
+                R uwx = R(0), uwy = R(0);
+                int nw = 0;
+                if (refl & 1) {
+                    const R *w = sx < 0 ? I.uw_lo[0] : I.uw_hi[0];
+                    uwx += w[0];
+                    uwy += w[1];
+                    nw++;
+                }
+                if (refl & 2) {
+                    const R *w = sy < 0 ? I.uw_lo[1] : I.uw_hi[1];
+                    uwx += w[0];
+                    uwy += w[1];
+                    nw++;
+                }
+                const R eu = (R(ex9(i)) * uwx + R(ey9(i)) * uwy) / R(nw);
+                const R mw = R(2) * w9<R>(i) * eu * R(3);
+                t[i] = two_sum(t[i], mw * (rRc + rBc), tlo);
+                m[i] = two_sum(m[i], mw * (flc ? rBc : rRc), mlo);
+                sh = I.shift[i];
+            }
+        }
+        loT += tlo;
+        R e1, e2;
+        const R o = two_sum(two_sum(sh, t[i], e1), -m[i], e2);
+        const R olo = (e1 + e2) + (tlo - mlo);
+        fR[i] = fj ? o : m[i];
+        fB[i] = fj ? m[i] : o;
+        loR += fj ? olo : mlo;
+        loB += fj ? mlo : olo;
     }
     R rR = R(0), rB = R(0);
 #pragma unroll
@@ -579,14 +686,33 @@ __device__ __forceinline__ void stream2_cell(const Inst<R> &I, int x, int y) {
     const int fl = minority(I, rR, rB);
     // a change of flag re-expresses the rest population against the new
     // rest shift (the moving shifts are common to both flags)
-    if (fl != flc) fT[0] = (I.shift0[flc] - I.shift0[fl]) + fT[0];
-    R fM[Q9];
+    if (fl != flc) {
+        R d1, d2;
+        const R d = two_sum(I.shift0[flc], -I.shift0[fl], d1);
+        t[0] = two_sum(d, t[0], d2);
+        loT += d1 + d2;
+    }
+    // stored: the high parts; their rounding and every low part go to the
+    // rest populations through the remainder
+    R fT[Q9], fM[Q9];
+    CSum<R> gT, gM, sT, sM;
+    const R loM = fl ? loB : loR;
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
-        fM[i] = fl ? fB[i] : fR[i];
-        stp<R, P>(I, I.fT, i * I.plane + c, fT[i]);
-        stp<R, P>(I, I.fM, i * I.plane + c, fM[i]);
+        const R mh = fl ? fB[i] : fR[i];
+        gT.add(t[i]);
+        gM.add(mh);
+        if (i) {
+            fT[i] = stq<R, P>(I, I.fT, i, c, t[i]);
+            fM[i] = stq<R, P>(I, I.fM, i, c, mh);
+            sT.add(fT[i]);
+            sM.add(fM[i]);
+        }
     }
+    fT[0] = ((gT.s - sT.s) + (gT.c - sT.c)) + loT;
+    fM[0] = ((gM.s - sM.s) + (gM.c - sM.c)) + loM;
+    I.fT0[c] = fT[0];
+    I.fM0[c] = fM[0];
     I.flag[c] = (uint8_t)fl;
     store_moments(I, c, fT, fM, fl);
 }
@@ -722,8 +848,8 @@ __device__ __forceinline__ void sor_tile2(const Inst<R> &I, int round, int bx, i
         if (!(f & 1)) continue;
         R sp_ = fpx[q] + fpy[q] + (rx > 0 ? fpx[q - 1] : R(0)) + (ry > 0 ? fpy[q - RX] : R(0));
         R sc_ = fcx[q] + fcy[q] + (rx > 0 ? fcx[q - 1] : R(0)) + (ry > 0 ? fcy[q - RX] : R(0));
-        ip[q] = R(1) / (ip[q] + sp_);
-        ic[q] = R(1) / (ic[q] + sc_);
+        ip[q] = fdiv(R(1), ip[q] + sp_);
+        ic[q] = fdiv(R(1), ic[q] + sc_);
         if (rx > 0 && rx < RX - 1 && ry > 0 && ry < RY - 1) {
             int col = (f >> 1) & 1;
             int slot = atomicAdd(&count[col], 1);
@@ -1020,9 +1146,9 @@ __global__ void k_diag(Inst<R> I, int nblocks) {
         const int fl = I.flag[c];
         double rmin = 0, rtot = 0;
         for (int i = 0; i < Q; i++) {
-            rmin += double(ldp<R, P>(I, I.fM, i * I.plane + c));
+            rmin += double(ldq<R, P>(I, I.fM, I.fM0, i, c));
             rtot += double(i == 0 ? I.shift0[fl] : I.shift[i]) +
-                    double(ldp<R, P>(I, I.fT, i * I.plane + c));
+                    double(ldq<R, P>(I, I.fT, I.fT0, i, c));
         }
         v[0] = fl ? rtot - rmin : rmin;
         v[1] = fl ? rmin : rtot - rmin;
@@ -1082,11 +1208,24 @@ __global__ void k_diag(Inst<R> I, int nblocks) {
         double tq = block_final_sum<BS>(I.part, NDIAG + 3, q, nblocks);
         if (t == 0) I.ctl->diag[q] = tq;
     }
+    // the three maxima over the block partials, by the whole block
+    double mx[3] = {-1e300, -1e300, -1e300};
+    for (int k = t; k < nblocks; k += BS)
+#pragma unroll
+        for (int q = 0; q < 3; q++) mx[q] = fmax(mx[q], I.part[(long long)k * (NDIAG + 3) + NDIAG + q]);
+#pragma unroll
+    for (int q = 0; q < 3; q++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx[q] = fmax(mx[q], __shfl_down_sync(0xffffffffu, mx[q], o));
+    __syncthreads();
+    if ((t & 31) == 0)
+        for (int q = 0; q < 3; q++) shm[q][t >> 5] = mx[q];
+    __syncthreads();
     if (t != 0) return;
-    for (int q = NDIAG; q < NDIAG + 3; q++) {
+    for (int q = 0; q < 3; q++) {
         double m = -1e300;
-        for (int k = 0; k < nblocks; k++) m = fmax(m, I.part[(long long)k * (NDIAG + 3) + q]);
-        I.ctl->diag[q] = m;
+        for (int w = 0; w < BS / 32; w++) m = fmax(m, shm[q][w]);
+        I.ctl->diag[NDIAG + q] = m;
     }
     I.ctl->ticket = 0;
 }

@@ -26,12 +26,13 @@ namespace lbs {
 template <typename R>
 struct Mom3 {
     R rR, rB, drho, jx, jy, jz;
+    R rm_s, rm_c, dr_s, dr_c;  // minority mass and drho as unevaluated sums s + c
 };
 
 template <typename R>
 __device__ __forceinline__ Mom3<R> moments19(const Inst<R> &I, const R *fT, const R *fM,
                                             int flag) {
-    Mom3<R> m{R(0), R(0), R(0), R(0), R(0), R(0)};
+    Mom3<R> m{R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     CSum<R> rmc, drc;
 #pragma unroll
     for (int i = 0; i < Q19; i++) {
@@ -43,6 +44,10 @@ __device__ __forceinline__ Mom3<R> moments19(const Inst<R> &I, const R *fT, cons
     }
     const R rm = rmc.value();
     m.drho = drc.value();
+    m.rm_s = rmc.s;
+    m.rm_c = rmc.c;
+    m.dr_s = drc.s;
+    m.dr_c = drc.c;
     R rmaj = (I.rho_s[flag] - rm) + m.drho;
     m.rR = flag ? rmaj : rm;
     m.rB = flag ? rm : rmaj;
@@ -86,14 +91,24 @@ __global__ void k_init3(Inst<R> I, const double *phi, const double *psi, const d
     meq19<double>(rB, ux, uy, uz, double(I.alphaB), m);
     minv19<double>(m, fB);
     const int fl = (rR / double(I.rhoR0) <= rB / double(I.rhoB0)) ? 0 : 1;
+    double tT = 0, tM = 0, sT = 0, sM = 0;
 #pragma unroll
     for (int i = 0; i < Q19; i++) {
-        stp<R, P>(I, I.fT, i * I.plane + c, R((fR[i] + fB[i]) - double(shift_of(I, i, fl))));
-        stp<R, P>(I, I.fM, i * I.plane + c, R(fl ? fB[i] : fR[i]));
+        const double vT = (fR[i] + fB[i]) - double(shift_of(I, i, fl)), vM = fl ? fB[i] : fR[i];
+        tT += vT;
+        tM += vM;
+        if (i) {
+            sT += double(stq<R, P>(I, I.fT, i, c, R(vT)));
+            sM += double(stq<R, P>(I, I.fM, i, c, R(vM)));
+        }
     }
+    I.fT0[c] = R(tT - sT);
+    I.fM0[c] = R(tM - sM);
     I.flag[c] = (uint8_t)fl;
     I.psi[c] = psi ? R(psi[d]) : R(0);
     I.C[c] = C ? R(C[d]) : R(0);
+    I.psip[c] = I.psi[c];
+    I.Cp[c] = I.C[c];
     I.S[c] = R(0);
     I.B[c] = R(0);
 }
@@ -104,8 +119,8 @@ __global__ void k_moments3(Inst<R> I) {
     R fT[Q19], fM[Q19];
 #pragma unroll
     for (int i = 0; i < Q19; i++) {
-        fT[i] = ldp<R, P>(I, I.fT, i * I.plane + c);
-        fM[i] = ldp<R, P>(I, I.fM, i * I.plane + c);
+        fT[i] = ldq<R, P>(I, I.fT, I.fT0, i, c);
+        fM[i] = ldq<R, P>(I, I.fM, I.fM0, i, c);
     }
     store_moments3(I, c, fT, fM, I.flag[c]);
 }
@@ -113,14 +128,16 @@ __global__ void k_moments3(Inst<R> I) {
 // colour gradient by the isotropic stencil over the 18 neighbours, from the
 // colour fraction that is small on the cell's side (see k_grad2)
 template <typename R>
-__global__ void k_grad3(Inst<R> I) {
+__global__ void k_grad3(Inst<R> I, int guess = 1) {
     LBS_CELL3
     const bool blue_side = I.rhoN[c] <= R(0);
+    const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2),
+             Z = make_ax(z, I.nz, I.wall[2], 4);
     R gx = R(0), gy = R(0), gz = R(0);
 #pragma unroll
     for (int i = 1; i < Q19; i++) {
         int refl, sx, sy, sz;
-        long long j = nb3(I, x, y, z, ex19(i), ey19(i), ez19(i), refl, sx, sy, sz);
+        long long j = nbx3(I, X, Y, Z, ex19(i), ey19(i), ez19(i), refl, sx, sy, sz);
         R v = w19<R>(i) * frac(I, j, blue_side);
         if (ex19(i)) gx += R(ex19(i)) * v;
         if (ey19(i)) gy += R(ey19(i)) * v;
@@ -135,6 +152,7 @@ __global__ void k_grad3(Inst<R> I) {
     I.gz[c] = gz;
     I.a[c] = sqrt(gx * gx + gy * gy + gz * gz);
     I.chi[c] = R(2) * frac(I, c, false);
+    if (guess) sor_guess(I, c);
 }
 
 // normal, curvature (Eq. 7), grad psi, sigma (Eq. 8), interfacial force
@@ -143,16 +161,18 @@ template <typename R>
 __global__ void k_force3(Inst<R> I) {
     LBS_CELL3
     const R e2 = I.eps_n * I.eps_n;
+    const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2),
+             Z = make_ax(z, I.nz, I.wall[2], 4);
     R divn = R(0), dpx = R(0), dpy = R(0), dpz = R(0);
 #pragma unroll
     for (int i = 1; i < Q19; i++) {
         int refl, sx, sy, sz;
-        long long j = nb3(I, x, y, z, ex19(i), ey19(i), ez19(i), refl, sx, sy, sz);
+        long long j = nbx3(I, X, Y, Z, ex19(i), ey19(i), ez19(i), refl, sx, sy, sz);
         R gx = I.gx[j], gy = I.gy[j], gz = I.gz[j];
         if (refl & 1) gx = -gx;  // normal component mirrored with a sign change
         if (refl & 2) gy = -gy;
         if (refl & 4) gz = -gz;
-        const R inv = R(1) / sqrt(gx * gx + gy * gy + gz * gz + e2);
+        const R inv = frsq(gx * gx + gy * gy + gz * gz + e2);
         R s = R(0);
         if (ex19(i)) s += R(ex19(i)) * gx;
         if (ey19(i)) s += R(ey19(i)) * gy;
@@ -170,7 +190,7 @@ __global__ void k_force3(Inst<R> I) {
     const R gx = I.gx[c], gy = I.gy[c], gz = I.gz[c], a = I.a[c];
     R sigma, mco, Fx, Fy, Fz;
     if (eos(I, I.psi[c], sigma, mco)) {
-        const R inv = R(1) / sqrt(gx * gx + gy * gy + gz * gz + e2);
+        const R inv = frsq(gx * gx + gy * gy + gz * gz + e2);
         const R nx = -gx * inv, ny = -gy * inv, nz = -gz * inv;
         const R ndp = nx * dpx + ny * dpy + nz * dpz;
         Fx = -R(0.5) * sigma * kappa * gx - R(0.5) * a * mco * (dpx - ndp * nx);
@@ -190,9 +210,10 @@ __global__ void k_force3(Inst<R> I) {
     I.Fx[c] = Fx;
     I.Fy[c] = Fy;
     I.Fz[c] = Fz;
-    I.ux[c] = (I.jx[c] + R(0.5) * Fx) / rho;
-    I.uy[c] = (I.jy[c] + R(0.5) * Fy) / rho;
-    I.uz[c] = (I.jz[c] + R(0.5) * Fz) / rho;
+    const R irho = fdiv(R(1), rho);
+    I.ux[c] = (I.jx[c] + R(0.5) * Fx) * irho;
+    I.uy[c] = (I.jy[c] + R(0.5) * Fy) * irho;
+    I.uz[c] = (I.jz[c] + R(0.5) * Fz) * irho;
 }
 
 // explicit surfactant terms (Eqs. 22-27) and Crank-Nicolson right-hand sides
@@ -202,6 +223,8 @@ __global__ void k_fd3(Inst<R> I, double *Sout = nullptr, double *Bout = nullptr)
     LBS_CELL3
     const R u[3] = {I.ux[c], I.uy[c], I.uz[c]};
     const R *uax[3] = {I.ux, I.uy, I.uz};
+    const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2),
+             Z = make_ax(z, I.nz, I.wall[2], 4);
     R divP = R(0), divC = R(0);
 #pragma unroll
     for (int ax = 0; ax < 3; ax++) {
@@ -209,8 +232,8 @@ __global__ void k_fd3(Inst<R> I, double *Sout = nullptr, double *Bout = nullptr)
 #pragma unroll
         for (int k = -2; k <= 2; k++) {
             int refl, sx, sy, sz;
-            long long j = nb3(I, x, y, z, ax == 0 ? k : 0, ax == 1 ? k : 0, ax == 2 ? k : 0, refl,
-                              sx, sy, sz);
+            long long j = nbx3(I, X, Y, Z, ax == 0 ? k : 0, ax == 1 ? k : 0, ax == 2 ? k : 0,
+                               refl, sx, sy, sz);
             const R sgn = (refl & (1 << ax)) ? R(-1) : R(1);
             const R uj = uax[ax][j];
             Pl[k + 2] = sgn * I.psi[j] * I.a[j] * uj;
@@ -236,8 +259,8 @@ __global__ void k_fd3(Inst<R> I, double *Sout = nullptr, double *Bout = nullptr)
     for (int f = 0; f < 6; f++) {
         const int s = (f & 1) ? 1 : -1, ax = f >> 1;
         int refl, sx, sy, sz;
-        long long j2 = nb3(I, x, y, z, ax == 0 ? s : 0, ax == 1 ? s : 0, ax == 2 ? s : 0, refl,
-                           sx, sy, sz);
+        long long j2 = nbx3(I, X, Y, Z, ax == 0 ? s : 0, ax == 1 ? s : 0, ax == 2 ? s : 0,
+                            refl, sx, sy, sz);
         if (refl) continue;
         Lp += R(0.5) * (wp + (I.a[j2] + I.eps_w)) * (I.psi[j2] - psi);
         Lc += R(0.5) * (wc + (I.chi[j2] + I.eps_w)) * (I.C[j2] - Cc);
@@ -279,8 +302,8 @@ __global__ void __launch_bounds__(256) k_collide3(Inst<R> I) {
     const int fl = I.flag[c];
 #pragma unroll
     for (int i = 0; i < Q19; i++) {
-        fT[i] = ldp<R, P>(I, I.fT, i * I.plane + c);
-        fM[i] = ldp<R, P>(I, I.fM, i * I.plane + c);
+        fT[i] = ldq<R, P>(I, I.fT, I.fT0, i, c);
+        fM[i] = ldq<R, P>(I, I.fM, I.fM0, i, c);
     }
     const Mom3<R> mo = moments19(I, fT, fM, fl);
     const R rR = mo.rR, rB = mo.rB;
@@ -292,10 +315,12 @@ __global__ void __launch_bounds__(256) k_collide3(Inst<R> I) {
 
     // d_a(rho^k u_a), isotropic stencil, ghost velocities at walls
     R dR[3] = {R(0), R(0), R(0)}, dB[3] = {R(0), R(0), R(0)};
+    const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2),
+             Z = make_ax(z, I.nz, I.wall[2], 4);
 #pragma unroll
     for (int i = 1; i < Q19; i++) {
         int refl, sx, sy, sz;
-        long long j = nb3(I, x, y, z, ex19(i), ey19(i), ez19(i), refl, sx, sy, sz);
+        long long j = nbx3(I, X, Y, Z, ex19(i), ey19(i), ez19(i), refl, sx, sy, sz);
         R vx = I.ux[j], vy = I.uy[j], vz = I.uz[j];
         ghost_u3(I, refl, sx, sy, sz, vx, vy, vz);
         const R r1 = w19<R>(i) * I.rhoR[j], r2 = w19<R>(i) * I.rhoB[j];
@@ -350,8 +375,8 @@ __global__ void __launch_bounds__(256) k_collide3(Inst<R> I) {
 
     // s_v from the mixture viscosity (Eq. 43)
     const R rN = colour_fn(I, rR, rB);
-    const R inv_mu = (R(1) + rN) / (R(2) * I.muR0) + (R(1) - rN) / (R(2) * I.muB0);
-    const R sv = R(1) / (R(0.5) + R(1) / (inv_mu * Pk));
+    const R inv_mu = (R(1) + rN) * I.inv_2muR + (R(1) - rN) * I.inv_2muB;
+    const R sv = fdiv(R(1), R(0.5) + fdiv(R(1), inv_mu * Pk));
     const R uF = ux * Fx + uy * Fy + uz * Fz;
     const R xF = ux * Fx, yF = uy * Fy, zF = uz * Fz;
     R dm[Q19];
@@ -392,60 +417,135 @@ __global__ void __launch_bounds__(256) k_collide3(Inst<R> I) {
     // the moving directions (the rest equilibrium of Eq. 40: rho - 2P at rest,
     // P/6 on the axes, P/12 on the diagonals)
     const R ggx = I.gx[c], ggy = I.gy[c], ggz = I.gz[c];
-    const R gn = sqrt(ggx * ggx + ggy * ggy + ggz * ggz + I.eps_n * I.eps_n);
-    const R seg = I.beta * rR * rB / (rho * rho) * R(3) * Pk / gn;
-    const R fr = rmin / rdag;
+    const R seg = I.beta * rR * rB * R(3) * Pk *
+                  frsq(ggx * ggx + ggy * ggy + ggz * ggz + I.eps_n * I.eps_n) *
+                  fdiv(R(1), rho * rho);
+    const R fr = fdiv(rmin, rdag);
     const R sg = fl ? R(-1) : R(1);
+    // moving populations as stored; the rest populations close the cell's
+    // total and minority mass on the pre-collision values (see k_collide2)
+    CSum<R> sT, sM;
 #pragma unroll
-    for (int i = 0; i < Q19; i++) {
+    for (int i = 1; i < Q19; i++) {
         R eg = R(0);
         if (ex19(i)) eg += R(ex19(i)) * ggx;
         if (ey19(i)) eg += R(ey19(i)) * ggy;
         if (ez19(i)) eg += R(ez19(i)) * ggz;
-        const R segi = i == 0 ? R(0) : seg * w19<R>(i) * eg;
-        stp<R, P>(I, I.gT, i * I.plane + c, post[i]);
-        stp<R, P>(I, I.gM, i * I.plane + c, fr * (shift_of(I, i, fl) + post[i]) + sg * segi);
+        const R segi = seg * w19<R>(i) * eg;
+        sT.add(stq<R, P>(I, I.gT, i, c, post[i]));
+        sM.add(stq<R, P>(I, I.gM, i, c, fr * (I.shift[i] + post[i]) + sg * segi));
     }
+    I.gT0[c] = (mo.dr_s - sT.s) + (mo.dr_c - sT.c);
+    I.gM0[c] = (mo.rm_s - sM.s) + (mo.rm_c - sM.c);
     I.gflag[c] = (uint8_t)fl;
 }
 
 // streaming (Eq. 13, pull), half-way bounce-back with moving walls, moments
 // at t+1 (see k_stream2)
 template <typename R, typename P>
-__global__ void __launch_bounds__(256) k_stream3(Inst<R> I) {
+__global__ void __launch_bounds__(256, 3) k_stream3(Inst<R> I) {
     LBS_CELL3
-    R fT[Q19], fR[Q19], fB[Q19];
-    const R rRc = I.rhoR[c], rBc = I.rhoB[c];
     const int flc = I.gflag[c];
+    const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2),
+             Z = make_ax(z, I.nz, I.wall[2], 4);
+    // 1. the streamed (total, minority) pairs as stored at their sources;
+    //    slow: bit i set where the source's flag differs from the cell's or
+    //    the link crosses a wall (then the cell's own opposite population)
+    R t[Q19], m[Q19];
+    unsigned slow = 0, fbits = 0;
 #pragma unroll
     for (int i = 0; i < Q19; i++) {
         int refl, sx, sy, sz;
-        long long j = nb3(I, x, y, z, -ex19(i), -ey19(i), -ez19(i), refl, sx, sy, sz);
+        const long long j = nbx3(I, X, Y, Z, -ex19(i), -ey19(i), -ez19(i), refl, sx, sy, sz);
         if (!refl) {
-            fT[i] = ldp<R, P>(I, I.gT, i * I.plane + j);
+            t[i] = ldq<R, P>(I, I.gT, I.gT0, i, j);
+            m[i] = ldq<R, P>(I, I.gM, I.gM0, i, j);
             const int fj = I.gflag[j];
-            split(shift_of(I, i, fj), fT[i], ldp<R, P>(I, I.gM, i * I.plane + j), fj, fR[i],
-                  fB[i]);
+            fbits |= (unsigned)fj << i;
+            if (fj != flc) slow |= 1u << i;
         } else {
-            R uw[3] = {R(0), R(0), R(0)};
-            int nw = 0;
-            const int side[3] = {sx, sy, sz};
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                if (!(refl & (1 << a))) continue;
-                const R *w = side[a] < 0 ? I.uw_lo[a] : I.uw_hi[a];
-                uw[0] += w[0];
-                uw[1] += w[1];
-                uw[2] += w[2];
-                nw++;
-            }
-            const R eu = (R(ex19(i)) * uw[0] + R(ey19(i)) * uw[1] + R(ez19(i)) * uw[2]) / R(nw);
-            const R mw = R(2) * w19<R>(i) * eu * R(3);
-            const int io = opp19(i);
-            fT[i] = ldp<R, P>(I, I.gT, io * I.plane + c) + mw * (rRc + rBc);
-            const R mmin = ldp<R, P>(I, I.gM, io * I.plane + c) + mw * (flc ? rBc : rRc);
-            split(I.shift[i], fT[i], mmin, flc, fR[i], fB[i]);
+            t[i] = ldp<R, P>(I, I.gT, opp19(i) * I.plane + c);
+            m[i] = ldp<R, P>(I, I.gM, opp19(i) * I.plane + c);
+            fbits |= (unsigned)flc << i;
+            slow |= 1u << i;
         }
+    }
+    // 2. fast path: every population moves unchanged; the cell keeps its
+    //    flag unless its minority colour has become the majority
+    if (!slow) {
+        CSum<R> tot, mn;
+        R jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+        for (int i = 0; i < Q19; i++) {
+            tot.add(t[i]);
+            mn.add(m[i]);
+            if (ex19(i)) jx += R(ex19(i)) * t[i];
+            if (ey19(i)) jy += R(ey19(i)) * t[i];
+            if (ez19(i)) jz += R(ez19(i)) * t[i];
+        }
+        const R rmin = mn.value(), rmaj = (I.rho_s[flc] - rmin) + tot.value();
+        const R rR = flc ? rmaj : rmin, rB = flc ? rmin : rmaj;
+        if (minority(I, rR, rB) == flc) {
+#pragma unroll
+            for (int i = 1; i < Q19; i++) {
+                stp<R, P>(I, I.fT, (long long)i * I.plane + c, t[i]);
+                stp<R, P>(I, I.fM, (long long)i * I.plane + c, m[i]);
+            }
+            I.fT0[c] = t[0];
+            I.fM0[c] = m[0];
+            I.flag[c] = (uint8_t)flc;
+            I.rhoR[c] = rR;
+            I.rhoB[c] = rB;
+            I.rhoN[c] = colour_fn(I, rR, rB);
+            I.jx[c] = jx;
+            I.jy[c] = jy;
+            I.jz[c] = jz;
+            return;
+        }
+    }
+    // 3. general path: colours re-split where the flags differ, moving-wall
+    //    terms added; every value carried as hi + lo (TwoSum errors), and
+    //    the rest populations close the cell's masses exactly
+    const R rRc = I.rhoR[c], rBc = I.rhoB[c];
+    R fR[Q19], fB[Q19];
+    R loT = R(0), loR = R(0), loB = R(0);
+#pragma unroll
+    for (int i = 0; i < Q19; i++) {
+        const int fj = (fbits >> i) & 1;
+        R tlo = R(0), mlo = R(0);
+        R sh = shift_of(I, i, fj);
+        if ((slow >> i) & 1) {
+            int refl, sx, sy, sz;
+            nbx3(I, X, Y, Z, -ex19(i), -ey19(i), -ez19(i), refl, sx, sy, sz);
+            if (refl) {
+                R uw[3] = {R(0), R(0), R(0)};
+                int nw = 0;
+                const int side[3] = {sx, sy, sz};
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    if (!(refl & (1 << a))) continue;
+                    const R *w = side[a] < 0 ? I.uw_lo[a] : I.uw_hi[a];
+                    uw[0] += w[0];
+                    uw[1] += w[1];
+                    uw[2] += w[2];
+                    nw++;
+                }
+                const R eu =
+                    (R(ex19(i)) * uw[0] + R(ey19(i)) * uw[1] + R(ez19(i)) * uw[2]) / R(nw);
+                const R mw = R(2) * w19<R>(i) * eu * R(3);
+                t[i] = two_sum(t[i], mw * (rRc + rBc), tlo);
+                m[i] = two_sum(m[i], mw * (flc ? rBc : rRc), mlo);
+                sh = I.shift[i];
+            }
+        }
+        loT += tlo;
+        R e1, e2;
+        const R o = two_sum(two_sum(sh, t[i], e1), -m[i], e2);
+        const R olo = (e1 + e2) + (tlo - mlo);
+        fR[i] = fj ? o : m[i];
+        fB[i] = fj ? m[i] : o;
+        loR += fj ? olo : mlo;
+        loB += fj ? mlo : olo;
     }
     R rR = R(0), rB = R(0);
 #pragma unroll
@@ -454,14 +554,31 @@ __global__ void __launch_bounds__(256) k_stream3(Inst<R> I) {
         rB += fB[i];
     }
     const int fl = minority(I, rR, rB);
-    if (fl != flc) fT[0] = (I.shift0[flc] - I.shift0[fl]) + fT[0];
-    R fM[Q19];
+    if (fl != flc) {
+        R d1, d2;
+        const R d = two_sum(I.shift0[flc], -I.shift0[fl], d1);
+        t[0] = two_sum(d, t[0], d2);
+        loT += d1 + d2;
+    }
+    R fT[Q19], fM[Q19];
+    CSum<R> gT, gM, sT, sM;
+    const R loM = fl ? loB : loR;
 #pragma unroll
     for (int i = 0; i < Q19; i++) {
-        fM[i] = fl ? fB[i] : fR[i];
-        stp<R, P>(I, I.fT, i * I.plane + c, fT[i]);
-        stp<R, P>(I, I.fM, i * I.plane + c, fM[i]);
+        const R mh = fl ? fB[i] : fR[i];
+        gT.add(t[i]);
+        gM.add(mh);
+        if (i) {
+            fT[i] = stq<R, P>(I, I.fT, i, c, t[i]);
+            fM[i] = stq<R, P>(I, I.fM, i, c, mh);
+            sT.add(fT[i]);
+            sM.add(fM[i]);
+        }
     }
+    fT[0] = ((gT.s - sT.s) + (gT.c - sT.c)) + loT;
+    fM[0] = ((gM.s - sM.s) + (gM.c - sM.c)) + loM;
+    I.fT0[c] = fT[0];
+    I.fM0[c] = fM[0];
     I.flag[c] = (uint8_t)fl;
     store_moments3(I, c, fT, fM, fl);
 }
@@ -490,12 +607,14 @@ __global__ void __launch_bounds__(BS)
         const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
         const R wp = I.a[c] + I.eps_w, wc = I.chi[c] + I.eps_w;
         R dp = wp, dc = wc, op = I.rpsi[c], oc = I.rC[c];
+        const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2),
+                 Z = make_ax(z, I.nz, I.wall[2], 4);
 #pragma unroll
         for (int f = 0; f < 6; f++) {
             const int s = (f & 1) ? 1 : -1, ax = f >> 1;
             int refl, sx, sy, sz;
-            long long j = nb3(I, x, y, z, ax == 0 ? s : 0, ax == 1 ? s : 0, ax == 2 ? s : 0, refl,
-                              sx, sy, sz);
+            long long j = nbx3(I, X, Y, Z, ax == 0 ? s : 0, ax == 1 ? s : 0, ax == 2 ? s : 0,
+                               refl, sx, sy, sz);
             if (refl) continue;  // no flux through a wall
             const R fp = hp * (R(0.5) * (wp + (I.a[j] + I.eps_w)));
             const R fc = hc * (R(0.5) * (wc + (I.chi[j] + I.eps_w)));
@@ -505,7 +624,7 @@ __global__ void __launch_bounds__(BS)
             oc += fc * I.C[j];
         }
         const R p0 = I.psi[c], c0 = I.C[c];
-        const R d1 = I.omega * (op / dp - p0), d2 = I.omega * (oc / dc - c0);
+        const R d1 = I.omega * (fdiv(op, dp) - p0), d2 = I.omega * (fdiv(oc, dc) - c0);
         const R p1 = p0 + d1, c1 = c0 + d2;
         I.psi[c] = p1;
         I.C[c] = c1;

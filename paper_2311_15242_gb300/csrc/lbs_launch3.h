@@ -14,7 +14,7 @@ struct Launch3 {
     static void init(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s, const double *phi,
                      const double *psi, const double *C, const double *u);
     static void moments(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s);
-    static void grad(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s);
+    static void grad(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s, int guess = 1);
     static void force(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s);
     static void fd(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s, double *Sout,
                    double *Bout);

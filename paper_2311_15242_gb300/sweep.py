@@ -138,9 +138,12 @@ def generate(n, seed, steps, sample_every=500, batch_size=64, plain=False, stora
     S = np.zeros((n, 2))
     t0 = time.time()
     mlups = []
+    secs = np.zeros(n)
     if plain:
         for k, c in enumerate(cfgs):
+            t1 = time.time()
             re, ar, rs, as_ = run_plain(c, steps, sample_every, storage, window, seed=1000 + k)
+            secs[k] = time.time() - t1
             Y[k] = (re, ar)
             S[k] = (rs, as_)
             log(f"plain {k + 1}/{n} Re {re:.3f} AR {ar:.3f} ({time.time() - t0:.0f} s)")
@@ -156,7 +159,7 @@ def generate(n, seed, steps, sample_every=500, batch_size=64, plain=False, stora
             log(f"batch {i // batch_size + 1}: {m:.0f} MLUPS ({time.time() - t0:.0f} s)")
     ok = np.isfinite(Y).all(axis=1)
     log(f"{int(ok.sum())} of {n} solves finished ({n - int(ok.sum())} diverged)")
-    return dict(X=X, Y=Y, S=S, ok=ok, seed=seed, steps=steps, plain=plain,
+    return dict(X=X, Y=Y, S=S, ok=ok, seed=seed, steps=steps, plain=plain, solve_seconds=secs,
                 mlups=np.array(mlups), features=np.array(FEATURES), targets=np.array(TARGETS))
 
 
