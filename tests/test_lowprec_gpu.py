@@ -1,14 +1,15 @@
 """Shifted 16-bit population storage (FP16 and bfloat16, FP32 arithmetic,
 FP64 totals) against the FP64 oracle after 1000 steps.
 
-Every stored population is a small number (the total minus a rest state, or
-the cell's minority colour); FP16 values are kept scaled by 2^14.  The bounds
-below are the stated per-field accuracy of these forms (measured values in
-the design doc), not the FP32 tolerances: FP16 has an 11-bit and bfloat16 an 8-bit
-significand, and the colour-gradient interface is steered by differences of
-populations.  bfloat16 is gated on the density-ratio-1 droplet only; on the
-density-ratio-10 bubble its errors are reported, and the run must stay
-finite."""
+Every stored moving population is a small number (the total minus a rest
+state, or the cell's minority colour); FP16 values are kept scaled by 2^14.
+The rest populations are kept in FP32 and absorb the rounding of the moving
+ones, so every cell's colour masses are those of the FP32 arithmetic.  The
+bounds below are the stated per-field accuracy of these forms (about three
+times the measured errors), not the FP32 tolerances: FP16 has an 11-bit and
+bfloat16 an 8-bit significand, and the colour-gradient interface is steered
+by differences of populations.  The colour masses drift by at most 1e-7 of
+their value per step."""
 import numpy as np
 import pytest
 
@@ -20,9 +21,10 @@ from test_parity_gpu import bubble, droplet, errors, solver
 pytestmark = pytest.mark.gpu
 
 BOUNDS = {
-    ("f16", "droplet"): {"rho": 1e-5, "phi": 5e-3, "u": 1e-2, "psi": 2e-3, "C": 1e-3},
-    ("f16", "bubble"): {"rho": 3e-2, "phi": 6e-2, "u": 0.2, "psi": 5e-2, "C": 3e-2},
-    ("bf16", "droplet"): {"rho": 2e-4, "phi": 0.1, "u": 0.3, "psi": 5e-2, "C": 5e-2},
+    ("f16", "droplet"): {"rho": 5e-6, "phi": 1e-3, "u": 3e-3, "psi": 3e-4, "C": 1e-4},
+    ("f16", "bubble"): {"rho": 5e-4, "phi": 1.5e-3, "u": 1e-2, "psi": 2e-3, "C": 6e-4},
+    ("bf16", "droplet"): {"rho": 3e-5, "phi": 1e-2, "u": 5e-2, "psi": 5e-3, "C": 2e-4},
+    ("bf16", "bubble"): {"rho": 1e-2, "phi": 2e-2, "u": 7e-2, "psi": 7e-3, "C": 8e-3},
 }
 
 
@@ -57,5 +59,6 @@ def test_shifted_16bit_storage(oracle_runs, storage, case):
     if bound:
         for k, b in bound.items():
             assert err[k] <= b, (k, err[k], b)
-        assert abs(d["mass_R"] - d0["mass_R"]) / d0["mass_R"] / 1000 <= 1e-5
+        for k in ("mass_R", "mass_B"):
+            assert abs(d[k] - d0[k]) / d0[k] / 1000 <= 1e-7, (k, d[k], d0[k])
     s.close()

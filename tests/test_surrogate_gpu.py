@@ -69,7 +69,8 @@ def test_accuracy_against_plain_solves(trained):
     steady = d["S"][d["ok"]].max(axis=1) <= STEADY
     mean, unc = sg.predict(Xte)
     rel = np.abs(mean - Yte) / np.abs(Yte)
-    print("fit %.1f s (k = %.2f), loss %s" % (t_fit, sg.k, np.array2string(loss, precision=4)))
+    print("fit %.1f s (k = %s), loss %s" % (t_fit, np.array2string(sg.k, precision=2),
+                                           np.array2string(loss, precision=4)))
     print("held-out relative error (all %d): median Re %.3f AR %.3f; steady (%d): median Re %.3f "
           "AR %.3f, 90%% %.3f" % (len(rel), np.median(rel[:, 0]), np.median(rel[:, 1]),
                                   steady.sum(), np.median(rel[steady, 0]),
