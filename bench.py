@@ -337,6 +337,8 @@ def main():
                     help="skip timing the other population storage forms")
     ap.add_argument("--no-3d", action="store_true",
                     help="skip the D3Q19 (3D sheared droplet) measurement")
+    ap.add_argument("--sor-tile", type=int, default=None,
+                    help="blocked SOR variant (0..4) instead of tuning it")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched sweep measurement")
     ap.add_argument("--batch-steps", type=int, default=16,
@@ -368,6 +370,15 @@ def main():
     f = W.initial_fields(cfg, seed=0)
     s = Solver(cfg, storage=args.storage)
     s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    # blocked SOR variant: given, or chosen by timing on this context (steps of
+    # warm-up; the eager mode for kernel profilers takes it as given)
+    from paper_2311_15242_gb300 import autotune
+    if args.sor_tile is not None or args.eager:
+        tuned = {"sor": 4 if args.sor_tile is None else args.sor_tile}
+        s.set_sor_tile(tuned["sor"])
+    else:
+        tuned = autotune.tune_single(s, cfg["nx"], use_cache=False)
+        s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
     s.profile(True)
     if args.eager:
         s.set_graph(False)
@@ -462,6 +473,7 @@ def main():
             if st in forms:
                 continue
             s2 = Solver(cfg, storage=st, stream=stream)
+            s2.set_sor_tile(tuned["sor"])
             s2.init_fields(f["phi"], f["psi"], f["C"], f["u"])
             tt, _ = time_steps(s2, stream, flush, args.warmup, args.steps, torch, profiled=False)
             forms[st] = cells * args.steps / (tt / 1e3) / 1e6
@@ -503,6 +515,7 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
            "data": "synthetic",
            "config": {"workload": name, "cells": cells, "storage": args.storage,
+                      "sor_tile": tuned["sor"],
                       "l2": "flushed before every timed step (256 MiB write)",
                       "parallelism": f"replicas x{world}" if world > 1 else "single"},
            "roofline": roof, "kernel_ms": kmean, "sor_sweeps": sweeps, "sor_rounds": rounds,

@@ -237,6 +237,14 @@ int lbs_surfactant_total_static(int storage, const void *a, const void *chi,
 /* Release the context (and its device memory unless caller-supplied). */
 void lbs_destroy(lbs_ctx *c);
 
+/* Blocked SOR tile of a 2D context (Sec. 2.2 solves): 0 = 32x16 tiles with 2
+ * red-black sweeps a launch (default), 1 = 64x8 / 2, 2 = 16x16 / 2,
+ * 3 = 32x16 / 4, 4 = 32x32 / 4.  More sweeps a launch mean fewer launches and
+ * a wider halo (2 per sweep); the iterates, and so the results, do not
+ * depend on the choice except through where the convergence test falls
+ * (after every launch).  3D contexts take 0 only.  Errors: LBS_EINVAL. */
+int lbs_set_sor_tile(lbs_ctx *c, int variant);
+
 /* Human-readable description of the last error of c (never NULL). */
 const char *lbs_last_error(const lbs_ctx *c);
 
@@ -272,8 +280,9 @@ int lbs_batch_init_fields(lbs_batch *b, int k, const double *phi, const double *
 
 /* Tile shapes: the cell phases run tx x ty thread blocks, one cell per
  * thread (tx*ty a multiple of 32, at most 1024); sor_tile selects the
- * blocked SOR tile: 0 = 32x16, 1 = 64x8, 2 = 16x16 (2 sweeps a round each).
- * Default 32 x 8, 0.  Results do not depend on the choice. */
+ * blocked SOR tile and its sweeps a round as lbs_set_sor_tile (0..4).
+ * Default 32 x 8, 0.  The cell tile does not change results; the SOR tile
+ * only through where the convergence test falls. */
 int lbs_batch_set_tiles(lbs_batch *b, int tx, int ty, int sor_tile);
 
 /* Queue n steps of every instance. */

@@ -17,7 +17,7 @@ import json
 import os
 
 CELL_TILES = ((32, 8), (64, 4), (128, 2), (32, 4), (64, 2), (16, 16), (32, 16), (256, 1))
-SOR_TILES = (0, 1, 2)  # 32x16, 64x8, 16x16
+SOR_TILES = (0, 1, 2, 3, 4)  # 32x16, 64x8, 16x16 (2 sweeps a round); 32x16, 32x32 (4)
 STORAGE_NAMES = {0: "f64", 1: "f32", 2: "f16", 3: "bf16"}
 
 
@@ -115,3 +115,30 @@ def tune(batch, widths, lattice="d2q9", timer=None, cache_path=None, use_cache=T
         cache[key] = choice
         save_cache(path, cache)
     return {"key": key, "source": "timed", "timings": times, **choice}
+
+
+def tune_single(solver, width, lattice="d2q9", timer=None, cache_path=None, use_cache=True,
+                sor_tiles=SOR_TILES):
+    """Choose and apply the blocked SOR variant of a single 2D context
+    (anything with set_sor_tile(v) and a `storage` attribute); cached under
+    the same width classes with the suffix /single."""
+    timer = timer or cuda_timer
+    path = cache_path or default_cache_path()
+    key = cache_key(lattice, solver.storage, [width]) + "/single"
+    cache = load_cache(path) if use_cache else {}
+    if key in cache:
+        solver.set_sor_tile(cache[key]["sor"])
+        return {"key": key, "source": "cache", **cache[key]}
+    times = {}
+    for v in sor_tiles:
+        solver.set_sor_tile(v)
+        times[v] = float(timer(solver))
+    sv = min(sor_tiles, key=lambda v: times[v])
+    solver.set_sor_tile(sv)
+    choice = {"sor": sv, "ms_per_step": times[sv]}
+    if use_cache:
+        cache = load_cache(path)
+        cache[key] = choice
+        save_cache(path, cache)
+    return {"key": key, "source": "timed", "timings": {str(k): v for k, v in times.items()},
+            **choice}

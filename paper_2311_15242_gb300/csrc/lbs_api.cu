@@ -21,8 +21,29 @@ using namespace lbs;
 namespace {
 
 constexpr int BX = 32, BY = 8, BS = BX * BY;
-// blocked SOR: tile, sweeps per launch, threads
-constexpr int STX = 32, STY = 16, SK = 2, SBS = 256;
+constexpr int SBS = 256;  // threads of a blocked SOR launch
+
+// the blocked SOR kernel of variant v (tile and sweeps: sor_vtx / sor_vty / sor_vk)
+template <typename R>
+void *sor2_kernel(int v) {
+    switch (v) {
+    case 1: return (void *)k_sor_tb2<R, sor_vtx(1), sor_vty(1), sor_vk(1), SBS>;
+    case 2: return (void *)k_sor_tb2<R, sor_vtx(2), sor_vty(2), sor_vk(2), SBS>;
+    case 3: return (void *)k_sor_tb2<R, sor_vtx(3), sor_vty(3), sor_vk(3), SBS>;
+    case 4: return (void *)k_sor_tb2<R, sor_vtx(4), sor_vty(4), sor_vk(4), SBS>;
+    default: return (void *)k_sor_tb2<R, sor_vtx(0), sor_vty(0), sor_vk(0), SBS>;
+    }
+}
+template <typename R>
+size_t sor2_smem(int v) {
+    switch (v) {
+    case 1: return SorTile<R, sor_vtx(1), sor_vty(1), sor_vk(1), SBS>::smem_bytes();
+    case 2: return SorTile<R, sor_vtx(2), sor_vty(2), sor_vk(2), SBS>::smem_bytes();
+    case 3: return SorTile<R, sor_vtx(3), sor_vty(3), sor_vk(3), SBS>::smem_bytes();
+    case 4: return SorTile<R, sor_vtx(4), sor_vty(4), sor_vk(4), SBS>::smem_bytes();
+    default: return SorTile<R, sor_vtx(0), sor_vty(0), sor_vk(0), SBS>::smem_bytes();
+    }
+}
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -242,7 +263,7 @@ struct Solver : Base {
         block = dim3(BX, BY, 1);
         grid = dim3((p->nx + BX - 1) / BX, (p->ny + BY - 1) / BY, p->nz);
         if (D == 2) {
-            sor_grid = dim3((p->nx + STX - 1) / STX, (p->ny + STY - 1) / STY, 1);
+            set_sor_grid();
         } else {
             // red-black half-sweeps: one thread per cell pair along x
             using L3 = Launch3<R, P>;
@@ -254,9 +275,31 @@ struct Solver : Base {
         surf_grid = dim3((p->nx + BX - 1) / BX,
                          (unsigned)((rows + BY * SURF_STRIP - 1) / (BY * SURF_STRIP)), 1);
         surf_blocks = (int)(surf_grid.x * surf_grid.y);
-        using T = SorTile<R, STX, STY, SK, SBS>;
-        cudaFuncSetAttribute(k_sor_tb2<R, STX, STY, SK, SBS>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes());
+        for (int v = 0; v < kSorVariants; v++)
+            cudaFuncSetAttribute(sor2_kernel<R>(v), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sor2_smem<R>(v));
+    }
+
+    int sv = 0;  // blocked SOR variant (2D)
+    void set_sor_grid() {
+        sor_grid = dim3((I.nx + sor_vtx(sv) - 1) / sor_vtx(sv),
+                        (I.ny + sor_vty(sv) - 1) / sor_vty(sv), 1);
+    }
+    int set_sor_tile(int v) override {
+        if (v < 0 || v >= kSorVariants || (D == 3 && v != 0)) {
+            set_err(ctx, "SOR tile variant %d: 0..%d in 2D, 0 in 3D", v, kSorVariants - 1);
+            return LBS_EINVAL;
+        }
+        CK(cudaStreamSynchronize(ctx->stream));
+        sv = v;
+        if (D == 2) set_sor_grid();
+        if (gexec) {
+            CK(cudaGraphExecDestroy(gexec));
+            CK(cudaGraphDestroy(graph));
+            gexec = nullptr;
+            graph = nullptr;
+        }
+        return LBS_OK;
     }
 
     ~Solver() {
@@ -378,13 +421,12 @@ struct Solver : Base {
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             int maxr = sor_rounds(), eager = -1;
             if (D == 2) {
-                using T = SorTile<R, STX, STY, SK, SBS>;
                 void *args[] = {(void *)&I, (void *)&h, (void *)&maxr, (void *)&eager};
                 cudaKernelNodeParams kp = {};
-                kp.func = (void *)k_sor_tb2<R, STX, STY, SK, SBS>;
+                kp.func = sor2_kernel<R>(sv);
                 kp.gridDim = sor_grid;
                 kp.blockDim = dim3(SBS, 1, 1);
-                kp.sharedMemBytes = (unsigned)T::smem_bytes();
+                kp.sharedMemBytes = (unsigned)sor2_smem<R>(sv);
                 kp.kernelParams = args;
                 cudaGraphNode_t kn;
                 CK(cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp));
@@ -421,13 +463,13 @@ struct Solver : Base {
         return launch_check();
     }
 
-    // one SOR round outside a graph (eager mode): 2D one blocked launch of SK
+    // one SOR round outside a graph (eager mode): 2D one blocked launch of K
     // sweeps, 3D a red and a black half-sweep
     void launch_sor_round(cudaStream_t s, cudaGraphConditionalHandle h, int r) {
         if (D == 2) {
-            using T = SorTile<R, STX, STY, SK, SBS>;
-            k_sor_tb2<R, STX, STY, SK, SBS><<<sor_grid, SBS, T::smem_bytes(), s>>>(
-                I, h, sor_rounds(), r);
+            int maxr = sor_rounds();
+            void *args[] = {(void *)&I, (void *)&h, (void *)&maxr, (void *)&r};
+            cudaLaunchKernel(sor2_kernel<R>(sv), sor_grid, dim3(SBS), args, sor2_smem<R>(sv), s);
         } else {
             const dim3 b(L3::kSorBX, L3::kSorBY, 1);
             L3::sor(I, sor_grid, b, s, 0, h, sor_rounds(), r);
@@ -435,7 +477,7 @@ struct Solver : Base {
         }
     }
 
-    int sweeps_per_round() const { return D == 2 ? SK : 1; }
+    int sweeps_per_round() const { return D == 2 ? sor_vk(sv) : 1; }
 
     const void *inst() const override { return &I; }
     size_t inst_bytes() const override { return sizeof(I); }
@@ -898,6 +940,11 @@ int lbs_get_macro(lbs_ctx *c, double *g, double *a, double *F, double *u, double
 int lbs_set_graph(lbs_ctx *c, int enable) {
     if (!c || !c->impl) return LBS_EINVAL;
     return c->impl->set_graph(enable);
+}
+
+int lbs_set_sor_tile(lbs_ctx *c, int variant) {
+    if (!c || !c->impl) return LBS_EINVAL;
+    return c->impl->set_sor_tile(variant);
 }
 
 int lbs_step_kernel_count(const lbs_ctx *c) {

@@ -162,43 +162,31 @@ __global__ void kb_surf2(const Inst<R> *__restrict__ insts, const WorkItem *__re
 constexpr int kSurfBX = 32, kSurfBY = 8, kSurfBS = kSurfBX * kSurfBY;
 constexpr int kSorBS = 256;
 
-// SOR tile variants (TX x TY, K sweeps per round): 32x16, 64x8, 16x16
-template <typename R, int V>
-struct SorV;
 template <typename R>
-struct SorV<R, 0> {
-    static constexpr int TX = 32, TY = 16, K = 2;
-};
-template <typename R>
-struct SorV<R, 1> {
-    static constexpr int TX = 64, TY = 8, K = 2;
-};
-template <typename R>
-struct SorV<R, 2> {
-    static constexpr int TX = 16, TY = 16, K = 2;
-};
-constexpr int kSorVariants = 3;
-
-void *sor_kernel(bool dbl, int v) {
-    if (dbl) {
-        if (v == 0) return (void *)kb_sor2<double, 32, 16, 2, kSorBS>;
-        if (v == 1) return (void *)kb_sor2<double, 64, 8, 2, kSorBS>;
-        return (void *)kb_sor2<double, 16, 16, 2, kSorBS>;
+void *sor_kernel_t(int v) {
+    switch (v) {
+    case 1: return (void *)kb_sor2<R, sor_vtx(1), sor_vty(1), sor_vk(1), kSorBS>;
+    case 2: return (void *)kb_sor2<R, sor_vtx(2), sor_vty(2), sor_vk(2), kSorBS>;
+    case 3: return (void *)kb_sor2<R, sor_vtx(3), sor_vty(3), sor_vk(3), kSorBS>;
+    case 4: return (void *)kb_sor2<R, sor_vtx(4), sor_vty(4), sor_vk(4), kSorBS>;
+    default: return (void *)kb_sor2<R, sor_vtx(0), sor_vty(0), sor_vk(0), kSorBS>;
     }
-    if (v == 0) return (void *)kb_sor2<float, 32, 16, 2, kSorBS>;
-    if (v == 1) return (void *)kb_sor2<float, 64, 8, 2, kSorBS>;
-    return (void *)kb_sor2<float, 16, 16, 2, kSorBS>;
 }
+void *sor_kernel(bool dbl, int v) { return dbl ? sor_kernel_t<double>(v) : sor_kernel_t<float>(v); }
 
 template <typename R>
 size_t sor_smem(int v) {
-    if (v == 0) return SorTile<R, 32, 16, 2, kSorBS>::smem_bytes();
-    if (v == 1) return SorTile<R, 64, 8, 2, kSorBS>::smem_bytes();
-    return SorTile<R, 16, 16, 2, kSorBS>::smem_bytes();
+    switch (v) {
+    case 1: return SorTile<R, sor_vtx(1), sor_vty(1), sor_vk(1), kSorBS>::smem_bytes();
+    case 2: return SorTile<R, sor_vtx(2), sor_vty(2), sor_vk(2), kSorBS>::smem_bytes();
+    case 3: return SorTile<R, sor_vtx(3), sor_vty(3), sor_vk(3), kSorBS>::smem_bytes();
+    case 4: return SorTile<R, sor_vtx(4), sor_vty(4), sor_vk(4), kSorBS>::smem_bytes();
+    default: return SorTile<R, sor_vtx(0), sor_vty(0), sor_vk(0), kSorBS>::smem_bytes();
+    }
 }
 void sor_tile_shape(int v, int &tx, int &ty) {
-    tx = v == 1 ? 64 : (v == 0 ? 32 : 16);
-    ty = v == 1 ? 8 : 16;
+    tx = sor_vtx(v);
+    ty = sor_vty(v);
 }
 
 }  // namespace
@@ -257,6 +245,7 @@ struct Batch : lbs_batch {
     int tx = 32, ty = 8, sv = 0;
     int g_cells[6] = {0}, g_sor = 0, g_surf = 0;
     int max_rounds = 1;
+    int max_iter = 1;  // largest sor_max_iter of the instances
     int last_rounds = 4;
     bool use_graph = true;
     static constexpr int kGraphSteps = 8;
@@ -332,7 +321,7 @@ struct Batch : lbs_batch {
                 return LBS_EINVAL;
             }
             std::memcpy(&h[k], c->impl->inst(), sizeof(Inst<R>));
-            if (p[k].sor_max_iter > max_rounds * 2) max_rounds = (p[k].sor_max_iter + 1) / 2;
+            if (p[k].sor_max_iter > max_iter) max_iter = p[k].sor_max_iter;
         }
         BCK(cudaMalloc(&d_insts, n * sizeof(Inst<R>)));
         BCK(cudaMemcpy(d_insts, h.data(), n * sizeof(Inst<R>), cudaMemcpyHostToDevice));
@@ -383,6 +372,7 @@ struct Batch : lbs_batch {
         tx = tx_;
         ty = ty_;
         sv = sv_;
+        max_rounds = (max_iter + sor_vk(sv) - 1) / sor_vk(sv);
         int stx, sty;
         sor_tile_shape(sv, stx, sty);
         std::vector<WorkItem> cells, sor, surf;
@@ -480,7 +470,8 @@ struct Batch : lbs_batch {
                 if (hb.active <= 0) break;
             }
         }
-        kb_surf2<R, kSurfBS><<<g_surf, dim3(kSurfBX, kSurfBY), 0, s>>>(d_insts, d_surf, n_surf, 2);
+        kb_surf2<R, kSurfBS><<<g_surf, dim3(kSurfBX, kSurfBY), 0, s>>>(d_insts, d_surf, n_surf,
+                                                                       sor_vk(sv));
         kb_cells2<R, P, OP_SCALE><<<g_cells[5], blk, 0, s>>>(d_insts, d_cells, n_cells);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {

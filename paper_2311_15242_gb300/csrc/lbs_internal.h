@@ -27,6 +27,8 @@ struct Base {
     // host copy of the device descriptor Inst<R> of this instance, and its size
     virtual const void *inst() const = 0;
     virtual size_t inst_bytes() const = 0;
+    // blocked SOR tile variant (2D), see lbs_set_sor_tile
+    virtual int set_sor_tile(int v) = 0;
 };
 
 // parameter check shared by every entry point (message into err)

@@ -764,6 +764,13 @@ struct SorTile {
     }
 };
 
+// the blocked SOR variants (256 threads): tile TX x TY, K sweeps a launch.
+// A larger K halves the launches at the price of a wider halo (2K).
+constexpr int kSorVariants = 5;
+__host__ __device__ constexpr int sor_vtx(int v) { return v == 1 ? 64 : (v == 2 ? 16 : 32); }
+__host__ __device__ constexpr int sor_vty(int v) { return v == 1 ? 8 : (v == 4 ? 32 : 16); }
+__host__ __device__ constexpr int sor_vk(int v) { return v >= 3 ? 4 : 2; }
+
 // convergence of a round: the largest update of its last sweep is within
 // sor_tol of the largest value, or (single precision) the updates stopped
 // shrinking at a level within 8 sor_tol, i.e. at the rounding floor

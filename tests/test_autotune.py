@@ -70,3 +70,24 @@ def test_corrupt_cache_is_ignored(tmp_path):
     path.write_text("{not json")
     r = AT.tune(FakeBatch(), [64], timer=fake_timer(costs()), cache_path=str(path))
     assert r["source"] == "timed"
+
+
+class FakeSolver:
+    storage = 1
+
+    def __init__(self):
+        self.calls = []
+
+    def set_sor_tile(self, v):
+        self.calls.append(v)
+
+
+def test_single_context_sor_variant(tmp_path):
+    path = str(tmp_path / "tiles.json")
+    cost = {0: 5.0, 1: 6.0, 2: 7.0, 3: 4.0, 4: 4.5}
+    s = FakeSolver()
+    r = AT.tune_single(s, 256, timer=lambda b: cost[b.calls[-1]], cache_path=path)
+    assert r["sor"] == 3 and s.calls[-1] == 3 and r["key"] == "d2q9/f32/w256/single"
+    s2 = FakeSolver()
+    r2 = AT.tune_single(s2, 200, timer=lambda b: 1 / 0, cache_path=path)
+    assert r2["source"] == "cache" and s2.calls == [3]
