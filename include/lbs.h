@@ -237,12 +237,13 @@ int lbs_surfactant_total_static(int storage, const void *a, const void *chi,
 /* Release the context (and its device memory unless caller-supplied). */
 void lbs_destroy(lbs_ctx *c);
 
-/* Blocked SOR tile of a 2D context (Sec. 2.2 solves): 0 = 32x16 tiles with 2
- * red-black sweeps a launch (default), 1 = 64x8 / 2, 2 = 16x16 / 2,
- * 3 = 32x16 / 4, 4 = 32x32 / 4.  More sweeps a launch mean fewer launches and
- * a wider halo (2 per sweep); the iterates, and so the results, do not
- * depend on the choice except through where the convergence test falls
- * (after every launch).  3D contexts take 0 only.  Errors: LBS_EINVAL. */
+/* Blocked SOR tile of a 2D context (Sec. 2.2 solves), as tile / red-black
+ * sweeps a launch / threads: 0 = 32x16 / 2 / 256 (default), 1 = 64x8 / 2 /
+ * 256, 2 = 16x16 / 2 / 256, 3 = 32x16 / 4 / 256, 4 = 32x32 / 4 / 256,
+ * 5 = 32x32 / 4 / 512, 6 = 64x16 / 4 / 512.  More sweeps a launch mean fewer
+ * launches and a wider halo (2 per sweep); the iterates, and so the results,
+ * do not depend on the choice except through where the convergence test
+ * falls (after every launch).  3D contexts take 0 only.  Errors: LBS_EINVAL. */
 int lbs_set_sor_tile(lbs_ctx *c, int variant);
 
 /* Human-readable description of the last error of c (never NULL). */

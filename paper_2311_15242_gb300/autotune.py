@@ -17,7 +17,7 @@ import json
 import os
 
 CELL_TILES = ((32, 8), (64, 4), (128, 2), (32, 4), (64, 2), (16, 16), (32, 16), (256, 1))
-SOR_TILES = (0, 1, 2, 3, 4)  # 32x16, 64x8, 16x16 (2 sweeps a round); 32x16, 32x32 (4)
+SOR_TILES = tuple(range(7))  # the variants of lbs_set_sor_tile
 STORAGE_NAMES = {0: "f64", 1: "f32", 2: "f16", 3: "bf16"}
 
 

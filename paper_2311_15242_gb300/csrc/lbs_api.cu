@@ -21,29 +21,35 @@ using namespace lbs;
 namespace {
 
 constexpr int BX = 32, BY = 8, BS = BX * BY;
-constexpr int SBS = 256;  // threads of a blocked SOR launch
 
-// the blocked SOR kernel of variant v (tile and sweeps: sor_vtx / sor_vty / sor_vk)
+// the blocked SOR kernel of variant v (tile, sweeps and threads:
+// sor_vtx / sor_vty / sor_vk / sor_vbs)
+#define LBS_SORV(v) sor_vtx(v), sor_vty(v), sor_vk(v), sor_vbs(v)
 template <typename R>
 void *sor2_kernel(int v) {
     switch (v) {
-    case 1: return (void *)k_sor_tb2<R, sor_vtx(1), sor_vty(1), sor_vk(1), SBS>;
-    case 2: return (void *)k_sor_tb2<R, sor_vtx(2), sor_vty(2), sor_vk(2), SBS>;
-    case 3: return (void *)k_sor_tb2<R, sor_vtx(3), sor_vty(3), sor_vk(3), SBS>;
-    case 4: return (void *)k_sor_tb2<R, sor_vtx(4), sor_vty(4), sor_vk(4), SBS>;
-    default: return (void *)k_sor_tb2<R, sor_vtx(0), sor_vty(0), sor_vk(0), SBS>;
+    case 1: return (void *)k_sor_tb2<R, LBS_SORV(1)>;
+    case 2: return (void *)k_sor_tb2<R, LBS_SORV(2)>;
+    case 3: return (void *)k_sor_tb2<R, LBS_SORV(3)>;
+    case 4: return (void *)k_sor_tb2<R, LBS_SORV(4)>;
+    case 5: return (void *)k_sor_tb2<R, LBS_SORV(5)>;
+    case 6: return (void *)k_sor_tb2<R, LBS_SORV(6)>;
+    default: return (void *)k_sor_tb2<R, LBS_SORV(0)>;
     }
 }
 template <typename R>
 size_t sor2_smem(int v) {
     switch (v) {
-    case 1: return SorTile<R, sor_vtx(1), sor_vty(1), sor_vk(1), SBS>::smem_bytes();
-    case 2: return SorTile<R, sor_vtx(2), sor_vty(2), sor_vk(2), SBS>::smem_bytes();
-    case 3: return SorTile<R, sor_vtx(3), sor_vty(3), sor_vk(3), SBS>::smem_bytes();
-    case 4: return SorTile<R, sor_vtx(4), sor_vty(4), sor_vk(4), SBS>::smem_bytes();
-    default: return SorTile<R, sor_vtx(0), sor_vty(0), sor_vk(0), SBS>::smem_bytes();
+    case 1: return SorTile<R, LBS_SORV(1)>::smem_bytes();
+    case 2: return SorTile<R, LBS_SORV(2)>::smem_bytes();
+    case 3: return SorTile<R, LBS_SORV(3)>::smem_bytes();
+    case 4: return SorTile<R, LBS_SORV(4)>::smem_bytes();
+    case 5: return SorTile<R, LBS_SORV(5)>::smem_bytes();
+    case 6: return SorTile<R, LBS_SORV(6)>::smem_bytes();
+    default: return SorTile<R, LBS_SORV(0)>::smem_bytes();
     }
 }
+#undef LBS_SORV
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -425,7 +431,7 @@ struct Solver : Base {
                 cudaKernelNodeParams kp = {};
                 kp.func = sor2_kernel<R>(sv);
                 kp.gridDim = sor_grid;
-                kp.blockDim = dim3(SBS, 1, 1);
+                kp.blockDim = dim3(sor_vbs(sv), 1, 1);
                 kp.sharedMemBytes = (unsigned)sor2_smem<R>(sv);
                 kp.kernelParams = args;
                 cudaGraphNode_t kn;
@@ -469,7 +475,8 @@ struct Solver : Base {
         if (D == 2) {
             int maxr = sor_rounds();
             void *args[] = {(void *)&I, (void *)&h, (void *)&maxr, (void *)&r};
-            cudaLaunchKernel(sor2_kernel<R>(sv), sor_grid, dim3(SBS), args, sor2_smem<R>(sv), s);
+            cudaLaunchKernel(sor2_kernel<R>(sv), sor_grid, dim3(sor_vbs(sv)), args, sor2_smem<R>(sv),
+                             s);
         } else {
             const dim3 b(L3::kSorBX, L3::kSorBY, 1);
             L3::sor(I, sor_grid, b, s, 0, h, sor_rounds(), r);

@@ -160,16 +160,18 @@ __global__ void kb_surf2(const Inst<R> *__restrict__ insts, const WorkItem *__re
 }
 
 constexpr int kSurfBX = 32, kSurfBY = 8, kSurfBS = kSurfBX * kSurfBY;
-constexpr int kSorBS = 256;
 
+#define LBS_SORV(v) sor_vtx(v), sor_vty(v), sor_vk(v), sor_vbs(v)
 template <typename R>
 void *sor_kernel_t(int v) {
     switch (v) {
-    case 1: return (void *)kb_sor2<R, sor_vtx(1), sor_vty(1), sor_vk(1), kSorBS>;
-    case 2: return (void *)kb_sor2<R, sor_vtx(2), sor_vty(2), sor_vk(2), kSorBS>;
-    case 3: return (void *)kb_sor2<R, sor_vtx(3), sor_vty(3), sor_vk(3), kSorBS>;
-    case 4: return (void *)kb_sor2<R, sor_vtx(4), sor_vty(4), sor_vk(4), kSorBS>;
-    default: return (void *)kb_sor2<R, sor_vtx(0), sor_vty(0), sor_vk(0), kSorBS>;
+    case 1: return (void *)kb_sor2<R, LBS_SORV(1)>;
+    case 2: return (void *)kb_sor2<R, LBS_SORV(2)>;
+    case 3: return (void *)kb_sor2<R, LBS_SORV(3)>;
+    case 4: return (void *)kb_sor2<R, LBS_SORV(4)>;
+    case 5: return (void *)kb_sor2<R, LBS_SORV(5)>;
+    case 6: return (void *)kb_sor2<R, LBS_SORV(6)>;
+    default: return (void *)kb_sor2<R, LBS_SORV(0)>;
     }
 }
 void *sor_kernel(bool dbl, int v) { return dbl ? sor_kernel_t<double>(v) : sor_kernel_t<float>(v); }
@@ -177,13 +179,16 @@ void *sor_kernel(bool dbl, int v) { return dbl ? sor_kernel_t<double>(v) : sor_k
 template <typename R>
 size_t sor_smem(int v) {
     switch (v) {
-    case 1: return SorTile<R, sor_vtx(1), sor_vty(1), sor_vk(1), kSorBS>::smem_bytes();
-    case 2: return SorTile<R, sor_vtx(2), sor_vty(2), sor_vk(2), kSorBS>::smem_bytes();
-    case 3: return SorTile<R, sor_vtx(3), sor_vty(3), sor_vk(3), kSorBS>::smem_bytes();
-    case 4: return SorTile<R, sor_vtx(4), sor_vty(4), sor_vk(4), kSorBS>::smem_bytes();
-    default: return SorTile<R, sor_vtx(0), sor_vty(0), sor_vk(0), kSorBS>::smem_bytes();
+    case 1: return SorTile<R, LBS_SORV(1)>::smem_bytes();
+    case 2: return SorTile<R, LBS_SORV(2)>::smem_bytes();
+    case 3: return SorTile<R, LBS_SORV(3)>::smem_bytes();
+    case 4: return SorTile<R, LBS_SORV(4)>::smem_bytes();
+    case 5: return SorTile<R, LBS_SORV(5)>::smem_bytes();
+    case 6: return SorTile<R, LBS_SORV(6)>::smem_bytes();
+    default: return SorTile<R, LBS_SORV(0)>::smem_bytes();
     }
 }
+#undef LBS_SORV
 void sor_tile_shape(int v, int &tx, int &ty) {
     tx = sor_vtx(v);
     ty = sor_vty(v);
@@ -401,7 +406,7 @@ struct Batch : lbs_batch {
                              (void *)kb_cells2<R, P, OP_COLLIDE>, (void *)kb_cells2<R, P, OP_STREAM>,
                              (void *)kb_cells2<R, P, OP_GRAD>, (void *)kb_cells2<R, P, OP_SCALE>};
         for (int o = 0; o < 6; o++) g_cells[o] = persistent_grid(fk[o], th, 0, n_cells);
-        g_sor = persistent_grid(sor_kernel(sizeof(R) == 8, sv), kSorBS, sor_smem<R>(sv), n_sor);
+        g_sor = persistent_grid(sor_kernel(sizeof(R) == 8, sv), sor_vbs(sv), sor_smem<R>(sv), n_sor);
         g_surf = persistent_grid((void *)kb_surf2<R, kSurfBS>, kSurfBS, 0, n_surf);
         return LBS_OK;
     }
@@ -449,7 +454,7 @@ struct Batch : lbs_batch {
             cudaKernelNodeParams kp = {};
             kp.func = fsor;
             kp.gridDim = dim3(g_sor, 1, 1);
-            kp.blockDim = dim3(kSorBS, 1, 1);
+            kp.blockDim = dim3(sor_vbs(sv), 1, 1);
             kp.sharedMemBytes = (unsigned)smem;
             kp.kernelParams = args;
             cudaGraphNode_t kn;
@@ -463,7 +468,7 @@ struct Batch : lbs_batch {
             for (int r = 0; r < max_rounds; r++) {
                 void *args[] = {(void *)&d_insts, (void *)&d_sor, (void *)&n_sor, (void *)&d_bc,
                                 (void *)&h0, (void *)&max_rounds, (void *)&graph_mode};
-                BCK(cudaLaunchKernel(fsor, dim3(g_sor), dim3(kSorBS), args, smem, s));
+                BCK(cudaLaunchKernel(fsor, dim3(g_sor), dim3(sor_vbs(sv)), args, smem, s));
                 BatchCtl hb;
                 BCK(cudaMemcpyAsync(&hb, d_bc, sizeof(hb), cudaMemcpyDeviceToHost, s));
                 BCK(cudaStreamSynchronize(s));

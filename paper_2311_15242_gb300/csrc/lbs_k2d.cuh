@@ -583,23 +583,26 @@ __device__ __forceinline__ void stream2_cell(const Inst<R> &I, int x, int y) {
     //    cell's own opposite population is reflected)
     R t[Q9], m[Q9];
     unsigned slow = 0, fbits = 0;
+    // (branch-free: a reflected link reads the cell's own opposite
+    // population, so that every load of the loop can be in flight at once)
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         int refl, sx, sy;
         const long long j = nbx2(I, X, Y, -ex9(i), -ey9(i), refl, sx, sy);
-        if (!refl) {
-            t[i] = ldq<R, P>(I, I.gT, I.gT0, i, j);
-            m[i] = ldq<R, P>(I, I.gM, I.gM0, i, j);
-            const int fj = I.gflag[j];
-            fbits |= (unsigned)fj << i;
-            if (fj != flc) slow |= 1u << i;
-        } else {
-            t[i] = ldp<R, P>(I, I.gT, opp9(i) * I.plane + c);
-            m[i] = ldp<R, P>(I, I.gM, opp9(i) * I.plane + c);
-            fbits |= (unsigned)flc << i;
-            slow |= 1u << i;
+        if (i == 0) {
+            t[0] = I.gT0[c];
+            m[0] = I.gM0[c];
+            continue;
         }
+        const long long src = refl ? c : j;
+        const long long k = (long long)(refl ? opp9(i) : i) * I.plane + src;
+        t[i] = ldp<R, P>(I, I.gT, k);
+        m[i] = ldp<R, P>(I, I.gM, k);
+        const int fj = I.gflag[src];
+        fbits |= (unsigned)fj << i;
+        if (fj != flc || refl) slow |= 1u << i;
     }
+    fbits |= (unsigned)flc;  // (i = 0: the cell's own flag)
     // 2. fast path: every population moves unchanged (no rounding anywhere);
     //    the cell keeps its flag unless its minority has become the majority
     if (!slow) {
@@ -764,12 +767,19 @@ struct SorTile {
     }
 };
 
-// the blocked SOR variants (256 threads): tile TX x TY, K sweeps a launch.
-// A larger K halves the launches at the price of a wider halo (2K).
-constexpr int kSorVariants = 5;
-__host__ __device__ constexpr int sor_vtx(int v) { return v == 1 ? 64 : (v == 2 ? 16 : 32); }
-__host__ __device__ constexpr int sor_vty(int v) { return v == 1 ? 8 : (v == 4 ? 32 : 16); }
+// the blocked SOR variants: tile TX x TY, K sweeps a launch, BS threads.
+// A larger K halves the launches at the price of a wider halo (2K); more
+// threads a block put more loads of the region in flight.
+//   v:   0      1     2      3      4      5      6
+//   TX:  32     64    16     32     32     32     64
+//   TY:  16     8     16     16     32     32     16
+//   K:   2      2     2      4      4      4      4
+//   BS:  256    256   256    256    256    512    512
+constexpr int kSorVariants = 7;
+__host__ __device__ constexpr int sor_vtx(int v) { return (v == 1 || v == 6) ? 64 : (v == 2 ? 16 : 32); }
+__host__ __device__ constexpr int sor_vty(int v) { return v == 1 ? 8 : ((v == 4 || v == 5) ? 32 : 16); }
 __host__ __device__ constexpr int sor_vk(int v) { return v >= 3 ? 4 : 2; }
+__host__ __device__ constexpr int sor_vbs(int v) { return v >= 5 ? 512 : 256; }
 
 // convergence of a round: the largest update of its last sweep is within
 // sor_tol of the largest value, or (single precision) the updates stopped

@@ -453,23 +453,26 @@ __global__ void __launch_bounds__(256, 3) k_stream3(Inst<R> I) {
     //    the link crosses a wall (then the cell's own opposite population)
     R t[Q19], m[Q19];
     unsigned slow = 0, fbits = 0;
+    // (branch-free: a reflected link reads the cell's own opposite
+    // population, so that every load of the loop can be in flight at once)
 #pragma unroll
     for (int i = 0; i < Q19; i++) {
         int refl, sx, sy, sz;
         const long long j = nbx3(I, X, Y, Z, -ex19(i), -ey19(i), -ez19(i), refl, sx, sy, sz);
-        if (!refl) {
-            t[i] = ldq<R, P>(I, I.gT, I.gT0, i, j);
-            m[i] = ldq<R, P>(I, I.gM, I.gM0, i, j);
-            const int fj = I.gflag[j];
-            fbits |= (unsigned)fj << i;
-            if (fj != flc) slow |= 1u << i;
-        } else {
-            t[i] = ldp<R, P>(I, I.gT, opp19(i) * I.plane + c);
-            m[i] = ldp<R, P>(I, I.gM, opp19(i) * I.plane + c);
-            fbits |= (unsigned)flc << i;
-            slow |= 1u << i;
+        if (i == 0) {
+            t[0] = I.gT0[c];
+            m[0] = I.gM0[c];
+            continue;
         }
+        const long long src = refl ? c : j;
+        const long long k = (long long)(refl ? opp19(i) : i) * I.plane + src;
+        t[i] = ldp<R, P>(I, I.gT, k);
+        m[i] = ldp<R, P>(I, I.gM, k);
+        const int fj = I.gflag[src];
+        fbits |= (unsigned)fj << i;
+        if (fj != flc || refl) slow |= 1u << i;
     }
+    fbits |= (unsigned)flc;  // (i = 0: the cell's own flag)
     // 2. fast path: every population moves unchanged; the cell keeps its
     //    flag unless its minority colour has become the majority
     if (!slow) {
