@@ -496,6 +496,9 @@ def main():
         for st in ("bf16", "f32", "f16"):
             s3 = Solver(cfg3, storage=st, stream=stream)
             s3.init_fields(f3["phi"], f3["psi"], f3["C"], f3["u"])
+            t3 = autotune.tune_single(s3, cfg3["nx"], lattice="d3q19", use_cache=False)
+            d3.setdefault("sor_variant", {})[st] = t3["sor"]
+            s3.init_fields(f3["phi"], f3["psi"], f3["C"], f3["u"])
             s3.profile(True)
             tt, km = time_steps(s3, stream, flush, args.warmup, args.steps3, torch)
             d3["mlups"][st] = cells3 * args.steps3 / (tt / 1e3) / 1e6

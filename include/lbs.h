@@ -243,7 +243,10 @@ void lbs_destroy(lbs_ctx *c);
  * 5 = 32x32 / 4 / 512, 6 = 64x16 / 4 / 512.  More sweeps a launch mean fewer
  * launches and a wider halo (2 per sweep); the iterates, and so the results,
  * do not depend on the choice except through where the convergence test
- * falls (after every launch).  3D contexts take 0 only.  Errors: LBS_EINVAL. */
+ * falls (after every launch).  3D contexts: 0 = a red and a black
+ * half-sweep a sweep, in place (default), 1 = one full red-black sweep a
+ * launch with 32x8 tiles marching through 16-plane chunks of z in shared
+ * memory.  Errors: LBS_EINVAL. */
 int lbs_set_sor_tile(lbs_ctx *c, int variant);
 
 /* Human-readable description of the last error of c (never NULL). */

@@ -117,11 +117,17 @@ def tune(batch, widths, lattice="d2q9", timer=None, cache_path=None, use_cache=T
     return {"key": key, "source": "timed", "timings": times, **choice}
 
 
+SOR_TILES_3D = (0, 1)  # red-black half-sweeps; z-marching full sweeps
+
+
 def tune_single(solver, width, lattice="d2q9", timer=None, cache_path=None, use_cache=True,
-                sor_tiles=SOR_TILES):
-    """Choose and apply the blocked SOR variant of a single 2D context
-    (anything with set_sor_tile(v) and a `storage` attribute); cached under
-    the same width classes with the suffix /single."""
+                sor_tiles=None):
+    """Choose and apply the SOR variant of a single context (anything with
+    set_sor_tile(v) and a `storage` attribute): the blocked tiles in 2D, the
+    two sweep forms in 3D; cached under the same width classes with the
+    suffix /single."""
+    if sor_tiles is None:
+        sor_tiles = SOR_TILES_3D if lattice == "d3q19" else SOR_TILES
     timer = timer or cuda_timer
     path = cache_path or default_cache_path()
     key = cache_key(lattice, solver.storage, [width]) + "/single"

@@ -51,6 +51,25 @@ void *Launch3<R, P>::sor_fn() {
     return (void *)k_sor_rb3<R, kBS3>;
 }
 
+constexpr int kZmTX = 32, kZmTY = 8, kZmZC = 16, kZmBS = 256;
+
+template <typename R, typename P>
+void *Launch3<R, P>::zm_fn() {
+    return (void *)k_sor_zm3<R, kZmTX, kZmTY, kZmZC, kZmBS>;
+}
+template <typename R, typename P>
+dim3 Launch3<R, P>::zm_grid(int nx, int ny, int nz) {
+    return dim3((nx + kZmTX - 1) / kZmTX, (ny + kZmTY - 1) / kZmTY, (nz + kZmZC - 1) / kZmZC);
+}
+template <typename R, typename P>
+int Launch3<R, P>::zm_threads() {
+    return kZmBS;
+}
+template <typename R, typename P>
+size_t Launch3<R, P>::zm_smem() {
+    return SorZm<R, kZmTX, kZmTY, kZmZC, kZmBS>::smem_bytes();
+}
+
 template struct Launch3<double, double>;
 template struct Launch3<float, float>;
 template struct Launch3<float, __half>;

@@ -240,7 +240,7 @@ struct Solver : Base {
                 I.mcor2[f] = R(e2 - pk / 3.0);
             }
         }
-        I.sor_pingpong = D == 2;
+        I.sor_pingpong = D == 2;  // (set by set_sor_grid)
         size_t pb = (size_t)L.plane;
         P *pops = (P *)(ws + L.pops_off);
         I.fT = pops;
@@ -268,15 +268,7 @@ struct Solver : Base {
         stage = (double *)(ws + L.stage_off);
         block = dim3(BX, BY, 1);
         grid = dim3((p->nx + BX - 1) / BX, (p->ny + BY - 1) / BY, p->nz);
-        if (D == 2) {
-            set_sor_grid();
-        } else {
-            // red-black half-sweeps: one thread per cell pair along x
-            using L3 = Launch3<R, P>;
-            const int hx = (p->nx + 1) / 2;
-            sor_grid = dim3((hx + L3::kSorBX - 1) / L3::kSorBX,
-                            (p->ny + L3::kSorBY - 1) / L3::kSorBY, p->nz);
-        }
+        set_sor_grid();
         const long long rows = (long long)p->ny * p->nz;
         surf_grid = dim3((p->nx + BX - 1) / BX,
                          (unsigned)((rows + BY * SURF_STRIP - 1) / (BY * SURF_STRIP)), 1);
@@ -284,21 +276,37 @@ struct Solver : Base {
         for (int v = 0; v < kSorVariants; v++)
             cudaFuncSetAttribute(sor2_kernel<R>(v), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sor2_smem<R>(v));
+        if (D == 3)
+            cudaFuncSetAttribute(Launch3<R, P>::zm_fn(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Launch3<R, P>::zm_smem());
     }
 
-    int sv = 0;  // blocked SOR variant (2D)
+    // SOR variant: 2D the blocked tile (sor_vtx ...); 3D 0 = red-black
+    // half-sweeps in place, 1 = z-marching full sweeps (ping-pong buffers)
+    int sv = 0;
     void set_sor_grid() {
-        sor_grid = dim3((I.nx + sor_vtx(sv) - 1) / sor_vtx(sv),
-                        (I.ny + sor_vty(sv) - 1) / sor_vty(sv), 1);
+        using L3 = Launch3<R, P>;
+        if (D == 2) {
+            sor_grid = dim3((I.nx + sor_vtx(sv) - 1) / sor_vtx(sv),
+                            (I.ny + sor_vty(sv) - 1) / sor_vty(sv), 1);
+        } else if (sv == 1) {
+            sor_grid = L3::zm_grid(I.nx, I.ny, I.nz);
+        } else {
+            // red-black half-sweeps: one thread per cell pair along x
+            const int hx = (I.nx + 1) / 2;
+            sor_grid = dim3((hx + L3::kSorBX - 1) / L3::kSorBX,
+                            (I.ny + L3::kSorBY - 1) / L3::kSorBY, I.nz);
+        }
+        I.sor_pingpong = (D == 2 || sv == 1) ? 1 : 0;
     }
     int set_sor_tile(int v) override {
-        if (v < 0 || v >= kSorVariants || (D == 3 && v != 0)) {
-            set_err(ctx, "SOR tile variant %d: 0..%d in 2D, 0 in 3D", v, kSorVariants - 1);
+        if (v < 0 || v >= (D == 2 ? kSorVariants : 2)) {
+            set_err(ctx, "SOR variant %d: 0..%d in 2D, 0..1 in 3D", v, kSorVariants - 1);
             return LBS_EINVAL;
         }
         CK(cudaStreamSynchronize(ctx->stream));
         sv = v;
-        if (D == 2) set_sor_grid();
+        set_sor_grid();
         if (gexec) {
             CK(cudaGraphExecDestroy(gexec));
             CK(cudaGraphDestroy(graph));
@@ -436,6 +444,17 @@ struct Solver : Base {
                 kp.kernelParams = args;
                 cudaGraphNode_t kn;
                 CK(cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp));
+            } else if (sv == 1) {
+                // body: one z-marching sweep
+                void *args[] = {(void *)&I, (void *)&h, (void *)&maxr, (void *)&eager};
+                cudaKernelNodeParams kp = {};
+                kp.func = L3::zm_fn();
+                kp.gridDim = sor_grid;
+                kp.blockDim = dim3(L3::zm_threads(), 1, 1);
+                kp.sharedMemBytes = (unsigned)L3::zm_smem();
+                kp.kernelParams = args;
+                cudaGraphNode_t kn;
+                CK(cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp));
             } else {
                 // body: red half-sweep, then black half-sweep
                 cudaGraphNode_t kn[2];
@@ -477,6 +496,10 @@ struct Solver : Base {
             void *args[] = {(void *)&I, (void *)&h, (void *)&maxr, (void *)&r};
             cudaLaunchKernel(sor2_kernel<R>(sv), sor_grid, dim3(sor_vbs(sv)), args, sor2_smem<R>(sv),
                              s);
+        } else if (sv == 1) {
+            int maxr = sor_rounds();
+            void *args[] = {(void *)&I, (void *)&h, (void *)&maxr, (void *)&r};
+            cudaLaunchKernel(L3::zm_fn(), sor_grid, dim3(L3::zm_threads()), args, L3::zm_smem(), s);
         } else {
             const dim3 b(L3::kSorBX, L3::kSorBY, 1);
             L3::sor(I, sor_grid, b, s, 0, h, sor_rounds(), r);
@@ -499,9 +522,10 @@ struct Solver : Base {
     }
 
     // kernels of one step with the SOR loop at the round count of the last
-    // diagnostics (4 before the first): 2D one launch a round, 3D two
+    // diagnostics (4 before the first): one launch a round, two for the 3D
+    // red-black half-sweeps
     int kernel_count() const override {
-        const int per_round = D == 2 ? 1 : 2;
+        const int per_round = (D == 3 && sv == 0) ? 2 : 1;
         return I.transport ? 7 + per_round * last_rounds : 4;
     }
     int last_rounds = 4;

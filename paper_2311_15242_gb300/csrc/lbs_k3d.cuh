@@ -668,6 +668,195 @@ __global__ void __launch_bounds__(BS)
     }
 }
 
+// ---------------------------------------------------------------------------
+// k_sor_zm3: one full red-black SOR sweep per launch (Sec. 2.2) with the
+// planes of a z-chunk marched through shared memory.  A block owns a TX x TY
+// tile of (x, y) and ZC planes of z; it keeps a ring of 5 planes of the
+// (TX + 4) x (TY + 4) region (the tile and a 2-cell halo): psi, C, the two
+// right-hand sides and the two weights a + eps_w, chi + eps_w.  At step k it
+// prefetches plane k + 3, updates red on plane k + 1 over the tile and a
+// 1-cell ring (the values the neighbouring blocks compute for those cells,
+// from the same old black values) and black on plane k over the tile, then
+// writes plane k of the tile.  psi and C are read from one buffer and
+// written to the other (rounds alternate, as in 2D), so no block reads
+// values written in the same launch.  The red phase only reads black cells
+// and the black phase only red ones (every periodic axis has even length),
+// so the updates are made in place in shared memory.
+// ---------------------------------------------------------------------------
+template <typename R, int TX, int TY, int ZC, int BS>
+struct SorZm {
+    static constexpr int RX = TX + 4, RY = TY + 4, NP = RX * RY, RING = 5;
+    // per ring slot and region cell: psi, C, rhs psi, rhs C, w psi, w C; one
+    // flag byte (bit0 in the domain)
+    static constexpr size_t smem_bytes() { return (size_t)RING * NP * (6 * sizeof(R) + 1) + 16; }
+};
+
+template <typename R, int TX, int TY, int ZC, int BS>
+__global__ void __launch_bounds__(BS)
+    k_sor_zm3(Inst<R> I, cudaGraphConditionalHandle loop, int max_rounds, int eager_round) {
+    using T = SorZm<R, TX, TY, ZC, BS>;
+    constexpr int RX = T::RX, RY = T::RY, NP = T::NP, RING = T::RING;
+    if (eager_round > 0 && I.ctl->sor_exec < eager_round) return;  // loop already ended
+    const int round = I.ctl->sor_exec;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sp = (R *)smem_raw;              // [RING][NP] each
+    R *sc = sp + RING * NP, *bp = sc + RING * NP, *bc = bp + RING * NP;
+    R *wp = bc + RING * NP, *wc = wp + RING * NP;
+    uint8_t *fl = (uint8_t *)(wc + RING * NP);
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX - 2, y0 = blockIdx.y * TY - 2;
+    const int zs = blockIdx.z * ZC, ze = min(zs + ZC, I.nz);
+    const R *pin = (round & 1) ? I.psi2 : I.psi;
+    const R *cin = (round & 1) ? I.C2 : I.C;
+    R *pout = (round & 1) ? I.psi : I.psi2;
+    R *cout = (round & 1) ? I.C : I.C2;
+    const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
+    R v[4] = {R(0), R(0), R(0), R(0)};
+
+    // load plane z (any integer; mapped) into ring slot z mod RING
+    auto load_plane = [&](int z) {
+        const int slot = ((z % RING) + RING) % RING;
+        int zr = 0, zside;
+        const int Z = map_axis(z, I.nz, I.wall[2], 4, zr, zside);
+        for (int q = tid; q < NP; q += BS) {
+            const int rx = q % RX, ry = q / RX;
+            int refl = zr, sx, sy;
+            const int X = map_axis(x0 + rx, I.nx, I.wall[0], 1, refl, sx);
+            const int Y = map_axis(y0 + ry, I.ny, I.wall[1], 2, refl, sy);
+            const int k = slot * NP + q;
+            if (!refl) {
+                const long long c = ((long long)Z * I.ny + Y) * I.pitch + X;
+                sp[k] = pin[c];
+                sc[k] = cin[c];
+                bp[k] = I.rpsi[c];
+                bc[k] = I.rC[c];
+                wp[k] = I.a[c] + I.eps_w;
+                wc[k] = I.chi[c] + I.eps_w;
+                fl[k] = 1;
+            } else {
+                sp[k] = sc[k] = bp[k] = bc[k] = wp[k] = wc[k] = R(0);
+                fl[k] = 0;
+            }
+        }
+    };
+    // one cell update at region index q of plane z (slot s); the six faces:
+    // +-x, +-y in the plane, the planes z - 1 and z + 1; no flux across a
+    // wall or outside the domain (flag 0)
+    auto update = [&](int z, int q, bool track) {
+        const int s0 = ((z % RING) + RING) % RING;
+        const int sm = (s0 + RING - 1) % RING, spl = (s0 + 1) % RING;
+        const int k = s0 * NP + q;
+        const R w0p = wp[k], w0c = wc[k];
+        R dp = w0p, dc = w0c, op = bp[k], oc = bc[k];
+        const int nbk[6] = {k - 1, k + 1, k - RX, k + RX, sm * NP + q, spl * NP + q};
+#pragma unroll
+        for (int f = 0; f < 6; f++) {
+            const int j = nbk[f];
+            if (!fl[j]) continue;
+            const R fp = hp * (R(0.5) * (w0p + wp[j]));
+            const R fc = hc * (R(0.5) * (w0c + wc[j]));
+            dp += fp;
+            dc += fc;
+            op += fp * sp[j];
+            oc += fc * sc[j];
+        }
+        const R p0 = sp[k], c0 = sc[k];
+        const R d1 = I.omega * (fdiv(op, dp) - p0), d2 = I.omega * (fdiv(oc, dc) - c0);
+        const R p1 = p0 + d1, c1 = c0 + d2;
+        sp[k] = p1;
+        sc[k] = c1;
+        if (track) {
+            v[0] = fmax(v[0], fabs(d1));
+            v[1] = fmax(v[1], fabs(d2));
+            v[2] = fmax(v[2], fabs(p1));
+            v[3] = fmax(v[3], fabs(c1));
+        }
+    };
+    const bool zwall = I.wall[2] != 0;
+    // step k needs planes k - 1 .. k + 2 (red of k + 1, black of k); planes
+    // zs - 2 .. zs first; step k prefetches plane k + 3 into the slot of
+    // plane k - 2.  The march starts at k = zs - 2 (red of the plane below
+    // the chunk).
+    for (int z = zs - 2; z <= zs; z++) load_plane(z);
+    __syncthreads();
+    for (int k = zs - 2; k < ze; k++) {
+        if (k + 3 <= ze + 1) load_plane(k + 3);
+        // red on plane k + 1 over the tile and a 1-cell ring
+        if (k + 1 <= ze) {
+            const int zr = k + 1;
+            const bool zin = zr >= 0 && zr < I.nz;
+            if (zin || !zwall) {
+                constexpr int AX = TX + 2, AY = TY + 2;
+                for (int a = tid; a < AX * AY; a += BS) {
+                    const int rx = 1 + a % AX, ry = 1 + a / AX;
+                    const int q = ry * RX + rx;
+                    const int s0 = ((zr % RING) + RING) % RING;
+                    if (!fl[s0 * NP + q]) continue;
+                    const int gx = x0 + rx, gy = y0 + ry;
+                    // red: (x + y + z) even; a periodic wrap of even length
+                    // keeps the parity, a reflected cell is outside (flag 0)
+                    if ((gx + gy + zr) & 1) continue;
+                    const bool own = rx >= 2 && rx < 2 + TX && ry >= 2 && ry < 2 + TY &&
+                                     gx < I.nx && gy < I.ny && zr >= zs && zr < ze;
+                    update(zr, q, own);
+                }
+            }
+        }
+        __syncthreads();
+        // black on plane k over the tile
+        if (k >= zs) {
+            for (int a = tid; a < TX * TY; a += BS) {
+                const int rx = 2 + a % TX, ry = 2 + a / TX;
+                const int gx = x0 + rx, gy = y0 + ry;
+                if (gx >= I.nx || gy >= I.ny) continue;
+                if (!((gx + gy + k) & 1)) continue;  // black: odd
+                update(k, ry * RX + rx, true);
+            }
+        }
+        __syncthreads();
+        // write plane k of the tile
+        if (k >= zs) {
+            const int s0 = ((k % RING) + RING) % RING;
+            for (int a = tid; a < TX * TY; a += BS) {
+                const int rx = 2 + a % TX, ry = 2 + a / TX;
+                const int gx = x0 + rx, gy = y0 + ry;
+                if (gx >= I.nx || gy >= I.ny) continue;
+                const long long c = ((long long)k * I.ny + gy) * I.pitch + gx;
+                pout[c] = sp[s0 * NP + ry * RX + rx];
+                cout[c] = sc[s0 * NP + ry * RX + rx];
+            }
+        }
+    }
+    __syncthreads();
+    // block maxima of the sweep -> round slot; the last block decides
+    __shared__ R sh[4][BS / 32];
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
+    if ((tid & 31) == 0)
+        for (int q = 0; q < 4; q++) sh[q][tid >> 5] = v[q];
+    __syncthreads();
+    if (tid == 0)
+        for (int q = 0; q < 4; q++) {
+            R m = R(0);
+            for (int w = 0; w < BS / 32; w++) m = fmax(m, sh[q][w]);
+            atomic_max_pos(&I.ctl->sweep[round][q], double(m));
+        }
+    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    if (!last_block(&I.ctl->sor_ticket, nb)) return;
+    if (tid != 0) return;
+    Ctl *ctl = I.ctl;
+    ctl->sor_ticket = 0;
+    const bool stop = sor_round_stop<R>(ctl, round, double(I.sor_tol), max_rounds);
+    if (eager_round < 0) {
+        ctl->sor_exec = round + 1;
+        if (stop) cudaGraphSetConditional(loop, 0);
+    } else {
+        ctl->sor_exec = stop ? -(round + 1) - 1000000 : round + 1;
+    }
+}
+
 #undef LBS_CELL3
 
 }  // namespace lbs

@@ -27,6 +27,12 @@ struct Launch3 {
     // the half-sweep kernel, for a kernel node of the SOR loop's body graph
     static void *sor_fn();
     static constexpr int kSorBX = 32, kSorBY = 8;
+    // one full sweep with z-marching tiles (k_sor_zm3): kernel, grid,
+    // threads and shared memory
+    static void *zm_fn();
+    static dim3 zm_grid(int nx, int ny, int nz);
+    static int zm_threads();
+    static size_t zm_smem();
 };
 
 }  // namespace lbs

@@ -150,3 +150,21 @@ def test_full_size_shear_3d(storage):
     for k in ("mass_R", "mass_B"):
         assert abs(d[k] - d0[k]) / d0[k] / n <= per_step, (k, d[k], d0[k])
     s.close()
+
+
+@pytest.mark.parametrize("make", [shear, bubble3], ids=["shear", "bubble"])
+def test_zmarch_sor_matches_oracle_3d(make):
+    """The z-marching full-sweep SOR (variant 1: planes of a z-chunk in shared
+    memory, ping-pong buffers) gives the oracle's solution, FP64, through
+    walls on z (shear) and on x and z (bubble)."""
+    cfg = make()
+    f = W.initial_fields(cfg, seed=7, noise=0.02, u0=1e-4)
+    o = Oracle(cfg)
+    o.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    s = solver(cfg, "f64")
+    s.set_sor_tile(1)
+    s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    o.step(30)
+    s.step(30)
+    err = errors(o.fields(), s.fields())
+    assert max(err.values()) < 1e-9, err
