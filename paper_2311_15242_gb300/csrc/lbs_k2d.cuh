@@ -1047,7 +1047,7 @@ __device__ __forceinline__ int sor_rounds_done(int e) { return e >= 0 ? e : -(e 
 // k_surf: every thread sums a strip of SURF_STRIP cells along y with a
 // compensated (Kahan) sum in R; strips are added in FP64 (no per-cell FP64:
 // the FP64 pipe of GB300 is narrow).
-constexpr int SURF_STRIP = 16;
+constexpr int SURF_STRIP = 4;
 
 // block (bx, by) of a (gdx x .) grid of blockDim-shaped blocks
 template <typename R, int BS>
@@ -1221,10 +1221,17 @@ __global__ void k_diag(Inst<R> I, int nblocks) {
         I.part[(long long)b * (NDIAG + 3) + NDIAG + 2] = mm[2];
     }
     if (!last_block(&I.ctl->ticket, nblocks)) return;
-    for (int q = 0; q < NDIAG; q++) {
-        double tq = block_final_sum<BS>(I.part, NDIAG + 3, q, nblocks);
-        if (t == 0) I.ctl->diag[q] = tq;
-    }
+    // the NDIAG sums over the block partials in one pass (fixed order)
+    double acc[NDIAG];
+#pragma unroll
+    for (int q = 0; q < NDIAG; q++) acc[q] = 0.0;
+    for (int k = t; k < nblocks; k += BS)
+#pragma unroll
+        for (int q = 0; q < NDIAG; q++) acc[q] += I.part[(long long)k * (NDIAG + 3) + q];
+    double tot[NDIAG];
+    block_sum<BS, NDIAG>(acc, tot);
+    if (t == 0)
+        for (int q = 0; q < NDIAG; q++) I.ctl->diag[q] = tot[q];
     // the three maxima over the block partials, by the whole block
     double mx[3] = {-1e300, -1e300, -1e300};
     for (int k = t; k < nblocks; k += BS)

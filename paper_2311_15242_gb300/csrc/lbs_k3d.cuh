@@ -695,7 +695,7 @@ template <typename R, int TX, int TY, int ZC, int BS>
 __global__ void __launch_bounds__(BS)
     k_sor_zm3(Inst<R> I, cudaGraphConditionalHandle loop, int max_rounds, int eager_round) {
     using T = SorZm<R, TX, TY, ZC, BS>;
-    constexpr int RX = T::RX, RY = T::RY, NP = T::NP, RING = T::RING;
+    constexpr int RX = T::RX, NP = T::NP, RING = T::RING;
     if (eager_round > 0 && I.ctl->sor_exec < eager_round) return;  // loop already ended
     const int round = I.ctl->sor_exec;
     extern __shared__ __align__(16) unsigned char smem_raw[];
