@@ -56,9 +56,9 @@ POP_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture of the source tree with this hash on this workload
-# (profiles/step_bubble_rise_256x1024_f32.md); reported only while the
+# (profiles/step_bubble_rise_256x1024_f32.md, SOR variant 4); reported only while the
 # kernels are unchanged.
-TRAFFIC = {"kernel": "sor", "src_sha": "be4fac46d6f868c3", "bytes_per_launch": 6311680}
+TRAFFIC = {"kernel": "sor", "src_sha": "42a87ab80c34c202", "bytes_per_launch": 6317056}
 
 
 def src_hash():
@@ -156,6 +156,40 @@ class Clocks:
         return {"sm_mhz": statistics.median(r[0] for r in self.rows),
                 "sm_max_mhz": max(r[1] for r in self.rows), "reasons": reasons,
                 "samples": len(self.rows), "source": "nvml" if self.nv is not None else "nvidia-smi"}
+
+
+def profile_case(args):
+    """Small workloads stepped with individual launches, for kernel
+    profilers (ncu cannot trace the kernel nodes of a graph that holds a
+    conditional node): 3d = the sheared droplet at 128 x 64 x 64 (state
+    about 4x the L2), batch = the first 8 instances of the 64-instance sweep
+    with the bench's tiles (32 x 4, SOR variant 5)."""
+    import torch
+    from paper_2311_15242_gb300 import Batch, Solver
+    torch.cuda.set_device(0)
+    if args.profile_case == "3d":
+        cfg = W.shear_droplet_3d(nx=128, ny=64, nz=64, R=12.0)
+        f = W.initial_fields(cfg)
+        s = Solver(cfg, storage=args.storage3d)
+        s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+        s.set_graph(False)
+        s.step(args.steps)
+        s.sync()
+        print(json.dumps({"profile_case": "3d", "cells": cfg["nx"] * cfg["ny"] * cfg["nz"],
+                          "steps": args.steps, "sor_sweeps": s.diagnostics()["sor_iters_psi"]}))
+        return 0
+    cfgs = W.bubble_sweep_2d(64, seed=0)[:8]
+    b = Batch(cfgs, storage="f32")
+    for k, c in enumerate(cfgs):
+        f = W.initial_fields(c, seed=k)
+        b.init_fields(k, f["phi"], f["psi"], f["C"], f["u"])
+    b.set_tiles(32, 4, 5)
+    b.set_graph(False)
+    b.step(args.steps)
+    b.sync()
+    print(json.dumps({"profile_case": "batch", "instances": len(cfgs),
+                      "cells": sum(c["nx"] * c["ny"] for c in cfgs), "steps": args.steps}))
+    return 0
 
 
 def workload3d():
@@ -339,6 +373,10 @@ def main():
                     help="skip the D3Q19 (3D sheared droplet) measurement")
     ap.add_argument("--sor-tile", type=int, default=None,
                     help="blocked SOR variant (0..4) instead of tuning it")
+    ap.add_argument("--profile-case", choices=["3d", "batch"], default=None,
+                    help="run a small workload with individual launches for kernel "
+                         "profilers and exit (see profile_case)")
+    ap.add_argument("--storage3d", default="bf16", choices=["f32", "f64", "f16", "bf16"])
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched sweep measurement")
     ap.add_argument("--batch-steps", type=int, default=16,
@@ -350,6 +388,8 @@ def main():
                          "(for kernel profilers)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.profile_case:
+        return profile_case(args)
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
