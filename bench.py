@@ -58,7 +58,8 @@ POP_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 # capture of the source tree with this hash on this workload
 # (profiles/step_bubble_rise_256x1024_f32.md, SOR variant 4); reported only while the
 # kernels are unchanged.
-TRAFFIC = {"kernel": "sor", "src_sha": "42a87ab80c34c202", "bytes_per_launch": 6317056}
+TRAFFIC = {"kernel": "sor", "sor_tile": 4, "src_sha": "42a87ab80c34c202",
+           "bytes_per_launch": 6317056}
 
 
 def src_hash():
@@ -312,6 +313,21 @@ def workload():
     return cfg, name
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over the ranks of the job (its time is its slowest
+    rank's)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells_per_rank, steps, world, ms):
+    """Cells updated by all ranks per second (weak scaling: every rank runs
+    its own replica of the workload), in millions."""
+    return world * cells_per_rank * steps / (ms / 1e3) / 1e6
+
+
 def reference_arm(args, rank):
     """FP64 CPU oracle on the host cores, same workload and metric."""
     if rank != 0:
@@ -462,10 +478,8 @@ def main():
     s.sync()
     total_ms = float(sum(times))
     if world > 1:
-        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * cells * args.steps / (total_ms / 1e3) / 1e6
+        total_ms = max_over_ranks(total_ms, dist, "cuda")
+    value = whole_job_mlups(cells, args.steps, world, total_ms)
 
     # per-group device time (mean over the timed steps)
     groups = list(ktimes[0].keys())
@@ -483,7 +497,9 @@ def main():
     hbm, src = peaks()
     achieved = alg / (launch_ms / 1e3) / 1e9
     sha = src_hash()
-    traffic = TRAFFIC["bytes_per_launch"] if (TRAFFIC["src_sha"] == sha and dom == TRAFFIC["kernel"]) else None
+    traffic = (TRAFFIC["bytes_per_launch"]
+               if (TRAFFIC["src_sha"] == sha and dom == TRAFFIC["kernel"]
+                   and tuned["sor"] == TRAFFIC["sor_tile"]) else None)
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
             "peak_source": src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
             "alg_bytes_per_launch": alg, "avg_launch_ms": launch_ms}

@@ -132,7 +132,8 @@ struct Solver : Base {
     double *stage;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
-    dim3 grid, block, sor_grid, surf_grid;
+    dim3 grid, block, sor_grid, surf_grid, diag_grid;
+    int diag_blocks = 0;
     int surf_blocks = 0;
     bool prof = false;
     cudaEvent_t ev[LBS_K_NGROUPS + 1] = {};
@@ -273,6 +274,8 @@ struct Solver : Base {
         surf_grid = dim3((p->nx + BX - 1) / BX,
                          (unsigned)((rows + BY * SURF_STRIP - 1) / (BY * SURF_STRIP)), 1);
         surf_blocks = (int)(surf_grid.x * surf_grid.y);
+        diag_grid = dim3(grid.x, (p->ny + BY * DIAG_STRIP - 1) / (BY * DIAG_STRIP), p->nz);
+        diag_blocks = (int)(diag_grid.x * diag_grid.y * diag_grid.z);
         for (int v = 0; v < kSorVariants; v++)
             cudaFuncSetAttribute(sor2_kernel<R>(v), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sor2_smem<R>(v));
@@ -685,9 +688,9 @@ struct Solver : Base {
         cudaStream_t s = ctx->stream;
         k_force(s);
         if (D == 2)
-            k_diag<R, P, BS, Q9><<<grid, block, 0, s>>>(I, L.nblocks);
+            k_diag<R, P, BS, Q9><<<diag_grid, block, 0, s>>>(I, diag_blocks);
         else
-            L3::diag(I, grid, block, s, L.nblocks);
+            L3::diag(I, diag_grid, block, s, diag_blocks);
         r = launch_check();
         if (r) return r;
         Ctl h;

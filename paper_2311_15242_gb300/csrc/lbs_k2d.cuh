@@ -1146,16 +1146,21 @@ __global__ void k_tick(Inst<R> I) {
 // Q = 9 (D2Q9) or 19 (D3Q19); the grid's z index is the cell's z.
 // ---------------------------------------------------------------------------
 constexpr int NDIAG = 20;
+constexpr int DIAG_STRIP = 16;  // cells per thread along y
 template <typename R, typename P, int BS, int Q>
 __global__ void k_diag(Inst<R> I, int nblocks) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * DIAG_STRIP;
     const int z = blockIdx.z;
     // 0 mR, 1 mB, 2 surf, 3 cnt, 4 sux, 5 suy, 6 sx, 7 sy, 8 sxx, 9 syy,
     // 10 psum, 11 pcnt, 12-14 (unused), 15 suz, 16 sz, 17 szz, 18 sxz, 19 sxy
+    // (every thread a strip of DIAG_STRIP cells along y)
     double v[NDIAG] = {0};
-    double pmin = 1e300, pmax = -1e300, umax = 0;
-    if (x < I.nx && y < I.ny) {
+    double pmin = 1e300, pmax = -1e300;
+    float umax = 0.0f;
+    for (int kk = 0; kk < DIAG_STRIP && x < I.nx; kk++) {
+        const int y = y0 + kk;
+        if (y >= I.ny) break;
         long long c = ((long long)z * I.ny + y) * I.pitch + x;
         double rN = I.rhoN[c];
         // colour masses: the exact FP64 sums of the stored populations
@@ -1167,33 +1172,33 @@ __global__ void k_diag(Inst<R> I, int nblocks) {
             rtot += double(i == 0 ? I.shift0[fl] : I.shift[i]) +
                     double(ldq<R, P>(I, I.fT, I.fT0, i, c));
         }
-        v[0] = fl ? rtot - rmin : rmin;
-        v[1] = fl ? rmin : rtot - rmin;
-        v[2] = double(I.a[c] + I.eps_w) * double(I.psi[c]) +
-               double(I.chi[c] + I.eps_w) * double(I.C[c]);
-        double ux = I.ux[c], uy = I.uy[c], uz = Q == 19 ? double(I.uz[c]) : 0.0;
+        v[0] += fl ? rtot - rmin : rmin;
+        v[1] += fl ? rmin : rtot - rmin;
+        v[2] += double(I.a[c] + I.eps_w) * double(I.psi[c]) +
+                double(I.chi[c] + I.eps_w) * double(I.C[c]);
+        const float ux = float(I.ux[c]), uy = float(I.uy[c]), uz = Q == 19 ? float(I.uz[c]) : 0.0f;
         if (rN >= 0) {
-            v[3] = 1;
-            v[4] = ux;
-            v[5] = uy;
-            v[6] = x;
-            v[7] = y;
-            v[8] = double(x) * x;
-            v[9] = double(y) * y;
-            v[15] = uz;
-            v[16] = z;
-            v[17] = double(z) * z;
-            v[18] = double(x) * z;
-            v[19] = double(x) * y;
+            v[3] += 1;
+            v[4] += ux;
+            v[5] += uy;
+            v[6] += x;
+            v[7] += y;
+            v[8] += double(x) * x;
+            v[9] += double(y) * y;
+            v[15] += uz;
+            v[16] += z;
+            v[17] += double(z) * z;
+            v[18] += double(x) * z;
+            v[19] += double(x) * y;
         }
         if (fabs(rN) < 0.5) {
             double p = I.psi[c];
-            v[10] = p;
-            v[11] = 1;
-            pmin = p;
-            pmax = p;
+            v[10] += p;
+            v[11] += 1;
+            pmin = fmin(pmin, p);
+            pmax = fmax(pmax, p);
         }
-        umax = sqrt(ux * ux + uy * uy + uz * uz);
+        umax = fmaxf(umax, sqrtf(ux * ux + uy * uy + uz * uz));
     }
     int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     double s[NDIAG];
