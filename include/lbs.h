@@ -237,6 +237,12 @@ int lbs_surfactant_total_static(int storage, const void *a, const void *chi,
 /* Release the context (and its device memory unless caller-supplied). */
 void lbs_destroy(lbs_ctx *c);
 
+/* Result of the queued steps for a monitoring loop: waits for the stream
+ * (status as lbs_sync), then out[0] = steps taken, out[1] = total surfactant
+ * before the last rescale (Sec. 2.2), out[2] = the rescale factor.  A copy
+ * of 24 bytes from the context's control block; no kernel is launched. */
+int lbs_step_result(lbs_ctx *c, double *out);
+
 /* Blocked SOR tile of a 2D context (Sec. 2.2 solves), as tile / red-black
  * sweeps a launch / threads: 0 = 32x16 / 2 / 256 (default), 1 = 64x8 / 2 /
  * 256, 2 = 16x16 / 2 / 256, 3 = 32x16 / 4 / 256, 4 = 32x32 / 4 / 256,

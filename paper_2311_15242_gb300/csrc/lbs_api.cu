@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <cstddef>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -512,6 +513,22 @@ struct Solver : Base {
 
     int sweeps_per_round() const { return D == 2 ? sor_vk(sv) : 1; }
 
+    int step_result(double *out) override {
+        int r = sync();
+        if (r) return r;
+        struct {
+            long long step;
+            double M0, pre, scale;
+        } h;
+        static_assert(offsetof(Ctl, step) == 0 && offsetof(Ctl, scale) == 3 * sizeof(double),
+                      "control block layout");
+        CK(cudaMemcpy(&h, I.ctl, sizeof(h), cudaMemcpyDeviceToHost));
+        out[0] = double(h.step);
+        out[1] = h.pre;
+        out[2] = h.scale;
+        return LBS_OK;
+    }
+
     const void *inst() const override { return &I; }
     size_t inst_bytes() const override { return sizeof(I); }
 
@@ -974,6 +991,11 @@ int lbs_get_macro(lbs_ctx *c, double *g, double *a, double *F, double *u, double
 int lbs_set_graph(lbs_ctx *c, int enable) {
     if (!c || !c->impl) return LBS_EINVAL;
     return c->impl->set_graph(enable);
+}
+
+int lbs_step_result(lbs_ctx *c, double *out) {
+    if (!c || !c->impl || !out) return LBS_EINVAL;
+    return c->impl->step_result(out);
 }
 
 int lbs_set_sor_tile(lbs_ctx *c, int variant) {

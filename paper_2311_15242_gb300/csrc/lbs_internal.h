@@ -29,6 +29,8 @@ struct Base {
     virtual size_t inst_bytes() const = 0;
     // blocked SOR tile variant (2D), see lbs_set_sor_tile
     virtual int set_sor_tile(int v) = 0;
+    // step counter, total surfactant before the last rescale, rescale factor
+    virtual int step_result(double *out3) = 0;
 };
 
 // parameter check shared by every entry point (message into err)

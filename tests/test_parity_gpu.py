@@ -159,3 +159,19 @@ def test_stage_fields_match_oracle(make):
         for k in ("g", "a", "F", "u", "S", "B"):
             err = np.abs(a[k] - b[k]).max() / max(np.abs(a[k]).max(), 1e-300)
             assert err < 1e-9, (t, k, err)
+
+
+def test_step_result_matches_diagnostics():
+    """lbs_step_result (a 24-byte read, no kernel) reports the step count, the
+    total surfactant before the last rescale and the factor, as the full
+    diagnostics do."""
+    cfg = bubble()
+    f = W.initial_fields(cfg, seed=2)
+    s = solver(cfg, "f32")
+    s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    s.step(7)
+    n, pre, scale = s.step_result()
+    d = s.diagnostics()
+    assert n == d["step"] == 7
+    assert pre == d["surf_pre_rescale"] and scale == d["rescale_factor"]
+    assert abs(scale - 1.0) < 1e-4
