@@ -176,3 +176,33 @@ def test_diverging_instance_is_isolated():
     b.set_active(1, False)
     b.step(8)
     assert b.status() == [0, 0, 0]
+
+
+@pytest.mark.parametrize("sor", [3, 5, 6])
+def test_batch_four_sweep_variants(sor):
+    """The 4-sweeps-a-launch SOR tiles in a batch: FP64 against the oracle,
+    and FP32 against single contexts with the same variant."""
+    from paper_2311_15242_gb300 import Solver
+    cfgs = small_sweep(3)
+    b, fs = make_batch(cfgs, "f64")
+    b.set_tiles(32, 4, sor)
+    b.step(20)
+    for k, (c, f) in enumerate(zip(cfgs, fs)):
+        o = Oracle(c)
+        o.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+        o.step(20)
+        err = errors(o.fields(), b.fields(k))
+        assert max(err.values()) < 1e-9, (sor, k, err)
+    b.close()
+    b, fs = make_batch(cfgs, "f32")
+    b.set_tiles(64, 2, sor)
+    b.step(16)
+    for k, (c, f) in enumerate(zip(cfgs, fs)):
+        s = Solver(c, storage="f32")
+        s.set_sor_tile(sor)
+        s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+        s.step(16)
+        err = errors(s.fields(), b.fields(k))
+        assert max(err.values()) <= 1e-5, (sor, k, err)
+        s.close()
+    b.close()
