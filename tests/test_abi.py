@@ -87,3 +87,19 @@ def test_3d_validation_on_host():
     q.ny = 20 * 17
     b2 = L.lbs_workspace_bytes(ctypes.byref(q), lbs.LBS_F32)
     assert b3 > b2
+
+
+def test_no_cpu_fallback_without_a_device():
+    """Without a CUDA device every entry point of the binding refuses to run
+    (no CPU fallback); the check is skipped where a device exists."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import workloads as W
+    from paper_2311_15242_gb300 import Batch, Mlp, Solver
+    with pytest.raises(RuntimeError, match="CUDA device"):
+        Solver(W.droplet_adsorption_2d(n=16, R=4.0))
+    with pytest.raises(RuntimeError, match="CUDA device"):
+        Batch([W.droplet_adsorption_2d(n=16, R=4.0)])
+    with pytest.raises(RuntimeError, match="CUDA device"):
+        Mlp(1, 5, 8, 1, 2)
