@@ -39,7 +39,8 @@ UNIT = "MLUPS"
 
 # Algorithmic bytes per cell of each kernel group in FP32 (each input and
 # output field of the group read or written once; derivation in the design doc).
-ALG_BYTES_F32 = {"force": 44, "fd": 48, "collide": 176, "stream": 172, "grad": 28,
+# (2D: the fd terms run inside the collide kernel, so that group carries both)
+ALG_BYTES_F32 = {"force": 44, "fd": 48, "collide": 176 + 48, "stream": 172, "grad": 28,
                  "surf": 40}
 # one blocked SOR launch (round): psi, C, a, chi and the two right-hand sides
 # read once, psi and C written once, whatever the sweeps it runs in shared memory

@@ -383,17 +383,16 @@ struct Solver : Base {
         mark(s, LBS_K_FORCE);
         k_force(s);
         ran[LBS_K_FORCE] = true;
+        // 2D: the explicit surfactant terms and the collision in one kernel
+        // (timed in the collide group); 3D: two kernels
         mark(s, LBS_K_FD);
-        if (I.transport) {
-            if (D == 2)
-                k_fd2<R><<<grid, block, 0, s>>>(I);
-            else
-                L3::fd(I, grid, block, s, nullptr, nullptr);
+        if (I.transport && D == 3) {
+            L3::fd(I, grid, block, s, nullptr, nullptr);
             ran[LBS_K_FD] = true;
         }
         mark(s, LBS_K_COLLIDE);
         if (D == 2)
-            k_collide2<R, P><<<grid, block, 0, s>>>(I);
+            k_fdcollide2<R, P><<<grid, block, 0, s>>>(I);
         else
             L3::collide(I, grid, block, s);
         ran[LBS_K_COLLIDE] = true;
@@ -546,7 +545,8 @@ struct Solver : Base {
     // red-black half-sweeps
     int kernel_count() const override {
         const int per_round = (D == 3 && sv == 0) ? 2 : 1;
-        return I.transport ? 7 + per_round * last_rounds : 4;
+        const int cells = D == 2 ? 4 : 5;  // 2D: fd fused with collide
+        return I.transport ? cells + 2 + per_round * last_rounds : 4;
     }
     int last_rounds = 4;
 

@@ -36,7 +36,7 @@ struct BatchCtl {
     int active;           // instances still iterating in the current solve
 };
 
-enum { OP_FORCE, OP_FD, OP_COLLIDE, OP_STREAM, OP_GRAD, OP_SCALE };
+enum { OP_FORCE, OP_FDCOLLIDE, OP_STREAM, OP_GRAD, OP_SCALE, NOPS };
 
 // copy descriptor k into shared memory (all threads; uniform) and return
 // whether the instance is alive (an instance whose total went non-finite is
@@ -72,10 +72,11 @@ __global__ void kb_cells2(const Inst<R> *__restrict__ insts, const WorkItem *__r
         const int x = it.x0 + threadIdx.x, y = it.y0 + threadIdx.y;
         if (OP == OP_FORCE)
             force2_cell(sI, x, y);
-        else if (OP == OP_FD)
+        else if (OP == OP_FDCOLLIDE) {
+            // (the explicit surfactant terms and the collision in one pass)
             fd2_cell(sI, x, y, nullptr, nullptr);
-        else if (OP == OP_COLLIDE)
             collide2_cell<R, P>(sI, x, y);
+        }
         else if (OP == OP_STREAM)
             stream2_cell<R, P>(sI, x, y);
         else if (OP == OP_GRAD)
@@ -248,7 +249,7 @@ struct Batch : lbs_batch {
     WorkItem *d_cells = nullptr, *d_sor = nullptr, *d_surf = nullptr;
     int n_cells = 0, n_sor = 0, n_surf = 0;
     int tx = 32, ty = 8, sv = 0;
-    int g_cells[6] = {0}, g_sor = 0, g_surf = 0;
+    int g_cells[NOPS] = {0}, g_sor = 0, g_surf = 0;
     int max_rounds = 1;
     int max_iter = 1;  // largest sor_max_iter of the instances
     int last_rounds = 4;
@@ -402,10 +403,10 @@ struct Batch : lbs_batch {
         n_surf = (int)surf.size();
         BCK(cudaMemcpy(d_act, act.data(), n * sizeof(int), cudaMemcpyHostToDevice));
         const int th = tx * ty;
-        const void *fk[6] = {(void *)kb_cells2<R, P, OP_FORCE>, (void *)kb_cells2<R, P, OP_FD>,
-                             (void *)kb_cells2<R, P, OP_COLLIDE>, (void *)kb_cells2<R, P, OP_STREAM>,
-                             (void *)kb_cells2<R, P, OP_GRAD>, (void *)kb_cells2<R, P, OP_SCALE>};
-        for (int o = 0; o < 6; o++) g_cells[o] = persistent_grid(fk[o], th, 0, n_cells);
+        const void *fk[NOPS] = {(void *)kb_cells2<R, P, OP_FORCE>, (void *)kb_cells2<R, P, OP_FDCOLLIDE>,
+                             (void *)kb_cells2<R, P, OP_STREAM>, (void *)kb_cells2<R, P, OP_GRAD>,
+                             (void *)kb_cells2<R, P, OP_SCALE>};
+        for (int o = 0; o < NOPS; o++) g_cells[o] = persistent_grid(fk[o], th, 0, n_cells);
         g_sor = persistent_grid(sor_kernel(sizeof(R) == 8, sv), sor_vbs(sv), sor_smem<R>(sv), n_sor);
         g_surf = persistent_grid((void *)kb_surf2<R, kSurfBS>, kSurfBS, 0, n_surf);
         return LBS_OK;
@@ -425,11 +426,11 @@ struct Batch : lbs_batch {
     // the launches of one step of the whole batch
     int enqueue_step(cudaStream_t s, bool capturing) {
         const dim3 blk(tx, ty, 1);
-        kb_cells2<R, P, OP_FORCE><<<g_cells[0], blk, 0, s>>>(d_insts, d_cells, n_cells);
-        kb_cells2<R, P, OP_FD><<<g_cells[1], blk, 0, s>>>(d_insts, d_cells, n_cells);
-        kb_cells2<R, P, OP_COLLIDE><<<g_cells[2], blk, 0, s>>>(d_insts, d_cells, n_cells);
-        kb_cells2<R, P, OP_STREAM><<<g_cells[3], blk, 0, s>>>(d_insts, d_cells, n_cells);
-        kb_cells2<R, P, OP_GRAD><<<g_cells[4], blk, 0, s>>>(d_insts, d_cells, n_cells);
+        kb_cells2<R, P, OP_FORCE><<<g_cells[OP_FORCE], blk, 0, s>>>(d_insts, d_cells, n_cells);
+        kb_cells2<R, P, OP_FDCOLLIDE><<<g_cells[OP_FDCOLLIDE], blk, 0, s>>>(d_insts, d_cells,
+                                                                          n_cells);
+        kb_cells2<R, P, OP_STREAM><<<g_cells[OP_STREAM], blk, 0, s>>>(d_insts, d_cells, n_cells);
+        kb_cells2<R, P, OP_GRAD><<<g_cells[OP_GRAD], blk, 0, s>>>(d_insts, d_cells, n_cells);
         kb_sor_begin<R><<<1, 256, 0, s>>>(d_insts, d_act, n, d_bc);
         void *fsor = sor_kernel(sizeof(R) == 8, sv);
         const size_t smem = sor_smem<R>(sv);
@@ -477,7 +478,7 @@ struct Batch : lbs_batch {
         }
         kb_surf2<R, kSurfBS><<<g_surf, dim3(kSurfBX, kSurfBY), 0, s>>>(d_insts, d_surf, n_surf,
                                                                        sor_vk(sv));
-        kb_cells2<R, P, OP_SCALE><<<g_cells[5], blk, 0, s>>>(d_insts, d_cells, n_cells);
+        kb_cells2<R, P, OP_SCALE><<<g_cells[OP_SCALE], blk, 0, s>>>(d_insts, d_cells, n_cells);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
             berr(this, "kernel launch failed: %s", cudaGetErrorString(e));
@@ -604,9 +605,10 @@ struct Batch : lbs_batch {
         return LBS_OK;
     }
 
-    // launches of one step: 5 cell phases, the SOR opener, the rounds of the
-    // slowest instance at the last diagnostics, the total and the rescale
-    int kernel_count() const override { return 8 + last_rounds; }
+    // launches of one step: 4 cell phases (fd fused with collide), the SOR
+    // opener, the rounds of the slowest instance at the last diagnostics, the
+    // total and the rescale
+    int kernel_count() const override { return 7 + last_rounds; }
 
     int set_graph(int on) override {
         use_graph = bool(on);

@@ -561,6 +561,16 @@ __device__ __forceinline__ void collide2_cell(const Inst<R> &I, int x, int y) {
     I.gflag[c] = (uint8_t)fl;
 }
 
+// the explicit surfactant terms and the collision in one pass: both read
+// only what k_force and the previous stream / grad kernels wrote, and they
+// write disjoint fields
+template <typename R, typename P>
+__global__ void k_fdcollide2(Inst<R> I) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I.transport) fd2_cell(I, x, y, nullptr, nullptr);
+    collide2_cell<R, P>(I, x, y);
+}
+
 template <typename R, typename P>
 __global__ void k_collide2(Inst<R> I) {
     collide2_cell<R, P>(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
