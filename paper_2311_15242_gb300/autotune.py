@@ -17,7 +17,7 @@ import json
 import os
 
 CELL_TILES = ((32, 8), (64, 4), (128, 2), (32, 4), (64, 2), (16, 16), (32, 16), (256, 1))
-SOR_TILES = tuple(range(7))  # the variants of lbs_set_sor_tile
+SOR_TILES = tuple(range(9))  # the variants of lbs_set_sor_tile
 STORAGE_NAMES = {0: "f64", 1: "f32", 2: "f16", 3: "bf16"}
 
 
@@ -95,7 +95,11 @@ def tune(batch, widths, lattice="d2q9", timer=None, cache_path=None, use_cache=T
     times = {}
 
     def run(tx, ty, sv):
-        batch.set_tiles(tx, ty, sv)
+        try:
+            batch.set_tiles(tx, ty, sv)
+        except RuntimeError:  # (a variant too large for this storage form)
+            times[f"{tx}x{ty}/{sv}"] = float("inf")
+            return float("inf")
         t = float(timer(batch))
         times[f"{tx}x{ty}/{sv}"] = t
         return t
@@ -137,7 +141,11 @@ def tune_single(solver, width, lattice="d2q9", timer=None, cache_path=None, use_
         return {"key": key, "source": "cache", **cache[key]}
     times = {}
     for v in sor_tiles:
-        solver.set_sor_tile(v)
+        try:
+            solver.set_sor_tile(v)
+        except RuntimeError:  # (a variant too large for this storage form)
+            times[v] = float("inf")
+            continue
         times[v] = float(timer(solver))
     sv = min(sor_tiles, key=lambda v: times[v])
     solver.set_sor_tile(sv)

@@ -35,6 +35,8 @@ void *sor2_kernel(int v) {
     case 4: return (void *)k_sor_tb2<R, LBS_SORV(4)>;
     case 5: return (void *)k_sor_tb2<R, LBS_SORV(5)>;
     case 6: return (void *)k_sor_tb2<R, LBS_SORV(6)>;
+    case 7: return (void *)k_sor_tb2<R, LBS_SORV(7)>;
+    case 8: return (void *)k_sor_tb2<R, LBS_SORV(8)>;
     default: return (void *)k_sor_tb2<R, LBS_SORV(0)>;
     }
 }
@@ -47,6 +49,8 @@ size_t sor2_smem(int v) {
     case 4: return SorTile<R, LBS_SORV(4)>::smem_bytes();
     case 5: return SorTile<R, LBS_SORV(5)>::smem_bytes();
     case 6: return SorTile<R, LBS_SORV(6)>::smem_bytes();
+    case 7: return SorTile<R, LBS_SORV(7)>::smem_bytes();
+    case 8: return SorTile<R, LBS_SORV(8)>::smem_bytes();
     default: return SorTile<R, LBS_SORV(0)>::smem_bytes();
     }
 }
@@ -278,8 +282,10 @@ struct Solver : Base {
         diag_grid = dim3(grid.x, (p->ny + BY * DIAG_STRIP - 1) / (BY * DIAG_STRIP), p->nz);
         diag_blocks = (int)(diag_grid.x * diag_grid.y * diag_grid.z);
         for (int v = 0; v < kSorVariants; v++)
-            cudaFuncSetAttribute(sor2_kernel<R>(v), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sor2_smem<R>(v));
+            if (sor2_fits(v))
+                cudaFuncSetAttribute(sor2_kernel<R>(v),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sor2_smem<R>(v));
         if (D == 3)
             cudaFuncSetAttribute(Launch3<R, P>::zm_fn(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Launch3<R, P>::zm_smem());
@@ -303,9 +309,21 @@ struct Solver : Base {
         }
         I.sor_pingpong = (D == 2 || sv == 1) ? 1 : 0;
     }
+    // variant v's shared memory fits a block on this device
+    static bool sor2_fits(int v) {
+        int dev = 0, lim = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        return sor2_smem<R>(v) <= (size_t)lim;
+    }
     int set_sor_tile(int v) override {
         if (v < 0 || v >= (D == 2 ? kSorVariants : 2)) {
             set_err(ctx, "SOR variant %d: 0..%d in 2D, 0..1 in 3D", v, kSorVariants - 1);
+            return LBS_EINVAL;
+        }
+        if (D == 2 && !sor2_fits(v)) {
+            set_err(ctx, "SOR variant %d needs %zu bytes of shared memory a block in this "
+                         "storage form", v, sor2_smem<R>(v));
             return LBS_EINVAL;
         }
         CK(cudaStreamSynchronize(ctx->stream));

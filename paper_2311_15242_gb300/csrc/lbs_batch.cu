@@ -172,6 +172,8 @@ void *sor_kernel_t(int v) {
     case 4: return (void *)kb_sor2<R, LBS_SORV(4)>;
     case 5: return (void *)kb_sor2<R, LBS_SORV(5)>;
     case 6: return (void *)kb_sor2<R, LBS_SORV(6)>;
+    case 7: return (void *)kb_sor2<R, LBS_SORV(7)>;
+    case 8: return (void *)kb_sor2<R, LBS_SORV(8)>;
     default: return (void *)kb_sor2<R, LBS_SORV(0)>;
     }
 }
@@ -186,6 +188,8 @@ size_t sor_smem(int v) {
     case 4: return SorTile<R, LBS_SORV(4)>::smem_bytes();
     case 5: return SorTile<R, LBS_SORV(5)>::smem_bytes();
     case 6: return SorTile<R, LBS_SORV(6)>::smem_bytes();
+    case 7: return SorTile<R, LBS_SORV(7)>::smem_bytes();
+    case 8: return SorTile<R, LBS_SORV(8)>::smem_bytes();
     default: return SorTile<R, LBS_SORV(0)>::smem_bytes();
     }
 }
@@ -338,6 +342,7 @@ struct Batch : lbs_batch {
         BCK(cudaMalloc(&d_act, n * sizeof(int)));
         BCK(cudaMemcpy(d_act, act.data(), n * sizeof(int), cudaMemcpyHostToDevice));
         for (int v = 0; v < kSorVariants; v++) {
+            if (!sor_fits(v)) continue;
             void *f = sor_kernel(sizeof(R) == 8, v);
             BCK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sor_smem<R>(v)));
@@ -366,11 +371,23 @@ struct Batch : lbs_batch {
         return LBS_OK;
     }
 
+    static bool sor_fits(int v) {
+        int dev = 0, lim = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        return sor_smem<R>(v) <= (size_t)lim;
+    }
+
     int set_tiles(int tx_, int ty_, int sv_) override {
         if (tx_ < 1 || ty_ < 1 || tx_ * ty_ > 1024 || (tx_ * ty_) % 32 || sv_ < 0 ||
             sv_ >= kSorVariants) {
             berr(this, "tile %dx%d / SOR variant %d: block of 32..1024 threads (a multiple of 32) "
                        "and variant 0..%d required", tx_, ty_, sv_, kSorVariants - 1);
+            return LBS_EINVAL;
+        }
+        if (!sor_fits(sv_)) {
+            berr(this, "SOR variant %d needs %zu bytes of shared memory a block in this storage "
+                       "form", sv_, sor_smem<R>(sv_));
             return LBS_EINVAL;
         }
         BCK(cudaStreamSynchronize(stream));

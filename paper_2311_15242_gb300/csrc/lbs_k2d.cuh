@@ -780,15 +780,18 @@ struct SorTile {
 // the blocked SOR variants: tile TX x TY, K sweeps a launch, BS threads.
 // A larger K halves the launches at the price of a wider halo (2K); more
 // threads a block put more loads of the region in flight.
-//   v:   0      1     2      3      4      5      6
-//   TX:  32     64    16     32     32     32     64
-//   TY:  16     8     16     16     32     32     16
-//   K:   2      2     2      4      4      4      4
-//   BS:  256    256   256    256    256    512    512
-constexpr int kSorVariants = 7;
+//   v:   0      1     2      3      4      5      6      7      8
+//   TX:  32     64    16     32     32     32     64     32     32
+//   TY:  16     8     16     16     32     32     16     32     16
+//   K:   2      2     2      4      4      4      4      6      8
+//   BS:  256    256   256    256    256    512    512    512    512
+// (variants 7 and 8 exceed the shared memory of a block in double precision)
+constexpr int kSorVariants = 9;
 __host__ __device__ constexpr int sor_vtx(int v) { return (v == 1 || v == 6) ? 64 : (v == 2 ? 16 : 32); }
-__host__ __device__ constexpr int sor_vty(int v) { return v == 1 ? 8 : ((v == 4 || v == 5) ? 32 : 16); }
-__host__ __device__ constexpr int sor_vk(int v) { return v >= 3 ? 4 : 2; }
+__host__ __device__ constexpr int sor_vty(int v) {
+    return v == 1 ? 8 : ((v == 4 || v == 5 || v == 7) ? 32 : 16);
+}
+__host__ __device__ constexpr int sor_vk(int v) { return v == 8 ? 8 : (v == 7 ? 6 : (v >= 3 ? 4 : 2)); }
 __host__ __device__ constexpr int sor_vbs(int v) { return v >= 5 ? 512 : 256; }
 
 // convergence of a round: the largest update of its last sweep is within

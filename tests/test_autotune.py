@@ -84,7 +84,7 @@ class FakeSolver:
 
 def test_single_context_sor_variant(tmp_path):
     path = str(tmp_path / "tiles.json")
-    cost = {0: 5.0, 1: 6.0, 2: 7.0, 3: 4.0, 4: 4.5, 5: 4.2, 6: 4.8}
+    cost = {0: 5.0, 1: 6.0, 2: 7.0, 3: 4.0, 4: 4.5, 5: 4.2, 6: 4.8, 7: 4.9, 8: 5.5}
     s = FakeSolver()
     r = AT.tune_single(s, 256, timer=lambda b: cost[b.calls[-1]], cache_path=path)
     assert r["sor"] == 3 and s.calls[-1] == 3 and r["key"] == "d2q9/f32/w256/single"

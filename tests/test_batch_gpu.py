@@ -178,6 +178,31 @@ def test_diverging_instance_is_isolated():
     assert b.status() == [0, 0, 0]
 
 
+@pytest.mark.parametrize("sor", [7, 8])
+def test_batch_wide_halo_variants(sor):
+    """The 6- and 8-sweep tiles in a batch: refused in FP64, and in FP32
+    equal to single contexts with the same variant within rounding."""
+    from paper_2311_15242_gb300 import Solver
+    from paper_2311_15242_gb300.lbs import LbsError
+    cfgs = small_sweep(3)
+    b, _ = make_batch(cfgs, "f64")
+    with pytest.raises(LbsError):
+        b.set_tiles(32, 4, sor)
+    b.close()
+    b, fs = make_batch(cfgs, "f32")
+    b.set_tiles(32, 4, sor)
+    b.step(16)
+    for k, (c, f) in enumerate(zip(cfgs, fs)):
+        s = Solver(c, storage="f32")
+        s.set_sor_tile(sor)
+        s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+        s.step(16)
+        err = errors(s.fields(), b.fields(k))
+        assert max(err.values()) <= 1e-5, (sor, k, err)
+        s.close()
+    b.close()
+
+
 @pytest.mark.parametrize("sor", [3, 5, 6])
 def test_batch_four_sweep_variants(sor):
     """The 4-sweeps-a-launch SOR tiles in a batch: FP64 against the oracle,

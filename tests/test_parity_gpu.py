@@ -179,8 +179,8 @@ def test_step_result_matches_diagnostics():
 
 @pytest.mark.parametrize("variant", range(7))
 def test_every_blocked_sor_variant_matches_oracle(variant):
-    """Each blocked SOR tile (2 or 4 red-black sweeps a launch, 256 or 512
-    threads) converges to the oracle's solution (FP64, 25 steps of the
+    """Each blocked SOR tile that fits FP64 (2 or 4 red-black sweeps a
+    launch, 256 or 512 threads) converges to the oracle's solution (FP64, 25 steps of the
     ragged 72 x 44 droplet)."""
     cfg = droplet()
     f = W.initial_fields(cfg, seed=11, noise=0.02, u0=1e-4)
@@ -193,3 +193,32 @@ def test_every_blocked_sor_variant_matches_oracle(variant):
     s.step(25)
     err = errors(o.fields(), s.fields())
     assert max(err.values()) < 1e-9, (variant, err)
+
+
+@pytest.mark.parametrize("variant", [7, 8])
+def test_wide_halo_sor_variants(variant):
+    """The 6- and 8-sweep tiles (halo 12 and 16 cells) hold FP32 regions
+    only: in FP64 the context refuses them; in FP32 they match the oracle
+    within the FP32 tolerances and the 4-sweep tile within rounding."""
+    from paper_2311_15242_gb300.lbs import LbsError
+    cfg = droplet()
+    f = W.initial_fields(cfg, seed=11, noise=0.02, u0=1e-4)
+    s = solver(cfg, "f64")
+    with pytest.raises(LbsError):
+        s.set_sor_tile(variant)
+    s.close()
+    o = Oracle(cfg)
+    o.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    o.step(25)
+    out = {}
+    for v in (variant, 4):
+        s = solver(cfg, "f32")
+        s.set_sor_tile(v)
+        s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+        s.step(25)
+        out[v] = s.fields()
+        s.close()
+    err = errors(o.fields(), out[variant])
+    assert within(err, F32_TOL), (variant, err)
+    err = errors(out[4], out[variant])
+    assert max(err.values()) < 1e-5, (variant, err)
