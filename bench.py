@@ -579,6 +579,7 @@ def main():
                       "l2": "flushed before every timed step (256 MiB write)",
                       "parallelism": f"replicas x{world}" if world > 1 else "single"},
            "roofline": roof, "kernel_ms": kmean, "sor_sweeps": sweeps, "sor_rounds": rounds,
+           "sor_tune_ms": tuned.get("timings"),
            "gpu_launches": args.steps * s.kernel_count(),
            "forms_mlups": forms, "d3q19": d3, "batched": batched,
            "clocks": clk, "e2e": e2e, "impl": "lbs", "src_sha": sha}

@@ -759,21 +759,39 @@ __device__ __forceinline__ bool sweep_converged(const Ctl *ctl, int k, double to
 // region border by one cell, so after K sweeps the tile interior holds exactly
 // the values global red-black SOR would have.  psi and C are read from one
 // global buffer and the interior is written to the other (rounds alternate),
-// so no block reads values written by the same round.  The updates of a
-// half-sweep are staged in registers and written after a barrier, which keeps
-// same-colour neighbours across an odd periodic seam deterministic.
-// Round r skips when round r-1 met the tolerance on its last sweep.
+// so no block reads values written by the same round.  Round r skips when
+// round r-1 met the tolerance on its last sweep.
+//
+// Two forms of the tile (same iterates):
+//  - checkerboard (every periodic axis of even length, the usual case): the
+//    colour of region cell (rx, ry) is (rx + ry) & 1, since tile origins are
+//    even, and no two cells of one colour are neighbours, so a half-sweep
+//    updates its colour in place.  Shared arrays are split by colour,
+//    A[c][ry][rx / 2], so the cells a warp updates and the neighbours it
+//    reads are consecutive words; half-sweep t of 2K updates only the
+//    rectangle of margin 2K - 1 - t around the tile, the cells that still
+//    reach the tile interior;
+//  - list (an odd periodic axis): cells of one colour meet across the seam,
+//    so the updates of a half-sweep are staged in registers and written after
+//    a barrier (a deterministic Jacobi step within the colour), over lists of
+//    the cells of each colour.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned int nblocks);
 
 template <typename R, int TX, int TY, int K, int BS>
 struct SorTile {
     static constexpr int H = 2 * K, RX = TX + 2 * H, RY = TY + 2 * H, NR = RX * RY;
+    // checkerboard form: a colour plane of RY rows of RXH words, planes NHP
+    // apart (16 words of padding put the planes' banks half a warp apart)
+    static constexpr int RXH = RX / 2, NH = RY * RXH, NHP = NH + 16;
+    static_assert(TX % 2 == 0 && TY % 2 == 0, "SOR tiles have even sides");
     // per region cell: psi, C, rhs psi, rhs C, inverse diagonals (2), face
     // coefficients to the +x and +y neighbours (2 fields x 2), one flag byte;
-    // and the cell lists of the two colours (2-byte indices)
+    // the list form adds the cell lists of the two colours (2-byte indices)
+    static constexpr size_t list_bytes() { return (size_t)NR * (10 * sizeof(R) + 1 + 2 * 2) + 16; }
+    static constexpr size_t cb_bytes() { return (size_t)2 * NHP * (10 * sizeof(R) + 1) + 16; }
     static constexpr size_t smem_bytes() {
-        return (size_t)NR * (10 * sizeof(R) + 1 + 2 * 2) + 16;
+        return list_bytes() > cb_bytes() ? list_bytes() : cb_bytes();
     }
 };
 
@@ -809,11 +827,150 @@ __device__ __forceinline__ bool round_converged(const Ctl *ctl, int r, double to
     return d1 >= 0.5 * d0;
 }
 
-// one tile (bx, by) of round `round` of instance I, in smem_raw
-// (SorTile::smem_bytes()); folds the tile's maxima into the round's slot
+// block maxima of the last sweep (|dpsi|, |dC|, |psi|, |C|) -> round slot
+template <typename R, int BS>
+__device__ __forceinline__ void sor_fold_maxima(const Inst<R> &I, int round, R v[4]) {
+    __shared__ R sh[4][BS / 32];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
+    if ((tid & 31) == 0)
+        for (int q = 0; q < 4; q++) sh[q][tid >> 5] = v[q];
+    __syncthreads();
+    if (tid == 0)
+        for (int q = 0; q < 4; q++) {
+            R m = R(0);
+            for (int w = 0; w < BS / 32; w++) m = fmax(m, sh[q][w]);
+            atomic_max_pos(&I.ctl->sweep[round][q], double(m));
+        }
+}
+
+// checkerboard form of a tile (see above)
 template <typename R, int TX, int TY, int K, int BS>
-__device__ __forceinline__ void sor_tile2(const Inst<R> &I, int round, int bx, int by,
-                                          unsigned char *smem_raw) {
+__device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx, int by,
+                                             unsigned char *smem_raw) {
+    using T = SorTile<R, TX, TY, K, BS>;
+    constexpr int RX = T::RX, RY = T::RY, H = T::H, RXH = T::RXH, NH = T::NH, NHP = T::NHP;
+    constexpr int NS = 2 * NHP;
+    R *sp = (R *)smem_raw, *sc = sp + NS, *bp = sc + NS, *bc = bp + NS;
+    R *ip = bc + NS, *ic = ip + NS;                    // 1 / diagonal
+    R *fpx = ic + NS, *fpy = fpx + NS, *fcx = fpy + NS, *fcy = fcx + NS;  // faces +x, +y
+    uint8_t *fl = (uint8_t *)(fcy + NS);               // 1: in the domain
+    const int tid = threadIdx.x;
+    const int x0 = bx * TX - H, y0 = by * TY - H;      // even
+    const R *pin = (round & 1) ? I.psi2 : I.psi;
+    const R *cin = (round & 1) ? I.C2 : I.C;
+    R *pout = (round & 1) ? I.psi : I.psi2;
+    R *cout = (round & 1) ? I.C : I.C2;
+    // 1. load in row order (coalesced); ip / ic hold the weights a + eps,
+    //    chi + eps for now, zero outside the domain
+    for (int q = tid; q < RX * RY; q += BS) {
+        const int rx = q % RX, ry = q / RX;
+        int refl = 0, sx, sy;
+        const int X = map_axis(x0 + rx, I.nx, I.wall[0], 1, refl, sx);
+        const int Y = map_axis(y0 + ry, I.ny, I.wall[1], 2, refl, sy);
+        const int s = ((rx + ry) & 1) * NHP + ry * RXH + (rx >> 1);
+        if (!refl) {
+            const long long c = (long long)Y * I.pitch + X;
+            sp[s] = pin[c];
+            sc[s] = cin[c];
+            bp[s] = I.rpsi[c];
+            bc[s] = I.rC[c];
+            ip[s] = I.a[c] + I.eps_w;
+            ic[s] = I.chi[c] + I.eps_w;
+        } else {
+            sp[s] = sc[s] = bp[s] = bc[s] = ip[s] = ic[s] = R(0);
+        }
+        fl[s] = !refl;
+    }
+    __syncthreads();
+    // 2. face coefficients h (w_c + w_nb)/2 of Eq. 28 towards +x and +y; zero
+    //    across a wall or the region edge
+    const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
+    for (int q = tid; q < 2 * NH; q += BS) {
+        const int c = q >= NH, r = q - c * NH, ry = r / RXH, j = r - ry * RXH;
+        const int rx = 2 * j + ((c ^ ry) & 1);
+        const int s = c * NHP + r, o = (1 - c) * NHP + ry * RXH;
+        const bool in = fl[s];
+        const bool ex = in && rx < RX - 1 && fl[o + ((rx + 1) >> 1)];
+        const bool ny = in && ry < RY - 1 && fl[o + RXH + j];
+        const int e = o + ((rx + 1) >> 1), n = o + RXH + j;
+        fpx[s] = ex ? hp * R(0.5) * (ip[s] + ip[e]) : R(0);
+        fcx[s] = ex ? hc * R(0.5) * (ic[s] + ic[e]) : R(0);
+        fpy[s] = ny ? hp * R(0.5) * (ip[s] + ip[n]) : R(0);
+        fcy[s] = ny ? hc * R(0.5) * (ic[s] + ic[n]) : R(0);
+    }
+    __syncthreads();
+    // 3. inverse diagonals w + sum of the four faces (zero outside the domain,
+    //    where the weights are zero: those cells stay zero in every sweep)
+    for (int q = tid; q < 2 * NH; q += BS) {
+        const int c = q >= NH, r = q - c * NH, ry = r / RXH, j = r - ry * RXH;
+        const int rx = 2 * j + ((c ^ ry) & 1);
+        const int s = c * NHP + r, o = (1 - c) * NHP + ry * RXH;
+        if (!fl[s]) continue;
+        const int w = o + ((rx - 1) >> 1), so = o - RXH + j;
+        const R sp_ = fpx[s] + fpy[s] + (rx > 0 ? fpx[w] : R(0)) + (ry > 0 ? fpy[so] : R(0));
+        const R sc_ = fcx[s] + fcy[s] + (rx > 0 ? fcx[w] : R(0)) + (ry > 0 ? fcy[so] : R(0));
+        ip[s] = fdiv(R(1), ip[s] + sp_);
+        ic[s] = fdiv(R(1), ic[s] + sc_);
+    }
+    __syncthreads();
+    // 2K half-sweeps in place; half-sweep t updates colour t & 1 over the
+    // rectangle of margin m = 2K - 1 - t around the tile
+    R v[4] = {R(0), R(0), R(0), R(0)};  // maxima of the last sweep (never FP64 per cell)
+#pragma unroll
+    for (int t = 0; t < 2 * K; t++) {
+        const int c = t & 1, m = 2 * K - 1 - t;
+        const int lo = H - m, xhi = H + TX + m, yhi = H + TY + m;  // lo >= 1
+        const int jlo = lo >> 1, jn = ((xhi - 1) >> 1) - jlo + 1;
+        const int n = (yhi - lo) * jn;
+        const bool last = t >= 2 * K - 2;
+        for (int idx = tid; idx < n; idx += BS) {
+            const int ry = lo + idx / jn, j = jlo + idx % jn;
+            const int rx = 2 * j + ((c ^ ry) & 1);
+            if (rx < lo || rx >= xhi) continue;
+            const int s = c * NHP + ry * RXH + j, o = (1 - c) * NHP + ry * RXH;
+            const int e = o + ((rx + 1) >> 1), w = o + ((rx - 1) >> 1);
+            const int nn = o + RXH + j, so = o - RXH + j;
+            const R op = bp[s] + fpx[s] * sp[e] + fpy[s] * sp[nn] + fpx[w] * sp[w] +
+                         fpy[so] * sp[so];
+            const R oc = bc[s] + fcx[s] * sc[e] + fcy[s] * sc[nn] + fcx[w] * sc[w] +
+                         fcy[so] * sc[so];
+            const R p0 = sp[s], c0 = sc[s];
+            const R dp = I.omega * (op * ip[s] - p0);
+            const R dc = I.omega * (oc * ic[s] - c0);
+            const R p1 = p0 + dp, c1 = c0 + dc;
+            sp[s] = p1;
+            sc[s] = c1;
+            if (last && rx >= H && rx < H + TX && ry >= H && ry < H + TY && x0 + rx < I.nx &&
+                y0 + ry < I.ny) {
+                v[0] = fmax(v[0], fabs(dp));
+                v[1] = fmax(v[1], fabs(dc));
+                v[2] = fmax(v[2], fabs(p1));
+                v[3] = fmax(v[3], fabs(c1));
+            }
+        }
+        __syncthreads();
+    }
+    // tile interior back to the other buffer, in row order
+    for (int q = tid; q < TX * TY; q += BS) {
+        const int rx = H + q % TX, ry = H + q / TX;
+        const int gx = x0 + rx, gy = y0 + ry;
+        if (gx >= I.nx || gy >= I.ny) continue;
+        const int s = ((rx + ry) & 1) * NHP + ry * RXH + (rx >> 1);
+        const long long c = (long long)gy * I.pitch + gx;
+        pout[c] = sp[s];
+        cout[c] = sc[s];
+    }
+    sor_fold_maxima<R, BS>(I, round, v);
+}
+
+// list form of a tile (see above)
+template <typename R, int TX, int TY, int K, int BS>
+__device__ __forceinline__ void sor_tile2_list(const Inst<R> &I, int round, int bx, int by,
+                                               unsigned char *smem_raw) {
     using T = SorTile<R, TX, TY, K, BS>;
     constexpr int RX = T::RX, RY = T::RY, NR = T::NR, H = T::H;
     R *sp = (R *)smem_raw, *sc = sp + NR, *bp = sc + NR, *bc = bp + NR;
@@ -938,21 +1095,18 @@ __device__ __forceinline__ void sor_tile2(const Inst<R> &I, int round, int bx, i
         pout[c] = sp[q];
         cout[c] = sc[q];
     }
-    // block maxima of the last sweep -> round slot
-    __shared__ R sh[4][BS / 32];
-#pragma unroll
-    for (int q = 0; q < 4; q++)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
-    if ((tid & 31) == 0)
-        for (int q = 0; q < 4; q++) sh[q][tid >> 5] = v[q];
-    __syncthreads();
-    if (tid == 0)
-        for (int q = 0; q < 4; q++) {
-            R m = R(0);
-            for (int w = 0; w < BS / 32; w++) m = fmax(m, sh[q][w]);
-            atomic_max_pos(&I.ctl->sweep[round][q], double(m));
-        }
+    sor_fold_maxima<R, BS>(I, round, v);
+}
+
+// one tile (bx, by) of round `round` of instance I, in smem_raw
+// (SorTile::smem_bytes()); folds the tile's maxima into the round's slot
+template <typename R, int TX, int TY, int K, int BS>
+__device__ __forceinline__ void sor_tile2(const Inst<R> &I, int round, int bx, int by,
+                                          unsigned char *smem_raw) {
+    if ((I.wall[0] || !(I.nx & 1)) && (I.wall[1] || !(I.ny & 1)))
+        sor_tile2_cb<R, TX, TY, K, BS>(I, round, bx, by, smem_raw);
+    else
+        sor_tile2_list<R, TX, TY, K, BS>(I, round, bx, by, smem_raw);
 }
 
 // decision after a round of instance ctl: converged, or out of rounds
