@@ -173,6 +173,8 @@ def profile_case(args):
         cfg = W.shear_droplet_3d(nx=128, ny=64, nz=64, R=12.0)
         f = W.initial_fields(cfg)
         s = Solver(cfg, storage=args.storage3d)
+        if args.sor_tile_3d is not None:
+            s.set_sor_tile(args.sor_tile_3d)
         s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
         s.set_graph(False)
         s.step(args.steps)
@@ -389,7 +391,9 @@ def main():
     ap.add_argument("--no-3d", action="store_true",
                     help="skip the D3Q19 (3D sheared droplet) measurement")
     ap.add_argument("--sor-tile", type=int, default=None,
-                    help="blocked SOR variant (0..4) instead of tuning it")
+                    help="blocked SOR variant of the 2D step (0..8) instead of tuning it")
+    ap.add_argument("--sor-tile-3d", type=int, default=None,
+                    help="SOR variant of the 3D step (0..2) instead of tuning it")
     ap.add_argument("--profile-case", choices=["3d", "batch"], default=None,
                     help="run a small workload with individual launches for kernel "
                          "profilers and exit (see profile_case)")
@@ -553,7 +557,12 @@ def main():
         for st in ("bf16", "f32", "f16"):
             s3 = Solver(cfg3, storage=st, stream=stream)
             s3.init_fields(f3["phi"], f3["psi"], f3["C"], f3["u"])
-            t3 = autotune.tune_single(s3, cfg3["nx"], lattice="d3q19", use_cache=False)
+            if args.sor_tile_3d is not None:
+                s3.set_sor_tile(args.sor_tile_3d)
+                t3 = {"sor": args.sor_tile_3d}
+            else:
+                t3 = autotune.tune_single(s3, cfg3["nx"], lattice="d3q19", use_cache=False)
+                d3.setdefault("sor_tune_ms", {})[st] = t3.get("timings")
             d3.setdefault("sor_variant", {})[st] = t3["sor"]
             s3.init_fields(f3["phi"], f3["psi"], f3["C"], f3["u"])
             s3.profile(True)

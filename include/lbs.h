@@ -246,13 +246,16 @@ int lbs_step_result(lbs_ctx *c, double *out);
 /* Blocked SOR tile of a 2D context (Sec. 2.2 solves), as tile / red-black
  * sweeps a launch / threads: 0 = 32x16 / 2 / 256 (default), 1 = 64x8 / 2 /
  * 256, 2 = 16x16 / 2 / 256, 3 = 32x16 / 4 / 256, 4 = 32x32 / 4 / 256,
- * 5 = 32x32 / 4 / 512, 6 = 64x16 / 4 / 512.  More sweeps a launch mean fewer
- * launches and a wider halo (2 per sweep); the iterates, and so the results,
- * do not depend on the choice except through where the convergence test
- * falls (after every launch).  3D contexts: 0 = a red and a black
- * half-sweep a sweep, in place (default), 1 = one full red-black sweep a
- * launch with 32x8 tiles marching through 16-plane chunks of z in shared
- * memory.  Errors: LBS_EINVAL. */
+ * 5 = 32x32 / 4 / 512, 6 = 64x16 / 4 / 512, 7 = 32x32 / 6 / 512,
+ * 8 = 32x16 / 8 / 512 (7 and 8 exceed a block's shared memory in FP64 and
+ * are refused there).  More sweeps a launch mean fewer launches and a wider
+ * halo (2 per sweep); the iterates, and so the results, do not depend on the
+ * choice except through where the convergence test falls (after every
+ * launch).  3D contexts: 0 = a red and a black half-sweep a sweep, in place,
+ * one thread a cell (default), 1 = one full red-black sweep a launch with
+ * 32x8 tiles marching through 16-plane chunks of z in shared memory, 2 and
+ * 3 = the half-sweeps of 0 with each thread marching a cell pair through 8
+ * or 4 planes of z.  Errors: LBS_EINVAL. */
 int lbs_set_sor_tile(lbs_ctx *c, int variant);
 
 /* Human-readable description of the last error of c (never NULL). */

@@ -121,7 +121,7 @@ def tune(batch, widths, lattice="d2q9", timer=None, cache_path=None, use_cache=T
     return {"key": key, "source": "timed", "timings": times, **choice}
 
 
-SOR_TILES_3D = (0, 1)  # red-black half-sweeps; z-marching full sweeps
+SOR_TILES_3D = (0, 1, 2, 3)  # red-black half-sweeps; z-marching full sweeps; column marching
 
 
 def tune_single(solver, width, lattice="d2q9", timer=None, cache_path=None, use_cache=True,

@@ -41,14 +41,36 @@ template <typename R, typename P>
 void Launch3<R, P>::diag(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s, int nblocks) {
     k_diag<R, P, 256, Q19><<<g, b, 0, s>>>(I, nblocks);
 }
+// column marching: planes a thread updates, 8 (variant 2) or 4 (variant 3,
+// twice the blocks for grids that would not fill the GPU)
+constexpr int cm_planes(int variant) { return variant == 3 ? 4 : 8; }
+
 template <typename R, typename P>
 void Launch3<R, P>::sor(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s, int colour,
-                        cudaGraphConditionalHandle h, int max_rounds, int eager_round) {
-    k_sor_rb3<R, kBS3><<<g, b, 0, s>>>(I, colour, h, max_rounds, eager_round);
+                        cudaGraphConditionalHandle h, int max_rounds, int eager_round,
+                        int variant) {
+    if (variant == 2)
+        k_sor_cm3<R, kBS3, 8><<<g, b, 0, s>>>(I, colour, h, max_rounds, eager_round);
+    else if (variant == 3)
+        k_sor_cm3<R, kBS3, 4><<<g, b, 0, s>>>(I, colour, h, max_rounds, eager_round);
+    else
+        k_sor_rb3<R, kBS3><<<g, b, 0, s>>>(I, colour, h, max_rounds, eager_round);
 }
 template <typename R, typename P>
-void *Launch3<R, P>::sor_fn() {
+void *Launch3<R, P>::sor_fn(int variant) {
+    if (variant == 2) return (void *)k_sor_cm3<R, kBS3, 8>;
+    if (variant == 3) return (void *)k_sor_cm3<R, kBS3, 4>;
     return (void *)k_sor_rb3<R, kBS3>;
+}
+template <typename R, typename P>
+dim3 Launch3<R, P>::sor_grid(int variant, int nx, int ny, int nz) {
+    const int hx = (nx + 1) / 2;  // cell pairs along x
+    const dim3 g((hx + kSorBX - 1) / kSorBX, (ny + kSorBY - 1) / kSorBY, nz);
+    if (variant == 2 || variant == 3) {
+        const int zc = cm_planes(variant);
+        return dim3(g.x, g.y, (nz + zc - 1) / zc);
+    }
+    return g;
 }
 
 constexpr int kZmTX = 32, kZmTY = 8, kZmZC = 16, kZmBS = 256;

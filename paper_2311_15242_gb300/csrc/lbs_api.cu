@@ -292,7 +292,8 @@ struct Solver : Base {
     }
 
     // SOR variant: 2D the blocked tile (sor_vtx ...); 3D 0 = red-black
-    // half-sweeps in place, 1 = z-marching full sweeps (ping-pong buffers)
+    // half-sweeps in place, 1 = z-marching full sweeps (ping-pong buffers),
+    // 2, 3 = red-black half-sweeps in place by column marching (8 or 4 planes)
     int sv = 0;
     void set_sor_grid() {
         using L3 = Launch3<R, P>;
@@ -302,10 +303,9 @@ struct Solver : Base {
         } else if (sv == 1) {
             sor_grid = L3::zm_grid(I.nx, I.ny, I.nz);
         } else {
-            // red-black half-sweeps: one thread per cell pair along x
-            const int hx = (I.nx + 1) / 2;
-            sor_grid = dim3((hx + L3::kSorBX - 1) / L3::kSorBX,
-                            (I.ny + L3::kSorBY - 1) / L3::kSorBY, I.nz);
+            // red-black half-sweeps: one thread per cell pair along x (and per
+            // plane, or per chunk of planes when column marching)
+            sor_grid = L3::sor_grid(sv, I.nx, I.ny, I.nz);
         }
         I.sor_pingpong = (D == 2 || sv == 1) ? 1 : 0;
     }
@@ -317,8 +317,8 @@ struct Solver : Base {
         return sor2_smem<R>(v) <= (size_t)lim;
     }
     int set_sor_tile(int v) override {
-        if (v < 0 || v >= (D == 2 ? kSorVariants : 2)) {
-            set_err(ctx, "SOR variant %d: 0..%d in 2D, 0..1 in 3D", v, kSorVariants - 1);
+        if (v < 0 || v >= (D == 2 ? kSorVariants : 4)) {
+            set_err(ctx, "SOR variant %d: 0..%d in 2D, 0..3 in 3D", v, kSorVariants - 1);
             return LBS_EINVAL;
         }
         if (D == 2 && !sor2_fits(v)) {
@@ -484,7 +484,7 @@ struct Solver : Base {
                     void *args[] = {(void *)&I, (void *)&col, (void *)&h, (void *)&maxr,
                                     (void *)&eager};
                     cudaKernelNodeParams kp = {};
-                    kp.func = L3::sor_fn();
+                    kp.func = L3::sor_fn(sv);
                     kp.gridDim = sor_grid;
                     kp.blockDim = dim3(L3::kSorBX, L3::kSorBY, 1);
                     kp.sharedMemBytes = 0;
@@ -523,8 +523,8 @@ struct Solver : Base {
             cudaLaunchKernel(L3::zm_fn(), sor_grid, dim3(L3::zm_threads()), args, L3::zm_smem(), s);
         } else {
             const dim3 b(L3::kSorBX, L3::kSorBY, 1);
-            L3::sor(I, sor_grid, b, s, 0, h, sor_rounds(), r);
-            L3::sor(I, sor_grid, b, s, 1, h, sor_rounds(), r);
+            L3::sor(I, sor_grid, b, s, 0, h, sor_rounds(), r, sv);
+            L3::sor(I, sor_grid, b, s, 1, h, sor_rounds(), r, sv);
         }
     }
 
@@ -562,7 +562,7 @@ struct Solver : Base {
     // diagnostics (4 before the first): one launch a round, two for the 3D
     // red-black half-sweeps
     int kernel_count() const override {
-        const int per_round = (D == 3 && sv == 0) ? 2 : 1;
+        const int per_round = (D == 3 && sv != 1) ? 2 : 1;
         const int cells = D == 2 ? 4 : 5;  // 2D: fd fused with collide
         return I.transport ? cells + 2 + per_round * last_rounds : 4;
     }

@@ -265,6 +265,18 @@ __device__ __forceinline__ long long nbx3(const Inst<R> &I, const Ax &X, const A
     return ((long long)Z.v[dz + 2] * I.ny + Y.v[dy + 2]) * I.pitch + X.v[dx + 2];
 }
 
+// two consecutive elements (one aligned vector load or store)
+template <typename R>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using T = float2;
+};
+template <>
+struct Vec2<double> {
+    using T = double2;
+};
+
 // division and inverse square root: IEEE in double precision; in single
 // precision the hardware approximations (about 2 ulp), whose errors are of
 // the order of the FP32 rounding of the stored fields

@@ -865,25 +865,53 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
     R *pout = (round & 1) ? I.psi : I.psi2;
     R *cout = (round & 1) ? I.C : I.C2;
     // 1. load in row order (coalesced); ip / ic hold the weights a + eps,
-    //    chi + eps for now, zero outside the domain
-    for (int q = tid; q < RX * RY; q += BS) {
-        const int rx = q % RX, ry = q / RX;
-        int refl = 0, sx, sy;
-        const int X = map_axis(x0 + rx, I.nx, I.wall[0], 1, refl, sx);
-        const int Y = map_axis(y0 + ry, I.ny, I.wall[1], 2, refl, sy);
-        const int s = ((rx + ry) & 1) * NHP + ry * RXH + (rx >> 1);
-        if (!refl) {
-            const long long c = (long long)Y * I.pitch + X;
-            sp[s] = pin[c];
-            sc[s] = cin[c];
-            bp[s] = I.rpsi[c];
-            bc[s] = I.rC[c];
-            ip[s] = I.a[c] + I.eps_w;
-            ic[s] = I.chi[c] + I.eps_w;
-        } else {
-            sp[s] = sc[s] = bp[s] = bc[s] = ip[s] = ic[s] = R(0);
+    //    chi + eps for now, zero outside the domain.  A thread loads U cells
+    //    into registers before it stores any, so that their loads are in
+    //    flight together (a store to shared memory would otherwise order the
+    //    next cell's loads behind it).
+    constexpr int U = 3;
+    for (int q0 = tid; q0 < RX * RY; q0 += U * BS) {
+        R vv[U][6];
+        int ss[U];
+        bool in[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int q = q0 + u * BS;
+            in[u] = false;
+            ss[u] = -1;
+            if (q >= RX * RY) continue;
+            const int rx = q % RX, ry = q / RX;
+            int refl = 0, sx, sy;
+            const int X = map_axis(x0 + rx, I.nx, I.wall[0], 1, refl, sx);
+            const int Y = map_axis(y0 + ry, I.ny, I.wall[1], 2, refl, sy);
+            ss[u] = ((rx + ry) & 1) * NHP + ry * RXH + (rx >> 1);
+            in[u] = !refl;
+            if (!refl) {
+                const long long c = (long long)Y * I.pitch + X;
+                vv[u][0] = pin[c];
+                vv[u][1] = cin[c];
+                vv[u][2] = I.rpsi[c];
+                vv[u][3] = I.rC[c];
+                vv[u][4] = I.a[c];
+                vv[u][5] = I.chi[c];
+            }
         }
-        fl[s] = !refl;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int s = ss[u];
+            if (s < 0) continue;
+            if (in[u]) {
+                sp[s] = vv[u][0];
+                sc[s] = vv[u][1];
+                bp[s] = vv[u][2];
+                bc[s] = vv[u][3];
+                ip[s] = vv[u][4] + I.eps_w;
+                ic[s] = vv[u][5] + I.eps_w;
+            } else {
+                sp[s] = sc[s] = bp[s] = bc[s] = ip[s] = ic[s] = R(0);
+            }
+            fl[s] = in[u];
+        }
     }
     __syncthreads();
     // 2. face coefficients h (w_c + w_nb)/2 of Eq. 28 towards +x and +y; zero

@@ -586,6 +586,44 @@ __global__ void __launch_bounds__(256, 3) k_stream3(Inst<R> I) {
     store_moments3(I, c, fT, fM, fl);
 }
 
+// block maxima of a half-sweep -> the round's slot; after the black
+// half-sweep the last block decides whether another round runs
+template <typename R, int BS>
+__device__ __forceinline__ void sor3_finish(const Inst<R> &I, int round, int colour, R v[4],
+                                            cudaGraphConditionalHandle loop, int max_rounds,
+                                            int eager_round) {
+    __shared__ R sh[4][BS / 32];
+    const int t = threadIdx.x + threadIdx.y * blockDim.x;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
+    if ((t & 31) == 0)
+        for (int q = 0; q < 4; q++) sh[q][t >> 5] = v[q];
+    __syncthreads();
+    if (t == 0)
+        for (int q = 0; q < 4; q++) {
+            R m = R(0);
+            for (int w = 0; w < BS / 32; w++) m = fmax(m, sh[q][w]);
+            atomic_max_pos(&I.ctl->sweep[round][q], double(m));
+        }
+    if (colour == 0) return;
+    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    if (!last_block(&I.ctl->sor_ticket, nb)) return;
+    if (t != 0) return;
+    Ctl *ctl = I.ctl;
+    ctl->sor_ticket = 0;
+    const bool conv = round_converged<R>(ctl, round, double(I.sor_tol));
+    const bool stop = conv || round + 1 >= max_rounds;
+    if (stop && !conv) ctl->status |= ST_NOCONV;
+    if (eager_round < 0) {
+        ctl->sor_exec = round + 1;
+        if (stop) cudaGraphSetConditional(loop, 0);
+    } else {
+        ctl->sor_exec = stop ? -(round + 1) - 1000000 : round + 1;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // k_sor_rb3: one half-sweep of red-black SOR (omega of Sec. 2.2) for
 // (w - h L_w) x = rhs on psi and C, updating the cells of one colour
@@ -636,36 +674,156 @@ __global__ void __launch_bounds__(BS)
         v[2] = fabs(p1);
         v[3] = fabs(c1);
     }
-    __shared__ R sh[4][BS / 32];
-    const int t = threadIdx.x + threadIdx.y * blockDim.x;
-#pragma unroll
-    for (int q = 0; q < 4; q++)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
-    if ((t & 31) == 0)
-        for (int q = 0; q < 4; q++) sh[q][t >> 5] = v[q];
-    __syncthreads();
-    if (t == 0)
-        for (int q = 0; q < 4; q++) {
-            R m = R(0);
-            for (int w = 0; w < BS / 32; w++) m = fmax(m, sh[q][w]);
-            atomic_max_pos(&I.ctl->sweep[round][q], double(m));
-        }
-    if (colour == 0) return;
-    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
-    if (!last_block(&I.ctl->sor_ticket, nb)) return;
-    if (t != 0) return;
-    Ctl *ctl = I.ctl;
-    ctl->sor_ticket = 0;
-    const bool conv = round_converged<R>(ctl, round, double(I.sor_tol));
-    const bool stop = conv || round + 1 >= max_rounds;
-    if (stop && !conv) ctl->status |= ST_NOCONV;
-    if (eager_round < 0) {
-        ctl->sor_exec = round + 1;
-        if (stop) cudaGraphSetConditional(loop, 0);
-    } else {
-        ctl->sor_exec = stop ? -(round + 1) - 1000000 : round + 1;
+    sor3_finish<R, BS>(I, round, colour, v, loop, max_rounds, eager_round);
+}
+
+// ---------------------------------------------------------------------------
+// k_sor_cm3: the half-sweep of k_sor_rb3 (same faces, summed in the same
+// order) by column marching.  Lane l of a warp owns the cell pair
+// x0 = 2 (32 bx + l), x0 + 1 of row y (a warp is one row) and marches z over
+// a chunk of ZC planes; on plane z it updates the pair's cell of the current
+// colour, x0 + k with k = (colour + y + z) mod 2.  The pair's psi, C, a and
+// chi on planes z - 1, z and z + 1 stay in registers (plane z + 2 is loaded
+// a step ahead).  The x-neighbour outside the pair is the adjacent lane's
+// pair: k is the same for the whole warp, so all lanes take the same side;
+// only the warp's and the domain's end lanes load it.  The y-neighbours and
+// the right-hand sides are loaded.  The cells a half-sweep reads (the other
+// colour) and writes (its colour) are disjoint, so no thread reads a value
+// another thread writes.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Pair4 {  // psi, C, a, chi of a cell pair on one plane
+    R p0, p1, c0, c1, a0, a1, x0, x1;
+    bool wall;  // the plane lies beyond a wall
+};
+
+template <typename R>
+__device__ __forceinline__ void load_pair3(const Inst<R> &I, int x0, bool act, int y, int zz,
+                                           Pair4<R> &q) {
+    int refl = 0, side;
+    const int z = map_axis(zz, I.nz, I.wall[2], 4, refl, side);
+    q.wall = refl != 0;
+    if (!act || refl) {
+        q.p0 = q.p1 = q.c0 = q.c1 = q.a0 = q.a1 = q.x0 = q.x1 = R(0);
+        return;
     }
+    using V = typename Vec2<R>::T;
+    const long long c = cell3(I, x0, y, z);  // even: x0 and the pitch are even
+    const V p = *(const V *)&I.psi[c], cc = *(const V *)&I.C[c];
+    const V a = *(const V *)&I.a[c], x = *(const V *)&I.chi[c];
+    q.p0 = p.x;
+    q.p1 = p.y;
+    q.c0 = cc.x;
+    q.c1 = cc.y;
+    q.a0 = a.x;
+    q.a1 = a.y;
+    q.x0 = x.x;
+    q.x1 = x.y;
+}
+
+template <typename R, int BS, int ZC>
+__global__ void __launch_bounds__(BS)
+    k_sor_cm3(Inst<R> I, int colour, cudaGraphConditionalHandle loop, int max_rounds,
+              int eager_round) {
+    if (eager_round > 0 && I.ctl->sor_exec < eager_round) return;  // loop already ended
+    const int round = I.ctl->sor_exec;
+    const int lane = threadIdx.x;  // blockDim.x == 32
+    const int x0 = 2 * (blockIdx.x * 32 + lane);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int zs = blockIdx.z * ZC, ze = min(zs + ZC, I.nz);
+    const bool act = x0 < I.nx;
+    R v[4] = {R(0), R(0), R(0), R(0)};
+    if (y < I.ny) {  // (the whole warp)
+        const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
+        int side;
+        // neighbours along y, the pair's partner beyond a wall (odd nx), and
+        // the x-neighbours outside the pair: x0 - 1 (k = 0), x0 + 2 (k = 1)
+        int rym = 0, ryp = 0, rpart = 0, rxa = 0, rxb = 0;
+        const int ym = map_axis(y - 1, I.ny, I.wall[1], 2, rym, side);
+        const int yp = map_axis(y + 1, I.ny, I.wall[1], 2, ryp, side);
+        map_axis(x0 + 1, I.nx, I.wall[0], 1, rpart, side);
+        const int xa = map_axis(x0 - 1, I.nx, I.wall[0], 1, rxa, side);
+        const int xb = map_axis(x0 + 2, I.nx, I.wall[0], 1, rxb, side);
+        // the adjacent lane holds that neighbour when it is inside the domain
+        const bool sha = lane > 0 && x0 >= 2, shb = lane < 31 && x0 + 2 < I.nx;
+        Pair4<R> Pm, P0, Pp, Pn;
+        load_pair3(I, x0, act, y, zs - 1, Pm);
+        load_pair3(I, x0, act, y, zs, P0);
+        load_pair3(I, x0, act, y, zs + 1, Pp);
+        for (int z = zs; z < ze; z++) {
+            if (z + 2 <= ze) load_pair3(I, x0, act, y, z + 2, Pn);
+            const int k = (colour + y + z) & 1;
+            // the adjacent lane's cell next to the pair on plane z
+            const R op_ = k ? __shfl_down_sync(0xffffffffu, P0.p0, 1)
+                            : __shfl_up_sync(0xffffffffu, P0.p1, 1);
+            const R oc_ = k ? __shfl_down_sync(0xffffffffu, P0.c0, 1)
+                            : __shfl_up_sync(0xffffffffu, P0.c1, 1);
+            const R oa_ = k ? __shfl_down_sync(0xffffffffu, P0.a0, 1)
+                            : __shfl_up_sync(0xffffffffu, P0.a1, 1);
+            const R ox_ = k ? __shfl_down_sync(0xffffffffu, P0.x0, 1)
+                            : __shfl_up_sync(0xffffffffu, P0.x1, 1);
+            const int xu = x0 + k;
+            if (act && xu < I.nx) {
+                const long long c = cell3(I, xu, y, z);
+                const R au = k ? P0.a1 : P0.a0, xu_ = k ? P0.x1 : P0.x0;
+                const R p0 = k ? P0.p1 : P0.p0, c0 = k ? P0.c1 : P0.c0;
+                const R wp = au + I.eps_w, wc = xu_ + I.eps_w;
+                R dp = wp, dc = wc, op = I.rpsi[c], oc = I.rC[c];
+                auto face = [&](R an, R xn, R pn, R cn) {
+                    const R fp = hp * (R(0.5) * (wp + (an + I.eps_w)));
+                    const R fc = hc * (R(0.5) * (wc + (xn + I.eps_w)));
+                    dp += fp;
+                    dc += fc;
+                    op += fp * pn;
+                    oc += fc * cn;
+                };
+                // the x-neighbour outside the pair: adjacent lane or loaded
+                const bool orefl = k ? rxb : rxa;
+                R na = oa_, nx_ = ox_, np = op_, nc = oc_;
+                if (!orefl && !(k ? shb : sha)) {
+                    const long long j = cell3(I, k ? xb : xa, y, z);
+                    na = I.a[j];
+                    nx_ = I.chi[j];
+                    np = I.psi[j];
+                    nc = I.C[j];
+                }
+                // -x, +x: (other, partner) for k = 0, (partner, other) for k = 1
+                if (k) {
+                    face(P0.a0, P0.x0, P0.p0, P0.c0);
+                    if (!orefl) face(na, nx_, np, nc);
+                } else {
+                    if (!orefl) face(na, nx_, np, nc);
+                    if (!rpart) face(P0.a1, P0.x1, P0.p1, P0.c1);
+                }
+                if (!rym) {
+                    const long long j = cell3(I, xu, ym, z);
+                    face(I.a[j], I.chi[j], I.psi[j], I.C[j]);
+                }
+                if (!ryp) {
+                    const long long j = cell3(I, xu, yp, z);
+                    face(I.a[j], I.chi[j], I.psi[j], I.C[j]);
+                }
+                if (!Pm.wall)
+                    face(k ? Pm.a1 : Pm.a0, k ? Pm.x1 : Pm.x0, k ? Pm.p1 : Pm.p0,
+                         k ? Pm.c1 : Pm.c0);
+                if (!Pp.wall)
+                    face(k ? Pp.a1 : Pp.a0, k ? Pp.x1 : Pp.x0, k ? Pp.p1 : Pp.p0,
+                         k ? Pp.c1 : Pp.c0);
+                const R d1 = I.omega * (fdiv(op, dp) - p0), d2 = I.omega * (fdiv(oc, dc) - c0);
+                const R p1 = p0 + d1, c1 = c0 + d2;
+                I.psi[c] = p1;
+                I.C[c] = c1;
+                v[0] = fmax(v[0], fabs(d1));
+                v[1] = fmax(v[1], fabs(d2));
+                v[2] = fmax(v[2], fabs(p1));
+                v[3] = fmax(v[3], fabs(c1));
+            }
+            Pm = P0;
+            P0 = Pp;
+            Pp = Pn;
+        }
+    }
+    sor3_finish<R, BS>(I, round, colour, v, loop, max_rounds, eager_round);
 }
 
 // ---------------------------------------------------------------------------

@@ -152,19 +152,53 @@ def test_full_size_shear_3d(storage):
     s.close()
 
 
-@pytest.mark.parametrize("make", [shear, bubble3], ids=["shear", "bubble"])
-def test_zmarch_sor_matches_oracle_3d(make):
+def bubble3_wide_odd():
+    """Walled bubble whose rows span two warps of cell pairs and end in an
+    odd column (x = 66 next to the wall)."""
+    return bubble3(nx=67, ny=20, nz=11)
+
+
+def shear_wide():
+    """Sheared droplet whose periodic rows span two warps of cell pairs."""
+    return shear(nx=70, ny=12, nz=9, R=3.5)
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3], ids=["zmarch", "column8", "column4"])
+@pytest.mark.parametrize("make", [shear, bubble3, shear_wide, bubble3_wide_odd],
+                         ids=["shear", "bubble", "shear_wide", "bubble_wide_odd"])
+def test_marching_sor_matches_oracle_3d(make, variant):
     """The z-marching full-sweep SOR (variant 1: planes of a z-chunk in shared
-    memory, ping-pong buffers) gives the oracle's solution, FP64, through
-    walls on z (shear) and on x and z (bubble)."""
+    memory, ping-pong buffers) and the column-marching half-sweeps (variant
+    2: cell pairs marching through z with their planes in registers) give the
+    oracle's solution, FP64, through walls on z (shear) and on x and z
+    (bubble)."""
     cfg = make()
     f = W.initial_fields(cfg, seed=7, noise=0.02, u0=1e-4)
     o = Oracle(cfg)
     o.init_fields(f["phi"], f["psi"], f["C"], f["u"])
     s = solver(cfg, "f64")
-    s.set_sor_tile(1)
+    s.set_sor_tile(variant)
     s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
     o.step(30)
     s.step(30)
     err = errors(o.fields(), s.fields())
     assert max(err.values()) < 1e-9, err
+
+
+def test_column_marching_sor_equals_one_thread_a_cell():
+    """Column marching performs the red-black half-sweeps of variant 0 with
+    the same faces summed in the same order: FP32 fields after 20 steps of
+    the walled bubble agree to rounding."""
+    cfg = bubble3()
+    f = W.initial_fields(cfg, seed=5, noise=0.02, u0=1e-4)
+    out = {}
+    for v in (0, 2, 3):
+        s = solver(cfg, "f32")
+        s.set_sor_tile(v)
+        s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+        s.step(20)
+        out[v] = s.fields()
+        s.close()
+    for v in (2, 3):
+        err = errors(out[0], out[v])
+        assert max(err.values()) <= 1e-6, (v, err)
