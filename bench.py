@@ -57,10 +57,10 @@ POP_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture of the source tree with this hash on this workload
-# (profiles/step_bubble_rise_256x1024_f32.md, SOR variant 4); reported only while the
+# (profiles/step_bubble_rise_256x1024_f32.md, SOR variant 5); reported only while the
 # kernels are unchanged.
-TRAFFIC = {"kernel": "sor", "sor_tile": 4, "src_sha": "42a87ab80c34c202",
-           "bytes_per_launch": 6317056}
+TRAFFIC = {"kernel": "sor", "sor_tile": 5, "src_sha": "e72900e1c2798358",
+           "bytes_per_launch": 6343168}
 
 
 def src_hash():
@@ -163,14 +163,14 @@ class Clocks:
 def profile_case(args):
     """Small workloads stepped with individual launches, for kernel
     profilers (ncu cannot trace the kernel nodes of a graph that holds a
-    conditional node): 3d = the sheared droplet at 128 x 64 x 64 (state
-    about 4x the L2), batch = the first 8 instances of the 64-instance sweep
+    conditional node): 3d = the sheared droplet at 256 x 128 x 64, half the
+    bench's cells (state about 3.5x the L2), batch = the first 8 instances of the 64-instance sweep
     with the bench's tiles (32 x 4, SOR variant 5)."""
     import torch
     from paper_2311_15242_gb300 import Batch, Solver
     torch.cuda.set_device(0)
     if args.profile_case == "3d":
-        cfg = W.shear_droplet_3d(nx=128, ny=64, nz=64, R=12.0)
+        cfg = W.shear_droplet_3d(nx=256, ny=128, nz=64, R=24.0)
         f = W.initial_fields(cfg)
         s = Solver(cfg, storage=args.storage3d)
         if args.sor_tile_3d is not None:

@@ -1275,6 +1275,10 @@ __device__ __forceinline__ void surf2_block(const Inst<R> &I, int mode, int nblo
     if (!last_block(&I.ctl->ticket, nblocks)) return;
     const double tot = block_final_sum<BS>(I.part, 1, 0, nblocks);
     int t = threadIdx.x + threadIdx.y * blockDim.x;
+    if (mode == 1) {  // the SOR convergence slots of the next solve start at zero
+        unsigned long long *sw = &I.ctl->sweep[0][0];
+        for (int k = t; k < KMAX_SWEEPS * 4; k += BS) sw[k] = 0ull;
+    }
     if (t != 0) return;
     Ctl *ctl = I.ctl;
     ctl->ticket = 0;
@@ -1297,8 +1301,6 @@ __device__ __forceinline__ void surf2_block(const Inst<R> &I, int mode, int nblo
     ctl->sor_iters = rounds * sweeps_per_round;
     ctl->sor_iters_parity = I.sor_pingpong ? (rounds & 1) : 0;
     ctl->sor_exec = 0;
-    for (int k = 0; k < KMAX_SWEEPS; k++)
-        for (int q = 0; q < 4; q++) ctl->sweep[k][q] = 0ull;
     ctl->step += 1;
 }
 
