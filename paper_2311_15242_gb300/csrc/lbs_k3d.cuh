@@ -721,6 +721,36 @@ __device__ __forceinline__ void load_pair3(const Inst<R> &I, int x0, bool act, i
     q.x1 = x.y;
 }
 
+// right-hand sides and the y-neighbours' a, chi, psi, C of the cell a
+// column-marching thread updates on one plane (zero where not needed)
+template <typename R>
+struct Nb3 {
+    R rp, rc, am, xm, pm, cm, ap, xp, pp, cp;
+};
+template <typename R>
+__device__ __forceinline__ void load_nb3(const Inst<R> &I, bool on, int xu, int y, int ym,
+                                         int yp, bool rym, bool ryp, int z, Nb3<R> &n) {
+    n.rp = n.rc = n.am = n.xm = n.pm = n.cm = n.ap = n.xp = n.pp = n.cp = R(0);
+    if (!on) return;
+    const long long c = cell3(I, xu, y, z);
+    n.rp = I.rpsi[c];
+    n.rc = I.rC[c];
+    if (!rym) {
+        const long long j = cell3(I, xu, ym, z);
+        n.am = I.a[j];
+        n.xm = I.chi[j];
+        n.pm = I.psi[j];
+        n.cm = I.C[j];
+    }
+    if (!ryp) {
+        const long long j = cell3(I, xu, yp, z);
+        n.ap = I.a[j];
+        n.xp = I.chi[j];
+        n.pp = I.psi[j];
+        n.cp = I.C[j];
+    }
+}
+
 template <typename R, int BS, int ZC>
 __global__ void __launch_bounds__(BS)
     k_sor_cm3(Inst<R> I, int colour, cudaGraphConditionalHandle loop, int max_rounds,
@@ -750,9 +780,22 @@ __global__ void __launch_bounds__(BS)
         load_pair3(I, x0, act, y, zs - 1, Pm);
         load_pair3(I, x0, act, y, zs, P0);
         load_pair3(I, x0, act, y, zs + 1, Pp);
+        // the loads of a plane's own cell and y-neighbours go out one plane
+        // ahead of its update (cells of the other colour and right-hand
+        // sides: nothing this half-sweep writes)
+        Nb3<R> nb;
+        {
+            const int xu = x0 + ((colour + y + zs) & 1);
+            load_nb3(I, act && xu < I.nx, xu, y, ym, yp, rym, ryp, zs, nb);
+        }
         for (int z = zs; z < ze; z++) {
             if (z + 2 <= ze) load_pair3(I, x0, act, y, z + 2, Pn);
             const int k = (colour + y + z) & 1;
+            const Nb3<R> cur = nb;
+            if (z + 1 < ze) {
+                const int xn = x0 + 1 - k;
+                load_nb3(I, act && xn < I.nx, xn, y, ym, yp, rym, ryp, z + 1, nb);
+            }
             // the adjacent lane's cell next to the pair on plane z
             const R op_ = k ? __shfl_down_sync(0xffffffffu, P0.p0, 1)
                             : __shfl_up_sync(0xffffffffu, P0.p1, 1);
@@ -768,7 +811,7 @@ __global__ void __launch_bounds__(BS)
                 const R au = k ? P0.a1 : P0.a0, xu_ = k ? P0.x1 : P0.x0;
                 const R p0 = k ? P0.p1 : P0.p0, c0 = k ? P0.c1 : P0.c0;
                 const R wp = au + I.eps_w, wc = xu_ + I.eps_w;
-                R dp = wp, dc = wc, op = I.rpsi[c], oc = I.rC[c];
+                R dp = wp, dc = wc, op = cur.rp, oc = cur.rc;
                 auto face = [&](R an, R xn, R pn, R cn) {
                     const R fp = hp * (R(0.5) * (wp + (an + I.eps_w)));
                     const R fc = hc * (R(0.5) * (wc + (xn + I.eps_w)));
@@ -795,14 +838,8 @@ __global__ void __launch_bounds__(BS)
                     if (!orefl) face(na, nx_, np, nc);
                     if (!rpart) face(P0.a1, P0.x1, P0.p1, P0.c1);
                 }
-                if (!rym) {
-                    const long long j = cell3(I, xu, ym, z);
-                    face(I.a[j], I.chi[j], I.psi[j], I.C[j]);
-                }
-                if (!ryp) {
-                    const long long j = cell3(I, xu, yp, z);
-                    face(I.a[j], I.chi[j], I.psi[j], I.C[j]);
-                }
+                if (!rym) face(cur.am, cur.xm, cur.pm, cur.cm);
+                if (!ryp) face(cur.ap, cur.xp, cur.pp, cur.cp);
                 if (!Pm.wall)
                     face(k ? Pm.a1 : Pm.a0, k ? Pm.x1 : Pm.x0, k ? Pm.p1 : Pm.p0,
                          k ? Pm.c1 : Pm.c0);
