@@ -1257,18 +1257,26 @@ __device__ __forceinline__ void surf2_block(const Inst<R> &I, int mode, int nblo
     const bool alt = I.sor_pingpong && mode == 1 && (rounds & 1);
     const R *P = alt ? I.psi2 : I.psi;
     const R *Cc = alt ? I.C2 : I.C;
-    R sum = R(0), comp = R(0);
-    if (x < I.nx)
-        for (int k = 0; k < SURF_STRIP; k++) {
-            int y = y0 + k;
-            if (y >= rows) break;
-            long long c = (long long)y * I.pitch + x;
-            R v = (I.a[c] + I.eps_w) * P[c] + (I.chi[c] + I.eps_w) * Cc[c];
-            R yv = v - comp;
-            R t = sum + yv;
-            comp = (t - sum) - yv;
-            sum = t;
+    // the strip's loads first (all in flight together), then the sum in order
+    R val[SURF_STRIP];
+#pragma unroll
+    for (int k = 0; k < SURF_STRIP; k++) {
+        const int y = y0 + k;
+        val[k] = R(0);
+        if (x < I.nx && y < rows) {
+            const long long c = (long long)y * I.pitch + x;
+            val[k] = (I.a[c] + I.eps_w) * P[c] + (I.chi[c] + I.eps_w) * Cc[c];
         }
+    }
+    R sum = R(0), comp = R(0);
+#pragma unroll
+    for (int k = 0; k < SURF_STRIP; k++) {
+        if (x >= I.nx || y0 + k >= rows) break;
+        const R yv = val[k] - comp;
+        const R t = sum + yv;
+        comp = (t - sum) - yv;
+        sum = t;
+    }
     double v[1] = {double(sum) - double(comp)};
     int b = bx + by * gdx;
     block_sum<BS, 1>(v, I.part + b);
