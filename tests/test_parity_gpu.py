@@ -134,14 +134,25 @@ def test_edge_cases_small_and_ragged():
         assert max(err.values()) < 1e-9, (cfg["nx"], cfg["ny"], err)
 
 
-def test_full_size_bubble_rise_sampled():
+@pytest.mark.parametrize("variant", [0, 5])
+def test_full_size_bubble_rise_sampled(variant):
     """The 256 x 1024 walled bubble rise (D = 64, density ratio 10, Eo = 10,
     Bi = 1) in the launch configuration the benchmark times (FP32 storage,
-    one CUDA graph per step), against the oracle after a few steps."""
+    one CUDA graph per step, SOR variant 5 = the tile its tuner picks; 0 =
+    the default), against the oracle after a few steps: every cell."""
+    from paper_2311_15242_gb300 import Solver
     cfg = W.bubble_rise_2d()
-    o, s = run_both(cfg, 10, "f32", noise=0.0)
+    f = W.initial_fields(cfg, seed=7)
+    o = Oracle(cfg)
+    o.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    s = Solver(cfg, storage="f32")
+    s.set_sor_tile(variant)
+    s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    o.step(10)
+    s.step(10)
     err = errors(o.fields(), s.fields())
     assert within(err, F32_TOL), err
+    s.close()
 
 
 @pytest.mark.parametrize("make", [droplet, bubble], ids=["droplet", "bubble"])
