@@ -396,6 +396,26 @@ struct Solver : Base {
             L3::force(I, grid, block, s);
     }
 
+    // a kernel that directly follows another kernel of the step (no event or
+    // conditional node between them) launches as its programmatic dependent:
+    // it starts while that kernel's last blocks run and waits (pdl_wait) for
+    // its completion before touching any field.  With profiling events
+    // between the groups, an ordinary launch.
+    template <typename... K, typename... A>
+    void launch_dep(void (*k)(K...), dim3 g, dim3 b, cudaStream_t s, A... args) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = g;
+        cfg.blockDim = b;
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = prof ? 0 : 1;
+        cudaLaunchKernelEx(&cfg, k, args...);
+    }
+
     int enqueue_step(cudaStream_t s) {
         for (bool &r : ran) r = false;
         mark(s, LBS_K_FORCE);
@@ -410,19 +430,19 @@ struct Solver : Base {
         }
         mark(s, LBS_K_COLLIDE);
         if (D == 2)
-            k_fdcollide2<R, P><<<grid, block, 0, s>>>(I);
+            launch_dep(k_fdcollide2<R, P>, grid, block, s, I);
         else
             L3::collide(I, grid, block, s);
         ran[LBS_K_COLLIDE] = true;
         mark(s, LBS_K_STREAM);
         if (D == 2)
-            k_stream2<R, P><<<grid, block, 0, s>>>(I);
+            launch_dep(k_stream2<R, P>, grid, block, s, I);
         else
             L3::stream(I, grid, block, s);
         ran[LBS_K_STREAM] = true;
         mark(s, LBS_K_GRAD);
         if (D == 2)
-            k_grad2<R><<<grid, block, 0, s>>>(I);
+            launch_dep(k_grad2<R>, grid, block, s, I, 1);
         else
             L3::grad(I, grid, block, s);
         ran[LBS_K_GRAD] = true;
@@ -500,7 +520,10 @@ struct Solver : Base {
         mark(s, LBS_K_SURF);
         if (I.transport) {
             k_surf2<R, BS><<<surf_grid, block, 0, s>>>(I, 1, surf_blocks, sweeps_per_round());
-            k_scale2<R><<<grid, block, 0, s>>>(I);
+            if (D == 2)
+                launch_dep(k_scale2<R>, grid, block, s, I);
+            else
+                k_scale2<R><<<grid, block, 0, s>>>(I);
         } else {
             k_tick<R><<<1, 32, 0, s>>>(I);
         }

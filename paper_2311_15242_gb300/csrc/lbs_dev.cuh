@@ -265,6 +265,15 @@ __device__ __forceinline__ long long nbx3(const Inst<R> &I, const Ax &X, const A
     return ((long long)Z.v[dz + 2] * I.ny + Y.v[dy + 2]) * I.pitch + X.v[dx + 2];
 }
 
+// programmatic dependent launch.  A kernel launched as the programmatic
+// dependent of the kernel before it in the stream waits in pdl_wait until
+// that kernel has finished and its writes are visible; for an ordinary launch
+// pdl_wait returns at once.  pdl_trigger lets the dependent grid launch (its
+// blocks then wait in pdl_wait) once every block of this grid has run it, so
+// its launch overlaps this grid's tail.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 // two consecutive elements (one aligned vector load or store)
 template <typename R>
 struct Vec2;

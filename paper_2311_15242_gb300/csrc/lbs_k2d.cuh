@@ -257,6 +257,7 @@ __device__ __forceinline__ void grad2_cell(const Inst<R> &I, int x, int y, bool 
 // guess: also form the SOR initial guess (every step; not at initialisation)
 template <typename R>
 __global__ void k_grad2(Inst<R> I, int guess = 1) {
+    pdl_wait();
     grad2_cell(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
                guess != 0);
 }
@@ -318,6 +319,7 @@ __device__ __forceinline__ void force2_cell(const Inst<R> &I, int x, int y) {
 
 template <typename R>
 __global__ void k_force2(Inst<R> I) {
+    pdl_trigger();
     force2_cell(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
 
@@ -566,6 +568,8 @@ __device__ __forceinline__ void collide2_cell(const Inst<R> &I, int x, int y) {
 // write disjoint fields
 template <typename R, typename P>
 __global__ void k_fdcollide2(Inst<R> I) {
+    pdl_wait();
+    pdl_trigger();
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (I.transport) fd2_cell(I, x, y, nullptr, nullptr);
     collide2_cell<R, P>(I, x, y);
@@ -732,6 +736,8 @@ __device__ __forceinline__ void stream2_cell(const Inst<R> &I, int x, int y) {
 
 template <typename R, typename P>
 __global__ void k_stream2(Inst<R> I) {
+    pdl_wait();
+    pdl_trigger();
     stream2_cell<R, P>(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
 
@@ -1314,6 +1320,7 @@ __device__ __forceinline__ void surf2_block(const Inst<R> &I, int mode, int nblo
 
 template <typename R, int BS>
 __global__ void k_surf2(Inst<R> I, int mode, int nblocks, int sweeps_per_round) {
+    pdl_trigger();
     surf2_block<R, BS>(I, mode, nblocks, sweeps_per_round, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
@@ -1336,6 +1343,7 @@ __device__ __forceinline__ void scale2_cell(const Inst<R> &I, int x, int y, int 
 
 template <typename R>
 __global__ void k_scale2(Inst<R> I) {
+    pdl_wait();
     scale2_cell(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y, (int)blockIdx.z);
 }
 
