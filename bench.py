@@ -205,6 +205,42 @@ def workload3d():
     return cfg, "shear_droplet_3d_256x128x128_Ca0.2"
 
 
+# compulsory state of a coupled step, bytes per cell-update: the two
+# population sets read and written once, and psi, C, S, B (FP32) read and
+# written once; the whole step's HBM roofline is peak / B_STEP MLUPS
+B_STEP = {("d2q9", "f32"): 2 * 18 * 4 + 2 * 4 * 4, ("d2q9", "f16"): 2 * 18 * 2 + 32,
+          ("d2q9", "bf16"): 2 * 18 * 2 + 32, ("d3q19", "f32"): 2 * 38 * 4 + 32,
+          ("d3q19", "f16"): 2 * 38 * 2 + 32, ("d3q19", "bf16"): 2 * 38 * 2 + 32}
+
+
+def step_roofline(mlups, lattice, storage, hbm, where):
+    """MLUPS x B_STEP against the measured HBM bandwidth ("where" says
+    whether the state lives in HBM or fits in the L2)."""
+    b = B_STEP[(lattice, storage)]
+    gbs = mlups * 1e6 * b / 1e9
+    return {"b_alg_per_cell": b, "achieved_gbs": gbs, "frac": gbs / hbm, "state": where}
+
+
+def roofline2(kmean, cells, storage, rounds, hbm, src, traffic=None):
+    """Roofline of the dominant kernel group of a 2D step (FP32 bytes of
+    ALG_BYTES_F32; one SOR launch is one round)."""
+    groups = [g for g in kmean if g in ALG_BYTES_F32 or g == "sor"]
+    dom = max(groups, key=lambda g: kmean[g])
+    scale = 2 if storage == "f64" else 1  # (16-bit forms: fields stay FP32)
+    if dom == "sor":
+        alg = SOR_BYTES_PER_ROUND_F32 * scale * cells
+        launch_ms = kmean[dom] / rounds
+    else:
+        alg = ALG_BYTES_F32[dom] * scale * cells
+        launch_ms = kmean[dom]
+    achieved = alg / (launch_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+            "launch_timing": "in-graph CUDA events on the solver's stream over the "
+                             "profiled pass of the same steps after the timed region",
+            "peak_source": src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+            "alg_bytes_per_launch": alg, "avg_launch_ms": launch_ms}
+
+
 def roofline3(kmean, cells, storage, rounds, hbm, src):
     """Roofline of the dominant kernel group of the 3D step (bytes as above;
     the SOR group's launch is one half-sweep, two per round)."""
@@ -399,6 +435,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip timing the other population storage forms")
+    ap.add_argument("--no-big2d", action="store_true",
+                    help="skip the 4096 x 4096 bubble-array measurement")
     ap.add_argument("--no-3d", action="store_true",
                     help="skip the D3Q19 (3D sheared droplet) measurement")
     ap.add_argument("--sor-tile", type=int, default=None,
@@ -509,25 +547,14 @@ def main():
     kmean = {g: float(np.mean([k[g] for k in ktimes])) for g in groups}
     dg = s.diagnostics()
     sweeps, rounds = dg["sor_iters_psi"], max(dg["sor_rounds"], 1)
-    dom = max((g for g in groups if g in ALG_BYTES_F32 or g == "sor"), key=lambda g: kmean[g])
-    scale = 2 if args.storage == "f64" else 1  # (16-bit forms: fields stay FP32)
-    if dom == "sor":  # one launch = one round
-        alg = SOR_BYTES_PER_ROUND_F32 * scale * cells
-        launch_ms = kmean[dom] / rounds
-    else:
-        alg = ALG_BYTES_F32[dom] * scale * cells
-        launch_ms = kmean[dom]
     hbm, src = peaks()
-    achieved = alg / (launch_ms / 1e3) / 1e9
     sha = src_hash()
-    traffic = (TRAFFIC["bytes_per_launch"]
-               if (TRAFFIC["src_sha"] == sha and dom == TRAFFIC["kernel"]
-                   and tuned["sor"] == TRAFFIC["sor_tile"]) else None)
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-            "launch_timing": "in-graph CUDA events on the solver's stream over the "
-                             "profiled pass of the same steps after the timed region",
-            "peak_source": src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-            "alg_bytes_per_launch": alg, "avg_launch_ms": launch_ms}
+    roof = roofline2(kmean, cells, args.storage, rounds, hbm, src)
+    if (TRAFFIC["src_sha"] == sha and roof["kernel"] == TRAFFIC["kernel"]
+            and tuned["sor"] == TRAFFIC["sor_tile"]):
+        roof["traffic"] = TRAFFIC["bytes_per_launch"]
+    steproof = {"2d_" + args.storage: step_roofline(value / world, "d2q9", args.storage, hbm,
+                                                   "L2 (46 MB of state)")}
 
     # end to end through the C ABI with host buffers
     pin = {k: torch.from_numpy(np.ascontiguousarray(f[k])).pin_memory().numpy()
@@ -558,6 +585,7 @@ def main():
             s2.init_fields(f["phi"], f["psi"], f["C"], f["u"])
             tt, _ = time_steps(s2, stream, flush, args.warmup, args.steps, torch, profiled=False)
             forms[st] = cells * args.steps / (tt / 1e3) / 1e6
+            steproof["2d_" + st] = step_roofline(forms[st], "d2q9", st, hbm, "L2 (46 MB of state)")
             s2.close()
 
     # the batched sweep (64 2D instances) against the same instances run one
@@ -565,6 +593,10 @@ def main():
     batched = None
     if rank == 0 and not args.no_batch:
         batched = bench_batch(args, stream, flush, torch)
+        for st in ("f32", "f16"):
+            if batched.get("mlups_" + st):
+                steproof["batched_" + st] = step_roofline(batched["mlups_" + st], "d2q9", st,
+                                                          hbm, "HBM (8.0 M cells)")
 
     # the D3Q19 configuration (3D sheared droplet), each storage form
     d3 = None
@@ -595,7 +627,38 @@ def main():
                 d3["sor_sweeps"] = dg3["sor_iters_psi"]
                 d3["roofline"] = roofline3(km, cells3, st, r3, hbm, src)
                 d3["gpu_launches_per_step"] = s3.kernel_count()
+            steproof["3d_" + st] = step_roofline(d3["mlups"][st], "d3q19", st, hbm,
+                                                 "HBM (1.1 GB of state)")
             s3.close()
+
+    # one 2D instance far beyond the L2: the bubble rise's physics on a
+    # 4096 x 4096 grid with a 16 x 16 array of bubbles (16.8 M cells)
+    big = None
+    if rank == 0 and not args.no_big2d:
+        cfgb = W.bubble_array_2d()
+        cellsb = cfgb["nx"] * cfgb["ny"]
+        fb = W.initial_fields(cfgb)
+        big = {"workload": "bubble_array_2d D2Q9 4096x4096 walls-x periodic-y, 16x16 bubbles "
+                           "D=64 (the bubble rise's physics)", "cells": cellsb, "mlups": {},
+               "ms_per_step": {}, "steps": args.steps3, "warmup": args.warmup}
+        for st in ("f32", "f16"):
+            sb = Solver(cfgb, storage=st, stream=stream)
+            sb.init_fields(fb["phi"], fb["psi"], fb["C"], fb["u"])
+            tb = autotune.tune_single(sb, cfgb["nx"], use_cache=False)
+            big.setdefault("sor_variant", {})[st] = tb["sor"]
+            sb.init_fields(fb["phi"], fb["psi"], fb["C"], fb["u"])
+            tt, km = time_steps(sb, stream, flush, args.warmup, args.steps3, torch)
+            big["mlups"][st] = cellsb * args.steps3 / (tt / 1e3) / 1e6
+            big["ms_per_step"][st] = tt / args.steps3
+            if st == "f32":
+                dgb = sb.diagnostics()
+                big["kernel_ms"] = km
+                big["sor_sweeps"] = dgb["sor_iters_psi"]
+                big["roofline"] = roofline2(km, cellsb, st, max(dgb["sor_rounds"], 1), hbm, src)
+            steproof["big2d_" + st] = step_roofline(big["mlups"][st], "d2q9", st, hbm,
+                                                    "HBM (3 GB of state)")
+            sb.close()
+        del fb
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
@@ -609,7 +672,8 @@ def main():
            "roofline": roof, "kernel_ms": kmean, "sor_sweeps": sweeps, "sor_rounds": rounds,
            "sor_tune_ms": tuned.get("timings"),
            "gpu_launches": args.steps * s.kernel_count(),
-           "forms_mlups": forms, "d3q19": d3, "batched": batched,
+           "forms_mlups": forms, "d3q19": d3, "batched": batched, "big2d": big,
+           "step_roofline": steproof,
            "clocks": clk, "e2e": e2e, "impl": "lbs", "src_sha": sha}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, name)

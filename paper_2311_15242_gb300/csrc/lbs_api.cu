@@ -106,6 +106,7 @@ struct Layout {
 // the 4 rest-population planes of fT, fM, gT, gM and the previous time
 // level of psi and C
 constexpr int kScal2 = 21, kScal3 = 25, kRest = 6;
+constexpr int kCoef2 = 6;  // 2D SOR coefficient planes (faces and inverse diagonals)
 
 template <typename R, typename P>
 Layout layout_of(const lbs_params *p) {
@@ -117,7 +118,7 @@ Layout layout_of(const lbs_params *p) {
     L.pops_off = 0;
     size_t pops = 4 * (size_t)(d3 ? Q19 : Q9) * (size_t)L.plane * sizeof(P);
     L.scal_off = pops;
-    size_t scal = ((d3 ? kScal3 : kScal2) + kRest) * pb;
+    size_t scal = ((d3 ? kScal3 : kScal2) + kRest + (d3 ? 0 : kCoef2)) * pb;
     L.flag_off = align_up(L.scal_off + scal, 256);
     L.ctl_off = align_up(L.flag_off + 2 * (size_t)L.plane, 256);
     L.part_off = align_up(L.ctl_off + sizeof(Ctl), 256);
@@ -268,6 +269,10 @@ struct Solver : Base {
             R **fr[] = {&I.fT0, &I.fM0, &I.gT0, &I.gM0, &I.psip, &I.Cp};
             const int base = D == 3 ? kScal3 : kScal2;
             for (int k = 0; k < kRest; k++) *fr[k] = sc + (base + k) * pb;
+        }
+        if (D == 2) {
+            R **fc[] = {&I.sfx, &I.sfy, &I.scx, &I.scy, &I.sip, &I.sic};
+            for (int k = 0; k < kCoef2; k++) *fc[k] = sc + (kScal2 + kRest + k) * pb;
         }
         I.ctl = (Ctl *)(ws + L.ctl_off);
         I.part = (double *)(ws + L.part_off);

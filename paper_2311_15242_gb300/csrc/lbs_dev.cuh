@@ -133,6 +133,10 @@ struct Inst {
     R *psi, *C, *S, *B, *rpsi, *rC;
     R *psi2, *C2;             // second buffers of the blocked SOR rounds
     R *psip, *Cp;             // psi, C of the previous time level (SOR initial guess)
+    // 2D: the coefficients of the step's CN systems, written by the first SOR
+    // round and read by the later ones: faces towards +x and +y of the psi
+    // and C systems and their inverse diagonals (null in 3D)
+    R *sfx, *sfy, *scx, *scy, *sip, *sic;
     Ctl *ctl;
     double *part;             // per-block partial sums of reductions
 };

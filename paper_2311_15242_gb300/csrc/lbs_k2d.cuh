@@ -870,87 +870,120 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
     const R *cin = (round & 1) ? I.C2 : I.C;
     R *pout = (round & 1) ? I.psi : I.psi2;
     R *cout = (round & 1) ? I.C : I.C2;
-    // 1. load in row order (coalesced); ip / ic hold the weights a + eps,
-    //    chi + eps for now, zero outside the domain.  A thread loads U cells
-    //    into registers before it stores any, so that their loads are in
-    //    flight together (a store to shared memory would otherwise order the
-    //    next cell's loads behind it).
-    constexpr int U = 3;
-    for (int q0 = tid; q0 < RX * RY; q0 += U * BS) {
-        R vv[U][6];
-        int ss[U];
-        bool in[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int q = q0 + u * BS;
-            in[u] = false;
-            ss[u] = -1;
-            if (q >= RX * RY) continue;
+    // The coefficients (faces, inverse diagonals) depend only on a and chi,
+    // fixed during the solve: round 0 builds them from a and chi (steps 1-3)
+    // and stores those of its tile interior; later rounds load them (step 1').
+    const bool first = round == 0 || I.sfx == nullptr;
+    if (!first) {
+        // 1'. load psi, C, the right-hand sides and the coefficients, in row
+        //     order; zero outside the domain
+        for (int q = tid; q < RX * RY; q += BS) {
             const int rx = q % RX, ry = q / RX;
             int refl = 0, sx, sy;
             const int X = map_axis(x0 + rx, I.nx, I.wall[0], 1, refl, sx);
             const int Y = map_axis(y0 + ry, I.ny, I.wall[1], 2, refl, sy);
-            ss[u] = ((rx + ry) & 1) * NHP + ry * RXH + (rx >> 1);
-            in[u] = !refl;
+            const int s = ((rx + ry) & 1) * NHP + ry * RXH + (rx >> 1);
             if (!refl) {
                 const long long c = (long long)Y * I.pitch + X;
-                vv[u][0] = pin[c];
-                vv[u][1] = cin[c];
-                vv[u][2] = I.rpsi[c];
-                vv[u][3] = I.rC[c];
-                vv[u][4] = I.a[c];
-                vv[u][5] = I.chi[c];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int s = ss[u];
-            if (s < 0) continue;
-            if (in[u]) {
-                sp[s] = vv[u][0];
-                sc[s] = vv[u][1];
-                bp[s] = vv[u][2];
-                bc[s] = vv[u][3];
-                ip[s] = vv[u][4] + I.eps_w;
-                ic[s] = vv[u][5] + I.eps_w;
+                sp[s] = pin[c];
+                sc[s] = cin[c];
+                bp[s] = I.rpsi[c];
+                bc[s] = I.rC[c];
+                fpx[s] = I.sfx[c];
+                fpy[s] = I.sfy[c];
+                fcx[s] = I.scx[c];
+                fcy[s] = I.scy[c];
+                ip[s] = I.sip[c];
+                ic[s] = I.sic[c];
             } else {
-                sp[s] = sc[s] = bp[s] = bc[s] = ip[s] = ic[s] = R(0);
+                sp[s] = sc[s] = bp[s] = bc[s] = fpx[s] = fpy[s] = fcx[s] = fcy[s] = ip[s] =
+                    ic[s] = R(0);
             }
-            fl[s] = in[u];
         }
+        __syncthreads();
+    } else {
+        // 1. load in row order (coalesced); ip / ic hold the weights a + eps,
+        //    chi + eps for now, zero outside the domain.  A thread loads U cells
+        //    into registers before it stores any, so that their loads are in
+        //    flight together (a store to shared memory would otherwise order the
+        //    next cell's loads behind it).
+        constexpr int U = 3;
+        for (int q0 = tid; q0 < RX * RY; q0 += U * BS) {
+            R vv[U][6];
+            int ss[U];
+            bool in[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int q = q0 + u * BS;
+                in[u] = false;
+                ss[u] = -1;
+                if (q >= RX * RY) continue;
+                const int rx = q % RX, ry = q / RX;
+                int refl = 0, sx, sy;
+                const int X = map_axis(x0 + rx, I.nx, I.wall[0], 1, refl, sx);
+                const int Y = map_axis(y0 + ry, I.ny, I.wall[1], 2, refl, sy);
+                ss[u] = ((rx + ry) & 1) * NHP + ry * RXH + (rx >> 1);
+                in[u] = !refl;
+                if (!refl) {
+                    const long long c = (long long)Y * I.pitch + X;
+                    vv[u][0] = pin[c];
+                    vv[u][1] = cin[c];
+                    vv[u][2] = I.rpsi[c];
+                    vv[u][3] = I.rC[c];
+                    vv[u][4] = I.a[c];
+                    vv[u][5] = I.chi[c];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int s = ss[u];
+                if (s < 0) continue;
+                if (in[u]) {
+                    sp[s] = vv[u][0];
+                    sc[s] = vv[u][1];
+                    bp[s] = vv[u][2];
+                    bc[s] = vv[u][3];
+                    ip[s] = vv[u][4] + I.eps_w;
+                    ic[s] = vv[u][5] + I.eps_w;
+                } else {
+                    sp[s] = sc[s] = bp[s] = bc[s] = ip[s] = ic[s] = R(0);
+                }
+                fl[s] = in[u];
+            }
+        }
+        __syncthreads();
+        // 2. face coefficients h (w_c + w_nb)/2 of Eq. 28 towards +x and +y; zero
+        //    across a wall or the region edge
+        const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
+        for (int q = tid; q < 2 * NH; q += BS) {
+            const int c = q >= NH, r = q - c * NH, ry = r / RXH, j = r - ry * RXH;
+            const int rx = 2 * j + ((c ^ ry) & 1);
+            const int s = c * NHP + r, o = (1 - c) * NHP + ry * RXH;
+            const bool in = fl[s];
+            const bool ex = in && rx < RX - 1 && fl[o + ((rx + 1) >> 1)];
+            const bool ny = in && ry < RY - 1 && fl[o + RXH + j];
+            const int e = o + ((rx + 1) >> 1), n = o + RXH + j;
+            fpx[s] = ex ? hp * R(0.5) * (ip[s] + ip[e]) : R(0);
+            fcx[s] = ex ? hc * R(0.5) * (ic[s] + ic[e]) : R(0);
+            fpy[s] = ny ? hp * R(0.5) * (ip[s] + ip[n]) : R(0);
+            fcy[s] = ny ? hc * R(0.5) * (ic[s] + ic[n]) : R(0);
+        }
+        __syncthreads();
+        // 3. inverse diagonals w + sum of the four faces (zero outside the domain,
+        //    where the weights are zero: those cells stay zero in every sweep)
+        for (int q = tid; q < 2 * NH; q += BS) {
+            const int c = q >= NH, r = q - c * NH, ry = r / RXH, j = r - ry * RXH;
+            const int rx = 2 * j + ((c ^ ry) & 1);
+            const int s = c * NHP + r, o = (1 - c) * NHP + ry * RXH;
+            if (!fl[s]) continue;
+            const int w = o + ((rx - 1) >> 1), so = o - RXH + j;
+            const R sp_ = fpx[s] + fpy[s] + (rx > 0 ? fpx[w] : R(0)) + (ry > 0 ? fpy[so] : R(0));
+            const R sc_ = fcx[s] + fcy[s] + (rx > 0 ? fcx[w] : R(0)) + (ry > 0 ? fcy[so] : R(0));
+            ip[s] = fdiv(R(1), ip[s] + sp_);
+            ic[s] = fdiv(R(1), ic[s] + sc_);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    // 2. face coefficients h (w_c + w_nb)/2 of Eq. 28 towards +x and +y; zero
-    //    across a wall or the region edge
-    const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
-    for (int q = tid; q < 2 * NH; q += BS) {
-        const int c = q >= NH, r = q - c * NH, ry = r / RXH, j = r - ry * RXH;
-        const int rx = 2 * j + ((c ^ ry) & 1);
-        const int s = c * NHP + r, o = (1 - c) * NHP + ry * RXH;
-        const bool in = fl[s];
-        const bool ex = in && rx < RX - 1 && fl[o + ((rx + 1) >> 1)];
-        const bool ny = in && ry < RY - 1 && fl[o + RXH + j];
-        const int e = o + ((rx + 1) >> 1), n = o + RXH + j;
-        fpx[s] = ex ? hp * R(0.5) * (ip[s] + ip[e]) : R(0);
-        fcx[s] = ex ? hc * R(0.5) * (ic[s] + ic[e]) : R(0);
-        fpy[s] = ny ? hp * R(0.5) * (ip[s] + ip[n]) : R(0);
-        fcy[s] = ny ? hc * R(0.5) * (ic[s] + ic[n]) : R(0);
-    }
-    __syncthreads();
-    // 3. inverse diagonals w + sum of the four faces (zero outside the domain,
-    //    where the weights are zero: those cells stay zero in every sweep)
-    for (int q = tid; q < 2 * NH; q += BS) {
-        const int c = q >= NH, r = q - c * NH, ry = r / RXH, j = r - ry * RXH;
-        const int rx = 2 * j + ((c ^ ry) & 1);
-        const int s = c * NHP + r, o = (1 - c) * NHP + ry * RXH;
-        if (!fl[s]) continue;
-        const int w = o + ((rx - 1) >> 1), so = o - RXH + j;
-        const R sp_ = fpx[s] + fpy[s] + (rx > 0 ? fpx[w] : R(0)) + (ry > 0 ? fpy[so] : R(0));
-        const R sc_ = fcx[s] + fcy[s] + (rx > 0 ? fcx[w] : R(0)) + (ry > 0 ? fcy[so] : R(0));
-        ip[s] = fdiv(R(1), ip[s] + sp_);
-        ic[s] = fdiv(R(1), ic[s] + sc_);
-    }
-    __syncthreads();
     // 2K half-sweeps in place; half-sweep t updates colour t & 1 over the
     // rectangle of margin m = 2K - 1 - t around the tile
     R v[4] = {R(0), R(0), R(0), R(0)};  // maxima of the last sweep (never FP64 per cell)
@@ -997,6 +1030,14 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
         const long long c = (long long)gy * I.pitch + gx;
         pout[c] = sp[s];
         cout[c] = sc[s];
+        if (first && I.sfx) {
+            I.sfx[c] = fpx[s];
+            I.sfy[c] = fpy[s];
+            I.scx[c] = fcx[s];
+            I.scy[c] = fcy[s];
+            I.sip[c] = ip[s];
+            I.sic[c] = ic[s];
+        }
     }
     sor_fold_maxima<R, BS>(I, round, v);
 }
