@@ -379,6 +379,7 @@ struct ora_ctx {
     int D, Q;
     long N;
     int e[QMAX][3], opp[QMAX];
+    int mir[8][QMAX];              /* direction mirrored on the axes of a bit mask */
     double w[QMAX];
     double *fR, *fB, *fR2, *fB2;   /* [Q][N] */
     double *psi, *C, *Sp, *Bp;     /* [N] */
@@ -431,12 +432,18 @@ static long nb(const ora_ctx *o, int x, int y, int z, const int *d, int *refl,
 
 /* velocity seen at a ghost node (reading R21): for each wall crossed,
    u -> 2 u_wall - u, i.e. linear in the normal direction with the wall
-   velocity half-way (no-slip, half-way bounce-back) */
+   velocity half-way (no-slip, half-way bounce-back); for each mirror plane
+   crossed, the mirror image: the normal component changes sign, the
+   tangential ones are kept (free slip) */
 static void ghost_u(const ora_ctx *o, const double *u, long j, int refl,
                     const int *side, double *out) {
     for (int b = 0; b < 3; b++) out[b] = u[b * o->N + j];
     for (int a = 0; a < 3; a++) {
         if (!(refl & (1 << a))) continue;
+        if (o->p.wall[a] == 2) {
+            out[a] = -out[a];
+            continue;
+        }
         const double *uw = side[a] < 0 ? o->p.uw_lo[a] : o->p.uw_hi[a];
         for (int b = 0; b < 3; b++) out[b] = 2.0 * uw[b] - out[b];
     }
@@ -709,6 +716,14 @@ ora_ctx *ora_create(const ora_params *p) {
             if (o->e[k][0] == -o->e[i][0] && o->e[k][1] == -o->e[i][1] &&
                 o->e[k][2] == -o->e[i][2])
                 o->opp[i] = k;
+    for (int m = 0; m < 8; m++)
+        for (int i = 0; i < o->Q; i++)
+            for (int k = 0; k < o->Q; k++) {
+                int same = 1;
+                for (int a = 0; a < 3; a++)
+                    same &= o->e[k][a] == ((m >> a) & 1 ? -o->e[i][a] : o->e[i][a]);
+                if (same) o->mir[m][i] = k;
+            }
     long N = o->N, QN = (long)o->Q * N;
     o->fR = calloc(QN, sizeof(double));
     o->fB = calloc(QN, sizeof(double));
@@ -879,22 +894,28 @@ static int one_step(ora_ctx *o) {
 
     /* 4. streaming, Eq. 13, written as a pull: f_i(x, t+1) = f_i^{++}(x - e_i).
           A link that crosses a wall is reflected (half-way bounce-back); a
-          moving wall adds 2 w_i rho^k (e_i . u_w)/cs2 (reading R22). */
+          moving wall adds 2 w_i rho^k (e_i . u_w)/cs2 (reading R22).  A link
+          that crosses only mirror planes brings the mirror image of its
+          source: the population of the mirrored direction at the mirrored
+          cell (specular reflection). */
+    int bbmask = 0;
+    for (int a = 0; a < 3; a++) bbmask |= (p->wall[a] == 1) << a;
     FOR_CELLS(o) {
         long c = idx(o, x, y, z);
         for (int i = 0; i < Q; i++) {
             int back[3] = {-o->e[i][0], -o->e[i][1], -o->e[i][2]};
             int refl, side[3];
             long j = nb(o, x, y, z, back, &refl, side);
-            if (!refl) {
-                o->fR[i * N + c] = o->fR2[i * N + j];
-                o->fB[i * N + c] = o->fB2[i * N + j];
+            if (!(refl & bbmask)) {
+                int is = o->mir[refl][i];
+                o->fR[i * N + c] = o->fR2[is * N + j];
+                o->fB[i * N + c] = o->fB2[is * N + j];
                 continue;
             }
             double uw[3] = {0, 0, 0};
             int nw = 0;
             for (int a = 0; a < 3; a++) {
-                if (!(refl & (1 << a))) continue;
+                if (!(refl & bbmask & (1 << a))) continue;
                 const double *v = side[a] < 0 ? p->uw_lo[a] : p->uw_hi[a];
                 for (int b = 0; b < 3; b++) uw[b] += v[b];
                 nw++;

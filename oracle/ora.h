@@ -25,7 +25,9 @@ extern "C" {
 typedef struct {
     int nx, ny, nz;
     /* per axis: 0 = periodic, 1 = half-way bounce-back walls at both ends
-       (Sec. 3.2, 3.3, 3.4: "half-way bounce-back", ref. [57]) */
+       (Sec. 3.2, 3.3, 3.4: "half-way bounce-back", ref. [57]), 2 = mirror
+       (symmetry) planes half-way beyond both ends (Sec. 3.1: "symmetric
+       boundary conditions"; free slip, specular reflection of populations) */
     int wall[3];
     /* velocity vector of the wall at the low / high end of each axis
        (Sec. 3.3: walls moving with opposite velocities) */
