@@ -70,7 +70,10 @@ typedef struct {
                                  3D: every periodic axis of even length (the
                                  red-black SOR updates in place) */
     int wall[3];              /* per axis: 0 periodic, 1 half-way bounce-back
-                                 walls at both ends (Secs. 3.2-3.4, ref. [57]) */
+                                 walls at both ends (Secs. 3.2-3.4, ref. [57]),
+                                 2 mirror (symmetry) planes half-way beyond
+                                 both ends (Sec. 3.1): specular reflection,
+                                 free slip, scalars mirrored, no flux */
     double uw_lo[3][3];       /* velocity of the low wall of each axis (Sec. 3.3) */
     double uw_hi[3][3];       /* velocity of the high wall of each axis */
     double rhoR0, rhoB0;      /* pure-phase densities (Eq. 6) */

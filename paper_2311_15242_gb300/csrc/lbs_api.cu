@@ -157,8 +157,10 @@ struct Solver : Base {
         I.nz = p->nz;
         I.pitch = L.pitch;
         I.plane = L.plane;
+        I.bbmask = 0;
         for (int a = 0; a < 3; a++) {
             I.wall[a] = p->wall[a];
+            I.bbmask |= (p->wall[a] == 1) << a;
             for (int b = 0; b < 3; b++) {
                 I.uw_lo[a][b] = R(p->uw_lo[a][b]);
                 I.uw_hi[a][b] = R(p->uw_hi[a][b]);
@@ -840,9 +842,21 @@ int validate(const lbs_params *p, char *err, size_t n) {
             snprintf(err, n, "3D grids need an even size on periodic axis %d (got %d)", a, dims[a]);
             return LBS_EINVAL;
         }
+        if (p->wall[a] < 0 || p->wall[a] > 2) {
+            snprintf(err, n, "axis %d: 0 periodic, 1 bounce-back walls, 2 mirror planes (got %d)",
+                     a, p->wall[a]);
+            return LBS_EINVAL;
+        }
         if (p->wall[a] && dims[a] < 3) {
             snprintf(err, n, "walled axis %d needs at least 3 nodes", a);
             return LBS_EINVAL;
+        }
+        if (p->wall[a] == 2) {
+            for (int b = 0; b < 3; b++)
+                if (p->uw_lo[a][b] != 0 || p->uw_hi[a][b] != 0) {
+                    snprintf(err, n, "mirror planes do not move (axis %d)", a);
+                    return LBS_EINVAL;
+                }
         }
         if (p->uw_lo[a][a] != 0 || p->uw_hi[a][a] != 0) {
             snprintf(err, n, "walls move tangentially only (axis %d)", a);

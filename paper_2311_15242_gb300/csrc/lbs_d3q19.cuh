@@ -27,6 +27,27 @@ __host__ __device__ constexpr int ez19(int i) {
 }
 // the directions come in opposite pairs (1,2), (3,4), ..., (17,18)
 __host__ __device__ constexpr int opp19(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+// the direction of i mirrored on the axes of bit mask m (bits x, y, z)
+__host__ __device__ constexpr int mir19c(int i, int m) {
+    int r = i;
+    for (int k = 0; k < 19; k++)
+        if (ex19(k) == ((m & 1) ? -ex19(i) : ex19(i)) &&
+            ey19(k) == ((m & 2) ? -ey19(i) : ey19(i)) && ez19(k) == ((m & 4) ? -ez19(i) : ez19(i)))
+            r = k;
+    return r;
+}
+__host__ __device__ __forceinline__ int mir19(int i, int m) {
+    switch (m) {
+    case 0: return i;
+    case 1: return mir19c(i, 1);
+    case 2: return mir19c(i, 2);
+    case 3: return mir19c(i, 3);
+    case 4: return mir19c(i, 4);
+    case 5: return mir19c(i, 5);
+    case 6: return mir19c(i, 6);
+    default: return mir19c(i, 7);
+    }
+}
 template <typename R>
 __host__ __device__ constexpr R w19(int i) {
     return i == 0 ? R(1.0 / 3.0) : (i <= 6 ? R(1.0 / 18.0) : R(1.0 / 36.0));

@@ -27,6 +27,19 @@ __host__ __device__ constexpr int ey9(int i) {
 __host__ __device__ constexpr int opp9(int i) {
     return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
 }
+// the direction of i mirrored on the axes of bit mask m (bit 0 x, bit 1 y):
+// a population crossing mirror planes comes back specularly reflected
+__host__ __device__ constexpr int mir9c(int i, int m) {
+    int r = i;
+    for (int k = 0; k < 9; k++)
+        if (ex9(k) == ((m & 1) ? -ex9(i) : ex9(i)) && ey9(k) == ((m & 2) ? -ey9(i) : ey9(i)))
+            r = k;
+    return r;
+}
+// (with i a compile-time constant every case folds to a constant)
+__host__ __device__ __forceinline__ int mir9(int i, int m) {
+    return m == 0 ? i : m == 1 ? mir9c(i, 1) : m == 2 ? mir9c(i, 2) : mir9c(i, 3);
+}
 template <typename R>
 __host__ __device__ constexpr R w9(int i) {
     return i == 0 ? R(4.0 / 9.0) : (i <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0));
@@ -92,7 +105,8 @@ struct Inst {
     int nx, ny, nz, pitch;   // pitch: elements per row (>= nx); cell (x, y, z) at
                              // (z ny + y) pitch + x
     long long plane;         // elements per scalar plane (pitch * ny * nz)
-    int wall[3];
+    int wall[3];              // per axis: 0 periodic, 1 bounce-back walls, 2 mirror planes
+    int bbmask;               // bit a set where axis a has bounce-back walls
     R uw_lo[3][3], uw_hi[3][3];
     R rhoR0, rhoB0, alphaR, alphaB, cs2R, cs2B, muR0, muB0;
     R inv_rhoR0, inv_rhoB0;  // 1 / rho^k0
@@ -311,6 +325,15 @@ __device__ __forceinline__ long long nb2(const Inst<R> &I, int x, int y, int dx,
 template <typename R>
 __device__ __forceinline__ void ghost_u2(const Inst<R> &I, int refl, int sx, int sy,
                                          R &u0, R &u1) {
+    // a mirror plane reflects the normal component only (free slip)
+    if (refl & ~I.bbmask & 1) {
+        u0 = -u0;
+        refl &= ~1;
+    }
+    if (refl & ~I.bbmask & 2) {
+        u1 = -u1;
+        refl &= ~2;
+    }
     if (refl & 1) {
         const R *w = sx < 0 ? I.uw_lo[0] : I.uw_hi[0];
         u0 = R(2) * w[0] - u0;
@@ -344,6 +367,11 @@ template <typename R>
 __device__ __forceinline__ void ghost_u3(const Inst<R> &I, int refl, int sx, int sy, int sz,
                                          R &u0, R &u1, R &u2) {
     const int side[3] = {sx, sy, sz};
+    // a mirror plane reflects the normal component only (free slip)
+    if (refl & ~I.bbmask & 1) u0 = -u0;
+    if (refl & ~I.bbmask & 2) u1 = -u1;
+    if (refl & ~I.bbmask & 4) u2 = -u2;
+    refl &= I.bbmask;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         if (!(refl & (1 << a))) continue;

@@ -594,7 +594,8 @@ __device__ __forceinline__ void stream2_cell(const Inst<R> &I, int x, int y) {
     // 1. the streamed (total, minority) pairs as stored at their sources
     //    (i = 0 stays in its own cell); slow: bit i set where the source's
     //    flag differs from the cell's or the link crosses a wall (then the
-    //    cell's own opposite population is reflected)
+    //    cell's own opposite population is reflected).  A link crossing only
+    //    mirror planes brings the mirrored population of the mirrored cell.
     R t[Q9], m[Q9];
     unsigned slow = 0, fbits = 0;
     // (branch-free: a reflected link reads the cell's own opposite
@@ -608,13 +609,14 @@ __device__ __forceinline__ void stream2_cell(const Inst<R> &I, int x, int y) {
             m[0] = I.gM0[c];
             continue;
         }
-        const long long src = refl ? c : j;
-        const long long k = (long long)(refl ? opp9(i) : i) * I.plane + src;
+        const int bb = refl & I.bbmask;
+        const long long src = bb ? c : j;
+        const long long k = (long long)(bb ? opp9(i) : mir9(i, refl)) * I.plane + src;
         t[i] = ldp<R, P>(I, I.gT, k);
         m[i] = ldp<R, P>(I, I.gM, k);
         const int fj = I.gflag[src];
         fbits |= (unsigned)fj << i;
-        if (fj != flc || refl) slow |= 1u << i;
+        if (fj != flc || bb) slow |= 1u << i;
     }
     fbits |= (unsigned)flc;  // (i = 0: the cell's own flag)
     // 2. fast path: every population moves unchanged (no rounding anywhere);
@@ -663,6 +665,7 @@ __device__ __forceinline__ void stream2_cell(const Inst<R> &I, int x, int y) {
         if ((slow >> i) & 1) {
             int refl, sx, sy;
             nbx2(I, X, Y, -ex9(i), -ey9(i), refl, sx, sy);
+            refl &= I.bbmask;  // (mirror planes reflect without a wall term)
             if (refl) {
                 R uwx = R(0), uwy = R(0);
                 int nw = 0;

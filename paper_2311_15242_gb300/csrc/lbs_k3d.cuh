@@ -464,13 +464,14 @@ __global__ void __launch_bounds__(256, 3) k_stream3(Inst<R> I) {
             m[0] = I.gM0[c];
             continue;
         }
-        const long long src = refl ? c : j;
-        const long long k = (long long)(refl ? opp19(i) : i) * I.plane + src;
+        const int bb = refl & I.bbmask;  // mirror planes: the mirrored source
+        const long long src = bb ? c : j;
+        const long long k = (long long)(bb ? opp19(i) : mir19(i, refl)) * I.plane + src;
         t[i] = ldp<R, P>(I, I.gT, k);
         m[i] = ldp<R, P>(I, I.gM, k);
         const int fj = I.gflag[src];
         fbits |= (unsigned)fj << i;
-        if (fj != flc || refl) slow |= 1u << i;
+        if (fj != flc || bb) slow |= 1u << i;
     }
     fbits |= (unsigned)flc;  // (i = 0: the cell's own flag)
     // 2. fast path: every population moves unchanged; the cell keeps its
@@ -520,6 +521,7 @@ __global__ void __launch_bounds__(256, 3) k_stream3(Inst<R> I) {
         if ((slow >> i) & 1) {
             int refl, sx, sy, sz;
             nbx3(I, X, Y, Z, -ex19(i), -ey19(i), -ez19(i), refl, sx, sy, sz);
+            refl &= I.bbmask;  // (mirror planes reflect without a wall term)
             if (refl) {
                 R uw[3] = {R(0), R(0), R(0)};
                 int nw = 0;

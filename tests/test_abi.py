@@ -56,6 +56,16 @@ def test_workspace_and_validation_on_host():
     assert L.lbs_create(ctypes.byref(bad), lbs.LBS_F32, None, None, 0, ctypes.byref(h)) == lbs.LBS_EINVAL
     assert b"3 nodes" in L.lbs_last_error(h)
     L.lbs_destroy(h)
+    # mirror planes (2) are accepted; other axis codes and moving mirrors not
+    ok = lbs.LbsParams()
+    L.lbs_params_default(ctypes.byref(ok), 63, 31, 1)
+    ok.wall[0] = ok.wall[1] = 2
+    assert L.lbs_workspace_bytes(ctypes.byref(ok), lbs.LBS_F32) > 0
+    ok.wall[1] = 3
+    assert L.lbs_workspace_bytes(ctypes.byref(ok), lbs.LBS_F32) == 0
+    ok.wall[1] = 2
+    ok.uw_lo[1][0] = 0.01
+    assert L.lbs_workspace_bytes(ctypes.byref(ok), lbs.LBS_F32) == 0
 
 
 def test_3d_validation_on_host():

@@ -155,6 +155,30 @@ def test_full_size_bubble_rise_sampled(variant):
     s.close()
 
 
+def mirror_bubble(nx=18, ny=16):
+    """Light droplet (density ratio 10, no gravity) in a quarter domain with
+    mirror planes on both axes (Sec. 3.1's symmetric boundaries, 2D)."""
+    c = W.bubble_rise_2d(nx=nx, ny=ny, D_b=14.0)
+    c.update(g=[0.0, 0.0, 0.0], center=[-0.5, -0.5, 0.0], sigma0=0.01, psi0=0.5,
+             wall=[2, 2, 0])
+    return c
+
+
+@pytest.mark.parametrize("shape", [(18, 16), (75, 45)], ids=["quarter", "ragged"])
+def test_mirror_planes_match_oracle(shape):
+    """Mirror planes (specular streaming, free-slip ghost velocity) against
+    the oracle in FP64 (rounding order only) and FP32 (the FP32 bounds),
+    after 30 steps with a seeded velocity; the 75 x 45 grid spans several
+    blocks and SOR tiles with odd sizes on both mirrored axes."""
+    cfg = mirror_bubble(*shape)
+    o, s = run_both(cfg, 30, "f64", u0=1e-4)
+    err = errors(o.fields(), s.fields())
+    assert max(err.values()) < 1e-9, err
+    o, s = run_both(cfg, 30, "f32", u0=1e-4)
+    err = errors(o.fields(), s.fields())
+    assert within(err, F32_TOL), err
+
+
 def test_bubble_array_against_oracle():
     """A 2 x 2 array of the bench's bubbles on 512 x 512 (the bubble rise's
     physics; 262,144 cells), FP32 storage and the SOR tile the bench's tuner
