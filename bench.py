@@ -435,6 +435,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip timing the other population storage forms")
+    ap.add_argument("--no-octant", action="store_true",
+                    help="skip the 3D adsorption octant measurement")
     ap.add_argument("--no-big2d", action="store_true",
                     help="skip the 4096 x 4096 bubble-array measurement")
     ap.add_argument("--no-3d", action="store_true",
@@ -631,6 +633,31 @@ def main():
                                                  "HBM (1.1 GB of state)")
             s3.close()
 
+    # Sec. 3.1's adsorption test in 3D: one octant of a droplet between mirror
+    # planes (R = 30, 150^3 cells), FP32 and bfloat16
+    octant = None
+    if rank == 0 and not args.no_octant:
+        cfgo = W.adsorption_octant_3d(R=30)
+        cellso = cfgo["nx"] * cfgo["ny"] * cfgo["nz"]
+        fo = W.initial_fields(cfgo)
+        octant = {"workload": "adsorption_octant_3d D3Q19 150^3, mirror planes on every axis, "
+                              "R=30, C0=5e-4, r_a=0.2 (Sec. 3.1)", "cells": cellso, "mlups": {},
+                  "ms_per_step": {}, "steps": args.steps3, "warmup": args.warmup}
+        for st in ("f32", "bf16"):
+            so = Solver(cfgo, storage=st, stream=stream)
+            so.init_fields(fo["phi"], fo["psi"], fo["C"], fo["u"])
+            to = autotune.tune_single(so, cfgo["nx"], lattice="d3q19", use_cache=False)
+            octant.setdefault("sor_variant", {})[st] = to["sor"]
+            so.init_fields(fo["phi"], fo["psi"], fo["C"], fo["u"])
+            tt, km = time_steps(so, stream, flush, args.warmup, args.steps3, torch)
+            octant["mlups"][st] = cellso * args.steps3 / (tt / 1e3) / 1e6
+            octant["ms_per_step"][st] = tt / args.steps3
+            if st == "f32":
+                octant["kernel_ms"] = km
+            steproof["octant3d_" + st] = step_roofline(octant["mlups"][st], "d3q19", st, hbm,
+                                                       "HBM (3.4 M cells)")
+            so.close()
+
     # one 2D instance far beyond the L2: the bubble rise's physics on a
     # 4096 x 4096 grid with a 16 x 16 array of bubbles (16.8 M cells)
     big = None
@@ -673,6 +700,7 @@ def main():
            "sor_tune_ms": tuned.get("timings"),
            "gpu_launches": args.steps * s.kernel_count(),
            "forms_mlups": forms, "d3q19": d3, "batched": batched, "big2d": big,
+           "adsorption_octant_3d": octant,
            "step_roofline": steproof,
            "clocks": clk, "e2e": e2e, "impl": "lbs", "src_sha": sha}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

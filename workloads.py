@@ -65,6 +65,43 @@ def droplet_adsorption_2d(n=128, R=25.0, C0=0.5):
     return c
 
 
+def adsorption_octant_3d(R=20, C0=0.0005):
+    """The paper's Sec. 3.1 test in 3D: one octant of a spherical droplet of
+    radius R in a 5R x 5R x 5R D3Q19 domain, the droplet centred at the
+    corner (-1/2, -1/2, -1/2) where three mirror planes meet (mirror planes
+    half-way beyond both ends of every axis; the paper's far faces are
+    periodic, which cannot coexist with the near mirror on one axis).
+    rho = 1/1, mu = 0.1/0.1, sigma = 0.1, D_s = D_b = 0.1, E0 = 0.5, source
+    j = r_a psi_inf C with r_a = 0.2 (adsorption only), psi = 0 initially,
+    C = C0 = 0.0005 in the blue fluid."""
+    n = int(round(5 * R))
+    c = base(n, n, n)
+    c.update(R=float(R), C0=float(C0), ra=0.2, source=1, wall=[2, 2, 2],
+             center=[-0.5, -0.5, -0.5], name="adsorption_octant_3d")
+    return c
+
+
+def adsorption_analytic(cfg, t, r):
+    """Short-time sharp-interface solutions of Sec. 3.1 for a sphere:
+    (C(r, t)/C0 of Eq. 29, psi(t)/psi_inf of Eq. 30), with D the bulk
+    diffusivity, m = r_a psi_inf / D, a = sqrt(pi D), eta = a (1 + R m)/R.
+    Eq. 29 is read with the product sqrt(pi D t)(1 + R m) divided by R in its
+    denominator (as printed it adds a length to 1; with the division the
+    interface value tends to the steady 1/(1 + R m), and Eq. 30's long-time
+    slope r_a C0/(1 + R m) follows)."""
+    from math import erfc, log, pi, sqrt
+    D, R, ra, pinf, C0 = cfg["Db"], cfg["R"], cfg["ra"], cfg["psi_inf"], cfg["C0"]
+    m = ra * pinf / D
+    a = sqrt(pi * D)
+    eta = a * (1 + R * m) / R
+    s = sqrt(pi * D * t)
+    amp = (m * s) / (1 + s * (1 + R * m) / R)
+    c = [1 - amp * (R / ri) * erfc((ri - R) / (2 * sqrt(D * t))) for ri in r]
+    psi = cfg["psi0"] / pinf + ra * C0 * (
+        t - (a * m / eta ** 3) * (eta ** 2 * t - 2 * eta * sqrt(t) + 2 * log(1 + eta * sqrt(t))))
+    return np.array(c), psi
+
+
 def bubble_rise_2d(nx=256, ny=1024, D_b=64.0, Eo=10.0, Mo=0.1, Bi=1.0, Pe=10.0,
                    k=1.0, h=0.5, E0=0.5, C0=0.5, sigma0=0.004, rho_ratio=10.0,
                    mu_ratio=10.0, y0=None):
