@@ -435,6 +435,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip timing the other population storage forms")
+    ap.add_argument("--no-migration", action="store_true",
+                    help="skip the 3D droplet migration measurement")
     ap.add_argument("--no-octant", action="store_true",
                     help="skip the 3D adsorption octant measurement")
     ap.add_argument("--no-big2d", action="store_true",
@@ -658,6 +660,28 @@ def main():
                                                        "HBM (3.4 M cells)")
             so.close()
 
+    # Sec. 3.2's migration test in 3D: a droplet driven by a fixed surfactant
+    # gradient (linear EOS, no transport), R = 30 in the 5R x 5R x 10R box
+    migration = None
+    if rank == 0 and not args.no_migration:
+        cfgm = W.migration_3d(R=30)
+        cellsm = cfgm["nx"] * cfgm["ny"] * cfgm["nz"]
+        fm = W.initial_fields(cfgm)
+        migration = {"workload": "migration_3d D3Q19 150x150x300, walls x/y, periodic z, R=30, "
+                                 "linear EOS, psi fixed at psi_inf z/L_z (Sec. 3.2)",
+                     "cells": cellsm, "mlups": {}, "ms_per_step": {}, "steps": args.steps3,
+                     "warmup": args.warmup}
+        for st in ("f32", "bf16"):
+            sm = Solver(cfgm, storage=st, stream=stream)
+            sm.init_fields(fm["phi"], fm["psi"], fm["C"], fm["u"])
+            tt, km = time_steps(sm, stream, flush, args.warmup, args.steps3, torch)
+            migration["mlups"][st] = cellsm * args.steps3 / (tt / 1e3) / 1e6
+            migration["ms_per_step"][st] = tt / args.steps3
+            if st == "f32":
+                migration["kernel_ms"] = km
+            sm.close()
+        del fm
+
     # one 2D instance far beyond the L2: the bubble rise's physics on a
     # 4096 x 4096 grid with a 16 x 16 array of bubbles (16.8 M cells)
     big = None
@@ -700,7 +724,7 @@ def main():
            "sor_tune_ms": tuned.get("timings"),
            "gpu_launches": args.steps * s.kernel_count(),
            "forms_mlups": forms, "d3q19": d3, "batched": batched, "big2d": big,
-           "adsorption_octant_3d": octant,
+           "adsorption_octant_3d": octant, "migration_3d": migration,
            "step_roofline": steproof,
            "clocks": clk, "e2e": e2e, "impl": "lbs", "src_sha": sha}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -81,6 +81,29 @@ def adsorption_octant_3d(R=20, C0=0.0005):
     return c
 
 
+def migration_3d(R=10, shape=(5, 5, 10), sigma0=0.001, E0=0.5):
+    """The paper's Sec. 3.2 test: a droplet of radius R in an
+    (shape[0] R) x (shape[1] R) x (shape[2] R) D3Q19 box (5R x 5R x 10R or
+    10R x 10R x 10R), bounce-back walls on x and y, periodic z, rho = 1/1,
+    mu = 0.1/0.1, linear equation of state sigma = sigma0 (1 - E0 psi/psi_inf)
+    with sigma0 = 0.001, E0 = 0.5, and insoluble surfactant held at
+    psi = psi_inf (z + 1/2) / L_z (Eq. 31; x_in = 0.5 at the droplet's
+    centre): no surfactant transport.  The Marangoni stress drives the
+    droplet towards +z; its terminal velocity in an unbounded fluid is the
+    YGB velocity of Eq. 32 (migration_ygb)."""
+    nx, ny, nz = (int(round(k * R)) for k in shape)
+    c = base(nx, ny, nz)
+    c.update(R=float(R), wall=[1, 1, 0], eos=1, sigma0=sigma0, E0=E0, psi_inf=1.0,
+             transport=0, C0=0.0, psi_profile="linear_z", name="migration_3d")
+    return c
+
+
+def migration_ygb(cfg):
+    """Eq. 32: U_YGB = 2 sigma0 E0 R / (L_z (6 mu^R0 + 9 mu^B0))."""
+    return 2 * cfg["sigma0"] * cfg["E0"] * cfg["R"] / (
+        cfg["nz"] * (6 * cfg["muR0"] + 9 * cfg["muB0"]))
+
+
 def adsorption_analytic(cfg, t, r):
     """Short-time sharp-interface solutions of Sec. 3.1 for a sphere:
     (C(r, t)/C0 of Eq. 29, psi(t)/psi_inf of Eq. 30), with D the bulk
@@ -225,7 +248,8 @@ def shear_droplet_3d(nx=256, ny=128, nz=128, R=24.0, Ca=0.2, Re=1.0, lam=1.0, C0
 def initial_fields(cfg, seed=None, noise=0.0, u0=None):
     """Colour field phi = tanh((R - r)/width) (red inside), psi = psi0 times
     the interface indicator (1 - phi^2) (or psi0 everywhere when
-    cfg["psi_profile"] == "uniform"), C = C0 (1 - phi)/2 (bulk surfactant
+    cfg["psi_profile"] == "uniform", psi_inf (z + 1/2)/nz when it is
+    "linear_z"), C = C0 (1 - phi)/2 (bulk surfactant
     in the blue fluid only).  With a seed, psi and C receive multiplicative
     uniform noise of relative amplitude `noise` and u gets an additive field
     of amplitude `u0` (both break mirror symmetry for parity tests).  With
@@ -244,6 +268,9 @@ def initial_fields(cfg, seed=None, noise=0.0, u0=None):
     phi = np.tanh((cfg["R"] - r) / cfg["width"])
     if cfg.get("psi_profile") == "uniform":
         psi = np.full_like(phi, cfg["psi0"])
+    elif cfg.get("psi_profile") == "linear_z":  # Eq. 31, every cell
+        zz = (np.arange(nz, dtype=np.float64) + 0.5) / nz
+        psi = cfg["psi_inf"] * np.broadcast_to(zz[:, None, None], phi.shape).copy()
     else:
         psi = cfg["psi0"] * (1.0 - phi ** 2)
     C = cfg["C0"] * 0.5 * (1.0 - phi)
