@@ -435,6 +435,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip timing the other population storage forms")
+    ap.add_argument("--no-bubble3d", action="store_true",
+                    help="skip the 3D bubble rise measurement")
     ap.add_argument("--no-migration", action="store_true",
                     help="skip the 3D droplet migration measurement")
     ap.add_argument("--no-octant", action="store_true",
@@ -660,6 +662,33 @@ def main():
                                                        "HBM (3.4 M cells)")
             so.close()
 
+    # Sec. 3.4's bubble rise in 3D with soluble surfactant (Eo = 1, Mo = 0.1,
+    # 2R/L_x = 0.4), R = 30 in the 5R x 5R x 10R channel
+    bubble3 = None
+    if rank == 0 and not args.no_bubble3d:
+        cfgr = W.bubble_rise_3d(R=30)
+        cellsr = cfgr["nx"] * cfgr["ny"] * cfgr["nz"]
+        fr = W.initial_fields(cfgr)
+        bubble3 = {"workload": "bubble_rise_3d D3Q19 150x150x300, walls x/y, periodic z, R=30, "
+                               "Eo=1, Mo=0.1, rho/mu ratio 10, Bi=10, Pe=10 (Sec. 3.4)",
+                   "cells": cellsr, "mlups": {}, "ms_per_step": {}, "steps": args.steps3,
+                   "warmup": args.warmup}
+        for st in ("f32", "bf16"):
+            sr = Solver(cfgr, storage=st, stream=stream)
+            sr.init_fields(fr["phi"], fr["psi"], fr["C"], fr["u"])
+            tr = autotune.tune_single(sr, cfgr["nx"], lattice="d3q19", use_cache=False)
+            bubble3.setdefault("sor_variant", {})[st] = tr["sor"]
+            sr.init_fields(fr["phi"], fr["psi"], fr["C"], fr["u"])
+            tt, km = time_steps(sr, stream, flush, args.warmup, args.steps3, torch)
+            bubble3["mlups"][st] = cellsr * args.steps3 / (tt / 1e3) / 1e6
+            bubble3["ms_per_step"][st] = tt / args.steps3
+            if st == "f32":
+                bubble3["kernel_ms"] = km
+            steproof["bubble3d_" + st] = step_roofline(bubble3["mlups"][st], "d3q19", st, hbm,
+                                                       "HBM (6.75 M cells)")
+            sr.close()
+        del fr
+
     # Sec. 3.2's migration test in 3D: a droplet driven by a fixed surfactant
     # gradient (linear EOS, no transport), R = 30 in the 5R x 5R x 10R box
     migration = None
@@ -725,6 +754,7 @@ def main():
            "gpu_launches": args.steps * s.kernel_count(),
            "forms_mlups": forms, "d3q19": d3, "batched": batched, "big2d": big,
            "adsorption_octant_3d": octant, "migration_3d": migration,
+           "bubble_rise_3d": bubble3,
            "step_roofline": steproof,
            "clocks": clk, "e2e": e2e, "impl": "lbs", "src_sha": sha}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -81,6 +81,38 @@ def adsorption_octant_3d(R=20, C0=0.0005):
     return c
 
 
+def bubble_rise_3d(R=10, shape=(5, 5, 10), Eo=1.0, Mo=0.1, surfactant=True, Bi=10.0,
+                   Pe=10.0, k=1.0, h=0.5, E0=0.5, C0=0.5, sigma0=0.004):
+    """The paper's Sec. 3.4 test: a buoyant bubble (red, rho^R0 = 0.1) of
+    radius R in a (shape[0] R) x (shape[1] R) x (shape[2] R) D3Q19 channel
+    of liquid (rho^B0 = 1, mu^R0/mu^B0 = 0.1, sigma0 = 0.004), bounce-back
+    walls on x and y, periodic z, gravity along -z, the bubble on the
+    channel's axis at z = 2R.  g and mu^B0 from Eo and Mo as in
+    bubble_rise_2d; with surfactant: E0 = 0.5, Pe_b = Pe_s = 10, k = 1,
+    h = 0.5, Bi = 10, a clean interface at first (x_in = 0), C0 = 0.5 (not
+    given in the paper); without, no surfactant at all (the clean case).
+    The clean bubble's terminal velocity in an unbounded liquid is the
+    Hadamard-Rybczynski velocity of Eq. 35 (bubble_rise_uth)."""
+    nx, ny, nz = (int(round(q * R)) for q in shape)
+    c = bubble_rise_2d(nx=nx, ny=ny, D_b=2.0 * R, Eo=Eo, Mo=Mo, Bi=Bi, Pe=Pe, k=k, h=h, E0=E0,
+                       C0=C0, sigma0=sigma0)
+    g = -c["g"][1]
+    aR, aB = _alphas(3, c["rhoR0"], c["rhoB0"])
+    c.update(nz=nz, wall=[1, 1, 0], g=[0.0, 0.0, -g], alphaR=aR, alphaB=aB,
+             center=[(nx - 1) / 2.0, (ny - 1) / 2.0, 2.0 * R], name="bubble_rise_3d")
+    if not surfactant:
+        c.update(transport=0, C0=0.0, psi0=0.0, ra=0.0, rd=0.0)
+    return c
+
+
+def bubble_rise_uth(cfg):
+    """Eq. 35: U_th = (2/3) g drho R^2 / mu^B0 (mu^B0 + mu^R0) / (2 mu^B0 + 3 mu^R0)."""
+    g = abs(cfg["g"][2])
+    drho = cfg["rhoB0"] - cfg["rhoR0"]
+    mB, mR = cfg["muB0"], cfg["muR0"]
+    return 2.0 / 3.0 * g * drho * cfg["R"] ** 2 / mB * (mB + mR) / (2 * mB + 3 * mR)
+
+
 def migration_3d(R=10, shape=(5, 5, 10), sigma0=0.001, E0=0.5):
     """The paper's Sec. 3.2 test: a droplet of radius R in an
     (shape[0] R) x (shape[1] R) x (shape[2] R) D3Q19 box (5R x 5R x 10R or
