@@ -158,9 +158,13 @@ struct Solver : Base {
         I.pitch = L.pitch;
         I.plane = L.plane;
         I.bbmask = 0;
+        I.mvmask = 0;
         for (int a = 0; a < 3; a++) {
             I.wall[a] = p->wall[a];
             I.bbmask |= (p->wall[a] == 1) << a;
+            bool moving = false;
+            for (int b = 0; b < 3; b++) moving |= p->uw_lo[a][b] != 0 || p->uw_hi[a][b] != 0;
+            I.mvmask |= (p->wall[a] == 1 && moving) << a;
             for (int b = 0; b < 3; b++) {
                 I.uw_lo[a][b] = R(p->uw_lo[a][b]);
                 I.uw_hi[a][b] = R(p->uw_hi[a][b]);

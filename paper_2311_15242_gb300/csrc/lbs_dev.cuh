@@ -107,6 +107,7 @@ struct Inst {
     long long plane;         // elements per scalar plane (pitch * ny * nz)
     int wall[3];              // per axis: 0 periodic, 1 bounce-back walls, 2 mirror planes
     int bbmask;               // bit a set where axis a has bounce-back walls
+    int mvmask;               // bit a set where those walls move
     R uw_lo[3][3], uw_hi[3][3];
     R rhoR0, rhoB0, alphaR, alphaB, cs2R, cs2B, muR0, muB0;
     R inv_rhoR0, inv_rhoB0;  // 1 / rho^k0

@@ -592,10 +592,11 @@ __device__ __forceinline__ void stream2_cell(const Inst<R> &I, int x, int y) {
     const int flc = I.gflag[c];
     const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2);
     // 1. the streamed (total, minority) pairs as stored at their sources
-    //    (i = 0 stays in its own cell); slow: bit i set where the source's
-    //    flag differs from the cell's or the link crosses a wall (then the
-    //    cell's own opposite population is reflected).  A link crossing only
-    //    mirror planes brings the mirrored population of the mirrored cell.
+    //    (i = 0 stays in its own cell); a link that crosses a wall reflects
+    //    the cell's own opposite population; one crossing only mirror planes
+    //    brings the mirrored population of the mirrored cell.  slow: bit i
+    //    set where the source's flag differs from the cell's or the link
+    //    crosses a moving wall.
     R t[Q9], m[Q9];
     unsigned slow = 0, fbits = 0;
     // (branch-free: a reflected link reads the cell's own opposite
@@ -616,7 +617,9 @@ __device__ __forceinline__ void stream2_cell(const Inst<R> &I, int x, int y) {
         m[i] = ldp<R, P>(I, I.gM, k);
         const int fj = I.gflag[src];
         fbits |= (unsigned)fj << i;
-        if (fj != flc || bb) slow |= 1u << i;
+        // (a static wall returns the cell's own opposite population unchanged:
+        // the fast path's plain move; a moving wall adds its momentum term)
+        if (fj != flc || (bb & I.mvmask)) slow |= 1u << i;
     }
     fbits |= (unsigned)flc;  // (i = 0: the cell's own flag)
     // 2. fast path: every population moves unchanged (no rounding anywhere);

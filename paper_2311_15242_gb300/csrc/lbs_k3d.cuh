@@ -449,8 +449,9 @@ __global__ void __launch_bounds__(256, 3) k_stream3(Inst<R> I) {
     const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2),
              Z = make_ax(z, I.nz, I.wall[2], 4);
     // 1. the streamed (total, minority) pairs as stored at their sources;
-    //    slow: bit i set where the source's flag differs from the cell's or
-    //    the link crosses a wall (then the cell's own opposite population)
+    //    a link that crosses a wall reflects the cell's own opposite
+    //    population; slow: bit i set where the source's flag differs from the
+    //    cell's or the link crosses a moving wall
     R t[Q19], m[Q19];
     unsigned slow = 0, fbits = 0;
     // (branch-free: a reflected link reads the cell's own opposite
@@ -471,7 +472,9 @@ __global__ void __launch_bounds__(256, 3) k_stream3(Inst<R> I) {
         m[i] = ldp<R, P>(I, I.gM, k);
         const int fj = I.gflag[src];
         fbits |= (unsigned)fj << i;
-        if (fj != flc || bb) slow |= 1u << i;
+        // (a static wall returns the cell's own opposite population unchanged:
+        // the fast path's plain move; a moving wall adds its momentum term)
+        if (fj != flc || (bb & I.mvmask)) slow |= 1u << i;
     }
     fbits |= (unsigned)flc;  // (i = 0: the cell's own flag)
     // 2. fast path: every population moves unchanged; the cell keeps its
