@@ -35,7 +35,10 @@ void Launch3<R, P>::collide(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s) {
 }
 template <typename R, typename P>
 void Launch3<R, P>::stream(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s) {
-    k_stream3<R, P><<<g, b, 0, s>>>(I);
+    if (I.wall[0] == 2 || I.wall[1] == 2 || I.wall[2] == 2)
+        k_stream3<R, P, true><<<g, b, 0, s>>>(I);
+    else
+        k_stream3<R, P, false><<<g, b, 0, s>>>(I);
 }
 template <typename R, typename P>
 void Launch3<R, P>::diag(const Inst<R> &I, dim3 g, dim3 b, cudaStream_t s, int nblocks) {

@@ -36,17 +36,13 @@ __host__ __device__ constexpr int mir19c(int i, int m) {
             r = k;
     return r;
 }
+// (with i a compile-time constant each candidate folds to a constant and the
+// choice is a chain of selects: no branch, so the loads that use the result
+// stay in flight together)
 __host__ __device__ __forceinline__ int mir19(int i, int m) {
-    switch (m) {
-    case 0: return i;
-    case 1: return mir19c(i, 1);
-    case 2: return mir19c(i, 2);
-    case 3: return mir19c(i, 3);
-    case 4: return mir19c(i, 4);
-    case 5: return mir19c(i, 5);
-    case 6: return mir19c(i, 6);
-    default: return mir19c(i, 7);
-    }
+    const int a = (m & 1) ? mir19c(i, 1) : i, b = (m & 1) ? mir19c(i, 3) : mir19c(i, 2);
+    const int c = (m & 1) ? mir19c(i, 5) : mir19c(i, 4), d = (m & 1) ? mir19c(i, 7) : mir19c(i, 6);
+    return (m & 4) ? ((m & 2) ? d : c) : ((m & 2) ? b : a);
 }
 template <typename R>
 __host__ __device__ constexpr R w19(int i) {

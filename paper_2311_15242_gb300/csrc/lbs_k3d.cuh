@@ -441,8 +441,9 @@ __global__ void __launch_bounds__(256) k_collide3(Inst<R> I) {
 }
 
 // streaming (Eq. 13, pull), half-way bounce-back with moving walls, moments
-// at t+1 (see k_stream2)
-template <typename R, typename P>
+// at t+1 (see k_stream2).  MIRROR: the grid has mirror planes (a separate
+// instantiation, so that grids without them keep the plain direction choice)
+template <typename R, typename P, bool MIRROR>
 __global__ void __launch_bounds__(256, 3) k_stream3(Inst<R> I) {
     LBS_CELL3
     const int flc = I.gflag[c];
@@ -467,7 +468,8 @@ __global__ void __launch_bounds__(256, 3) k_stream3(Inst<R> I) {
         }
         const int bb = refl & I.bbmask;  // mirror planes: the mirrored source
         const long long src = bb ? c : j;
-        const long long k = (long long)(bb ? opp19(i) : mir19(i, refl)) * I.plane + src;
+        const int dir = bb ? opp19(i) : (MIRROR ? mir19(i, refl) : i);
+        const long long k = (long long)dir * I.plane + src;
         t[i] = ldp<R, P>(I, I.gT, k);
         m[i] = ldp<R, P>(I, I.gM, k);
         const int fj = I.gflag[src];
