@@ -59,8 +59,8 @@ POP_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 # capture of the source tree with this hash on this workload
 # (profiles/step_bubble_rise_256x1024_f32.md, SOR variant 5); reported only while the
 # kernels are unchanged.
-TRAFFIC = {"kernel": "sor", "sor_tile": 5, "src_sha": "e72900e1c2798358",
-           "bytes_per_launch": 6343168}
+TRAFFIC = {"kernel": "sor", "sor_tile": 5, "src_sha": "525f9f0a5277e0a2",
+           "bytes_per_launch": 10542080}
 
 
 def src_hash():
