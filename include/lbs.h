@@ -261,6 +261,16 @@ int lbs_step_result(lbs_ctx *c, double *out);
  * or 4 planes of z.  Errors: LBS_EINVAL. */
 int lbs_set_sor_tile(lbs_ctx *c, int variant);
 
+/* 2D contexts: run every round of a solve's blocked SOR (Sec. 2.2) in one
+ * cooperative launch with a grid barrier between rounds (on, the default),
+ * or one launch a round inside the step graph's loop (off).  The rounds,
+ * and so the results, are the same either way.  The one-launch form applies
+ * when every periodic axis has even length and the variant's grid fits the
+ * device at once; otherwise, and in 3D, the setting has no effect.  A
+ * barrier that waits too long (about a second) reports LBS_ETIMEOUT.
+ * Errors: LBS_EINVAL (no context), LBS_ECUDA. */
+int lbs_set_sor_persistent(lbs_ctx *c, int on);
+
 /* Human-readable description of the last error of c (never NULL). */
 const char *lbs_last_error(const lbs_ctx *c);
 

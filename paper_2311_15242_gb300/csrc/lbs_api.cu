@@ -41,6 +41,20 @@ void *sor2_kernel(int v) {
     }
 }
 template <typename R>
+void *sor2_coop_kernel(int v) {
+    switch (v) {
+    case 1: return (void *)k_sor_coop2<R, LBS_SORV(1)>;
+    case 2: return (void *)k_sor_coop2<R, LBS_SORV(2)>;
+    case 3: return (void *)k_sor_coop2<R, LBS_SORV(3)>;
+    case 4: return (void *)k_sor_coop2<R, LBS_SORV(4)>;
+    case 5: return (void *)k_sor_coop2<R, LBS_SORV(5)>;
+    case 6: return (void *)k_sor_coop2<R, LBS_SORV(6)>;
+    case 7: return (void *)k_sor_coop2<R, LBS_SORV(7)>;
+    case 8: return (void *)k_sor_coop2<R, LBS_SORV(8)>;
+    default: return (void *)k_sor_coop2<R, LBS_SORV(0)>;
+    }
+}
+template <typename R>
 size_t sor2_smem(int v) {
     switch (v) {
     case 1: return SorTile<R, LBS_SORV(1)>::smem_bytes();
@@ -293,10 +307,14 @@ struct Solver : Base {
         diag_grid = dim3(grid.x, (p->ny + BY * DIAG_STRIP - 1) / (BY * DIAG_STRIP), p->nz);
         diag_blocks = (int)(diag_grid.x * diag_grid.y * diag_grid.z);
         for (int v = 0; v < kSorVariants; v++)
-            if (sor2_fits(v))
+            if (sor2_fits(v)) {
                 cudaFuncSetAttribute(sor2_kernel<R>(v),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sor2_smem<R>(v));
+                cudaFuncSetAttribute(sor2_coop_kernel<R>(v),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sor2_smem<R>(v));
+            }
         if (D == 3)
             cudaFuncSetAttribute(Launch3<R, P>::zm_fn(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Launch3<R, P>::zm_smem());
@@ -319,6 +337,51 @@ struct Solver : Base {
             sor_grid = L3::sor_grid(sv, I.nx, I.ny, I.nz);
         }
         I.sor_pingpong = (D == 2 || sv == 1) ? 1 : 0;
+        coop_ok = false;
+        if (D == 2) {
+            // one launch for all rounds: the checkerboard tiles (even periodic
+            // axes) and a grid that fits the device at once
+            int dev = 0, sms = 0, coop = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+            if (sor2_fits(sv))
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sor2_coop_kernel<R>(sv),
+                                                              sor_vbs(sv), sor2_smem<R>(sv));
+            const bool cb = (I.wall[0] || !(I.nx & 1)) && (I.wall[1] || !(I.ny & 1));
+            coop_ok = coop && cb && (long long)sor_grid.x * sor_grid.y <= (long long)per_sm * sms;
+        }
+    }
+    bool coop_ok = false;  // the one-launch SOR applies to this grid and variant
+    bool coop_on = true;   // and is wanted (lbs_set_sor_persistent)
+    bool use_coop() const { return D == 2 && coop_ok && coop_on; }
+    int set_sor_persistent(int on) override {
+        CK(cudaStreamSynchronize(ctx->stream));
+        coop_on = on != 0;
+        if (gexec) {
+            CK(cudaGraphExecDestroy(gexec));
+            CK(cudaGraphDestroy(graph));
+            gexec = nullptr;
+            graph = nullptr;
+        }
+        return LBS_OK;
+    }
+    // all rounds of the solve in one cooperative launch (k_sor_coop2)
+    int launch_sor_coop(cudaStream_t s) {
+        int maxr = sor_rounds();
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = sor_grid;
+        cfg.blockDim = dim3(sor_vbs(sv), 1, 1);
+        cfg.dynamicSmemBytes = sor2_smem<R>(sv);
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        void *args[] = {(void *)&I, (void *)&maxr};
+        CK(cudaLaunchKernelExC(&cfg, sor2_coop_kernel<R>(sv), args));
+        return LBS_OK;
     }
     // variant v's shared memory fits a block on this device
     static bool sor2_fits(int v) {
@@ -458,7 +521,12 @@ struct Solver : Base {
             L3::grad(I, grid, block, s);
         ran[LBS_K_GRAD] = true;
         mark(s, LBS_K_SOR);
-        if (I.transport && !capturing) {
+        if (I.transport && use_coop()) {
+            // every round in one cooperative launch (the same in a graph)
+            int r = launch_sor_coop(s);
+            if (r) return r;
+            ran[LBS_K_SOR] = true;
+        } else if (I.transport && !capturing) {
             // eager form (for profilers): the host reads the loop state after
             // every round and launches no round beyond the converged one
             for (int r = 0; r < sor_rounds(); r++) {
@@ -596,6 +664,7 @@ struct Solver : Base {
     // diagnostics (4 before the first): one launch a round, two for the 3D
     // red-black half-sweeps
     int kernel_count() const override {
+        if (I.transport && use_coop()) return (D == 2 ? 4 : 5) + 2 + 1;
         const int per_round = (D == 3 && sv != 1) ? 2 : 1;
         const int cells = D == 2 ? 4 : 5;  // 2D: fd fused with collide
         return I.transport ? cells + 2 + per_round * last_rounds : 4;
@@ -1065,6 +1134,11 @@ int lbs_step_result(lbs_ctx *c, double *out) {
 int lbs_set_sor_tile(lbs_ctx *c, int variant) {
     if (!c || !c->impl) return LBS_EINVAL;
     return c->impl->set_sor_tile(variant);
+}
+
+int lbs_set_sor_persistent(lbs_ctx *c, int on) {
+    if (!c || !c->impl) return LBS_EINVAL;
+    return c->impl->set_sor_persistent(on);
 }
 
 int lbs_step_kernel_count(const lbs_ctx *c) {

@@ -91,6 +91,8 @@ struct Ctl {
     float dscale_f;         // the same in single precision
     int sor_active;         // batched sweep: 1 while this instance's solve iterates
     int dead;               // non-finite total seen: a batch skips this instance
+    unsigned int bar_count; // grid barrier of the one-launch SOR: arrivals,
+    unsigned int bar_gen;   // and generation (bumped by the last arrival)
     // per sweep: max |d psi|, max |d C|, max |psi|, max |C| (bits of
     // non-negative doubles, compared as unsigned integers)
     unsigned long long sweep[KMAX_SWEEPS][4];

@@ -29,6 +29,9 @@ struct Base {
     virtual size_t inst_bytes() const = 0;
     // blocked SOR tile variant (2D), see lbs_set_sor_tile
     virtual int set_sor_tile(int v) = 0;
+    // all SOR rounds of a 2D solve in one launch where possible, see
+    // lbs_set_sor_persistent
+    virtual int set_sor_persistent(int on) = 0;
     // step counter, total surfactant before the last rescale, rescale factor
     virtual int step_result(double *out3) = 0;
 };

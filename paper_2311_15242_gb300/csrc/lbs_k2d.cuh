@@ -1190,6 +1190,66 @@ __device__ __forceinline__ void sor_tile2(const Inst<R> &I, int round, int bx, i
         sor_tile2_list<R, TX, TY, K, BS>(I, round, bx, by, smem_raw);
 }
 
+// ---------------------------------------------------------------------------
+// k_sor_coop2: every round of a solve in one cooperative launch (one tile a
+// block, all blocks resident) with a grid barrier between rounds in place of
+// the graph's WHILE loop.  The rounds run the same tiles as k_sor_tb2, so the
+// iterates are the same; every block reads the round's maxima after the
+// barrier and takes the same decision.  A barrier waits at most
+// kBarrierPolls polls (about a second), then reports ST_TIMEOUT and returns.
+// ---------------------------------------------------------------------------
+constexpr long long kBarrierPolls = 1LL << 24;
+
+// true in every thread of the block once every block of the grid arrived;
+// false when the wait gave up
+__device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned int nblocks) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned int *gen = &ctl->bar_gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        if (atomicAdd(&ctl->bar_count, 1u) == nblocks - 1) {
+            ctl->bar_count = 0;
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            long long polls = 0;
+            while (*gen == g) {
+                if (++polls > kBarrierPolls) {
+                    ok = 0;
+                    atomicOr(&ctl->status, int(ST_TIMEOUT));
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename R, int TX, int TY, int K, int BS>
+__global__ void __launch_bounds__(BS) k_sor_coop2(Inst<R> I, int max_rounds) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const unsigned int nb = gridDim.x * gridDim.y;
+    Ctl *ctl = I.ctl;
+    int round = 0;
+    bool conv = false;
+    for (;; round++) {
+        sor_tile2<R, TX, TY, K, BS>(I, round, blockIdx.x, blockIdx.y, smem_raw);
+        if (!grid_barrier(ctl, nb)) return;  // (ST_TIMEOUT set)
+        conv = round_converged<R>(ctl, round, double(I.sor_tol));
+        if (conv || round + 1 >= max_rounds) break;
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        if (!conv) ctl->status |= ST_NOCONV;
+        ctl->sor_exec = round + 1;  // rounds run: the result's buffer parity
+    }
+}
+
 // decision after a round of instance ctl: converged, or out of rounds
 template <typename R>
 __device__ __forceinline__ bool sor_round_stop(Ctl *ctl, int round, double tol, int max_rounds) {

@@ -282,6 +282,31 @@ def test_every_blocked_sor_variant_matches_oracle(variant):
     assert max(err.values()) < 1e-9, (variant, err)
 
 
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-6)])
+def test_one_launch_sor_equals_round_launches(storage, tol):
+    """Every SOR round of a solve in one cooperative launch (grid barrier
+    between rounds, lbs_set_sor_persistent on) and one launch a round in the
+    graph's loop run the same tile rounds: the fields agree to rounding after
+    25 steps, and the step launches a single SOR kernel."""
+    cfg = droplet()
+    f = W.initial_fields(cfg, seed=11, noise=0.02, u0=1e-4)
+    out, count = {}, {}
+    for on in (True, False):
+        s = solver(cfg, storage)
+        s.set_sor_tile(5)
+        s.set_sor_persistent(on)
+        s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+        s.step(25)
+        out[on] = s.fields()
+        count[on] = s.kernel_count()
+        d = s.diagnostics()
+        assert d["sor_iters_psi"] >= 4, d
+        s.close()
+    err = errors(out[False], out[True])
+    assert max(err.values()) <= tol, err
+    assert count[True] == 4 + 2 + 1 and count[False] > count[True], count
+
+
 @pytest.mark.parametrize("variant", [7, 8])
 def test_wide_halo_sor_variants(variant):
     """The 6- and 8-sweep tiles (halo 12 and 16 cells) hold FP32 regions
