@@ -58,10 +58,11 @@ POP_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 # DRAM bytes (read + write) per launch of the dominant kernel, by SOR tile
 # variant (the tuner's choice among 4, 5 and 6 varies between boxes), from ncu
 # captures of the source tree with this hash on this workload
-# (profiles/step_bubble_rise_256x1024_f32.md); reported only while the kernels
-# are unchanged.
-TRAFFIC = {"kernel": "sor", "src_sha": "525f9f0a5277e0a2",
-           "bytes_per_launch": {4: 10545408, 5: 10542080, 6: 10542080}}
+# (profiles/step_bubble_rise_256x1024_f32.md); one launch runs every round of
+# the solve (the cooperative form).  Reported only while the kernels are
+# unchanged and the step runs that form.
+TRAFFIC = {"kernel": "sor", "src_sha": "c487a97bafc0ebee", "sor_launches_per_step": 1,
+           "bytes_per_launch": {4: 6373632, 5: 6346496, 6: 6345728}}
 
 
 def src_hash():
@@ -222,15 +223,17 @@ def step_roofline(mlups, lattice, storage, hbm, where):
     return {"b_alg_per_cell": b, "achieved_gbs": gbs, "frac": gbs / hbm, "state": where}
 
 
-def roofline2(kmean, cells, storage, rounds, hbm, src, traffic=None):
+def roofline2(kmean, cells, storage, rounds, hbm, src, traffic=None, sor_launches=None):
     """Roofline of the dominant kernel group of a 2D step (FP32 bytes of
-    ALG_BYTES_F32; one SOR launch is one round)."""
+    ALG_BYTES_F32).  The SOR group runs `rounds` rounds in `sor_launches`
+    launches: one a round, or one for all rounds (the cooperative form)."""
     groups = [g for g in kmean if g in ALG_BYTES_F32 or g == "sor"]
     dom = max(groups, key=lambda g: kmean[g])
     scale = 2 if storage == "f64" else 1  # (16-bit forms: fields stay FP32)
     if dom == "sor":
-        alg = SOR_BYTES_PER_ROUND_F32 * scale * cells
-        launch_ms = kmean[dom] / rounds
+        n = sor_launches or rounds
+        alg = SOR_BYTES_PER_ROUND_F32 * scale * cells * rounds / n
+        launch_ms = kmean[dom] / n
     else:
         alg = ALG_BYTES_F32[dom] * scale * cells
         launch_ms = kmean[dom]
@@ -556,8 +559,11 @@ def main():
     sweeps, rounds = dg["sor_iters_psi"], max(dg["sor_rounds"], 1)
     hbm, src = peaks()
     sha = src_hash()
-    roof = roofline2(kmean, cells, args.storage, rounds, hbm, src)
+    sor_launches = s.kernel_count() - 6  # (2D: four cell kernels, total and rescale)
+    roof = roofline2(kmean, cells, args.storage, rounds, hbm, src, sor_launches=sor_launches)
+    roof["sor_launches_per_step"] = sor_launches
     if (TRAFFIC["src_sha"] == sha and roof["kernel"] == TRAFFIC["kernel"]
+            and sor_launches == TRAFFIC["sor_launches_per_step"]
             and tuned["sor"] in TRAFFIC["bytes_per_launch"]):
         roof["traffic"] = TRAFFIC["bytes_per_launch"][tuned["sor"]]
     steproof = {"2d_" + args.storage: step_roofline(value / world, "d2q9", args.storage, hbm,
@@ -735,7 +741,8 @@ def main():
                 dgb = sb.diagnostics()
                 big["kernel_ms"] = km
                 big["sor_sweeps"] = dgb["sor_iters_psi"]
-                big["roofline"] = roofline2(km, cellsb, st, max(dgb["sor_rounds"], 1), hbm, src)
+                big["roofline"] = roofline2(km, cellsb, st, max(dgb["sor_rounds"], 1), hbm, src,
+                                            sor_launches=sb.kernel_count() - 6)
             steproof["big2d_" + st] = step_roofline(big["mlups"][st], "d2q9", st, hbm,
                                                     "HBM (3 GB of state)")
             sb.close()
