@@ -271,6 +271,14 @@ int lbs_set_sor_tile(lbs_ctx *c, int variant);
  * Errors: LBS_EINVAL (no context), LBS_ECUDA. */
 int lbs_set_sor_persistent(lbs_ctx *c, int on);
 
+/* The most polls (about 64 ns each) a block of the one-launch SOR waits at
+ * the grid barrier between rounds before it gives up: the step then reports
+ * LBS_ETIMEOUT (at the next lbs_sync or lbs_diagnostics) instead of waiting
+ * on.  Default 2^24, about a second; 0 gives up at once unless every block
+ * has arrived.  After a timeout the fields are not valid: initialise them
+ * again.  Errors: LBS_EINVAL (no context, negative limit), LBS_ECUDA. */
+int lbs_set_sor_wait_limit(lbs_ctx *c, long long polls);
+
 /* Human-readable description of the last error of c (never NULL). */
 const char *lbs_last_error(const lbs_ctx *c);
 

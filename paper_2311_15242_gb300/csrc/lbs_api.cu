@@ -355,6 +355,22 @@ struct Solver : Base {
     bool coop_ok = false;  // the one-launch SOR applies to this grid and variant
     bool coop_on = true;   // and is wanted (lbs_set_sor_persistent)
     bool use_coop() const { return D == 2 && coop_ok && coop_on; }
+    long long coop_polls = kBarrierPolls;  // the barrier's wait limit
+    int set_sor_wait_limit(long long polls) override {
+        if (polls < 0) {
+            set_err(ctx, "wait limit must be >= 0 polls");
+            return LBS_EINVAL;
+        }
+        CK(cudaStreamSynchronize(ctx->stream));
+        coop_polls = polls;
+        if (gexec) {
+            CK(cudaGraphExecDestroy(gexec));
+            CK(cudaGraphDestroy(graph));
+            gexec = nullptr;
+            graph = nullptr;
+        }
+        return LBS_OK;
+    }
     int set_sor_persistent(int on) override {
         CK(cudaStreamSynchronize(ctx->stream));
         coop_on = on != 0;
@@ -379,7 +395,8 @@ struct Solver : Base {
         at[0].val.cooperative = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        void *args[] = {(void *)&I, (void *)&maxr};
+        long long polls = coop_polls;
+        void *args[] = {(void *)&I, (void *)&maxr, (void *)&polls};
         CK(cudaLaunchKernelExC(&cfg, sor2_coop_kernel<R>(sv), args));
         return LBS_OK;
     }
@@ -1134,6 +1151,11 @@ int lbs_step_result(lbs_ctx *c, double *out) {
 int lbs_set_sor_tile(lbs_ctx *c, int variant) {
     if (!c || !c->impl) return LBS_EINVAL;
     return c->impl->set_sor_tile(variant);
+}
+
+int lbs_set_sor_wait_limit(lbs_ctx *c, long long polls) {
+    if (!c || !c->impl) return LBS_EINVAL;
+    return c->impl->set_sor_wait_limit(polls);
 }
 
 int lbs_set_sor_persistent(lbs_ctx *c, int on) {

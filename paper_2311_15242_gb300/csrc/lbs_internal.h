@@ -32,6 +32,8 @@ struct Base {
     // all SOR rounds of a 2D solve in one launch where possible, see
     // lbs_set_sor_persistent
     virtual int set_sor_persistent(int on) = 0;
+    // most polls a block waits at that form's grid barrier
+    virtual int set_sor_wait_limit(long long polls) = 0;
     // step counter, total surfactant before the last rescale, rescale factor
     virtual int step_result(double *out3) = 0;
 };

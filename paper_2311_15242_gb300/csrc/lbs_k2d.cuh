@@ -1195,14 +1195,16 @@ __device__ __forceinline__ void sor_tile2(const Inst<R> &I, int round, int bx, i
 // block, all blocks resident) with a grid barrier between rounds in place of
 // the graph's WHILE loop.  The rounds run the same tiles as k_sor_tb2, so the
 // iterates are the same; every block reads the round's maxima after the
-// barrier and takes the same decision.  A barrier waits at most
-// kBarrierPolls polls (about a second), then reports ST_TIMEOUT and returns.
+// barrier and takes the same decision.  A barrier waits at most max_polls
+// polls (the default, kBarrierPolls, is about a second), then reports
+// ST_TIMEOUT and returns.
 // ---------------------------------------------------------------------------
 constexpr long long kBarrierPolls = 1LL << 24;
 
 // true in every thread of the block once every block of the grid arrived;
 // false when the wait gave up
-__device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned int nblocks) {
+__device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned int nblocks,
+                                             long long max_polls) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1217,7 +1219,7 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned int nblocks) {
         } else {
             long long polls = 0;
             while (*gen == g) {
-                if (++polls > kBarrierPolls) {
+                if (++polls > max_polls) {
                     ok = 0;
                     atomicOr(&ctl->status, int(ST_TIMEOUT));
                     break;
@@ -1232,7 +1234,8 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned int nblocks) {
 }
 
 template <typename R, int TX, int TY, int K, int BS>
-__global__ void __launch_bounds__(BS) k_sor_coop2(Inst<R> I, int max_rounds) {
+__global__ void __launch_bounds__(BS) k_sor_coop2(Inst<R> I, int max_rounds,
+                                                   long long max_polls) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const unsigned int nb = gridDim.x * gridDim.y;
     Ctl *ctl = I.ctl;
@@ -1240,7 +1243,7 @@ __global__ void __launch_bounds__(BS) k_sor_coop2(Inst<R> I, int max_rounds) {
     bool conv = false;
     for (;; round++) {
         sor_tile2<R, TX, TY, K, BS>(I, round, blockIdx.x, blockIdx.y, smem_raw);
-        if (!grid_barrier(ctl, nb)) return;  // (ST_TIMEOUT set)
+        if (!grid_barrier(ctl, nb, max_polls)) return;  // (ST_TIMEOUT set)
         conv = round_converged<R>(ctl, round, double(I.sor_tol));
         if (conv || round + 1 >= max_rounds) break;
     }

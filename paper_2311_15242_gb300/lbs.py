@@ -20,7 +20,7 @@ STORAGE = {"f64": LBS_F64, "f32": LBS_F32, "f16": LBS_F16, "bf16": LBS_BF16}
 EXPORTS = ("lbs_params_default", "lbs_workspace_bytes", "lbs_create",
            "lbs_init_fields", "lbs_step", "lbs_sync", "lbs_get_fields",
            "lbs_get_macro", "lbs_diagnostics", "lbs_profile", "lbs_kernel_times", "lbs_set_graph",
-           "lbs_step_kernel_count", "lbs_set_sor_tile", "lbs_set_sor_persistent",
+           "lbs_step_kernel_count", "lbs_set_sor_tile", "lbs_set_sor_persistent", "lbs_set_sor_wait_limit",
            "lbs_step_result",
            "lbs_surfactant_total_static",
            "lbs_destroy",
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
     L.lbs_set_graph.argtypes = [C.c_void_p, C.c_int]
     L.lbs_set_sor_tile.argtypes = [C.c_void_p, C.c_int]
     L.lbs_set_sor_persistent.argtypes = [C.c_void_p, C.c_int]
+    L.lbs_set_sor_wait_limit.argtypes = [C.c_void_p, C.c_longlong]
     L.lbs_step_result.argtypes = [C.c_void_p, _DP]
     L.lbs_get_macro.argtypes = [C.c_void_p] + [_DP] * 6
     L.lbs_surfactant_total_static.argtypes = [C.c_int] + [C.c_void_p] * 4 + [C.c_int] * 4 + [
@@ -275,6 +276,11 @@ class Solver:
     def set_sor_tile(self, variant):
         """Blocked SOR tile variant of a 2D context (see lbs_set_sor_tile)."""
         self._check(self.L.lbs_set_sor_tile(self.h, int(variant)))
+
+    def set_sor_wait_limit(self, polls):
+        """Most polls a block waits at the one-launch SOR's grid barrier
+        (see lbs_set_sor_wait_limit)."""
+        self._check(self.L.lbs_set_sor_wait_limit(self.h, int(polls)))
 
     def set_sor_persistent(self, on=True):
         """All SOR rounds of a 2D solve in one launch, or one launch a round

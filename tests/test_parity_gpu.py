@@ -307,6 +307,34 @@ def test_one_launch_sor_equals_round_launches(storage, tol):
     assert count[True] == 4 + 2 + 1 and count[False] > count[True], count
 
 
+def test_one_launch_sor_wait_limit_reports_timeout():
+    """The grid barrier of the one-launch SOR waits a bounded number of polls.
+    With a limit of one poll some block gives up before all 6 tiles' blocks
+    have arrived (they finish microseconds apart): the step reports
+    LBS_ETIMEOUT on the host, nothing hangs, and after a fresh initialisation
+    with the default limit the context steps normally again."""
+    from paper_2311_15242_gb300.lbs import LBS_ETIMEOUT, LbsError
+    cfg = droplet()
+    f = W.initial_fields(cfg, seed=11)
+    s = solver(cfg, "f32")
+    s.set_sor_tile(5)
+    s.set_sor_wait_limit(1)
+    s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    codes = []
+    for _ in range(5):
+        try:
+            s.step(1)
+            s.diagnostics()
+        except LbsError as e:
+            codes.append(e.code)
+    assert LBS_ETIMEOUT in codes, codes
+    s.set_sor_wait_limit(1 << 24)
+    s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    s.step(5)
+    assert s.diagnostics()["step"] == 5
+    s.close()
+
+
 @pytest.mark.parametrize("variant", [7, 8])
 def test_wide_halo_sor_variants(variant):
     """The 6- and 8-sweep tiles (halo 12 and 16 cells) hold FP32 regions
