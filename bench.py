@@ -61,8 +61,8 @@ POP_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 # (profiles/step_bubble_rise_256x1024_f32.md); one launch runs every round of
 # the solve (the cooperative form).  Reported only while the kernels are
 # unchanged and the step runs that form.
-TRAFFIC = {"kernel": "sor", "src_sha": "c487a97bafc0ebee", "sor_launches_per_step": 1,
-           "bytes_per_launch": {4: 6373632, 5: 6346496, 6: 6345728}}
+TRAFFIC = {"kernel": "sor", "src_sha": "3f4915649c246303", "sor_launches_per_step": 1,
+           "bytes_per_launch": {4: 6360832, 5: 6348800, 6: 6347776}}
 
 
 def src_hash():
