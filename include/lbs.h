@@ -197,10 +197,11 @@ int lbs_profile(lbs_ctx *c, int enable);
 int lbs_kernel_times(lbs_ctx *c, double *ms, int n);
 
 /* Queue each step as one CUDA graph (enable = 1, the default; the SOR
- * iteration is a conditional WHILE node that stops on convergence) or as
- * individual kernel launches with a host-side bound on the SOR rounds
- * (enable = 0, for kernel profilers that cannot trace conditional graphs).
- * Both forms compute the same numbers. */
+ * iteration is one cooperative launch, see lbs_set_sor_persistent, or a
+ * conditional WHILE node that stops on convergence) or as individual kernel
+ * launches with a host-side bound on the SOR rounds (enable = 0, for kernel
+ * profilers that cannot trace conditional graphs).  Both forms compute the
+ * same numbers. */
 int lbs_set_graph(lbs_ctx *c, int enable);
 
 /* Number of kernel launches one step queues (graph kernel nodes). */

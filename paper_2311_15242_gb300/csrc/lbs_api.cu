@@ -458,8 +458,9 @@ struct Solver : Base {
 
     // the launches of one time step, in order, captured into the step graph;
     // with profiling on, an event is recorded at every group boundary.  The
-    // SOR rounds run in a WHILE conditional node whose body is one blocked
-    // round; the round's last block ends the loop on convergence.
+    // SOR rounds run in one cooperative launch (2D, when the grid fits the
+    // device at once), else in a WHILE conditional node whose body is one
+    // round, whose last block ends the loop on convergence.
     int capture_step(cudaStream_t s, cudaGraph_t g) {
         CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0,
                                          cudaStreamCaptureModeThreadLocal));
@@ -476,9 +477,10 @@ struct Solver : Base {
         return LBS_OK;
     }
 
-    // launches of one step; inside a capture the SOR loop becomes the WHILE
-    // node, outside it a host loop of sor_rounds() launches that return at
-    // once after the round that converged
+    // launches of one step; the one-launch SOR is the same launch in a capture
+    // and outside it; otherwise, inside a capture the SOR loop becomes the
+    // WHILE node, outside it a host loop of sor_rounds() launches that return
+    // at once after the round that converged
     using L3 = Launch3<R, P>;
     void k_force(cudaStream_t s) {
         if (D == 2)
