@@ -57,21 +57,26 @@ POP_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 
 # DRAM bytes (read + write) per launch of the dominant kernel, by SOR tile
 # variant (the tuner's choice among 4, 5 and 6 varies between boxes), from ncu
-# captures of the source tree with this hash on this workload
-# (profiles/step_bubble_rise_256x1024_f32.md); one launch runs every round of
-# the solve (the cooperative form).  Reported only while the kernels are
-# unchanged and the step runs that form.
-TRAFFIC = {"kernel": "sor", "src_sha": "3f4915649c246303", "sor_launches_per_step": 1,
+# captures on this workload (profiles/step_bubble_rise_256x1024_f32.md, tree
+# 3f4915649c246303); one launch runs every round of the solve (the
+# cooperative form).  Reported only while the files that hold the kernel's
+# device code (SOR2_FILES) hash as below and the step runs that form.
+TRAFFIC = {"kernel": "sor", "kernel_sha": "f3fa312a6194681a", "sor_launches_per_step": 1,
            "bytes_per_launch": {4: 6360832, 5: 6348800, 6: 6347776}}
 
 
-def src_hash():
+def src_hash(files=None):
+    """Hash of the CUDA sources (every .cu/.cuh file, or the named ones)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2311_15242_gb300", "csrc")
     for n in sorted(os.listdir(d)):
-        if n.endswith((".cu", ".cuh")):
+        if n.endswith((".cu", ".cuh")) and (files is None or n in files):
             h.update(open(os.path.join(d, n), "rb").read())
     return h.hexdigest()[:16]
+
+
+# the files that hold the device code of the 2D SOR kernels
+SOR2_FILES = ("lbs_dev.cuh", "lbs_k2d.cuh")
 
 
 def peaks():
@@ -562,7 +567,7 @@ def main():
     sor_launches = s.kernel_count() - 6  # (2D: four cell kernels, total and rescale)
     roof = roofline2(kmean, cells, args.storage, rounds, hbm, src, sor_launches=sor_launches)
     roof["sor_launches_per_step"] = sor_launches
-    if (TRAFFIC["src_sha"] == sha and roof["kernel"] == TRAFFIC["kernel"]
+    if (TRAFFIC["kernel_sha"] == src_hash(SOR2_FILES) and roof["kernel"] == TRAFFIC["kernel"]
             and sor_launches == TRAFFIC["sor_launches_per_step"]
             and tuned["sor"] in TRAFFIC["bytes_per_launch"]):
         roof["traffic"] = TRAFFIC["bytes_per_launch"][tuned["sor"]]
