@@ -222,6 +222,35 @@ def test_marangoni_stress_of_flat_interface():
     assert np.abs(m["F"][1, 0].sum(axis=0)).max() < 1e-6 * np.abs(dsig).max()
 
 
+def test_marangoni_stress_3d_linear_eos():
+    """The same in 3D with the linear law of Sec. 3.2: a flat interface
+    normal to z (walls on z) with psi varying along x and y; summed along z,
+    the force of Eq. 9 is the surface gradient of sigma = sigma0 (1 - E0 psi
+    / psi_inf), i.e. -sigma0 E0 / psi_inf grad psi, in both tangential
+    directions, and its normal component vanishes.  On a function of one
+    coordinate the isotropic stencil is the central difference, whose
+    response to sin(k x) is sin(k) cos(k x); against that the sums agree to
+    ~5e-5 (the rest is the discrete integral of |grad rhoN| / 2 across the
+    interface)."""
+    nx, ny, nz = 24, 20, 22
+    c = W.base(nx, ny, nz)
+    c.update(wall=[0, 0, 1], transport=0, sigma0=0.01, E0=0.5, psi_inf=1.0, eos=1)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    phi = np.tanh((z - 10.5) / 2.0)
+    kx, ky = 2 * np.pi / nx, 2 * np.pi / ny
+    psi = 0.3 + 0.1 * np.sin(kx * x) + 0.05 * np.cos(ky * y)
+    o = Oracle(c)
+    o.init_fields(phi, psi, np.zeros_like(psi))
+    m = o.macro()
+    col = m["F"].sum(axis=1)  # (3, ny, nx): sums along z
+    gx = 0.1 * np.sin(kx) * np.cos(kx * x[0])
+    gy = -0.05 * np.sin(ky) * np.sin(ky * y[0])
+    scale = np.abs(0.01 * 0.5 * gx).max()
+    assert np.allclose(col[0], -0.01 * 0.5 * gx, rtol=0, atol=1e-3 * scale)
+    assert np.allclose(col[1], -0.01 * 0.5 * gy, rtol=0, atol=1e-3 * scale)
+    assert np.abs(col[2]).max() < 1e-6 * scale
+
+
 def test_adsorption_first_step_uptake():
     """Eqs. 20, 23: with psi = 0 initially the first step changes the interface
     total sum (|grad rhoN|+eps) psi only through the source, by
