@@ -567,7 +567,7 @@ __device__ __forceinline__ void collide2_cell(const Inst<R> &I, int x, int y) {
 // only what k_force and the previous stream / grad kernels wrote, and they
 // write disjoint fields
 template <typename R, typename P>
-__global__ void k_fdcollide2(Inst<R> I) {
+__global__ void __launch_bounds__(256, 4) k_fdcollide2(Inst<R> I) {
     pdl_wait();
     pdl_trigger();
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
