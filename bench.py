@@ -58,11 +58,11 @@ POP_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 # DRAM bytes (read + write) per launch of the dominant kernel, by SOR tile
 # variant (the tuner's choice among 4, 5 and 6 varies between boxes), from ncu
 # captures on this workload (profiles/step_bubble_rise_256x1024_f32.md, tree
-# 3f4915649c246303); one launch runs every round of the solve (the
+# 19504d1590c33fd4); one launch runs every round of the solve (the
 # cooperative form).  Reported only while the files that hold the kernel's
 # device code (SOR2_FILES) hash as below and the step runs that form.
-TRAFFIC = {"kernel": "sor", "kernel_sha": "f3fa312a6194681a", "sor_launches_per_step": 1,
-           "bytes_per_launch": {4: 6360832, 5: 6348800, 6: 6347776}}
+TRAFFIC = {"kernel": "sor", "kernel_sha": "2c8f3c801b4c5ec3", "sor_launches_per_step": 1,
+           "bytes_per_launch": {4: 6360832, 5: 6348288, 6: 6348288}}
 
 
 def src_hash(files=None):
