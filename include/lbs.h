@@ -276,9 +276,34 @@ int lbs_set_sor_persistent(lbs_ctx *c, int on);
  * the grid barrier between rounds before it gives up: the step then reports
  * LBS_ETIMEOUT (at the next lbs_sync or lbs_diagnostics) instead of waiting
  * on.  Default 2^24, about a second; 0 gives up at once unless every block
- * has arrived.  After a timeout the fields are not valid: initialise them
- * again.  Errors: LBS_EINVAL (no context, negative limit), LBS_ECUDA. */
+ * has arrived.  After a timeout the fields of that step are not valid
+ * (initialise them again or load a saved state); the next step's launch
+ * starts with a clear barrier.  Errors: LBS_EINVAL (no context, negative limit), LBS_ECUDA. */
 int lbs_set_sor_wait_limit(lbs_ctx *c, long long polls);
+
+/* Checkpoint and restart of a single context (Sec. 2.2's time stepping
+ * carries state from step to step: the populations of Eq. 13, psi and C,
+ * the Adams-Bashforth history S^{t-1}, B^{t-1} of Eqs. 23-24, the conserved
+ * total of the rescale and the step counter).  lbs_save_state waits for the
+ * queued steps (status as lbs_sync) and writes a raw copy of that state into
+ * the caller-owned host buffer buf: a header (grid, storage form, step
+ * counter, conserved total M0, last rescale) followed by every carried plane
+ * in its stored type (populations in the storage type; fields in the
+ * arithmetic type; flags as bytes), dense [z][y][x].  With buf == NULL it
+ * only sets *bytes to the size needed; a *bytes below that size gives
+ * LBS_EINVAL with *bytes set to the size needed.  On success *bytes is the
+ * size written.
+ * lbs_load_state copies such a buffer into a context of the same grid and
+ * storage form (other parameters may differ) and waits for the copy; the
+ * steps that follow give, bit for bit, what the saving context's steps would
+ * have given with the same parameters and SOR variant.  Status, arrival
+ * counters and SOR progress restart clear.  The buffer is not referenced
+ * after the call.
+ * Errors: LBS_EINVAL (no context, NULL arguments, buffer too small, a
+ * header of another grid, storage form or library version), LBS_ECUDA, or a
+ * pending step status (lbs_save_state). */
+int lbs_save_state(lbs_ctx *c, void *buf, size_t *bytes);
+int lbs_load_state(lbs_ctx *c, const void *buf, size_t bytes);
 
 /* Human-readable description of the last error of c (never NULL). */
 const char *lbs_last_error(const lbs_ctx *c);

@@ -5,6 +5,7 @@
 
 #include <cfloat>
 #include <cstddef>
+#include <cstdint>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -667,6 +668,151 @@ struct Solver : Base {
         return LBS_OK;
     }
 
+    // ---- checkpoint: the state that carries from one step to the next ----
+    // every plane a step reads before writing it: the moving populations
+    // (storage type) and the rest populations of the current set, the flags,
+    // the moments, colour gradient and weights of the current time level,
+    // u and F, psi and C, the Adams-Bashforth history S, B (Eqs. 23-24) and
+    // the previous time level psip, Cp of the SOR starting guess
+    struct Plane {
+        void *d;
+        size_t es;
+    };
+    int state_planes(Plane *out) const {
+        int n = 0;
+        for (int i = 1; i < Q; i++)
+            out[n++] = {(char *)I.fT + (size_t)i * L.plane * sizeof(P), sizeof(P)};
+        for (int i = 1; i < Q; i++)
+            out[n++] = {(char *)I.fM + (size_t)i * L.plane * sizeof(P), sizeof(P)};
+        R *const sc[] = {I.fT0, I.fM0, I.rhoR, I.rhoB, I.rhoN, I.jx, I.jy, I.gx, I.gy, I.a,
+                         I.chi, I.ux,  I.uy,  I.Fx,   I.Fy,   I.psi, I.C, I.S, I.B, I.psip, I.Cp};
+        for (R *f : sc) out[n++] = {f, sizeof(R)};
+        if (D == 3) {
+            R *const s3[] = {I.jz, I.gz, I.uz, I.Fz};
+            for (R *f : s3) out[n++] = {f, sizeof(R)};
+        }
+        out[n++] = {I.flag, 1};
+        return n;
+    }
+    static constexpr uint32_t kStateMagic = 0x5453424cu;  // "LBST"
+    static constexpr uint32_t kStateVersion = 1;
+    struct StateHeader {
+        uint32_t magic, version;
+        int32_t nx, ny, nz, storage, r_bytes, p_bytes, nplanes, sor_iters, sor_iters_parity, pad;
+        long long step;
+        double M0, pre, scale, dscale;
+        float dscale_f, pad_f;
+        unsigned long long total;
+    };
+    size_t state_bytes() const {
+        Plane pl[2 * Q19 + 32];
+        const int n = state_planes(pl);
+        const size_t N = (size_t)I.nx * I.ny * I.nz;
+        size_t b = sizeof(StateHeader);
+        for (int k = 0; k < n; k++) b += N * pl[k].es;
+        return b;
+    }
+    int save_state(void *buf, size_t *bytes) override {
+        const size_t need = state_bytes();
+        if (!buf) {
+            *bytes = need;
+            return LBS_OK;
+        }
+        if (*bytes < need) {
+            set_err(ctx, "state buffer of %zu bytes (need %zu)", *bytes, need);
+            *bytes = need;
+            return LBS_EINVAL;
+        }
+        int r = sync();
+        if (r) return r;
+        cudaStream_t s = ctx->stream;
+        Ctl h;
+        CK(cudaMemcpy(&h, I.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+        Plane pl[2 * Q19 + 32];
+        const int n = state_planes(pl);
+        StateHeader hd;
+        std::memset(&hd, 0, sizeof(hd));
+        hd.magic = kStateMagic;
+        hd.version = kStateVersion;
+        hd.nx = I.nx;
+        hd.ny = I.ny;
+        hd.nz = I.nz;
+        hd.storage = ctx->storage;
+        hd.r_bytes = (int)sizeof(R);
+        hd.p_bytes = (int)sizeof(P);
+        hd.nplanes = n;
+        hd.sor_iters = h.sor_iters;
+        hd.sor_iters_parity = h.sor_iters_parity;
+        hd.step = h.step;
+        hd.M0 = h.M0;
+        hd.pre = h.pre;
+        hd.scale = h.scale;
+        hd.dscale = h.dscale;
+        hd.dscale_f = h.dscale_f;
+        hd.total = need;
+        std::memcpy(buf, &hd, sizeof(hd));
+        char *o = (char *)buf + sizeof(hd);
+        const size_t rows = (size_t)I.ny * I.nz;
+        for (int k = 0; k < n; k++) {
+            const size_t w = (size_t)I.nx * pl[k].es;
+            CK(cudaMemcpy2DAsync(o, w, pl[k].d, (size_t)I.pitch * pl[k].es, w, rows,
+                                 cudaMemcpyDeviceToHost, s));
+            o += w * rows;
+        }
+        CK(cudaStreamSynchronize(s));
+        *bytes = need;
+        return LBS_OK;
+    }
+    int load_state(const void *buf, size_t bytes) override {
+        StateHeader hd;
+        if (bytes < sizeof(hd)) {
+            set_err(ctx, "state buffer of %zu bytes is shorter than its header", bytes);
+            return LBS_EINVAL;
+        }
+        std::memcpy(&hd, buf, sizeof(hd));
+        Plane pl[2 * Q19 + 32];
+        const int n = state_planes(pl);
+        if (hd.magic != kStateMagic || hd.version != kStateVersion) {
+            set_err(ctx, "not a saved state of this library version");
+            return LBS_EINVAL;
+        }
+        if (hd.nx != I.nx || hd.ny != I.ny || hd.nz != I.nz || hd.storage != ctx->storage ||
+            hd.r_bytes != (int)sizeof(R) || hd.p_bytes != (int)sizeof(P) || hd.nplanes != n) {
+            set_err(ctx, "saved state is %dx%dx%d storage %d; this context is %dx%dx%d storage %d",
+                    hd.nx, hd.ny, hd.nz, hd.storage, I.nx, I.ny, I.nz, ctx->storage);
+            return LBS_EINVAL;
+        }
+        if (hd.total != state_bytes() || bytes < hd.total) {
+            set_err(ctx, "saved state of %zu bytes, expected %zu", bytes, state_bytes());
+            return LBS_EINVAL;
+        }
+        cudaStream_t s = ctx->stream;
+        CK(cudaStreamSynchronize(s));
+        const char *o = (const char *)buf + sizeof(hd);
+        const size_t rows = (size_t)I.ny * I.nz;
+        for (int k = 0; k < n; k++) {
+            const size_t w = (size_t)I.nx * pl[k].es;
+            CK(cudaMemcpy2DAsync(pl[k].d, (size_t)I.pitch * pl[k].es, o, w, w, rows,
+                                 cudaMemcpyHostToDevice, s));
+            o += w * rows;
+        }
+        // the control block: counters and totals of the saved step; status,
+        // arrival counters and SOR progress start clear
+        Ctl h;
+        std::memset(&h, 0, sizeof(h));
+        h.step = hd.step;
+        h.M0 = hd.M0;
+        h.pre = hd.pre;
+        h.scale = hd.scale;
+        h.dscale = hd.dscale;
+        h.dscale_f = hd.dscale_f;
+        h.sor_iters = hd.sor_iters;
+        h.sor_iters_parity = hd.sor_iters_parity;
+        CK(cudaMemcpyAsync(I.ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        return LBS_OK;
+    }
+
     const void *inst() const override { return &I; }
     size_t inst_bytes() const override { return sizeof(I); }
 
@@ -878,7 +1024,8 @@ struct Solver : Base {
             d->centroid[1] = v[7] / cnt;
             d->centroid[2] = v[16] / cnt;
             double I2[3] = {v[8] - cnt * d->centroid[0] * d->centroid[0],
-                            v[9] - cnt * d->centroid[1] * d->centroid[1], 0};
+                            v[9] - cnt * d->centroid[1] * d->centroid[1],
+                            v[17] - cnt * d->centroid[2] * d->centroid[2]};
             int hor = vert == 0 ? 1 : 0;
             d->aspect_ratio = I2[vert] > 0 ? std::sqrt(I2[hor] / I2[vert]) : 0.0;
             double rad = D == 2 ? std::sqrt(cnt / M_PI) : std::cbrt(3 * cnt / (4 * M_PI));
@@ -1163,6 +1310,16 @@ int lbs_set_sor_wait_limit(lbs_ctx *c, long long polls) {
 int lbs_set_sor_persistent(lbs_ctx *c, int on) {
     if (!c || !c->impl) return LBS_EINVAL;
     return c->impl->set_sor_persistent(on);
+}
+
+int lbs_save_state(lbs_ctx *c, void *buf, size_t *bytes) {
+    if (!c || !c->impl || !bytes) return LBS_EINVAL;
+    return c->impl->save_state(buf, bytes);
+}
+
+int lbs_load_state(lbs_ctx *c, const void *buf, size_t bytes) {
+    if (!c || !c->impl || !buf) return LBS_EINVAL;
+    return c->impl->load_state(buf, bytes);
 }
 
 int lbs_step_kernel_count(const lbs_ctx *c) {

@@ -36,6 +36,9 @@ struct Base {
     virtual int set_sor_wait_limit(long long polls) = 0;
     // step counter, total surfactant before the last rescale, rescale factor
     virtual int step_result(double *out3) = 0;
+    // raw copy of the state between steps (lbs_save_state / lbs_load_state)
+    virtual int save_state(void *buf, size_t *bytes) = 0;
+    virtual int load_state(const void *buf, size_t bytes) = 0;
 };
 
 // parameter check shared by every entry point (message into err)

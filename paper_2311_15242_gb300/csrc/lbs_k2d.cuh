@@ -254,10 +254,16 @@ __device__ __forceinline__ void grad2_cell(const Inst<R> &I, int x, int y, bool 
     if (guess) sor_guess(I, c);
 }
 
-// guess: also form the SOR initial guess (every step; not at initialisation)
+// guess: also form the SOR initial guess (every step; not at initialisation).
+// The kernel runs just before the one-launch SOR of the step, so it also
+// clears that launch's grid-barrier arrival counter: a barrier that gave up
+// (ST_TIMEOUT) leaves a partial count behind, which would release the next
+// launch's first barrier early.
 template <typename R>
 __global__ void k_grad2(Inst<R> I, int guess = 1) {
     pdl_wait();
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+        I.ctl->bar_count = 0;
     grad2_cell(I, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
                guess != 0);
 }
@@ -1480,7 +1486,7 @@ __global__ void k_diag(Inst<R> I, int nblocks) {
     // (every thread a strip of DIAG_STRIP cells along y)
     double v[NDIAG] = {0};
     double pmin = 1e300, pmax = -1e300;
-    float umax = 0.0f;
+    double umax = 0.0;
     for (int kk = 0; kk < DIAG_STRIP && x < I.nx; kk++) {
         const int y = y0 + kk;
         if (y >= I.ny) break;
@@ -1499,7 +1505,10 @@ __global__ void k_diag(Inst<R> I, int nblocks) {
         v[1] += fl ? rmin : rtot - rmin;
         v[2] += double(I.a[c] + I.eps_w) * double(I.psi[c]) +
                 double(I.chi[c] + I.eps_w) * double(I.C[c]);
-        const float ux = float(I.ux[c]), uy = float(I.uy[c]), uz = Q == 19 ? float(I.uz[c]) : 0.0f;
+        // (velocities in the fields' own precision: FP64 storage gives FP64
+        // diagnostics)
+        const double ux = double(I.ux[c]), uy = double(I.uy[c]),
+                     uz = Q == 19 ? double(I.uz[c]) : 0.0;
         if (rN >= 0) {
             v[3] += 1;
             v[4] += ux;
@@ -1521,7 +1530,7 @@ __global__ void k_diag(Inst<R> I, int nblocks) {
             pmin = fmin(pmin, p);
             pmax = fmax(pmax, p);
         }
-        umax = fmaxf(umax, sqrtf(ux * ux + uy * uy + uz * uz));
+        umax = fmax(umax, sqrt(ux * ux + uy * uy + uz * uz));
     }
     int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     double s[NDIAG];

@@ -21,7 +21,7 @@ EXPORTS = ("lbs_params_default", "lbs_workspace_bytes", "lbs_create",
            "lbs_init_fields", "lbs_step", "lbs_sync", "lbs_get_fields",
            "lbs_get_macro", "lbs_diagnostics", "lbs_profile", "lbs_kernel_times", "lbs_set_graph",
            "lbs_step_kernel_count", "lbs_set_sor_tile", "lbs_set_sor_persistent", "lbs_set_sor_wait_limit",
-           "lbs_step_result",
+           "lbs_step_result", "lbs_save_state", "lbs_load_state",
            "lbs_surfactant_total_static",
            "lbs_destroy",
            "lbs_last_error", "lbs_batch_workspace_bytes", "lbs_batch_create",
@@ -110,6 +110,8 @@ def load(build_if_missing: bool = True):
     L.lbs_set_sor_persistent.argtypes = [C.c_void_p, C.c_int]
     L.lbs_set_sor_wait_limit.argtypes = [C.c_void_p, C.c_longlong]
     L.lbs_step_result.argtypes = [C.c_void_p, _DP]
+    L.lbs_save_state.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]
+    L.lbs_load_state.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
     L.lbs_get_macro.argtypes = [C.c_void_p] + [_DP] * 6
     L.lbs_surfactant_total_static.argtypes = [C.c_int] + [C.c_void_p] * 4 + [C.c_int] * 4 + [
         C.c_double, C.c_void_p, C.c_void_p]
@@ -272,6 +274,19 @@ class Solver:
         out = np.empty(3)
         self._check(self.L.lbs_step_result(self.h, _dp(out)))
         return int(out[0]), float(out[1]), float(out[2])
+
+    def save_state(self):
+        """Raw copy of the carried state (see lbs_save_state) as bytes."""
+        n = C.c_size_t(0)
+        self._check(self.L.lbs_save_state(self.h, None, C.byref(n)))
+        buf = (C.c_char * n.value)()
+        self._check(self.L.lbs_save_state(self.h, buf, C.byref(n)))
+        return bytes(buf[:n.value])
+
+    def load_state(self, state):
+        """Restore a state written by save_state (see lbs_load_state)."""
+        buf = C.create_string_buffer(bytes(state), len(state))
+        self._check(self.L.lbs_load_state(self.h, buf, len(state)))
 
     def set_sor_tile(self, variant):
         """Blocked SOR tile variant of a 2D context (see lbs_set_sor_tile)."""
