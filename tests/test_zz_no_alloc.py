@@ -56,6 +56,44 @@ def test_static_total_matches_diagnostics_twice(storage, rtol):
     s.close()
 
 
+@pytest.mark.parametrize("storage,rtol", [("f64", 1e-12), ("f32", 1e-6)])
+def test_static_total_3d_pitched_rows_twice(storage, rtol):
+    """A D3Q19 state (nz > 1) in rows padded beyond nx: the (z, y) rows are
+    flattened with the caller's pitch; matches the 3D context's surf_total."""
+    import torch
+
+    from paper_2311_15242_gb300 import lbs
+
+    nx, ny, nz = 34, 20, 17
+    cfg = W.shear_droplet_3d(nx=nx, ny=ny, nz=nz, R=5.0)
+    f = W.initial_fields(cfg, seed=4, noise=0.02)
+    s = _solver(cfg, storage)
+    s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    s.step(6)
+    ref = s.diagnostics()["surf_total"]
+    m, fld = s.macro(), s.fields()
+    dt = torch.float64 if storage == "f64" else torch.float32
+    pitch = nx + 7
+    dev = []
+    for x in (m["a"], 1.0 - fld["phi"], fld["psi"], fld["C"]):
+        t = torch.full((nz, ny, pitch), float("nan"), dtype=dt, device="cuda")
+        t[:, :, :nx] = torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dt)
+        dev.append(t)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    L = lbs.load()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        out.fill_(-1.0)
+        rc = L.lbs_surfactant_total_static(
+            lbs.STORAGE[storage], *[ctypes.c_void_p(t.data_ptr()) for t in dev], nx, ny, nz,
+            pitch, cfg["eps_w"], ctypes.c_void_p(out.data_ptr()),
+            ctypes.c_void_p(stream.cuda_stream))
+        assert rc == lbs.LBS_OK
+        torch.cuda.synchronize()
+        assert out.item() == pytest.approx(ref, rel=rtol)
+    s.close()
+
+
 def test_static_total_refuses_grids_beyond_its_scratch():
     from paper_2311_15242_gb300 import lbs
     L = lbs.load()
