@@ -454,11 +454,18 @@ static void ghost_u(const ora_ctx *o, const double *u, long j, int refl,
         for (int y = 0; y < (o)->p.ny; y++)   \
             for (int x = 0; x < (o)->p.nx; x++)
 
+/* The same loops shared out over the host's threads (OpenMP, when built
+   with it).  Used only where every cell writes its own outputs and reads
+   nothing written in the same loop, so the results do not depend on the
+   thread count; sums and the lexicographic SOR stay sequential. */
+#define PAR_CELLS(o) _Pragma("omp parallel for collapse(2) schedule(static)") FOR_CELLS(o)
+#define PAR_FOR _Pragma("omp parallel for schedule(static)")
+
 /* isotropic finite-difference gradient (Sec. 2.1 after Eq. 9, ref. [40]);
    reading R2: d_a X(x) = (1/cs2) sum_i w_i X(x + e_i) e_ia.
    Scalars are mirrored (even) at walls (reading R21). */
 static void grad_scalar(const ora_ctx *o, const double *X, double *G) {
-    FOR_CELLS(o) {
+    PAR_CELLS(o) {
         long c = idx(o, x, y, z);
         double s[3] = {0, 0, 0};
         for (int i = 1; i < o->Q; i++) {
@@ -484,7 +491,7 @@ static void macro(ora_ctx *o, const double *fR, const double *fB,
     long N = o->N;
     int D = o->D;
     /* colour densities and colour function, Eq. 6 (rho^k = sum_i f_i^k) */
-    for (long c = 0; c < N; c++) {
+    PAR_FOR for (long c = 0; c < N; c++) {
         double r = 0, b = 0;
         for (int i = 0; i < o->Q; i++) {
             r += fR[i * N + c];
@@ -499,7 +506,7 @@ static void macro(ora_ctx *o, const double *fR, const double *fB,
     /* colour gradient, its magnitude and the unit normal n = -grad/|grad|
        (after Eq. 6); reading R3 regularises the normalisation */
     grad_scalar(o, o->rhoN, o->g);
-    for (long c = 0; c < N; c++) {
+    PAR_FOR for (long c = 0; c < N; c++) {
         double s = 0;
         for (int a = 0; a < 3; a++) s += o->g[a * N + c] * o->g[a * N + c];
         o->a[c] = sqrt(s);
@@ -508,7 +515,7 @@ static void macro(ora_ctx *o, const double *fR, const double *fB,
     }
     /* curvature kappa = -div n, Eq. 7, with the isotropic derivative; at a
        wall the normal component of n is mirrored with a sign change */
-    FOR_CELLS(o) {
+    PAR_CELLS(o) {
         long c = idx(o, x, y, z);
         double s = 0;
         for (int i = 1; i < o->Q; i++) {
@@ -525,7 +532,7 @@ static void macro(ora_ctx *o, const double *fR, const double *fB,
     /* interfacial force, Eq. 9, plus buoyancy F_b = (rho - rhoB0) g (Sec. 3.4) */
     grad_scalar(o, psi, o->gpsi);
     double cmc = ora_cmc(p);
-    for (long c = 0; c < N; c++) {
+    PAR_FOR for (long c = 0; c < N; c++) {
         double sig, mco;
         ora_eos(p, psi[c], &sig, &mco);
         double F[3];
@@ -548,7 +555,7 @@ static void macro(ora_ctx *o, const double *fR, const double *fB,
         }
     }
     /* velocity with the half-force shift, Eq. 10 (F = F_s + F_b) */
-    for (long c = 0; c < N; c++) {
+    PAR_FOR for (long c = 0; c < N; c++) {
         double j[3] = {0, 0, 0};
         for (int i = 0; i < o->Q; i++) {
             double f = fR[i * N + c] + fB[i * N + c];
@@ -588,7 +595,7 @@ static double weno_plus(const double *v) {
 static void weno_div(const ora_ctx *o, const double *Psi, const double *u,
                      double *div) {
     long N = o->N;
-    FOR_CELLS(o) {
+    PAR_CELLS(o) {
         long c = idx(o, x, y, z);
         double s = 0;
         for (int d = 0; d < o->D; d++) {
@@ -623,7 +630,7 @@ int ora_weno_div(ora_ctx *o, const double *Psi, const double *u, double *div) {
    Reading R21: a face on a wall carries no flux. */
 static void diffuse(const ora_ctx *o, const double *W, const double *X,
                     double *L) {
-    for (long c = 0; c < o->N; c++) {
+    PAR_FOR for (long c = 0; c < o->N; c++) {
         double s = 0;
         for (int f = 0; f < 2 * o->D; f++) {
             long j = o->face[f * o->N + c];
@@ -855,7 +862,7 @@ static int one_step(ora_ctx *o) {
     }
 
     /* 3. collision + recolouring at every node (Eqs. 1-4, 11-12) */
-    FOR_CELLS(o) {
+    PAR_CELLS(o) {
         long c = idx(o, x, y, z);
         double fr[QMAX], fb[QMAX], fr2[QMAX], fb2[QMAX];
         for (int i = 0; i < Q; i++) {
@@ -900,7 +907,7 @@ static int one_step(ora_ctx *o) {
           cell (specular reflection). */
     int bbmask = 0;
     for (int a = 0; a < 3; a++) bbmask |= (p->wall[a] == 1) << a;
-    FOR_CELLS(o) {
+    PAR_CELLS(o) {
         long c = idx(o, x, y, z);
         for (int i = 0; i < Q; i++) {
             int back[3] = {-o->e[i][0], -o->e[i][1], -o->e[i][2]};
@@ -984,6 +991,20 @@ int ora_step(ora_ctx *o, int n) {
 }
 
 long long ora_step_count(const ora_ctx *o) { return o->step; }
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+/* host threads the cell loops use (1 without OpenMP); n <= 0 leaves it */
+int ora_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 int ora_macro(ora_ctx *o, double *rhoR, double *rhoB, double *rhoN, double *g,
               double *a, double *kappa, double *F, double *u, double *S,

@@ -83,6 +83,10 @@ int ora_set_pops(ora_ctx *o, const double *fR, const double *fB);
 /* set psi and C (after ora_init_fields; also resets the total M0) */
 int ora_set_surfactant(ora_ctx *o, const double *psi, const double *C);
 long long ora_step_count(const ora_ctx *o);
+/* host threads of the cell loops (OpenMP; 1 without it).  n > 0 sets the
+   count for the process; returns the count in use.  Results do not depend
+   on it: only loops whose cells are independent are shared out. */
+int ora_threads(int n);
 
 /* intermediate fields of one step at the current state, each [N] unless
    noted: rhoR, rhoB, rhoN, g[3][N] (colour gradient), a (=|grad rhoN|),

@@ -66,6 +66,8 @@ def lib():
         L.ora_set_surfactant.argtypes = [C.c_void_p, _DP, _DP]
         L.ora_step_count.restype = C.c_longlong
         L.ora_step_count.argtypes = [C.c_void_p]
+        L.ora_threads.restype = C.c_int
+        L.ora_threads.argtypes = [C.c_int]
         L.ora_macro.argtypes = [C.c_void_p] + [_DP] * 10
         L.ora_lattice.argtypes = [C.c_int, C.POINTER(C.c_int),
                                   C.POINTER(C.c_int), _DP, _DP, _DP]
@@ -116,6 +118,12 @@ def make_params(cfg: dict) -> OraParams:
     p.sor_tol = float(cfg.get("oracle_sor_tol", 1e-13))
     p.sor_max_iter = int(cfg.get("oracle_sor_max_iter", 10000))
     return p
+
+
+def threads(n=0):
+    """Host threads of the oracle's independent cell loops (OpenMP): n > 0
+    sets the count for the process; returns the count in use."""
+    return int(lib().ora_threads(int(n)))
 
 
 class Oracle:
