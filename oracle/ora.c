@@ -387,6 +387,10 @@ struct ora_ctx {
     double *rhoR, *rhoB, *rho, *rhoN, *g, *a, *n, *kap, *F, *u, *gpsi;
     double *S, *B, *rhs, *wt, *tmp, *Psi;
     long *face;                    /* [2D][N] face neighbours, -1 = wall */
+    /* boundary of each end of each axis: 0 periodic wrap, 1 bounce-back
+       wall, 2 mirror plane; both ends follow p.wall unless a slab of a
+       decomposed grid sets them (ora_set_ends) */
+    int end[3][2];
     long long step;
     double M0;
     double last_pre, last_scale;
@@ -414,7 +418,7 @@ static long nb(const ora_ctx *o, int x, int y, int z, const int *d, int *refl,
     for (int a = 0; a < 3; a++) {
         side[a] = 0;
         if (c[a] >= 0 && c[a] < n[a]) continue;
-        if (!o->p.wall[a]) {
+        if (!o->end[a][c[a] < 0 ? 0 : 1]) {
             c[a] = ((c[a] % n[a]) + n[a]) % n[a];
             continue;
         }
@@ -440,7 +444,7 @@ static void ghost_u(const ora_ctx *o, const double *u, long j, int refl,
     for (int b = 0; b < 3; b++) out[b] = u[b * o->N + j];
     for (int a = 0; a < 3; a++) {
         if (!(refl & (1 << a))) continue;
-        if (o->p.wall[a] == 2) {
+        if (o->end[a][side[a] < 0 ? 0 : 1] == 2) {
             out[a] = -out[a];
             continue;
         }
@@ -649,26 +653,14 @@ int ora_diffuse(ora_ctx *o, const double *w, const double *x, double *Lx) {
 /* SOR with relaxation factor omega (Sec. 2.2, after Eq. 28) for
    (W - h L_W) X = rhs, lexicographic order.  Reading R13: stop when the
    largest update of a sweep is <= sor_tol * max|X|. */
+static void sor_rows(const ora_ctx *o, const double *W, double h, const double *rhs,
+                     double *X, int r0, int r1, double *maxd, double *maxx);
 static int sor(const ora_ctx *o, const double *W, double h, const double *rhs,
                double *X) {
-    const double om = o->p.sor_omega;
+    const int rows = o->D == 2 ? o->p.ny : o->p.nz;
     for (int it = 1; it <= o->p.sor_max_iter; it++) {
         double maxd = 0, maxx = 0;
-        for (long c = 0; c < o->N; c++) { /* lexicographic: x fastest */
-            double diag = W[c], off = 0;
-            for (int f = 0; f < 2 * o->D; f++) {
-                long j = o->face[f * o->N + c];
-                if (j < 0) continue;
-                double wf = 0.5 * (W[c] + W[j]);
-                diag += h * wf;
-                off += h * wf * X[j];
-            }
-            double xn = (rhs[c] + off) / diag;
-            double dx = om * (xn - X[c]);
-            X[c] += dx;
-            if (fabs(dx) > maxd) maxd = fabs(dx);
-            if (fabs(X[c]) > maxx) maxx = fabs(X[c]);
-        }
+        sor_rows(o, W, h, rhs, X, 0, rows, &maxd, &maxx);
         if (maxd <= o->p.sor_tol * maxx) return it;
     }
     return -1;
@@ -700,6 +692,21 @@ static double surf_total(const ora_ctx *o, const double *a, const double *rN,
         kadd(&k, (1.0 - rN[c] + o->p.eps_w) * C[c]);
     }
     return k.s;
+}
+
+/* face neighbours of Eq. 28 (x-, x+, y-, y+, z-, z+); -1 across a wall */
+static void build_faces(ora_ctx *o) {
+    long N = o->N;
+    FOR_CELLS(o) {
+        long c = idx(o, x, y, z);
+        for (int d = 0; d < o->D; d++)
+            for (int s = 0; s < 2; s++) {
+                int off[3] = {0, 0, 0}, refl, side[3];
+                off[d] = s ? 1 : -1;
+                long j = nb(o, x, y, z, off, &refl, side);
+                o->face[(2 * d + s) * N + c] = refl ? -1 : j;
+            }
+    }
 }
 
 /* ------------------------------------------------------------------------
@@ -749,18 +756,21 @@ ora_ctx *ora_create(const ora_params *p) {
         ora_destroy(o);
         return NULL;
     }
-    /* face neighbours of Eq. 28 (x-, x+, y-, y+, z-, z+); -1 across a wall */
-    FOR_CELLS(o) {
-        long c = idx(o, x, y, z);
-        for (int d = 0; d < o->D; d++)
-            for (int s = 0; s < 2; s++) {
-                int off[3] = {0, 0, 0}, refl, side[3];
-                off[d] = s ? 1 : -1;
-                long j = nb(o, x, y, z, off, &refl, side);
-                o->face[(2 * d + s) * N + c] = refl ? -1 : j;
-            }
-    }
+    for (int a = 0; a < 3; a++) o->end[a][0] = o->end[a][1] = p->wall[a];
+    build_faces(o);
     return o;
+}
+
+/* Boundaries of the two ends of axis a (0 periodic wrap, 1 bounce-back
+   wall, 2 mirror plane).  A slab of a decomposed grid wraps at the ends
+   where it meets another slab: what the wrap brings into its outermost
+   ghost layers is overwritten by the exchange before it can matter. */
+int ora_set_ends(ora_ctx *o, int a, int lo, int hi) {
+    if (a < 0 || a > 2 || lo < 0 || lo > 2 || hi < 0 || hi > 2) return -1;
+    o->end[a][0] = lo;
+    o->end[a][1] = hi;
+    build_faces(o);
+    return 0;
 }
 
 void ora_destroy(ora_ctx *o) {
@@ -830,7 +840,9 @@ int ora_set_surfactant(ora_ctx *o, const double *psi, const double *C) {
  * S^t, B^t; collision, recolouring, streaming; colour weights at t+1;
  * Crank-Nicolson solve for psi, C at t+1; rescaling.
  * ---------------------------------------------------------------------- */
-static int one_step(ora_ctx *o) {
+/* steps 1-4: fields and forces at t, explicit terms S^t, B^t, collision,
+   recolouring, streaming */
+static void phase_lb(ora_ctx *o) {
     const ora_params *p = &o->p;
     long N = o->N;
     int D = o->D, Q = o->Q;
@@ -905,14 +917,16 @@ static int one_step(ora_ctx *o) {
           that crosses only mirror planes brings the mirror image of its
           source: the population of the mirrored direction at the mirrored
           cell (specular reflection). */
-    int bbmask = 0;
-    for (int a = 0; a < 3; a++) bbmask |= (p->wall[a] == 1) << a;
     PAR_CELLS(o) {
         long c = idx(o, x, y, z);
         for (int i = 0; i < Q; i++) {
             int back[3] = {-o->e[i][0], -o->e[i][1], -o->e[i][2]};
             int refl, side[3];
             long j = nb(o, x, y, z, back, &refl, side);
+            int bbmask = 0; /* axes whose crossing is a bounce-back wall */
+            for (int a = 0; a < 3; a++)
+                if ((refl & (1 << a)) && o->end[a][side[a] < 0 ? 0 : 1] == 1)
+                    bbmask |= 1 << a;
             if (!(refl & bbmask)) {
                 int is = o->mir[refl][i];
                 o->fR[i * N + c] = o->fR2[is * N + j];
@@ -934,52 +948,162 @@ static int one_step(ora_ctx *o) {
             o->fB[i * N + c] = o->fB2[io * N + c] + 2.0 * o->w[i] * o->rhoB[c] * eu / CS2;
         }
     }
+}
 
-    if (p->transport) {
-        /* 5. Crank-Nicolson right-hand sides with the weights of time t
-              (reading R12: a = |grad rhoN| + eps_w, chi = 1 - rhoN + eps_w);
-              Euler for the explicit part at t = 0 (Eq. 23), AB2 after (Eq. 24) */
-        const double ab_now = o->step == 0 ? 1.0 : 1.5;
-        const double ab_old = o->step == 0 ? 0.0 : -0.5;
-        double *rhsC = o->tmp;
-        for (long c = 0; c < N; c++) o->wt[c] = o->a[c] + p->eps_w;
-        diffuse(o, o->wt, o->psi, o->rhs);
-        for (long c = 0; c < N; c++)
-            o->rhs[c] = o->wt[c] * o->psi[c] + 0.5 * p->Ds * o->rhs[c] +
-                        ab_now * o->S[c] + ab_old * o->Sp[c];
-        for (long c = 0; c < N; c++) o->wt[c] = 1.0 - o->rhoN[c] + p->eps_w;
-        diffuse(o, o->wt, o->C, rhsC);
-        for (long c = 0; c < N; c++)
-            rhsC[c] = o->wt[c] * o->C[c] + 0.5 * p->Db * rhsC[c] +
-                      ab_now * o->B[c] + ab_old * o->Bp[c];
+/* step 5 (transport): the Crank-Nicolson right-hand sides with the
+   weights of time t, into rhs (psi) and tmp (C) */
+static void phase_rhs(ora_ctx *o) {
+    const ora_params *p = &o->p;
+    long N = o->N;
+    /* 5. Crank-Nicolson right-hand sides with the weights of time t
+          (reading R12: a = |grad rhoN| + eps_w, chi = 1 - rhoN + eps_w);
+          Euler for the explicit part at t = 0 (Eq. 23), AB2 after (Eq. 24) */
+    const double ab_now = o->step == 0 ? 1.0 : 1.5;
+    const double ab_old = o->step == 0 ? 0.0 : -0.5;
+    double *rhsC = o->tmp;
+    for (long c = 0; c < N; c++) o->wt[c] = o->a[c] + p->eps_w;
+    diffuse(o, o->wt, o->psi, o->rhs);
+    for (long c = 0; c < N; c++)
+        o->rhs[c] = o->wt[c] * o->psi[c] + 0.5 * p->Ds * o->rhs[c] +
+                    ab_now * o->S[c] + ab_old * o->Sp[c];
+    for (long c = 0; c < N; c++) o->wt[c] = 1.0 - o->rhoN[c] + p->eps_w;
+    diffuse(o, o->wt, o->C, rhsC);
+    for (long c = 0; c < N; c++)
+        rhsC[c] = o->wt[c] * o->C[c] + 0.5 * p->Db * rhsC[c] +
+                  ab_now * o->B[c] + ab_old * o->Bp[c];
+}
 
-        /* 6. weights at t+1 from the streamed populations */
-        macro(o, o->fR, o->fB, o->psi);
+/* one lexicographic SOR sweep (Sec. 2.2) over the rows [r0, r1) of the
+   slowest axis (y in 2D, z in 3D) for (W - h L_W) X = rhs; folds the largest
+   update and the largest |X| of the sweep into *maxd, *maxx */
+static void sor_rows(const ora_ctx *o, const double *W, double h, const double *rhs,
+                     double *X, int r0, int r1, double *maxd, double *maxx) {
+    const double om = o->p.sor_omega;
+    const long row = o->N / (o->D == 2 ? o->p.ny : o->p.nz);
+    for (long c = r0 * row; c < r1 * row; c++) { /* lexicographic: x fastest */
+        double diag = W[c], off = 0;
+        for (int f = 0; f < 2 * o->D; f++) {
+            long j = o->face[f * o->N + c];
+            if (j < 0) continue;
+            double wf = 0.5 * (W[c] + W[j]);
+            diag += h * wf;
+            off += h * wf * X[j];
+        }
+        double xn = (rhs[c] + off) / diag;
+        double dx = om * (xn - X[c]);
+        X[c] += dx;
+        if (fabs(dx) > *maxd) *maxd = fabs(dx);
+        if (fabs(X[c]) > *maxx) *maxx = fabs(X[c]);
+    }
+}
 
-        /* 7. implicit solves (W^{t+1} - (D/2) L_{W^{t+1}}) X^{t+1} = rhs by SOR */
-        for (long c = 0; c < N; c++) o->wt[c] = o->a[c] + p->eps_w;
-        int itp = sor(o, o->wt, 0.5 * p->Ds, o->rhs, o->psi);
-        for (long c = 0; c < N; c++) o->wt[c] = 1.0 - o->rhoN[c] + p->eps_w;
-        int itc = sor(o, o->wt, 0.5 * p->Db, rhsC, o->C);
-        o->last_it_psi = itp;
-        o->last_it_C = itc;
-        if (itp < 0 || itc < 0) return -4;
-
-        /* 8. rescale psi and C by one common factor so that the total
-              surfactant equals its initial value (reading R14) */
-        double Mt = surf_total(o, o->a, o->rhoN, o->psi, o->C);
-        double s = Mt > 0 ? o->M0 / Mt : 1.0;
+/* step 8 after the solves: rescale by s, keep the explicit terms as the
+   Adams-Bashforth history, count the step */
+static void phase_finish(ora_ctx *o, double s, double pre) {
+    long N = o->N;
+    if (o->p.transport) {
         for (long c = 0; c < N; c++) {
             o->psi[c] *= s;
             o->C[c] *= s;
         }
-        o->last_pre = Mt;
+        o->last_pre = pre;
         o->last_scale = s;
         memcpy(o->Sp, o->S, sizeof(double) * N);
         memcpy(o->Bp, o->B, sizeof(double) * N);
     }
     o->step++;
+}
+
+static int one_step(ora_ctx *o) {
+    const ora_params *p = &o->p;
+    long N = o->N;
+    phase_lb(o);
+    if (!p->transport) {
+        phase_finish(o, 1.0, 0.0);
+        return 0;
+    }
+    phase_rhs(o);
+    double *rhsC = o->tmp;
+
+    /* 6. weights at t+1 from the streamed populations */
+    macro(o, o->fR, o->fB, o->psi);
+
+    /* 7. implicit solves (W^{t+1} - (D/2) L_{W^{t+1}}) X^{t+1} = rhs by SOR */
+    for (long c = 0; c < N; c++) o->wt[c] = o->a[c] + p->eps_w;
+    int itp = sor(o, o->wt, 0.5 * p->Ds, o->rhs, o->psi);
+    for (long c = 0; c < N; c++) o->wt[c] = 1.0 - o->rhoN[c] + p->eps_w;
+    int itc = sor(o, o->wt, 0.5 * p->Db, rhsC, o->C);
+    o->last_it_psi = itp;
+    o->last_it_C = itc;
+    if (itp < 0 || itc < 0) return -4;
+
+    /* 8. rescale psi and C by one common factor so that the total
+          surfactant equals its initial value (reading R14) */
+    double Mt = surf_total(o, o->a, o->rhoN, o->psi, o->C);
+    phase_finish(o, Mt > 0 ? o->M0 / Mt : 1.0, Mt);
     return 0;
+}
+
+/* ---- building blocks of a step, for a grid decomposed into slabs ---- */
+
+int ora_phase(ora_ctx *o, int k) {
+    const ora_params *p = &o->p;
+    long N = o->N;
+    switch (k) {
+    case 0: phase_lb(o); return 0;
+    case 1: phase_rhs(o); return 0;
+    case 2: macro(o, o->fR, o->fB, o->psi); return 0;
+    case 3:
+        for (long c = 0; c < N; c++) o->wt[c] = o->a[c] + p->eps_w;
+        return 0;
+    case 4:
+        for (long c = 0; c < N; c++) o->wt[c] = 1.0 - o->rhoN[c] + p->eps_w;
+        return 0;
+    }
+    return -1;
+}
+
+int ora_sor_rows(ora_ctx *o, int which, int r0, int r1, double *maxd, double *maxx) {
+    if (which == 0)
+        sor_rows(o, o->wt, 0.5 * o->p.Ds, o->rhs, o->psi, r0, r1, maxd, maxx);
+    else
+        sor_rows(o, o->wt, 0.5 * o->p.Db, o->tmp, o->C, r0, r1, maxd, maxx);
+    return 0;
+}
+
+int ora_surf_rows(ora_ctx *o, int r0, int r1, double *ks) {
+    const long row = o->N / (o->D == 2 ? o->p.ny : o->p.nz);
+    ksum k = {ks[0], ks[1]};
+    for (long c = r0 * row; c < r1 * row; c++) {
+        kadd(&k, (o->a[c] + o->p.eps_w) * o->psi[c]);
+        kadd(&k, (1.0 - o->rhoN[c] + o->p.eps_w) * o->C[c]);
+    }
+    ks[0] = k.s;
+    ks[1] = k.c;
+    return 0;
+}
+
+int ora_finish(ora_ctx *o, double s, double pre, int itp, int itc) {
+    o->last_it_psi = itp;
+    o->last_it_C = itc;
+    phase_finish(o, s, pre);
+    return 0;
+}
+
+void ora_set_M0(ora_ctx *o, double M0) {
+    o->M0 = M0;
+    o->last_pre = M0;
+}
+
+double *ora_field(ora_ctx *o, const char *name) {
+    struct {
+        const char *n;
+        double *p;
+    } t[] = {{"fR", o->fR}, {"fB", o->fB}, {"psi", o->psi}, {"C", o->C}, {"Sp", o->Sp},
+             {"Bp", o->Bp}, {"a", o->a},   {"rhoN", o->rhoN}};
+    for (unsigned k = 0; k < sizeof(t) / sizeof(t[0]); k++)
+        if (!strcmp(t[k].n, name)) return t[k].p;
+    return NULL;
 }
 
 int ora_step(ora_ctx *o, int n) {

@@ -134,6 +134,27 @@ int ora_diffuse(ora_ctx *o, const double *w, const double *x, double *Lx);
 int ora_sor(ora_ctx *o, const double *w, double h, const double *rhs,
             double *x);
 
+/* ---- a step in phases, for a grid decomposed into slabs along its slowest
+   axis (rows: y in 2D, z in 3D); one_step is exactly these in order ---- */
+/* boundaries of the two ends of axis a: 0 periodic wrap, 1 bounce-back wall,
+   2 mirror plane (default: both ends as wall[a]) */
+int ora_set_ends(ora_ctx *o, int a, int lo, int hi);
+/* k = 0: fields at t, explicit terms, collision, streaming; 1: the
+   Crank-Nicolson right-hand sides (weights of t); 2: fields at t+1; 3, 4:
+   the SOR weights of psi, of C */
+int ora_phase(ora_ctx *o, int k);
+/* one lexicographic SOR sweep of psi (which 0) or C (1) over rows [r0, r1),
+   folding the largest update and |x| into *maxd, *maxx */
+int ora_sor_rows(ora_ctx *o, int which, int r0, int r1, double *maxd, double *maxx);
+/* continue the Kahan-compensated total surfactant ks = {sum, compensation}
+   over rows [r0, r1) */
+int ora_surf_rows(ora_ctx *o, int r0, int r1, double *ks);
+/* rescale psi and C by s, keep S, B as the history, count the step */
+int ora_finish(ora_ctx *o, double s, double pre, int itp, int itc);
+void ora_set_M0(ora_ctx *o, double M0);
+/* the context's own arrays: fR, fB ([Q][N]), psi, C, Sp, Bp, a, rhoN */
+double *ora_field(ora_ctx *o, const char *name);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,15 @@ def lib():
         L.ora_step_count.argtypes = [C.c_void_p]
         L.ora_threads.restype = C.c_int
         L.ora_threads.argtypes = [C.c_int]
+        L.ora_set_ends.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+        L.ora_phase.argtypes = [C.c_void_p, C.c_int]
+        _D = C.POINTER(C.c_double)
+        L.ora_sor_rows.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, _D, _D]
+        L.ora_surf_rows.argtypes = [C.c_void_p, C.c_int, C.c_int, _D]
+        L.ora_finish.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int]
+        L.ora_set_M0.argtypes = [C.c_void_p, C.c_double]
+        L.ora_field.restype = _D
+        L.ora_field.argtypes = [C.c_void_p, C.c_char_p]
         L.ora_macro.argtypes = [C.c_void_p] + [_DP] * 10
         L.ora_lattice.argtypes = [C.c_int, C.POINTER(C.c_int),
                                   C.POINTER(C.c_int), _DP, _DP, _DP]
