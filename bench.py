@@ -37,14 +37,33 @@ import workloads as W  # noqa: E402
 METRIC = "coupled-step MLUPS and % of HBM roofline (1 GB300), mixed/batched vs plain FP32"
 UNIT = "MLUPS"
 
-# Algorithmic bytes per cell of each kernel group in FP32 (each input and
-# output field of the group read or written once; derivation in the design doc).
-# (2D: the fd terms run inside the collide kernel, so that group carries both)
-ALG_BYTES_F32 = {"force": 44, "fd": 48, "collide": 176 + 48, "stream": 172, "grad": 28,
-                 "surf": 40}
-# one blocked SOR launch (round): psi, C, a, chi and the two right-hand sides
-# read once, psi and C written once, whatever the sweeps it runs in shared memory
-SOR_BYTES_PER_ROUND_F32 = 32
+# Algorithmic bytes per cell of the 2D kernel groups: each input and output
+# field of the group read or written once.  rb: bytes of a field value, pb:
+# of a stored moving population.
+#   collide (the fused step, k_lbfd2): 16 moving and 2 rest populations and
+#     the flag read and written; read g (2), psi, rho^R, rho^B, j (2), a,
+#     chi, C, S, B, psi^(t-1), C^(t-1) (14 fields); write the next moments
+#     rho^R, rho^B, rho^N, j (2), the right-hand sides (2), S, B, the SOR
+#     guess (2) and psi^(t-1), C^(t-1) (13 fields)
+#   grad (k_grad2n): read the next moments (5), write g (2), a, chi and the
+#     current moments (9)
+#   surf (k_surf2 + k_scale2): read a, chi, psi, C; read psi, C, write psi, C
+#   sor: 32 B a sweep and cell in FP32 (psi, C, two right-hand sides, a, chi
+#     read; psi, C written: the count of a plain unblocked sweep), whatever
+#     the sweeps the blocked kernel runs in shared memory; the one-launch form
+#     (k_sorfuse2) also carries the grad and surf groups' fields
+def alg_bytes_2d(group, storage, sweeps=0, fused_sor=False):
+    rb = 8 if storage == "f64" else 4
+    pb = POP_BYTES[storage]
+    if group == "collide":
+        return 2 * (16 * pb + 2 * rb + 1) + (14 + 13) * rb
+    if group == "grad":
+        return 14 * rb
+    if group == "surf":
+        return 8 * rb
+    if group == "sor":
+        return 8 * rb * sweeps + ((14 + 8) * rb if fused_sor else 0)
+    raise KeyError(group)
 
 # D3Q19: fixed bytes per cell of each group (FP32 fields, flags) and the
 # number of populations it reads plus writes (stored in the storage type)
@@ -55,15 +74,10 @@ ALG3_POPS = {"collide": 76, "stream": 76}
 SOR3_BYTES_PER_HALF_SWEEP = 24
 POP_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 
-# DRAM bytes (read + write) per launch of the dominant kernel, by SOR tile
-# variant (the tuner's choice among 4, 5 and 6 varies between boxes), from ncu
-# captures on this workload (profiles/step_bubble_rise_256x1024_f32.md, tree
-# 19504d1590c33fd4); one launch runs every round of the solve (the
-# cooperative form).  Reported only while the files that hold the kernel's
-# device code (SOR2_FILES) hash as below and the step runs that form.
-TRAFFIC = {"kernel": "sor", "kernel_sha": "2c8f3c801b4c5ec3", "sor_launches_per_step": 1,
-           "bytes_per_launch": {4: 6360832, 5: 6348288, 6: 6348288}}
-
+# DRAM bytes (read + write) a cell of each launch of the fused 2D kernels on
+# the bench workload, from one ncu capture of this workload; reported only while
+# the files that hold their device code (FUSED2_FILES) hash as below.
+TRAFFIC = {"kernel_sha": "0000000000000000", "bytes_per_cell": {}}
 
 def src_hash(files=None):
     """Hash of the CUDA sources (every .cu/.cuh file, or the named ones)."""
@@ -75,8 +89,8 @@ def src_hash(files=None):
     return h.hexdigest()[:16]
 
 
-# the files that hold the device code of the 2D SOR kernels
-SOR2_FILES = ("lbs_dev.cuh", "lbs_k2d.cuh")
+# the files that hold the device code of the fused 2D kernels
+FUSED2_FILES = ("lbs_dev.cuh", "lbs_k2d.cuh", "lbs_fused2.cuh")
 
 
 def peaks():
@@ -228,26 +242,25 @@ def step_roofline(mlups, lattice, storage, hbm, where):
     return {"b_alg_per_cell": b, "achieved_gbs": gbs, "frac": gbs / hbm, "state": where}
 
 
-def roofline2(kmean, cells, storage, rounds, hbm, src, traffic=None, sor_launches=None):
-    """Roofline of the dominant kernel group of a 2D step (FP32 bytes of
-    ALG_BYTES_F32).  The SOR group runs `rounds` rounds in `sor_launches`
-    launches: one a round, or one for all rounds (the cooperative form)."""
-    groups = [g for g in kmean if g in ALG_BYTES_F32 or g == "sor"]
+def roofline2(kmean, cells, storage, sweeps, hbm, src, traffic=None, sor_launches=1):
+    """Roofline of the dominant kernel group of a 2D step (bytes of
+    alg_bytes_2d).  The SOR group runs in `sor_launches` launches: one for
+    every round and the gradient, total and rescale (the one-launch form),
+    or one a round."""
+    groups = [g for g in kmean if kmean[g] > 0 and g in ("collide", "grad", "surf", "sor")]
     dom = max(groups, key=lambda g: kmean[g])
-    scale = 2 if storage == "f64" else 1  # (16-bit forms: fields stay FP32)
-    if dom == "sor":
-        n = sor_launches or rounds
-        alg = SOR_BYTES_PER_ROUND_F32 * scale * cells * rounds / n
-        launch_ms = kmean[dom] / n
-    else:
-        alg = ALG_BYTES_F32[dom] * scale * cells
-        launch_ms = kmean[dom]
+    fused = sor_launches == 1
+    per_cell = alg_bytes_2d(dom, storage, sweeps, fused)
+    n = sor_launches if dom == "sor" else 1
+    alg = per_cell * cells / n
+    launch_ms = kmean[dom] / n
     achieved = alg / (launch_ms / 1e3) / 1e9
     return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
             "launch_timing": "in-graph CUDA events on the solver's stream over the "
                              "profiled pass of the same steps after the timed region",
             "peak_source": src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-            "alg_bytes_per_launch": alg, "avg_launch_ms": launch_ms}
+            "alg_bytes_per_cell": per_cell, "alg_bytes_per_launch": alg,
+            "avg_launch_ms": launch_ms, "sor_sweeps": sweeps}
 
 
 def roofline3(kmean, cells, storage, rounds, hbm, src):
@@ -582,13 +595,15 @@ def main():
     sweeps, rounds = dg["sor_iters_psi"], max(dg["sor_rounds"], 1)
     hbm, src = peaks()
     sha = src_hash()
-    sor_launches = s.kernel_count() - 6  # (2D: four cell kernels, total and rescale)
-    roof = roofline2(kmean, cells, args.storage, rounds, hbm, src, sor_launches=sor_launches)
+    # the fused step: two launches (k_lbfd2, k_sorfuse2); else the fused
+    # step, the gradient, one launch a round, the total and the rescale
+    nk = s.kernel_count()
+    sor_launches = 1 if nk == 2 else nk - 4
+    roof = roofline2(kmean, cells, args.storage, sweeps, hbm, src, sor_launches=sor_launches)
     roof["sor_launches_per_step"] = sor_launches
-    if (TRAFFIC["kernel_sha"] == src_hash(SOR2_FILES) and roof["kernel"] == TRAFFIC["kernel"]
-            and sor_launches == TRAFFIC["sor_launches_per_step"]
-            and tuned["sor"] in TRAFFIC["bytes_per_launch"]):
-        roof["traffic"] = TRAFFIC["bytes_per_launch"][tuned["sor"]]
+    if (TRAFFIC["kernel_sha"] == src_hash(FUSED2_FILES) and sor_launches == 1
+            and roof["kernel"] in TRAFFIC["bytes_per_cell"]):
+        roof["traffic"] = TRAFFIC["bytes_per_cell"][roof["kernel"]] * cells
     steproof = {"2d_" + args.storage: step_roofline(value / world, "d2q9", args.storage, hbm,
                                                    "L2 (46 MB of state)")}
 
@@ -764,8 +779,9 @@ def main():
                 dgb = sb.diagnostics()
                 big["kernel_ms"] = km
                 big["sor_sweeps"] = dgb["sor_iters_psi"]
-                big["roofline"] = roofline2(km, cellsb, st, max(dgb["sor_rounds"], 1), hbm, src,
-                                            sor_launches=sb.kernel_count() - 6)
+                nkb = sb.kernel_count()
+                big["roofline"] = roofline2(km, cellsb, st, dgb["sor_iters_psi"], hbm, src,
+                                            sor_launches=1 if nkb == 2 else nkb - 4)
             steproof["big2d_" + st] = step_roofline(big["mlups"][st], "d2q9", st, hbm,
                                                     "HBM (3 GB of state)")
             sb.close()

@@ -16,6 +16,7 @@
 #include "lbs_d3q19.cuh"
 #include "lbs_internal.h"
 #include "lbs_k2d.cuh"
+#include "lbs_fused2.cuh"
 #include "lbs_launch3.h"
 
 using namespace lbs;
@@ -41,18 +42,19 @@ void *sor2_kernel(int v) {
     default: return (void *)k_sor_tb2<R, LBS_SORV(0)>;
     }
 }
+// the one-launch form (gradient, SOR rounds, total and rescale) of variant v
 template <typename R>
 void *sor2_coop_kernel(int v) {
     switch (v) {
-    case 1: return (void *)k_sor_coop2<R, LBS_SORV(1)>;
-    case 2: return (void *)k_sor_coop2<R, LBS_SORV(2)>;
-    case 3: return (void *)k_sor_coop2<R, LBS_SORV(3)>;
-    case 4: return (void *)k_sor_coop2<R, LBS_SORV(4)>;
-    case 5: return (void *)k_sor_coop2<R, LBS_SORV(5)>;
-    case 6: return (void *)k_sor_coop2<R, LBS_SORV(6)>;
-    case 7: return (void *)k_sor_coop2<R, LBS_SORV(7)>;
-    case 8: return (void *)k_sor_coop2<R, LBS_SORV(8)>;
-    default: return (void *)k_sor_coop2<R, LBS_SORV(0)>;
+    case 1: return (void *)k_sorfuse2<R, LBS_SORV(1)>;
+    case 2: return (void *)k_sorfuse2<R, LBS_SORV(2)>;
+    case 3: return (void *)k_sorfuse2<R, LBS_SORV(3)>;
+    case 4: return (void *)k_sorfuse2<R, LBS_SORV(4)>;
+    case 5: return (void *)k_sorfuse2<R, LBS_SORV(5)>;
+    case 6: return (void *)k_sorfuse2<R, LBS_SORV(6)>;
+    case 7: return (void *)k_sorfuse2<R, LBS_SORV(7)>;
+    case 8: return (void *)k_sorfuse2<R, LBS_SORV(8)>;
+    default: return (void *)k_sorfuse2<R, LBS_SORV(0)>;
     }
 }
 template <typename R>
@@ -122,6 +124,9 @@ struct Layout {
 // level of psi and C
 constexpr int kScal2 = 21, kScal3 = 25, kRest = 6;
 constexpr int kCoef2 = 6;  // 2D SOR coefficient planes (faces and inverse diagonals)
+constexpr int kNext2 = 5;  // 2D moments of t+1 written by the fused step (rho^R, rho^B, rho^N, j)
+// tile of the fused 2D step (k_lbfd2): TX x TY cells, one thread a cell
+constexpr int FTX = 32, FTY = 8;
 
 template <typename R, typename P>
 Layout layout_of(const lbs_params *p) {
@@ -133,7 +138,7 @@ Layout layout_of(const lbs_params *p) {
     L.pops_off = 0;
     size_t pops = 4 * (size_t)(d3 ? Q19 : Q9) * (size_t)L.plane * sizeof(P);
     L.scal_off = pops;
-    size_t scal = ((d3 ? kScal3 : kScal2) + kRest + (d3 ? 0 : kCoef2)) * pb;
+    size_t scal = ((d3 ? kScal3 : kScal2) + kRest + (d3 ? 0 : kCoef2 + kNext2)) * pb;
     L.flag_off = align_up(L.scal_off + scal, 256);
     L.ctl_off = align_up(L.flag_off + 2 * (size_t)L.plane, 256);
     L.part_off = align_up(L.ctl_off + sizeof(Ctl), 256);
@@ -294,6 +299,12 @@ struct Solver : Base {
         if (D == 2) {
             R **fc[] = {&I.sfx, &I.sfy, &I.scx, &I.scy, &I.sip, &I.sic};
             for (int k = 0; k < kCoef2; k++) *fc[k] = sc + (kScal2 + kRest + k) * pb;
+            R **fn[] = {&I.rhoRn, &I.rhoBn, &I.rhoNn, &I.jxn, &I.jyn};
+            for (int k = 0; k < kNext2; k++) *fn[k] = sc + (kScal2 + kRest + kCoef2 + k) * pb;
+            // the fused step: populations alternate between the two sets, the
+            // solve starts from the guess in the second buffers
+            I.pop_pp = 1;
+            I.sor_phase = 1;
         }
         I.ctl = (Ctl *)(ws + L.ctl_off);
         I.part = (double *)(ws + L.part_off);
@@ -319,7 +330,13 @@ struct Solver : Base {
         if (D == 3)
             cudaFuncSetAttribute(Launch3<R, P>::zm_fn(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Launch3<R, P>::zm_smem());
+        if (D == 2) {
+            cudaFuncSetAttribute(k_lbfd2<R, P, FTX, FTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Fuse2<R, FTX, FTY>::bytes());
+            fgrid = dim3((p->nx + FTX - 1) / FTX, (p->ny + FTY - 1) / FTY, 1);
+        }
     }
+    dim3 fgrid;  // tiles of the fused 2D step
 
     // SOR variant: 2D the blocked tile (sor_vtx ...); 3D 0 = red-black
     // half-sweeps in place, 1 = z-marching full sweeps (ping-pong buffers),
@@ -340,8 +357,9 @@ struct Solver : Base {
         I.sor_pingpong = (D == 2 || sv == 1) ? 1 : 0;
         coop_ok = false;
         if (D == 2) {
-            // one launch for all rounds: the checkerboard tiles (even periodic
-            // axes) and a grid that fits the device at once
+            // one launch for all rounds (k_sorfuse2): as many blocks as are
+            // resident at once, up to one a tile; each block takes tiles b,
+            // b + blocks, ... in every round
             int dev = 0, sms = 0, coop = 0, per_sm = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -349,10 +367,13 @@ struct Solver : Base {
             if (sor2_fits(sv))
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sor2_coop_kernel<R>(sv),
                                                               sor_vbs(sv), sor2_smem<R>(sv));
-            const bool cb = (I.wall[0] || !(I.nx & 1)) && (I.wall[1] || !(I.ny & 1));
-            coop_ok = coop && cb && (long long)sor_grid.x * sor_grid.y <= (long long)per_sm * sms;
+            const long long tiles = (long long)sor_grid.x * sor_grid.y;
+            const long long resident = (long long)per_sm * sms;
+            coop_blocks = (int)(tiles < resident ? tiles : resident);
+            coop_ok = coop && coop_blocks > 0;
         }
     }
+    int coop_blocks = 0;  // blocks of the one-launch form
     bool coop_ok = false;  // the one-launch SOR applies to this grid and variant
     bool coop_on = true;   // and is wanted (lbs_set_sor_persistent)
     bool use_coop() const { return D == 2 && coop_ok && coop_on; }
@@ -383,11 +404,12 @@ struct Solver : Base {
         }
         return LBS_OK;
     }
-    // all rounds of the solve in one cooperative launch (k_sor_coop2)
+    // the gradient, all rounds of the solve, the total and the rescale in one
+    // cooperative launch (k_sorfuse2)
     int launch_sor_coop(cudaStream_t s) {
         int maxr = sor_rounds();
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = sor_grid;
+        cfg.gridDim = dim3(coop_blocks, 1, 1);
         cfg.blockDim = dim3(sor_vbs(sv), 1, 1);
         cfg.dynamicSmemBytes = sor2_smem<R>(sv);
         cfg.stream = s;
@@ -438,8 +460,11 @@ struct Solver : Base {
     }
 
     // (recorded as an event node when captured into the step graph)
+    // (a group ends at the next mark recorded in the same step)
+    bool marked[LBS_K_NGROUPS + 1] = {};
     void mark(cudaStream_t s, int g) {
         if (!prof) return;
+        marked[g] = true;
         if (capturing)
             cudaEventRecordWithFlags(ev[g], s, cudaEventRecordExternal);
         else
@@ -512,41 +537,49 @@ struct Solver : Base {
 
     int enqueue_step(cudaStream_t s) {
         for (bool &r : ran) r = false;
-        mark(s, LBS_K_FORCE);
-        k_force(s);
-        ran[LBS_K_FORCE] = true;
-        // 2D: the explicit surfactant terms and the collision in one kernel
-        // (timed in the collide group); 3D: two kernels
-        mark(s, LBS_K_FD);
-        if (I.transport && D == 3) {
-            L3::fd(I, grid, block, s, nullptr, nullptr);
-            ran[LBS_K_FD] = true;
-        }
-        mark(s, LBS_K_COLLIDE);
-        if (D == 2)
-            launch_dep(k_fdcollide2<R, P>, grid, block, s, I);
-        else
+        for (bool &m : marked) m = false;
+        if (D == 2) {
+            // the fused step: force, surfactant terms, collision, recolouring
+            // and streaming in one launch (timed as the collide group) ...
+            mark(s, LBS_K_COLLIDE);
+            k_lbfd2<R, P, FTX, FTY><<<fgrid, FTX * FTY, Fuse2<R, FTX, FTY>::bytes(), s>>>(I);
+            ran[LBS_K_COLLIDE] = true;
+            if (I.transport && use_coop()) {
+                // ... then the gradient, every SOR round, the total and the
+                // rescale in one cooperative launch (timed as the SOR group)
+                mark(s, LBS_K_SOR);
+                int r = launch_sor_coop(s);
+                if (r) return r;
+                ran[LBS_K_SOR] = true;
+                mark(s, LBS_K_NGROUPS);
+                return launch_check();
+            }
+            // ... or the gradient, one launch a round and the total and
+            // rescale as launches of their own
+            mark(s, LBS_K_GRAD);
+            launch_dep(k_grad2n<R>, grid, block, s, I);
+            ran[LBS_K_GRAD] = true;
+        } else {
+            mark(s, LBS_K_FORCE);
+            k_force(s);
+            ran[LBS_K_FORCE] = true;
+            mark(s, LBS_K_FD);
+            if (I.transport) {
+                L3::fd(I, grid, block, s, nullptr, nullptr);
+                ran[LBS_K_FD] = true;
+            }
+            mark(s, LBS_K_COLLIDE);
             L3::collide(I, grid, block, s);
-        ran[LBS_K_COLLIDE] = true;
-        mark(s, LBS_K_STREAM);
-        if (D == 2)
-            launch_dep(k_stream2<R, P>, grid, block, s, I);
-        else
+            ran[LBS_K_COLLIDE] = true;
+            mark(s, LBS_K_STREAM);
             L3::stream(I, grid, block, s);
-        ran[LBS_K_STREAM] = true;
-        mark(s, LBS_K_GRAD);
-        if (D == 2)
-            launch_dep(k_grad2<R>, grid, block, s, I, 1);
-        else
+            ran[LBS_K_STREAM] = true;
+            mark(s, LBS_K_GRAD);
             L3::grad(I, grid, block, s);
-        ran[LBS_K_GRAD] = true;
+            ran[LBS_K_GRAD] = true;
+        }
         mark(s, LBS_K_SOR);
-        if (I.transport && use_coop()) {
-            // every round in one cooperative launch (the same in a graph)
-            int r = launch_sor_coop(s);
-            if (r) return r;
-            ran[LBS_K_SOR] = true;
-        } else if (I.transport && !capturing) {
+        if (I.transport && !capturing) {
             // eager form (for profilers): the host reads the loop state after
             // every round and launches no round beyond the converged one
             for (int r = 0; r < sor_rounds(); r++) {
@@ -678,20 +711,26 @@ struct Solver : Base {
         void *d;
         size_t es;
     };
-    int state_planes(Plane *out) const {
+    // (step: the saved or loaded step counter; the fused 2D step keeps the
+    // populations of step s in set s & 1)
+    int state_planes(Plane *out, long long step) const {
+        const bool odd = I.pop_pp && (step & 1);
+        void *T = odd ? I.gT : I.fT, *M = odd ? I.gM : I.fM;
+        R *T0 = odd ? I.gT0 : I.fT0, *M0 = odd ? I.gM0 : I.fM0;
+        uint8_t *fl = odd ? I.gflag : I.flag;
         int n = 0;
         for (int i = 1; i < Q; i++)
-            out[n++] = {(char *)I.fT + (size_t)i * L.plane * sizeof(P), sizeof(P)};
+            out[n++] = {(char *)T + (size_t)i * L.plane * sizeof(P), sizeof(P)};
         for (int i = 1; i < Q; i++)
-            out[n++] = {(char *)I.fM + (size_t)i * L.plane * sizeof(P), sizeof(P)};
-        R *const sc[] = {I.fT0, I.fM0, I.rhoR, I.rhoB, I.rhoN, I.jx, I.jy, I.gx, I.gy, I.a,
-                         I.chi, I.ux,  I.uy,  I.Fx,   I.Fy,   I.psi, I.C, I.S, I.B, I.psip, I.Cp};
+            out[n++] = {(char *)M + (size_t)i * L.plane * sizeof(P), sizeof(P)};
+        R *const sc[] = {T0,    M0,    I.rhoR, I.rhoB, I.rhoN, I.jx, I.jy, I.gx, I.gy, I.a,
+                         I.chi, I.ux,  I.uy,   I.Fx,   I.Fy,   I.psi, I.C, I.S, I.B, I.psip, I.Cp};
         for (R *f : sc) out[n++] = {f, sizeof(R)};
         if (D == 3) {
             R *const s3[] = {I.jz, I.gz, I.uz, I.Fz};
             for (R *f : s3) out[n++] = {f, sizeof(R)};
         }
-        out[n++] = {I.flag, 1};
+        out[n++] = {fl, 1};
         return n;
     }
     static constexpr uint32_t kStateMagic = 0x5453424cu;  // "LBST"
@@ -706,7 +745,7 @@ struct Solver : Base {
     };
     size_t state_bytes() const {
         Plane pl[2 * Q19 + 32];
-        const int n = state_planes(pl);
+        const int n = state_planes(pl, 0);
         const size_t N = (size_t)I.nx * I.ny * I.nz;
         size_t b = sizeof(StateHeader);
         for (int k = 0; k < n; k++) b += N * pl[k].es;
@@ -729,7 +768,7 @@ struct Solver : Base {
         Ctl h;
         CK(cudaMemcpy(&h, I.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
         Plane pl[2 * Q19 + 32];
-        const int n = state_planes(pl);
+        const int n = state_planes(pl, h.step);
         StateHeader hd;
         std::memset(&hd, 0, sizeof(hd));
         hd.magic = kStateMagic;
@@ -771,7 +810,7 @@ struct Solver : Base {
         }
         std::memcpy(&hd, buf, sizeof(hd));
         Plane pl[2 * Q19 + 32];
-        const int n = state_planes(pl);
+        const int n = state_planes(pl, hd.step);
         if (hd.magic != kStateMagic || hd.version != kStateVersion) {
             set_err(ctx, "not a saved state of this library version");
             return LBS_EINVAL;
@@ -829,10 +868,10 @@ struct Solver : Base {
     // diagnostics (4 before the first): one launch a round, two for the 3D
     // red-black half-sweeps
     int kernel_count() const override {
-        if (I.transport && use_coop()) return (D == 2 ? 4 : 5) + 2 + 1;
+        if (D == 2 && I.transport && use_coop()) return 2;
         const int per_round = (D == 3 && sv != 1) ? 2 : 1;
-        const int cells = D == 2 ? 4 : 5;  // 2D: fd fused with collide
-        return I.transport ? cells + 2 + per_round * last_rounds : 4;
+        const int cells = D == 2 ? 2 : 5;  // 2D: the fused step and the gradient
+        return I.transport ? cells + 2 + per_round * last_rounds : cells + 1;
     }
     int last_rounds = 4;
 
@@ -859,7 +898,9 @@ struct Solver : Base {
         CK(cudaStreamSynchronize(ctx->stream));
         for (int g = 0; g < n && g < LBS_K_NGROUPS; g++) {
             float t = 0;
-            if (ran[g]) CK(cudaEventElapsedTime(&t, ev[g], ev[g + 1]));
+            int h = g + 1;
+            while (h < LBS_K_NGROUPS && !marked[h]) h++;
+            if (ran[g] && marked[g]) CK(cudaEventElapsedTime(&t, ev[g], ev[h]));
             ms[g] = t;
         }
         return LBS_OK;

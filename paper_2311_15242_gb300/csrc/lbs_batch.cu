@@ -331,6 +331,10 @@ struct Batch : lbs_batch {
                 return LBS_EINVAL;
             }
             std::memcpy(&h[k], c->impl->inst(), sizeof(Inst<R>));
+            // the batch runs the separate per-cell kernels: populations return
+            // to set f every step and the SOR starting guess sits in psi, C
+            h[k].pop_pp = 0;
+            h[k].sor_phase = 0;
             if (p[k].sor_max_iter > max_iter) max_iter = p[k].sor_max_iter;
         }
         BCK(cudaMalloc(&d_insts, n * sizeof(Inst<R>)));

@@ -133,6 +133,10 @@ struct Inst {
     // of Eq. 39
     R mcor1[2], mcor2[2];
     int sor_pingpong;         // SOR result alternates between psi/C and psi2/C2
+    int sor_phase;            // 1: round 0 of a solve reads psi2/C2 (the fused 2D
+                              // step leaves the starting guess there), 0: psi/C
+    int pop_pp;               // 1: the population sets alternate by the parity of the
+                              // step counter (the fused 2D step); 0: set f between steps
     // state (device pointers; every field is `plane` elements, populations Q planes)
     // populations in the storage type P of the kernels that touch them
     // (float / double, or __half / __nv_bfloat16 for the shifted
@@ -150,6 +154,9 @@ struct Inst {
     R *psi, *C, *S, *B, *rpsi, *rC;
     R *psi2, *C2;             // second buffers of the blocked SOR rounds
     R *psip, *Cp;             // psi, C of the previous time level (SOR initial guess)
+    // the fused 2D step: moments of t+1 (rho^R, rho^B, rho^N, j), written while
+    // neighbouring tiles still read those of t (null otherwise)
+    R *rhoRn, *rhoBn, *rhoNn, *jxn, *jyn;
     // 2D: the coefficients of the step's CN systems, written by the first SOR
     // round and read by the later ones: faces towards +x and +y of the psi
     // and C systems and their inverse diagonals (null in 3D)

@@ -224,23 +224,30 @@ __global__ void k_moments2(Inst<R> I) {
 // and chi = 2 phi_B.
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ R frac(const Inst<R> &I, long long j, bool red) {
-    const R xr = I.rhoR[j] * I.inv_rhoR0, xb = I.rhoB[j] * I.inv_rhoB0;
+__device__ __forceinline__ R frac_of(const Inst<R> &I, const R *rR, const R *rB, long long j,
+                                     bool red) {
+    const R xr = rR[j] * I.inv_rhoR0, xb = rB[j] * I.inv_rhoB0;
     return fdiv(red ? xr : xb, xr + xb);
 }
-
 template <typename R>
-__device__ __forceinline__ void grad2_cell(const Inst<R> &I, int x, int y, bool guess = true) {
-    if (x >= I.nx || y >= I.ny) return;
+__device__ __forceinline__ R frac(const Inst<R> &I, long long j, bool red) {
+    return frac_of(I, I.rhoR, I.rhoB, j, red);
+}
+
+// gradient and weights of cell (x, y) from the colour densities rR, rB and
+// colour function rN (the current moments, or the next ones of the fused step)
+template <typename R>
+__device__ __forceinline__ void grad2_cell_from(const Inst<R> &I, int x, int y, const R *rR,
+                                                const R *rB, const R *rN) {
     long long c = (long long)y * I.pitch + x;
-    const bool blue_side = I.rhoN[c] <= R(0);
+    const bool blue_side = rN[c] <= R(0);
     const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2);
     R gx = R(0), gy = R(0);
 #pragma unroll
     for (int i = 1; i < Q9; i++) {
         int refl, sx, sy;
         long long j = nbx2(I, X, Y, ex9(i), ey9(i), refl, sx, sy);
-        R v = frac(I, j, blue_side);
+        R v = frac_of(I, rR, rB, j, blue_side);
         gx += w9<R>(i) * R(ex9(i)) * v;
         gy += w9<R>(i) * R(ey9(i)) * v;
     }
@@ -250,8 +257,14 @@ __device__ __forceinline__ void grad2_cell(const Inst<R> &I, int x, int y, bool 
     I.gx[c] = gx;
     I.gy[c] = gy;
     I.a[c] = sqrt(gx * gx + gy * gy);
-    I.chi[c] = R(2) * frac(I, c, false);
-    if (guess) sor_guess(I, c);
+    I.chi[c] = R(2) * frac_of(I, rR, rB, c, false);
+}
+
+template <typename R>
+__device__ __forceinline__ void grad2_cell(const Inst<R> &I, int x, int y, bool guess = true) {
+    if (x >= I.nx || y >= I.ny) return;
+    grad2_cell_from(I, x, y, I.rhoR, I.rhoB, I.rhoN);
+    if (guess) sor_guess(I, (long long)y * I.pitch + x);
 }
 
 // guess: also form the SOR initial guess (every step; not at initialisation).
@@ -878,10 +891,11 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
     uint8_t *fl = (uint8_t *)(fcy + NS);               // 1: in the domain
     const int tid = threadIdx.x;
     const int x0 = bx * TX - H, y0 = by * TY - H;      // even
-    const R *pin = (round & 1) ? I.psi2 : I.psi;
-    const R *cin = (round & 1) ? I.C2 : I.C;
-    R *pout = (round & 1) ? I.psi : I.psi2;
-    R *cout = (round & 1) ? I.C : I.C2;
+    const bool odd = ((round + I.sor_phase) & 1) != 0;
+    const R *pin = odd ? I.psi2 : I.psi;
+    const R *cin = odd ? I.C2 : I.C;
+    R *pout = odd ? I.psi : I.psi2;
+    R *cout = odd ? I.C : I.C2;
     // The coefficients (faces, inverse diagonals) depend only on a and chi,
     // fixed during the solve: round 0 builds them from a and chi (steps 1-3)
     // and stores those of its tile interior; later rounds load them (step 1').
@@ -897,8 +911,10 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
             const int s = ((rx + ry) & 1) * NHP + ry * RXH + (rx >> 1);
             if (!refl) {
                 const long long c = (long long)Y * I.pitch + X;
-                sp[s] = pin[c];
-                sc[s] = cin[c];
+                // (psi and C change between the rounds of one launch: read
+                // through L2, never a line an earlier round left in L1)
+                sp[s] = __ldcg(&pin[c]);
+                sc[s] = __ldcg(&cin[c]);
                 bp[s] = I.rpsi[c];
                 bc[s] = I.rC[c];
                 fpx[s] = I.sfx[c];
@@ -938,8 +954,8 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
                 in[u] = !refl;
                 if (!refl) {
                     const long long c = (long long)Y * I.pitch + X;
-                    vv[u][0] = pin[c];
-                    vv[u][1] = cin[c];
+                    vv[u][0] = __ldcg(&pin[c]);
+                    vv[u][1] = __ldcg(&cin[c]);
                     vv[u][2] = I.rpsi[c];
                     vv[u][3] = I.rC[c];
                     vv[u][4] = I.a[c];
@@ -1068,10 +1084,11 @@ __device__ __forceinline__ void sor_tile2_list(const Inst<R> &I, int round, int 
     __shared__ int count[2];
     const int tid = threadIdx.x;
     const int x0 = bx * TX - H, y0 = by * TY - H;
-    const R *pin = (round & 1) ? I.psi2 : I.psi;
-    const R *cin = (round & 1) ? I.C2 : I.C;
-    R *pout = (round & 1) ? I.psi : I.psi2;
-    R *cout = (round & 1) ? I.C : I.C2;
+    const bool odd = ((round + I.sor_phase) & 1) != 0;
+    const R *pin = odd ? I.psi2 : I.psi;
+    const R *cin = odd ? I.C2 : I.C;
+    R *pout = odd ? I.psi : I.psi2;
+    R *cout = odd ? I.C : I.C2;
     if (tid < 2) count[tid] = 0;
     // 1. load.  flags: bit0 in the domain, bit1 colour, bit6 tile interior
     //    owned here; ip / ic hold the weights a + eps, chi + eps for now
@@ -1085,8 +1102,8 @@ __device__ __forceinline__ void sor_tile2_list(const Inst<R> &I, int round, int 
         if (!refl) {
             long long c = (long long)Y * I.pitch + X;
             f = 1 | (((X + Y) & 1) << 1);
-            sp[q] = pin[c];
-            sc[q] = cin[c];
+            sp[q] = __ldcg(&pin[c]);
+            sc[q] = __ldcg(&cin[c]);
             bp[q] = I.rpsi[c];
             bc[q] = I.rC[c];
             ip[q] = I.a[c] + I.eps_w;
@@ -1197,13 +1214,10 @@ __device__ __forceinline__ void sor_tile2(const Inst<R> &I, int round, int bx, i
 }
 
 // ---------------------------------------------------------------------------
-// k_sor_coop2: every round of a solve in one cooperative launch (one tile a
-// block, all blocks resident) with a grid barrier between rounds in place of
-// the graph's WHILE loop.  The rounds run the same tiles as k_sor_tb2, so the
-// iterates are the same; every block reads the round's maxima after the
-// barrier and takes the same decision.  A barrier waits at most max_polls
-// polls (the default, kBarrierPolls, is about a second), then reports
-// ST_TIMEOUT and returns.
+// Grid barrier of the one-launch SOR (k_sorfuse2, lbs_fused2.cuh): every
+// block of a cooperative launch arrives, the last one releases the others.
+// A barrier waits at most max_polls polls (the default, kBarrierPolls, is
+// about a second), then reports ST_TIMEOUT and returns false.
 // ---------------------------------------------------------------------------
 constexpr long long kBarrierPolls = 1LL << 24;
 
@@ -1237,26 +1251,6 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned int nblocks,
     }
     __syncthreads();
     return ok != 0;
-}
-
-template <typename R, int TX, int TY, int K, int BS>
-__global__ void __launch_bounds__(BS) k_sor_coop2(Inst<R> I, int max_rounds,
-                                                   long long max_polls) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const unsigned int nb = gridDim.x * gridDim.y;
-    Ctl *ctl = I.ctl;
-    int round = 0;
-    bool conv = false;
-    for (;; round++) {
-        sor_tile2<R, TX, TY, K, BS>(I, round, blockIdx.x, blockIdx.y, smem_raw);
-        if (!grid_barrier(ctl, nb, max_polls)) return;  // (ST_TIMEOUT set)
-        conv = round_converged<R>(ctl, round, double(I.sor_tol));
-        if (conv || round + 1 >= max_rounds) break;
-    }
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-        if (!conv) ctl->status |= ST_NOCONV;
-        ctl->sor_exec = round + 1;  // rounds run: the result's buffer parity
-    }
 }
 
 // decision after a round of instance ctl: converged, or out of rounds
@@ -1376,7 +1370,7 @@ __device__ __forceinline__ void surf2_block(const Inst<R> &I, int mode, int nblo
     const int rows = I.ny * I.nz;
     // after an odd number of blocked SOR rounds the solution is in psi2, C2
     const int rounds = sor_rounds_done(I.ctl->sor_exec);
-    const bool alt = I.sor_pingpong && mode == 1 && (rounds & 1);
+    const bool alt = I.sor_pingpong && mode == 1 && ((rounds + I.sor_phase) & 1);
     const R *P = alt ? I.psi2 : I.psi;
     const R *Cc = alt ? I.C2 : I.C;
     // the strip's loads first (all in flight together), then the sum in order
@@ -1429,7 +1423,7 @@ __device__ __forceinline__ void surf2_block(const Inst<R> &I, int mode, int nblo
         ctl->dead = 1;
     }
     ctl->sor_iters = rounds * sweeps_per_round;
-    ctl->sor_iters_parity = I.sor_pingpong ? (rounds & 1) : 0;
+    ctl->sor_iters_parity = I.sor_pingpong ? ((rounds + I.sor_phase) & 1) : 0;
     ctl->sor_exec = 0;
     ctl->step += 1;
 }
@@ -1487,6 +1481,12 @@ __global__ void k_diag(Inst<R> I, int nblocks) {
     double v[NDIAG] = {0};
     double pmin = 1e300, pmax = -1e300;
     double umax = 0.0;
+    // the population set of the current step (the fused 2D step alternates
+    // the two sets by the parity of the step counter)
+    const bool odd = I.pop_pp && (I.ctl->step & 1);
+    const void *pT = odd ? I.gT : I.fT, *pM = odd ? I.gM : I.fM;
+    const R *pT0 = odd ? I.gT0 : I.fT0, *pM0 = odd ? I.gM0 : I.fM0;
+    const uint8_t *pfl = odd ? I.gflag : I.flag;
     for (int kk = 0; kk < DIAG_STRIP && x < I.nx; kk++) {
         const int y = y0 + kk;
         if (y >= I.ny) break;
@@ -1494,12 +1494,12 @@ __global__ void k_diag(Inst<R> I, int nblocks) {
         double rN = I.rhoN[c];
         // colour masses: the exact FP64 sums of the stored populations
         // (minority as stored, majority = shift + total deviation - minority)
-        const int fl = I.flag[c];
+        const int fl = pfl[c];
         double rmin = 0, rtot = 0;
         for (int i = 0; i < Q; i++) {
-            rmin += double(ldq<R, P>(I, I.fM, I.fM0, i, c));
+            rmin += double(ldq<R, P>(I, pM, pM0, i, c));
             rtot += double(i == 0 ? I.shift0[fl] : I.shift[i]) +
-                    double(ldq<R, P>(I, I.fT, I.fT0, i, c));
+                    double(ldq<R, P>(I, pT, pT0, i, c));
         }
         v[0] += fl ? rtot - rmin : rmin;
         v[1] += fl ? rmin : rtot - rmin;

@@ -1,20 +1,19 @@
 """The batched sweep (lbs_batch_*) against the FP64 oracle and against
 single-instance contexts.
 
-The batch runs the same per-cell bodies and the same SOR iterates as a
-single-instance context, whatever its tile shapes.  FP64 results match the
-oracle to 1e-9 per instance.  In FP32 the batched kernels are separate
-compilations of those bodies (the compiler may fuse a different set of
-multiply-adds), so batch and single-instance results agree to FP32 rounding
-(1e-5 after 20 steps, the FP32 parity tolerance of rho and phi), not
-bitwise; the SOR round counts agree."""
+The batch runs the per-cell kernels (force, fd + collision, streaming,
+gradient) and the same SOR iterates as a single-instance context, whatever
+its tile shapes; a single 2D context runs the fused tile kernel of the same
+step.  FP64 results match the oracle to 1e-9 per instance.  In FP32 the two
+forms round differently, so batch and single-instance results agree to FP32
+rounding (F32_IMPL_TOL), not bitwise; the SOR round counts agree."""
 import numpy as np
 import pytest
 
 import workloads as W
 from oracle.ora import Oracle
 
-from test_parity_gpu import F32_TOL, errors, within
+from test_parity_gpu import F32_IMPL_TOL, F32_TOL, errors, within
 
 pytestmark = pytest.mark.gpu
 
@@ -74,7 +73,7 @@ def test_batch_equals_single_instances(tiles):
         s.step(20)
         err = errors(s.fields(), b.fields(k))
         print(tiles, k, {key: "%.1e" % v for key, v in err.items()})
-        assert max(err.values()) <= 1e-5, (tiles, k, err)
+        assert within(err, F32_IMPL_TOL), (tiles, k, err)
         ds = s.diagnostics()
         assert ds["sor_rounds"] == db[k]["sor_rounds"]
         assert ds["mass_R"] == pytest.approx(db[k]["mass_R"], rel=1e-7)
@@ -198,7 +197,7 @@ def test_batch_wide_halo_variants(sor):
         s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
         s.step(16)
         err = errors(s.fields(), b.fields(k))
-        assert max(err.values()) <= 1e-5, (sor, k, err)
+        assert within(err, F32_IMPL_TOL), (sor, k, err)
         s.close()
     b.close()
 
@@ -228,6 +227,6 @@ def test_batch_four_sweep_variants(sor):
         s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
         s.step(16)
         err = errors(s.fields(), b.fields(k))
-        assert max(err.values()) <= 1e-5, (sor, k, err)
+        assert within(err, F32_IMPL_TOL), (sor, k, err)
         s.close()
     b.close()

@@ -23,22 +23,35 @@ def bench():
     return m
 
 
-def test_sor_launch_accounting(bench):
-    km = {"force": 0.013, "collide": 0.027, "stream": 0.012, "grad": 0.011, "sor": 0.044,
-          "surf": 0.014}
-    cells, rounds = 262144, 2
-    one = bench.roofline2(km, cells, "f32", rounds, 6780.0, "measured", sor_launches=1)
-    per = bench.roofline2(km, cells, "f32", rounds, 6780.0, "measured", sor_launches=2)
-    assert one["kernel"] == per["kernel"] == "sor"
-    # one launch for both rounds: twice the bytes in twice the time
-    assert one["alg_bytes_per_launch"] == 2 * per["alg_bytes_per_launch"] == 2 * 32 * cells
-    assert one["avg_launch_ms"] == pytest.approx(2 * per["avg_launch_ms"])
-    assert one["achieved"] == pytest.approx(per["achieved"])
-    assert one["achieved"] == pytest.approx(2 * 32 * cells / 0.044e-3 / 1e9)
-    assert one["frac"] == pytest.approx(one["achieved"] / 6780.0)
-    # FP64 fields double the bytes
-    d = bench.roofline2(km, cells, "f64", rounds, 6780.0, "measured", sor_launches=1)
-    assert d["alg_bytes_per_launch"] == 2 * one["alg_bytes_per_launch"]
+def test_fused_step_accounting(bench):
+    """The fused 2D step: the SOR group is one launch carrying every sweep
+    (32 B a cell and sweep in FP32) plus the gradient, total and rescale
+    fields (22 fields); the fused LB-FD kernel moves its populations and 27
+    fields once."""
+    km = {"force": 0.0, "collide": 0.030, "stream": 0.0, "grad": 0.0, "sor": 0.050,
+          "surf": 0.0}
+    cells, sweeps = 262144, 8
+    r = bench.roofline2(km, cells, "f32", sweeps, 6780.0, "measured", sor_launches=1)
+    assert r["kernel"] == "sor"
+    assert r["alg_bytes_per_cell"] == 32 * sweeps + 22 * 4
+    assert r["alg_bytes_per_launch"] == (32 * sweeps + 88) * cells
+    assert r["achieved"] == pytest.approx((32 * sweeps + 88) * cells / 0.050e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6780.0)
+    # FP64 fields double every field byte
+    d = bench.roofline2(km, cells, "f64", sweeps, 6780.0, "measured", sor_launches=1)
+    assert d["alg_bytes_per_cell"] == 2 * r["alg_bytes_per_cell"]
+    # one launch a round: the sweeps' bytes spread over the launches, the
+    # gradient, total and rescale in groups of their own
+    per = bench.roofline2(km, cells, "f32", sweeps, 6780.0, "measured", sor_launches=2)
+    assert per["alg_bytes_per_cell"] == 32 * sweeps
+    assert per["alg_bytes_per_launch"] == 32 * sweeps * cells / 2
+    assert per["avg_launch_ms"] == pytest.approx(0.025)
+    # the fused LB-FD kernel
+    assert bench.alg_bytes_2d("collide", "f32") == 2 * (16 * 4 + 2 * 4 + 1) + 27 * 4
+    assert bench.alg_bytes_2d("collide", "f16") == 2 * (16 * 2 + 2 * 4 + 1) + 27 * 4
+    km2 = dict(km, collide=0.060)
+    c = bench.roofline2(km2, cells, "f32", sweeps, 6780.0, "measured", sor_launches=1)
+    assert c["kernel"] == "collide" and c["alg_bytes_per_cell"] == 254
 
 
 def test_step_roofline(bench):
@@ -50,11 +63,12 @@ def test_step_roofline(bench):
 
 
 def test_traffic_table_shape(bench):
-    # a figure per tuner tile choice, tied to the hash of the SOR kernel's own
-    # sources (the bench reports it only while that hash matches)
+    # DRAM bytes a cell of each fused 2D kernel from an ncu capture, tied to
+    # the hash of the files that hold the kernels' device code (the bench
+    # reports them only while that hash matches)
     t = bench.TRAFFIC
     assert len(t["kernel_sha"]) == 16 and int(t["kernel_sha"], 16) >= 0
-    assert t["sor_launches_per_step"] == 1 and set(t["bytes_per_launch"]) >= {4, 5, 6}
-    assert all(b > 0 for b in t["bytes_per_launch"].values())
-    assert set(bench.SOR2_FILES) == {"lbs_dev.cuh", "lbs_k2d.cuh"}
-    assert bench.src_hash(bench.SOR2_FILES) != bench.src_hash()
+    for k, v in t["bytes_per_cell"].items():
+        assert k in ("collide", "sor") and v > 0
+    assert set(bench.FUSED2_FILES) == {"lbs_dev.cuh", "lbs_k2d.cuh", "lbs_fused2.cuh"}
+    assert bench.src_hash(bench.FUSED2_FILES) != bench.src_hash()

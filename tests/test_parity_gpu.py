@@ -21,6 +21,12 @@ pytestmark = pytest.mark.gpu
 
 FIELDS = ("rho", "u", "phi", "psi", "C")
 F32_TOL = {"rho": 1e-5, "phi": 1e-5, "u": 1e-4, "psi": 1e-4, "C": 1e-4}
+# two FP32 forms of the same step (the fused tile kernel against the separate
+# per-cell kernels of the batch, or the two SOR launch forms, whose totals sum
+# in different orders) agree to their rounding; the velocity, carried by the
+# curvature (a second difference of the FP32 colour field), spreads it most
+# (measured 5e-6 to 1.03e-5 after 16-25 steps); FP64 agrees to 1e-12
+F32_IMPL_TOL = {"rho": 1e-5, "phi": 1e-5, "u": 3e-5, "psi": 1e-5, "C": 1e-5}
 
 
 def within(err, tol):
@@ -284,10 +290,13 @@ def test_every_blocked_sor_variant_matches_oracle(variant):
 
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-6)])
 def test_one_launch_sor_equals_round_launches(storage, tol):
-    """Every SOR round of a solve in one cooperative launch (grid barrier
-    between rounds, lbs_set_sor_persistent on) and one launch a round in the
-    graph's loop run the same tile rounds: the fields agree to rounding after
-    25 steps, and the step launches a single SOR kernel."""
+    """Every SOR round of a solve in one cooperative launch (the gradient,
+    the rounds, the total and the rescale with grid barriers between them,
+    lbs_set_sor_persistent on) and one launch a round in the graph's loop
+    with the gradient, total and rescale as launches of their own run the
+    same tile rounds: the fields agree to rounding after 25 steps (the two
+    forms sum the total in different orders), and the fused step launches
+    two kernels."""
     cfg = droplet()
     f = W.initial_fields(cfg, seed=11, noise=0.02, u0=1e-4)
     out, count = {}, {}
@@ -303,8 +312,11 @@ def test_one_launch_sor_equals_round_launches(storage, tol):
         assert d["sor_iters_psi"] >= 4, d
         s.close()
     err = errors(out[False], out[True])
-    assert max(err.values()) <= tol, err
-    assert count[True] == 4 + 2 + 1 and count[False] > count[True], count
+    if storage == "f32":
+        assert within(err, F32_IMPL_TOL), err
+    else:
+        assert max(err.values()) <= tol, err
+    assert count[True] == 2 and count[False] > count[True], count
 
 
 def test_one_launch_sor_wait_limit_reports_timeout():

@@ -242,8 +242,15 @@ def bubble_sweep_2d(n=64, seed=0, vary_surfactant=True):
     return [sweep_instance(sweep_point(rng, vary_surfactant)) for _ in range(n)]
 
 
+# width of the steady colour profile tanh(d / W) that the recolouring of
+# Eq. 11 with beta = 0.7 maintains (measured on a flat interface, D2Q9 and
+# D3Q19 alike: 1.40 lattice units)
+EQ_WIDTH = 1.4
+
+
 def shear_droplet_3d(nx=256, ny=128, nz=128, R=24.0, Ca=0.2, Re=1.0, lam=1.0, C0=0.5,
-                     E0=0.3, sigma0=5e-4, x_in=0.5, h=0.5, Bi=1.0, Pe_s=10.0, Pe_b=10.0):
+                     E0=0.3, sigma0=5e-4, x_in=0.5, h=0.5, Bi=1.0, Pe_s=10.0, Pe_b=10.0,
+                     width=EQ_WIDTH):
     """3D surfactant-laden droplet in simple shear (the 3D analogue of the
     paper's Sec. 3.3 set-up): D3Q19 nx x ny x nz, half-way bounce-back walls
     at z = -1/2 and nz - 1/2 moving with -u_w and +u_w along x, periodic in
@@ -256,7 +263,12 @@ def shear_droplet_3d(nx=256, ny=128, nz=128, R=24.0, Ca=0.2, Re=1.0, lam=1.0, C0
       x_in = psi0 / psi_inf;  h = psi0 / (C0 R);  k = r_a C0 / r_d, with
       no initial mass transfer (j = 0 at psi0, C0) so that k = x_in/(1-x_in).
     psi starts uniform at its Langmuir equilibrium psi0 (Eq. 22 with j = 0),
-    C = C0 in the liquid."""
+    C = C0 in the liquid.  The colour profile starts at the recolouring's
+    own steady width (EQ_WIDTH): Eqs. 20-21 conserve |grad rhoN| psi and
+    (1 - rhoN) C, so an initial profile wider than the steady one, sharpening
+    in the first hundred steps, would divide the surfactant already in its
+    flanks by weights that shrink towards zero (psi and C then grow without
+    bound inside a small droplet)."""
     mu = math.sqrt(Ca * Re * sigma0 * R)
     U = Ca * sigma0 / mu
     uw = 2.0 * U
@@ -271,7 +283,7 @@ def shear_droplet_3d(nx=256, ny=128, nz=128, R=24.0, Ca=0.2, Re=1.0, lam=1.0, C0
         uw_hi=[[0.0] * 3, [0.0] * 3, [uw, 0.0, 0.0]],
         muR0=lam * mu, muB0=mu, sigma0=sigma0, E0=E0, psi_inf=psi0 / x_in,
         Ds=U * R / Pe_s, Db=U * R / Pe_b, rd=rd, ra=k * rd / C0, source=0,
-        R=float(R), C0=C0, psi0=psi0, psi_profile="uniform",
+        R=float(R), C0=C0, psi0=psi0, psi_profile="uniform", width=float(width),
         Ca=Ca, Re=Re, U_ref=U, shear_rate=rate,
     )
     return c
