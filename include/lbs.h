@@ -175,7 +175,12 @@ int lbs_diagnostics(lbs_ctx *c, lbs_diag *d);
 
 /* ---- measurement ----------------------------------------------------- */
 
-/* Kernel groups of one time step, in launch order. */
+/* Kernel groups of one time step, in launch order.  A 2D context runs the
+ * fused step: one launch for force, surfactant terms, collision,
+ * recolouring and streaming (timed as LBS_K_COLLIDE) and one for the
+ * gradient at t+1, every SOR round, the total and the rescale (timed as
+ * LBS_K_SOR; with lbs_set_sor_persistent off, LBS_K_GRAD, LBS_K_SOR and
+ * LBS_K_SURF run as launches of their own).  A 3D context runs every group. */
 typedef enum {
     LBS_K_FORCE = 0,   /* force and velocity, Eqs. 5-10 */
     LBS_K_FD = 1,      /* explicit surfactant terms and CN right-hand sides */
@@ -262,14 +267,16 @@ int lbs_step_result(lbs_ctx *c, double *out);
  * or 4 planes of z.  Errors: LBS_EINVAL. */
 int lbs_set_sor_tile(lbs_ctx *c, int variant);
 
-/* 2D contexts: run every round of a solve's blocked SOR (Sec. 2.2) in one
- * cooperative launch with a grid barrier between rounds (on, the default),
- * or one launch a round inside the step graph's loop (off).  The rounds,
- * and so the results, are the same either way.  The one-launch form applies
- * when every periodic axis has even length and the variant's grid fits the
- * device at once; otherwise, and in 3D, the setting has no effect.  A
- * barrier that waits too long (about a second) reports LBS_ETIMEOUT.
- * Errors: LBS_EINVAL (no context), LBS_ECUDA. */
+/* 2D contexts: run the colour gradient at t+1, every round of a solve's
+ * blocked SOR (Sec. 2.2), the total surfactant and the rescale in one
+ * cooperative launch with grid barriers between them (on, the default; as
+ * many blocks as are resident at once, each taking every gridsize-th tile of
+ * a round), or the gradient, one launch a round inside the step graph's
+ * loop, the total and the rescale as launches of their own (off).  The
+ * rounds are the same either way; the totals are summed in different
+ * orders, so FP32 results agree to rounding.  In 3D the setting has no
+ * effect.  A barrier that waits too long (about a second) reports
+ * LBS_ETIMEOUT.  Errors: LBS_EINVAL (no context), LBS_ECUDA. */
 int lbs_set_sor_persistent(lbs_ctx *c, int on);
 
 /* The most polls (about 64 ns each) a block of the one-launch SOR waits at

@@ -314,6 +314,42 @@ struct Vec2<double> {
     using T = double2;
 };
 
+// ---------------------------------------------------------------------------
+// The rescale of the total surfactant (Sec. 2.2) applied to one value:
+// x (1 + d) with d = s - 1 = O(1e-7).  In double precision one fused
+// rounding.  In single precision x d is one or two ulps of x, and rounding
+// x + x d to nearest errs the same way in every cell whose value and
+// exponent agree (the whole bulk liquid), a bias of the rescaled total of up
+// to half an ulp each step; instead the result is one of the two
+// neighbouring floats, the upper with probability equal to the distance of
+// x (1 + d) above the lower, so the rounding error is zero on average.  The
+// probability draw is SplitMix64 (Steele, Lea & Flood 2014) of the cell,
+// the field and the step: reproducible, a restarted run draws the same.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+__device__ __forceinline__ double rescale_one(double x, double d, unsigned long long) {
+    return fma(x, d, x);
+}
+__device__ __forceinline__ float rescale_one(float x, double d, unsigned long long key) {
+    const double v = fma(double(x), d, double(x));
+    const float r = __double2float_rn(v);
+    if (double(r) == v) return r;
+    const float lo = double(r) < v ? r : nextafterf(r, -INFINITY);
+    const float hi = double(r) < v ? nextafterf(r, INFINITY) : r;
+    const double frac = (v - double(lo)) / (double(hi) - double(lo));
+    const double u = double(mix64(key) >> 11) * 0x1.0p-53;
+    return u < frac ? hi : lo;
+}
+// the draw of cell c, field k (0 psi, 1 C), step n
+__device__ __forceinline__ unsigned long long rescale_key(long long c, int k, long long n) {
+    return (unsigned long long)c * 2ull + (unsigned long long)k + ((unsigned long long)n << 40);
+}
+
 // division and inverse square root: IEEE in double precision; in single
 // precision the hardware approximations (about 2 ulp), whose errors are of
 // the order of the FP32 rounding of the stored fields

@@ -88,12 +88,20 @@ __device__ __forceinline__ PopSets<R> pop_sets(const Inst<R> &I) {
     return p;
 }
 
+// phases 2-6 of k_lbfd2 over the loaded tile; EDGE (block-uniform): the
+// tile's halo holds mirror images (walls, mirror planes), so the reflection
+// codes are read; without it every slot is a cell of the grid and every link
+// a plain pull.  It is tested at run time, not compiled into two versions:
+// the cells a tile recomputes from its neighbours' data (forces in the halo,
+// collisions of the ring) must come out bit for bit as the neighbour's own,
+// since the owner closes each cell's mass with the populations it streams
+// out, and a differently compiled copy could fuse other multiply-adds.
 template <typename R, typename P, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
+__device__ __forceinline__ void lbfd2_tile(const Inst<R> &I, const PopSets<R> &ps,
+                                           unsigned char *smem_raw, const bool EDGE) {
     using F = Fuse2<R, TX, TY>;
     constexpr int W3 = F::W3, N3 = F::N3, W2 = F::W2, N2 = F::N2, W1 = F::W1, N1 = F::N1;
     constexpr int NT = F::NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     R *gx3 = (R *)smem_raw, *gy3 = gx3 + N3, *ps3 = gy3 + N3, *nx3 = ps3 + N3, *ny3 = nx3 + N3;
     R *rR2 = ny3 + N3, *rB2 = rR2 + N2, *jx2 = rB2 + N2, *jy2 = jx2 + N2, *a2 = jy2 + N2;
     R *ch2 = a2 + N2, *Cs2 = ch2 + N2, *ux2 = Cs2 + N2, *uy2 = ux2 + N2, *Fx2 = uy2 + N2;
@@ -103,46 +111,6 @@ __global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
     int16_t *src1 = (int16_t *)(((uintptr_t)(flag1 + N1) + 1) & ~(uintptr_t)1);
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const PopSets<R> ps = pop_sets(I);
-    // the one-launch SOR follows: its grid barrier starts from a clear count
-    // whatever an earlier launch that gave up left behind
-    if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) I.ctl->bar_count = 0;
-
-    // 1. the halo-3 region: g (normal component mirrored at walls and
-    //    mirror planes), psi; the halo-2 part also rho^R, rho^B, j, a, chi, C
-    for (int q = tid; q < N3; q += NT) {
-        const int x = q % W3 - 3, y = q / W3 - 3;
-        int refl = 0, sx, sy;
-        const int X = map_axis(x0 + x, I.nx, I.wall[0], 1, refl, sx);
-        const int Y = map_axis(y0 + y, I.ny, I.wall[1], 2, refl, sy);
-        const bool valid = X >= 0 && X < I.nx && Y >= 0 && Y < I.ny;
-        code3[q] = (uint8_t)((refl & 3) | (sx > 0 ? RC_HX : 0) | (sy > 0 ? RC_HY : 0) |
-                             (valid ? 0 : RC_NONE));
-        const bool h2 = x >= -2 && x < TX + 2 && y >= -2 && y < TY + 2;
-        const int k = F::i2(x, y);
-        if (valid) {
-            const long long c = (long long)Y * I.pitch + X;
-            R g0 = I.gx[c], g1 = I.gy[c];
-            if (refl & 1) g0 = -g0;
-            if (refl & 2) g1 = -g1;
-            gx3[q] = g0;
-            gy3[q] = g1;
-            ps3[q] = I.psi[c];
-            if (h2) {
-                rR2[k] = I.rhoR[c];
-                rB2[k] = I.rhoB[c];
-                jx2[k] = I.jx[c];
-                jy2[k] = I.jy[c];
-                a2[k] = I.a[c];
-                ch2[k] = I.chi[c];
-                Cs2[k] = I.C[c];
-            }
-        } else {
-            gx3[q] = gy3[q] = ps3[q] = R(0);
-            if (h2) rR2[k] = rB2[k] = jx2[k] = jy2[k] = a2[k] = ch2[k] = Cs2[k] = R(0);
-        }
-    }
-    __syncthreads();
 
     // 2. interface normals n = -g / sqrt(|g|^2 + eps_n^2) (reading R3)
     const R e2 = I.eps_n * I.eps_n;
@@ -158,7 +126,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
     for (int q = tid; q < N2; q += NT) {
         const int x = q % W2 - 2, y = q / W2 - 2;
         const int k3 = F::i3(x, y);
-        if (code3[k3] & (RC_RX | RC_RY | RC_NONE)) continue;
+        if (EDGE && (code3[k3] & (RC_RX | RC_RY | RC_NONE))) continue;
         R divn = R(0), dpx = R(0), dpy = R(0);
 #pragma unroll
         for (int i = 1; i < Q9; i++) {
@@ -196,6 +164,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
     __syncthreads();
     // mirror images: the velocity and force of the source cell with the
     // normal components mirrored (the source is a cell of this tile)
+    if (EDGE) {
     for (int q = tid; q < N2; q += NT) {
         const int x = q % W2 - 2, y = q / W2 - 2;
         const uint8_t cd = code3[F::i3(x, y)];
@@ -221,6 +190,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
         Fy2[q] = f1;
     }
     __syncthreads();
+    }
 
     // 4. the explicit surfactant terms and right-hand sides of the tile's
     //    cells (Eqs. 22-28), and the SOR starting guess 2 x^t - x^(t-1)
@@ -232,14 +202,14 @@ __global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
 #pragma unroll
         for (int k = -2; k <= 2; k++) {
             int j3 = F::i3(tx + k, ty), j2 = F::i2(tx + k, ty);
-            uint8_t cd = code3[j3];
+            uint8_t cd = EDGE ? code3[j3] : 0;
             R sgn = (cd & RC_RX) ? R(-1) : R(1);
             R u = (cd & RC_RX) ? -ux2[j2] : ux2[j2];  // the source cell's own value
             Px[k + 2] = sgn * ps3[j3] * a2[j2] * u;
             Cx[k + 2] = sgn * Cs2[j2] * ch2[j2] * u;
             j3 = F::i3(tx, ty + k);
             j2 = F::i2(tx, ty + k);
-            cd = code3[j3];
+            cd = EDGE ? code3[j3] : 0;
             sgn = (cd & RC_RY) ? R(-1) : R(1);
             u = (cd & RC_RY) ? -uy2[j2] : uy2[j2];
             Py[k + 2] = sgn * ps3[j3] * a2[j2] * u;
@@ -261,7 +231,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
             const int dx = f == 0 ? -1 : (f == 1 ? 1 : 0);
             const int dy = f == 2 ? -1 : (f == 3 ? 1 : 0);
             const int j3 = F::i3(tx + dx, ty + dy), j2 = F::i2(tx + dx, ty + dy);
-            if (code3[j3] & (RC_RX | RC_RY)) continue;  // no flux through a wall
+            if (EDGE && (code3[j3] & (RC_RX | RC_RY))) continue;  // no flux through a wall
             Lp += R(0.5) * (wp + (a2[j2] + I.eps_w)) * (ps3[j3] - psi);
             Lc += R(0.5) * (wc + (ch2[j2] + I.eps_w)) * (Cs2[j2] - Cc);
         }
@@ -309,7 +279,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
             }
         }
         const int p1 = F::i1(x, y), k3 = F::i3(x, y), k2 = F::i2(x, y);
-        const uint8_t cd = code3[k3];
+        const uint8_t cd = EDGE ? code3[k3] : 0;
         if (cd & RC_NONE) {
             src1[p1] = -1;
             continue;
@@ -332,6 +302,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
         const int X = map_axis(x0 + x, I.nx, I.wall[0], 1, refl, sxx);
         const int Y = map_axis(y0 + y, I.ny, I.wall[1], 2, refl, syy);
         const long long cc = (long long)Y * I.pitch + X;
+        (void)refl;
         R fT[Q9], fM[Q9];
         const int fl = ps.sflag[cc];
         fT[0] = ps.sT0[cc];
@@ -352,14 +323,16 @@ __global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
 #pragma unroll
         for (int i = 1; i < Q9; i++) {
             const int j2 = k2 + ex9(i) + ey9(i) * W2;
-            const uint8_t cj = code3[k3 + ex9(i) + ey9(i) * W3];
             R vx = ux2[j2], vy = uy2[j2];
-            const int rj = cj & (RC_RX | RC_RY);
-            if (rj & 1) vx = -vx;  // back to the source cell's own velocity
-            if (rj & 2) vy = -vy;
-            const int sx = (rj & 1) ? ((cj & RC_HX) ? 1 : -1) : 0;
-            const int sy = (rj & 2) ? ((cj & RC_HY) ? 1 : -1) : 0;
-            ghost_u2(I, rj, sx, sy, vx, vy);
+            if (EDGE) {
+                const uint8_t cj = code3[k3 + ex9(i) + ey9(i) * W3];
+                const int rj = cj & (RC_RX | RC_RY);
+                if (rj & 1) vx = -vx;  // back to the source cell's own velocity
+                if (rj & 2) vy = -vy;
+                const int sx = (rj & 1) ? ((cj & RC_HX) ? 1 : -1) : 0;
+                const int sy = (rj & 2) ? ((cj & RC_HY) ? 1 : -1) : 0;
+                ghost_u2(I, rj, sx, sy, vx, vy);
+            }
             const R r1 = rR2[j2], r2 = rB2[j2];
             const R wx = w9<R>(i) * R(ex9(i)), wy = w9<R>(i) * R(ey9(i));
             dRx += wx * r1 * vx;
@@ -369,14 +342,23 @@ __global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
         }
         const R cR = R(1.8) * I.alphaR - R(0.8), cB = R(1.8) * I.alphaB - R(0.8);
         const R Qx = R(3) * (cR * dRx + cB * dBx), Qy = R(3) * (cR * dRy + cB * dBy);
+        // the non-conserved moments of Eq. 36 (rows e, epsilon, q_x, q_y,
+        // p_xx, p_xy) of the shifted totals, from partial sums of the axis
+        // (1-4) and diagonal (5-8) directions
         R mT[Q9];
-#pragma unroll
-        for (int jm = 0; jm < Q9; jm++) {
-            R s = R(0);
-#pragma unroll
-            for (int i = 0; i < Q9; i++)
-                if (m9(jm, i) != 0) s += R(m9(jm, i)) * fT[i];
-            mT[jm] = s;
+        {
+            const R a13 = fT[1] + fT[3], a24 = fT[2] + fT[4];
+            const R a57 = fT[5] + fT[7], a68 = fT[6] + fT[8];
+            const R S1 = a13 + a24, S2 = a57 + a68;
+            const R d13 = fT[1] - fT[3], d24 = fT[2] - fT[4];
+            const R d57 = fT[5] - fT[7], d86 = fT[8] - fT[6];
+            mT[0] = mT[3] = mT[5] = R(0);  // (not used: conserved rows)
+            mT[1] = (R(2) * S2 - S1) - R(4) * fT[0];
+            mT[2] = (S2 - R(2) * S1) + R(4) * fT[0];
+            mT[4] = (d57 + d86) - R(2) * d13;
+            mT[6] = (d57 - d86) - R(2) * d24;
+            mT[7] = a13 - a24;
+            mT[8] = a57 - a68;
         }
         const R u2 = ux * ux + uy * uy;
         const R aBm = R(3.6) * I.alphaB + R(0.4), aRm = R(3.6) * I.alphaR + R(0.4);
@@ -413,17 +395,26 @@ __global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
         for (int jm = 0; jm < Q9; jm++)
             dm[jm] = (-Sd[jm] * neq[jm] + (R(1) - R(0.5) * Sd[jm]) * (Cm[jm] + Fh[jm])) *
                      (R(1) / R(mnorm9(jm)));
+        // f + M^T dm (dm already divided by the row norms; dm_0 = 0): the
+        // columns of Eq. 36 share the axis and diagonal combinations
         R post[Q9];
+        {
+            const R A = -dm[1] - R(2) * dm[2], Bd = R(2) * dm[1] + dm[2];
+            const R X1 = dm[3] - R(2) * dm[4], Y1 = dm[5] - R(2) * dm[6];
+            const R X2 = dm[3] + dm[4], Y2 = dm[5] + dm[6];
+            post[0] = fT[0] + (R(4) * dm[2] - R(4) * dm[1]);
+            post[1] = fT[1] + ((A + X1) + dm[7]);
+            post[2] = fT[2] + ((A + Y1) - dm[7]);
+            post[3] = fT[3] + ((A - X1) + dm[7]);
+            post[4] = fT[4] + ((A - Y1) - dm[7]);
+            post[5] = fT[5] + ((Bd + X2) + (Y2 + dm[8]));
+            post[6] = fT[6] + ((Bd - X2) + (Y2 - dm[8]));
+            post[7] = fT[7] + ((Bd - X2) - (Y2 - dm[8]));
+            post[8] = fT[8] + ((Bd + X2) - (Y2 + dm[8]));
+        }
         CSum<R> rdc;
 #pragma unroll
-        for (int i = 0; i < Q9; i++) {
-            R s = fT[i];
-#pragma unroll
-            for (int jm = 0; jm < Q9; jm++)
-                if (m9(jm, i) != 0) s += R(m9(jm, i)) * dm[jm];
-            post[i] = s;
-            rdc.add(shift_of(I, i, fl) + s);
-        }
+        for (int i = 0; i < Q9; i++) rdc.add(shift_of(I, i, fl) + post[i]);
         const R rdag = rdc.value();
         const R ggx = gx3[k3], ggy = gy3[k3];
         const R seg = I.beta * rR * rB * R(3) * pk *
@@ -461,11 +452,12 @@ __global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
     m[0] = pM01[p1];
 #pragma unroll
     for (int i = 1; i < Q9; i++) {
-        const uint8_t cj = code3[k3c - ex9(i) - ey9(i) * W3];
+        const uint8_t cj = EDGE ? code3[k3c - ex9(i) - ey9(i) * W3] : 0;
         const int refl = cj & (RC_RX | RC_RY);
         const int bb = refl & I.bbmask;
-        const int src = bb ? p1 : src1[p1 - ex9(i) - ey9(i) * W1];
-        const int k = bb ? opp9(i) : mir9(i, refl);
+        const int src = EDGE ? (bb ? p1 : src1[p1 - ex9(i) - ey9(i) * W1])
+                             : p1 - ex9(i) - ey9(i) * W1;
+        const int k = EDGE ? (bb ? opp9(i) : mir9(i, refl)) : i;
         t[i] = pT1[(k - 1) * N1 + src];
         m[i] = pM1[(k - 1) * N1 + src];
         const int fj = flag1[src];
@@ -585,6 +577,65 @@ __global__ void __launch_bounds__(TX * TY, 3) k_lbfd2(Inst<R> I) {
     I.jyn[c] = mo.jy;
 }
 
+template <typename R, typename P, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, sizeof(R) == 4 ? 4 : 2) k_lbfd2(Inst<R> I) {
+    using F = Fuse2<R, TX, TY>;
+    constexpr int W3 = F::W3, N3 = F::N3, N2 = F::N2, N1 = F::N1;
+    constexpr int NT = F::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // the halo slots this phase fills (layout as in lbfd2_tile)
+    R *gx3 = (R *)smem_raw, *gy3 = gx3 + N3, *ps3 = gy3 + N3;
+    R *rR2 = ps3 + 3 * N3, *rB2 = rR2 + N2, *jx2 = rB2 + N2, *jy2 = jx2 + N2, *a2 = jy2 + N2;
+    R *ch2 = a2 + N2, *Cs2 = ch2 + N2;
+    uint8_t *code3 = (uint8_t *)(rR2 + 11 * N2 + 18 * N1);
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const PopSets<R> ps = pop_sets(I);
+    // the one-launch SOR follows: its grid barrier starts from a clear count
+    // whatever an earlier launch that gave up left behind
+    if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) I.ctl->bar_count = 0;
+
+    // 1. the halo-3 region: g (normal component mirrored at walls and
+    //    mirror planes), psi; the halo-2 part also rho^R, rho^B, j, a, chi, C
+    int near_edge = 0;  // a slot of this thread is a mirror image or has no source
+    for (int q = tid; q < N3; q += NT) {
+        const int x = q % W3 - 3, y = q / W3 - 3;
+        int refl = 0, sx, sy;
+        const int X = map_axis(x0 + x, I.nx, I.wall[0], 1, refl, sx);
+        const int Y = map_axis(y0 + y, I.ny, I.wall[1], 2, refl, sy);
+        const bool valid = X >= 0 && X < I.nx && Y >= 0 && Y < I.ny;
+        code3[q] = (uint8_t)((refl & 3) | (sx > 0 ? RC_HX : 0) | (sy > 0 ? RC_HY : 0) |
+                             (valid ? 0 : RC_NONE));
+        near_edge |= (refl & 3) | !valid;
+        const bool h2 = x >= -2 && x < TX + 2 && y >= -2 && y < TY + 2;
+        const int k = F::i2(x, y);
+        if (valid) {
+            const long long c = (long long)Y * I.pitch + X;
+            R g0 = I.gx[c], g1 = I.gy[c];
+            if (refl & 1) g0 = -g0;
+            if (refl & 2) g1 = -g1;
+            gx3[q] = g0;
+            gy3[q] = g1;
+            ps3[q] = I.psi[c];
+            if (h2) {
+                rR2[k] = I.rhoR[c];
+                rB2[k] = I.rhoB[c];
+                jx2[k] = I.jx[c];
+                jy2[k] = I.jy[c];
+                a2[k] = I.a[c];
+                ch2[k] = I.chi[c];
+                Cs2[k] = I.C[c];
+            }
+        } else {
+            gx3[q] = gy3[q] = ps3[q] = R(0);
+            if (h2) rR2[k] = rB2[k] = jx2[k] = jy2[k] = a2[k] = ch2[k] = Cs2[k] = R(0);
+        }
+    }
+    // (the tile meets a wall or mirror plane: block-uniform)
+    const bool edge = __syncthreads_or(near_edge) != 0;
+    lbfd2_tile<R, P, TX, TY>(I, ps, smem_raw, edge);
+}
+
 // ---------------------------------------------------------------------------
 // Colour gradient and weights at t+1 from the next moments, and the next
 // moments copied over the current ones (cell (x, y)).
@@ -617,7 +668,7 @@ __global__ void k_grad2n(Inst<R> I) {
 //      b, b + nblocks, ...), a grid barrier after each round, the same stop
 //      decision in every block;
 //   3. the total surfactant sum (a + eps) psi + (chi + eps) C of the result
-//      (FP32 compensated sums per thread, FP64 across threads and blocks),
+//      (products and sums in FP64),
 //      grid barrier, every block adds the block partials in the same order;
 //   4. rescale psi, C by M0 / total (Sec. 2.2) into the canonical buffers.
 // Every barrier waits at most max_polls polls, then reports ST_TIMEOUT.
@@ -628,11 +679,23 @@ __global__ void __launch_bounds__(BS) k_sorfuse2(Inst<R> I, int max_rounds, long
     const unsigned int nb = gridDim.x;
     const int tid = threadIdx.x;
     Ctl *ctl = I.ctl;
-    const long long ncell = (long long)I.nx * I.ny;
+    const long long step0 = ctl->step;  // (block 0 advances it at the end)
+    // the cells of this thread: every (nb BS)-th cell in row order from
+    // b BS + tid, walked as (x, y) with the stride split once into (sx, sy)
     const long long stride = (long long)nb * BS;
+    const int sx = int(stride % I.nx), sy = int(stride / I.nx);
+    const long long q0 = (long long)blockIdx.x * BS + tid;
+    const int x0 = int(q0 % I.nx), y0 = int(q0 / I.nx);
     // 1. gradient and weights of t+1
-    for (long long q = (long long)blockIdx.x * BS + tid; q < ncell; q += stride)
-        grad2_next_cell(I, int(q % I.nx), int(q / I.nx));
+    for (int x = x0, y = y0; y < I.ny;) {
+        grad2_next_cell(I, x, y);
+        x += sx;
+        y += sy;
+        if (x >= I.nx) {
+            x -= I.nx;
+            y++;
+        }
+    }
     if (!grid_barrier(ctl, nb, max_polls)) return;
     // 2. SOR rounds
     const int tiles_x = (I.nx + TX - 1) / TX, tiles_y = (I.ny + TY - 1) / TY;
@@ -654,17 +717,21 @@ __global__ void __launch_bounds__(BS) k_sorfuse2(Inst<R> I, int max_rounds, long
     const bool alt = ((round + I.sor_phase) & 1) != 0;
     const R *P = alt ? I.psi2 : I.psi;
     const R *Cq = alt ? I.C2 : I.C;
-    R sum = R(0), comp = R(0);
-    for (long long q = (long long)blockIdx.x * BS + tid; q < ncell; q += stride) {
-        const long long c = (q / I.nx) * I.pitch + q % I.nx;
-        const R v = (__ldcg(&I.a[c]) + I.eps_w) * __ldcg(&P[c]) +
-                    (__ldcg(&I.chi[c]) + I.eps_w) * __ldcg(&Cq[c]);
-        const R yv = v - comp;
-        const R tt = sum + yv;
-        comp = (tt - sum) - yv;
-        sum = tt;
+    // (the products in FP64, as lbs_diagnostics forms them: the rescale
+    // then holds the total that the diagnostics report; one pass a step)
+    double sum = 0.0;
+    for (int x = x0, y = y0; y < I.ny;) {
+        const long long c = (long long)y * I.pitch + x;
+        sum += double(__ldcg(&I.a[c]) + I.eps_w) * double(__ldcg(&P[c])) +
+               double(__ldcg(&I.chi[c]) + I.eps_w) * double(__ldcg(&Cq[c]));
+        x += sx;
+        y += sy;
+        if (x >= I.nx) {
+            x -= I.nx;
+            y++;
+        }
     }
-    double v[1] = {double(sum) - double(comp)};
+    double v[1] = {sum};
     double bsum[1];
     block_sum<BS, 1>(v, bsum);
     if (tid == 0) I.part[blockIdx.x] = bsum[0];
@@ -679,13 +746,18 @@ __global__ void __launch_bounds__(BS) k_sorfuse2(Inst<R> I, int max_rounds, long
     const double total = s_tot;
     const double scale = total > 0 ? ctl->M0 / total : 1.0;
     const double dscale = scale - 1.0;
-    // 4. rescale (x + x d with d = s - 1, one rounding: unbiased)
-    const R d = sizeof(R) == 4 ? R(float(dscale)) : R(dscale);
-    for (long long q = (long long)blockIdx.x * BS + tid; q < ncell; q += stride) {
-        const long long c = (q / I.nx) * I.pitch + q % I.nx;
+    // 4. rescale: x (1 + d), d = s - 1, rounded without bias (rescale_one)
+    for (int x = x0, y = y0; y < I.ny;) {
+        const long long c = (long long)y * I.pitch + x;
         const R p = __ldcg(&P[c]), r = __ldcg(&Cq[c]);
-        I.psi[c] = fma(p, d, p);
-        I.C[c] = fma(r, d, r);
+        I.psi[c] = rescale_one(p, dscale, rescale_key(c, 0, step0));
+        I.C[c] = rescale_one(r, dscale, rescale_key(c, 1, step0));
+        x += sx;
+        y += sy;
+        if (x >= I.nx) {
+            x -= I.nx;
+            y++;
+        }
     }
     if (blockIdx.x != 0) return;
     // the SOR convergence slots of the next solve start at zero (every block

@@ -878,17 +878,19 @@ __device__ __forceinline__ void sor_fold_maxima(const Inst<R> &I, int round, R v
         }
 }
 
-// checkerboard form of a tile (see above)
+// checkerboard form of a tile (see above).  The two systems are swept
+// together, so each region slot keeps its psi and C values side by side
+// (one 2-vector load a neighbour): X = (psi, C), Bv = right-hand sides,
+// Iv = inverse diagonals, FX / FY = face coefficients towards +x / +y.
 template <typename R, int TX, int TY, int K, int BS>
 __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx, int by,
                                              unsigned char *smem_raw) {
     using T = SorTile<R, TX, TY, K, BS>;
+    using V = typename Vec2<R>::T;
     constexpr int RX = T::RX, RY = T::RY, H = T::H, RXH = T::RXH, NH = T::NH, NHP = T::NHP;
     constexpr int NS = 2 * NHP;
-    R *sp = (R *)smem_raw, *sc = sp + NS, *bp = sc + NS, *bc = bp + NS;
-    R *ip = bc + NS, *ic = ip + NS;                    // 1 / diagonal
-    R *fpx = ic + NS, *fpy = fpx + NS, *fcx = fpy + NS, *fcy = fcx + NS;  // faces +x, +y
-    uint8_t *fl = (uint8_t *)(fcy + NS);               // 1: in the domain
+    V *X = (V *)smem_raw, *Bv = X + NS, *Iv = Bv + NS, *FX = Iv + NS, *FY = FX + NS;
+    uint8_t *fl = (uint8_t *)(FY + NS);                // 1: in the domain
     const int tid = threadIdx.x;
     const int x0 = bx * TX - H, y0 = by * TY - H;      // even
     const bool odd = ((round + I.sor_phase) & 1) != 0;
@@ -896,41 +898,36 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
     const R *cin = odd ? I.C2 : I.C;
     R *pout = odd ? I.psi : I.psi2;
     R *cout = odd ? I.C : I.C2;
+    const V zero = {R(0), R(0)};
     // The coefficients (faces, inverse diagonals) depend only on a and chi,
     // fixed during the solve: round 0 builds them from a and chi (steps 1-3)
     // and stores those of its tile interior; later rounds load them (step 1').
     const bool first = round == 0 || I.sfx == nullptr;
     if (!first) {
         // 1'. load psi, C, the right-hand sides and the coefficients, in row
-        //     order; zero outside the domain
+        //     order; zero outside the domain.  psi and C change between the
+        //     rounds of one launch: they are read through L2, never from a
+        //     line an earlier round left in L1.
         for (int q = tid; q < RX * RY; q += BS) {
             const int rx = q % RX, ry = q / RX;
             int refl = 0, sx, sy;
-            const int X = map_axis(x0 + rx, I.nx, I.wall[0], 1, refl, sx);
-            const int Y = map_axis(y0 + ry, I.ny, I.wall[1], 2, refl, sy);
+            const int Xc = map_axis(x0 + rx, I.nx, I.wall[0], 1, refl, sx);
+            const int Yc = map_axis(y0 + ry, I.ny, I.wall[1], 2, refl, sy);
             const int s = ((rx + ry) & 1) * NHP + ry * RXH + (rx >> 1);
             if (!refl) {
-                const long long c = (long long)Y * I.pitch + X;
-                // (psi and C change between the rounds of one launch: read
-                // through L2, never a line an earlier round left in L1)
-                sp[s] = __ldcg(&pin[c]);
-                sc[s] = __ldcg(&cin[c]);
-                bp[s] = I.rpsi[c];
-                bc[s] = I.rC[c];
-                fpx[s] = I.sfx[c];
-                fpy[s] = I.sfy[c];
-                fcx[s] = I.scx[c];
-                fcy[s] = I.scy[c];
-                ip[s] = I.sip[c];
-                ic[s] = I.sic[c];
+                const long long c = (long long)Yc * I.pitch + Xc;
+                X[s] = V{__ldcg(&pin[c]), __ldcg(&cin[c])};
+                Bv[s] = V{I.rpsi[c], I.rC[c]};
+                FX[s] = V{I.sfx[c], I.scx[c]};
+                FY[s] = V{I.sfy[c], I.scy[c]};
+                Iv[s] = V{I.sip[c], I.sic[c]};
             } else {
-                sp[s] = sc[s] = bp[s] = bc[s] = fpx[s] = fpy[s] = fcx[s] = fcy[s] = ip[s] =
-                    ic[s] = R(0);
+                X[s] = Bv[s] = FX[s] = FY[s] = Iv[s] = zero;
             }
         }
         __syncthreads();
     } else {
-        // 1. load in row order (coalesced); ip / ic hold the weights a + eps,
+        // 1. load in row order (coalesced); Iv holds the weights a + eps,
         //    chi + eps for now, zero outside the domain.  A thread loads U cells
         //    into registers before it stores any, so that their loads are in
         //    flight together (a store to shared memory would otherwise order the
@@ -948,18 +945,18 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
                 if (q >= RX * RY) continue;
                 const int rx = q % RX, ry = q / RX;
                 int refl = 0, sx, sy;
-                const int X = map_axis(x0 + rx, I.nx, I.wall[0], 1, refl, sx);
-                const int Y = map_axis(y0 + ry, I.ny, I.wall[1], 2, refl, sy);
+                const int Xc = map_axis(x0 + rx, I.nx, I.wall[0], 1, refl, sx);
+                const int Yc = map_axis(y0 + ry, I.ny, I.wall[1], 2, refl, sy);
                 ss[u] = ((rx + ry) & 1) * NHP + ry * RXH + (rx >> 1);
                 in[u] = !refl;
                 if (!refl) {
-                    const long long c = (long long)Y * I.pitch + X;
+                    const long long c = (long long)Yc * I.pitch + Xc;
                     vv[u][0] = __ldcg(&pin[c]);
                     vv[u][1] = __ldcg(&cin[c]);
                     vv[u][2] = I.rpsi[c];
                     vv[u][3] = I.rC[c];
-                    vv[u][4] = I.a[c];
-                    vv[u][5] = I.chi[c];
+                    vv[u][4] = __ldcg(&I.a[c]);
+                    vv[u][5] = __ldcg(&I.chi[c]);
                 }
             }
 #pragma unroll
@@ -967,14 +964,11 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
                 const int s = ss[u];
                 if (s < 0) continue;
                 if (in[u]) {
-                    sp[s] = vv[u][0];
-                    sc[s] = vv[u][1];
-                    bp[s] = vv[u][2];
-                    bc[s] = vv[u][3];
-                    ip[s] = vv[u][4] + I.eps_w;
-                    ic[s] = vv[u][5] + I.eps_w;
+                    X[s] = V{vv[u][0], vv[u][1]};
+                    Bv[s] = V{vv[u][2], vv[u][3]};
+                    Iv[s] = V{vv[u][4] + I.eps_w, vv[u][5] + I.eps_w};
                 } else {
-                    sp[s] = sc[s] = bp[s] = bc[s] = ip[s] = ic[s] = R(0);
+                    X[s] = Bv[s] = Iv[s] = zero;
                 }
                 fl[s] = in[u];
             }
@@ -991,10 +985,9 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
             const bool ex = in && rx < RX - 1 && fl[o + ((rx + 1) >> 1)];
             const bool ny = in && ry < RY - 1 && fl[o + RXH + j];
             const int e = o + ((rx + 1) >> 1), n = o + RXH + j;
-            fpx[s] = ex ? hp * R(0.5) * (ip[s] + ip[e]) : R(0);
-            fcx[s] = ex ? hc * R(0.5) * (ic[s] + ic[e]) : R(0);
-            fpy[s] = ny ? hp * R(0.5) * (ip[s] + ip[n]) : R(0);
-            fcy[s] = ny ? hc * R(0.5) * (ic[s] + ic[n]) : R(0);
+            const V ws = Iv[s], we = Iv[e], wn = Iv[n];
+            FX[s] = ex ? V{hp * R(0.5) * (ws.x + we.x), hc * R(0.5) * (ws.y + we.y)} : zero;
+            FY[s] = ny ? V{hp * R(0.5) * (ws.x + wn.x), hc * R(0.5) * (ws.y + wn.y)} : zero;
         }
         __syncthreads();
         // 3. inverse diagonals w + sum of the four faces (zero outside the domain,
@@ -1005,10 +998,12 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
             const int s = c * NHP + r, o = (1 - c) * NHP + ry * RXH;
             if (!fl[s]) continue;
             const int w = o + ((rx - 1) >> 1), so = o - RXH + j;
-            const R sp_ = fpx[s] + fpy[s] + (rx > 0 ? fpx[w] : R(0)) + (ry > 0 ? fpy[so] : R(0));
-            const R sc_ = fcx[s] + fcy[s] + (rx > 0 ? fcx[w] : R(0)) + (ry > 0 ? fcy[so] : R(0));
-            ip[s] = fdiv(R(1), ip[s] + sp_);
-            ic[s] = fdiv(R(1), ic[s] + sc_);
+            const V fx = FX[s], fy = FY[s];
+            const V fxw = rx > 0 ? FX[w] : zero, fyso = ry > 0 ? FY[so] : zero;
+            const R sp_ = fx.x + fy.x + fxw.x + fyso.x;
+            const R sc_ = fx.y + fy.y + fxw.y + fyso.y;
+            const V ws = Iv[s];
+            Iv[s] = V{fdiv(R(1), ws.x + sp_), fdiv(R(1), ws.y + sc_)};
         }
         __syncthreads();
     }
@@ -1029,16 +1024,15 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
             const int s = c * NHP + ry * RXH + j, o = (1 - c) * NHP + ry * RXH;
             const int e = o + ((rx + 1) >> 1), w = o + ((rx - 1) >> 1);
             const int nn = o + RXH + j, so = o - RXH + j;
-            const R op = bp[s] + fpx[s] * sp[e] + fpy[s] * sp[nn] + fpx[w] * sp[w] +
-                         fpy[so] * sp[so];
-            const R oc = bc[s] + fcx[s] * sc[e] + fcy[s] * sc[nn] + fcx[w] * sc[w] +
-                         fcy[so] * sc[so];
-            const R p0 = sp[s], c0 = sc[s];
-            const R dp = I.omega * (op * ip[s] - p0);
-            const R dc = I.omega * (oc * ic[s] - c0);
-            const R p1 = p0 + dp, c1 = c0 + dc;
-            sp[s] = p1;
-            sc[s] = c1;
+            const V xe = X[e], xn = X[nn], xw = X[w], xso = X[so];
+            const V fx = FX[s], fy = FY[s], fxw = FX[w], fyso = FY[so];
+            const V b = Bv[s], iv = Iv[s], x0v = X[s];
+            const R op = b.x + fx.x * xe.x + fy.x * xn.x + fxw.x * xw.x + fyso.x * xso.x;
+            const R oc = b.y + fx.y * xe.y + fy.y * xn.y + fxw.y * xw.y + fyso.y * xso.y;
+            const R dp = I.omega * (op * iv.x - x0v.x);
+            const R dc = I.omega * (oc * iv.y - x0v.y);
+            const R p1 = x0v.x + dp, c1 = x0v.y + dc;
+            X[s] = V{p1, c1};
             if (last && rx >= H && rx < H + TX && ry >= H && ry < H + TY && x0 + rx < I.nx &&
                 y0 + ry < I.ny) {
                 v[0] = fmax(v[0], fabs(dp));
@@ -1056,15 +1050,17 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
         if (gx >= I.nx || gy >= I.ny) continue;
         const int s = ((rx + ry) & 1) * NHP + ry * RXH + (rx >> 1);
         const long long c = (long long)gy * I.pitch + gx;
-        pout[c] = sp[s];
-        cout[c] = sc[s];
+        const V xs = X[s];
+        pout[c] = xs.x;
+        cout[c] = xs.y;
         if (first && I.sfx) {
-            I.sfx[c] = fpx[s];
-            I.sfy[c] = fpy[s];
-            I.scx[c] = fcx[s];
-            I.scy[c] = fcy[s];
-            I.sip[c] = ip[s];
-            I.sic[c] = ic[s];
+            const V fx = FX[s], fy = FY[s], iv = Iv[s];
+            I.sfx[c] = fx.x;
+            I.scx[c] = fx.y;
+            I.sfy[c] = fy.x;
+            I.scy[c] = fy.y;
+            I.sip[c] = iv.x;
+            I.sic[c] = iv.y;
         }
     }
     sor_fold_maxima<R, BS>(I, round, v);
@@ -1355,9 +1351,9 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket, unsigned int nb
 // loop that stopped stores -(rounds) - 1000000)
 __device__ __forceinline__ int sor_rounds_done(int e) { return e >= 0 ? e : -(e + 1000000); }
 
-// k_surf: every thread sums a strip of SURF_STRIP cells along y with a
-// compensated (Kahan) sum in R; strips are added in FP64 (no per-cell FP64:
-// the FP64 pipe of GB300 is narrow).
+// k_surf: every thread sums a strip of SURF_STRIP cells along y in FP64;
+// strips are added in FP64 across threads and blocks (one FP64 product pair
+// a cell and step: negligible beside the step's FP32 work).
 constexpr int SURF_STRIP = 4;
 
 // block (bx, by) of a (gdx x .) grid of blockDim-shaped blocks
@@ -1373,27 +1369,24 @@ __device__ __forceinline__ void surf2_block(const Inst<R> &I, int mode, int nblo
     const bool alt = I.sor_pingpong && mode == 1 && ((rounds + I.sor_phase) & 1);
     const R *P = alt ? I.psi2 : I.psi;
     const R *Cc = alt ? I.C2 : I.C;
-    // the strip's loads first (all in flight together), then the sum in order
-    R val[SURF_STRIP];
+    // the strip's loads first (all in flight together), then the sum in
+    // order; products and sums in FP64, as lbs_diagnostics forms them (one
+    // pass a step), so that the rescale holds the total the diagnostics report
+    double val[SURF_STRIP];
 #pragma unroll
     for (int k = 0; k < SURF_STRIP; k++) {
         const int y = y0 + k;
-        val[k] = R(0);
+        val[k] = 0.0;
         if (x < I.nx && y < rows) {
             const long long c = (long long)y * I.pitch + x;
-            val[k] = (I.a[c] + I.eps_w) * P[c] + (I.chi[c] + I.eps_w) * Cc[c];
+            val[k] = double(I.a[c] + I.eps_w) * double(P[c]) +
+                     double(I.chi[c] + I.eps_w) * double(Cc[c]);
         }
     }
-    R sum = R(0), comp = R(0);
+    double sum = 0.0;
 #pragma unroll
-    for (int k = 0; k < SURF_STRIP; k++) {
-        if (x >= I.nx || y0 + k >= rows) break;
-        const R yv = val[k] - comp;
-        const R t = sum + yv;
-        comp = (t - sum) - yv;
-        sum = t;
-    }
-    double v[1] = {double(sum) - double(comp)};
+    for (int k = 0; k < SURF_STRIP; k++) sum += val[k];
+    double v[1] = {sum};
     int b = bx + by * gdx;
     block_sum<BS, 1>(v, I.part + b);
     if (!last_block(&I.ctl->ticket, nblocks)) return;
@@ -1438,17 +1431,17 @@ template <typename R>
 __device__ __forceinline__ void scale2_cell(const Inst<R> &I, int x, int y, int z) {
     if (x >= I.nx || y >= I.ny) return;
     long long c = ((long long)z * I.ny + y) * I.pitch + x;
-    // the factor is 1 + O(1e-6): multiplying by it rounded to R would apply a
-    // quantised correction with the same bias every step; x + x d with
-    // d = s - 1 formed in double and one fused rounding is unbiased
-    const R d = sizeof(R) == 4 ? R(I.ctl->dscale_f) : R(I.ctl->dscale);
+    // x (1 + d) with d = s - 1 formed in double, rounded without bias
+    // (rescale_one); the step counter has already advanced
+    const double d = I.ctl->dscale;
+    const long long n = I.ctl->step - 1;
     // the blocked SOR leaves its result in the second buffer after an odd
     // number of rounds
     const bool alt = I.ctl->sor_iters_parity != 0;
     const R p = alt ? I.psi2[c] : I.psi[c];
     const R q = alt ? I.C2[c] : I.C[c];
-    I.psi[c] = fma(p, d, p);
-    I.C[c] = fma(q, d, q);
+    I.psi[c] = rescale_one(p, d, rescale_key(c, 0, n));
+    I.C[c] = rescale_one(q, d, rescale_key(c, 1, n));
 }
 
 template <typename R>
