@@ -184,12 +184,26 @@ class Clocks:
 def profile_case(args):
     """Small workloads stepped with individual launches, for kernel
     profilers (ncu cannot trace the kernel nodes of a graph that holds a
-    conditional node): 3d = the sheared droplet at 256 x 128 x 64, half the
-    bench's cells (state about 3.5x the L2), batch = the first 8 instances of the 64-instance sweep
-    with the bench's tiles (32 x 4, SOR variant 5)."""
+    conditional node): 2d = the bubble array on 2048 x 2048 (8 x 8 bubbles,
+    4.2 M cells, about 0.76 GB of FP32 state, 6x the L2) with the fused step,
+    3d = the sheared droplet at 256 x 128 x 64, half the bench's cells (state
+    about 3.5x the L2), batch = the first 8 instances of the 64-instance
+    sweep with the bench's tiles (32 x 4, SOR variant 5)."""
     import torch
     from paper_2311_15242_gb300 import Batch, Solver
     torch.cuda.set_device(0)
+    if args.profile_case == "2d":
+        cfg = W.bubble_array_2d(n=2048, k=8)
+        f = W.initial_fields(cfg)
+        s = Solver(cfg, storage=args.storage)
+        s.set_sor_tile(4 if args.sor_tile is None else args.sor_tile)
+        s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+        s.set_graph(False)
+        s.step(args.steps)
+        s.sync()
+        print(json.dumps({"profile_case": "2d", "cells": cfg["nx"] * cfg["ny"],
+                          "steps": args.steps, "sor_sweeps": s.diagnostics()["sor_iters_psi"]}))
+        return 0
     if args.profile_case == "3d":
         cfg = W.shear_droplet_3d(nx=256, ny=128, nz=64, R=24.0)
         f = W.initial_fields(cfg)
@@ -489,7 +503,7 @@ def main():
                     help="blocked SOR variant of the 2D step (0..8) instead of tuning it")
     ap.add_argument("--sor-tile-3d", type=int, default=None,
                     help="SOR variant of the 3D step (0..2) instead of tuning it")
-    ap.add_argument("--profile-case", choices=["3d", "batch"], default=None,
+    ap.add_argument("--profile-case", choices=["2d", "3d", "batch"], default=None,
                     help="run a small workload with individual launches for kernel "
                          "profilers and exit (see profile_case)")
     ap.add_argument("--storage3d", default="bf16", choices=["f32", "f64", "f16", "bf16"])

@@ -320,34 +320,54 @@ struct Vec2<double> {
 // rounding.  In single precision x d is one or two ulps of x, and rounding
 // x + x d to nearest errs the same way in every cell whose value and
 // exponent agree (the whole bulk liquid), a bias of the rescaled total of up
-// to half an ulp each step; instead the result is one of the two
-// neighbouring floats, the upper with probability equal to the distance of
-// x (1 + d) above the lower, so the rounding error is zero on average.  The
-// probability draw is SplitMix64 (Steele, Lea & Flood 2014) of the cell,
-// the field and the step: reproducible, a restarted run draws the same.
+// to half an ulp each step; instead the result is one of the two floats
+// around x + x d (formed exactly as s + e by TwoSum), the far one with
+// probability |e| / ulp, so the rounding error is zero on average.  The draw
+// is MurmurHash3's 32-bit finaliser (Appleby) of the cell, the field and the
+// step: reproducible, a restarted run draws the same.  FP32 arithmetic only
+// (the FP64 pipe of GB300 is narrow).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
-    x += 0x9E3779B97F4A7C15ull;
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-    return x ^ (x >> 31);
-}
-__device__ __forceinline__ double rescale_one(double x, double d, unsigned long long) {
-    return fma(x, d, x);
-}
-__device__ __forceinline__ float rescale_one(float x, double d, unsigned long long key) {
-    const double v = fma(double(x), d, double(x));
-    const float r = __double2float_rn(v);
-    if (double(r) == v) return r;
-    const float lo = double(r) < v ? r : nextafterf(r, -INFINITY);
-    const float hi = double(r) < v ? nextafterf(r, INFINITY) : r;
-    const double frac = (v - double(lo)) / (double(hi) - double(lo));
-    const double u = double(mix64(key) >> 11) * 0x1.0p-53;
-    return u < frac ? hi : lo;
+__device__ __forceinline__ unsigned int fmix32(unsigned int h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
 }
 // the draw of cell c, field k (0 psi, 1 C), step n
-__device__ __forceinline__ unsigned long long rescale_key(long long c, int k, long long n) {
-    return (unsigned long long)c * 2ull + (unsigned long long)k + ((unsigned long long)n << 40);
+__device__ __forceinline__ unsigned int rescale_key(long long c, int k, long long n) {
+    return fmix32((unsigned int)c ^ fmix32((unsigned int)(2 * n + k)));
+}
+__device__ __forceinline__ double rescale_one(double x, double d, float, unsigned int) {
+    return fma(x, d, x);
+}
+__device__ __forceinline__ float rescale_one(float x, double, float d, unsigned int key) {
+    float e;
+    const float s = two_sum(x, x * d, e);
+    if (e == 0.0f) return s;
+    const float nb = nextafterf(s, e > 0.0f ? INFINITY : -INFINITY);
+    const float frac = __fdividef(e, nb - s);  // in (0, 1/2]
+    const float u = float(key >> 8) * 0x1.0p-24f;
+    return u < frac ? nb : s;
+}
+
+// the product a b exactly as hi + lo (lo by one FMA), added to a compensated
+// sum (hi, lo): the total surfactant of the rescale to about 1e-14 in FP32
+// arithmetic
+__device__ __forceinline__ void comp_add_prod(float &hi, float &lo, float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    float e;
+    hi = two_sum(hi, p, e);
+    lo += e + pe;
+}
+__device__ __forceinline__ void comp_add_prod(double &hi, double &lo, double a, double b) {
+    const double p = a * b;
+    const double pe = fma(a, b, -p);
+    double e;
+    hi = two_sum(hi, p, e);
+    lo += e + pe;
 }
 
 // division and inverse square root: IEEE in double precision; in single

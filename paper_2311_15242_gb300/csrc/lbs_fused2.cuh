@@ -717,13 +717,13 @@ __global__ void __launch_bounds__(BS) k_sorfuse2(Inst<R> I, int max_rounds, long
     const bool alt = ((round + I.sor_phase) & 1) != 0;
     const R *P = alt ? I.psi2 : I.psi;
     const R *Cq = alt ? I.C2 : I.C;
-    // (the products in FP64, as lbs_diagnostics forms them: the rescale
-    // then holds the total that the diagnostics report; one pass a step)
-    double sum = 0.0;
+    // (each product exact as hi + lo, the thread's sum compensated: the
+    // total lbs_diagnostics forms in FP64, to rounding of the sum alone)
+    R hi = R(0), lo = R(0);
     for (int x = x0, y = y0; y < I.ny;) {
         const long long c = (long long)y * I.pitch + x;
-        sum += double(__ldcg(&I.a[c]) + I.eps_w) * double(__ldcg(&P[c])) +
-               double(__ldcg(&I.chi[c]) + I.eps_w) * double(__ldcg(&Cq[c]));
+        comp_add_prod(hi, lo, __ldcg(&I.a[c]) + I.eps_w, __ldcg(&P[c]));
+        comp_add_prod(hi, lo, __ldcg(&I.chi[c]) + I.eps_w, __ldcg(&Cq[c]));
         x += sx;
         y += sy;
         if (x >= I.nx) {
@@ -731,7 +731,7 @@ __global__ void __launch_bounds__(BS) k_sorfuse2(Inst<R> I, int max_rounds, long
             y++;
         }
     }
-    double v[1] = {sum};
+    double v[1] = {double(hi) + double(lo)};
     double bsum[1];
     block_sum<BS, 1>(v, bsum);
     if (tid == 0) I.part[blockIdx.x] = bsum[0];
@@ -746,12 +746,13 @@ __global__ void __launch_bounds__(BS) k_sorfuse2(Inst<R> I, int max_rounds, long
     const double total = s_tot;
     const double scale = total > 0 ? ctl->M0 / total : 1.0;
     const double dscale = scale - 1.0;
+    const float dscale_f = float(dscale);
     // 4. rescale: x (1 + d), d = s - 1, rounded without bias (rescale_one)
     for (int x = x0, y = y0; y < I.ny;) {
         const long long c = (long long)y * I.pitch + x;
         const R p = __ldcg(&P[c]), r = __ldcg(&Cq[c]);
-        I.psi[c] = rescale_one(p, dscale, rescale_key(c, 0, step0));
-        I.C[c] = rescale_one(r, dscale, rescale_key(c, 1, step0));
+        I.psi[c] = rescale_one(p, dscale, dscale_f, rescale_key(c, 0, step0));
+        I.C[c] = rescale_one(r, dscale, dscale_f, rescale_key(c, 1, step0));
         x += sx;
         y += sy;
         if (x >= I.nx) {

@@ -1370,23 +1370,28 @@ __device__ __forceinline__ void surf2_block(const Inst<R> &I, int mode, int nblo
     const R *P = alt ? I.psi2 : I.psi;
     const R *Cc = alt ? I.C2 : I.C;
     // the strip's loads first (all in flight together), then the sum in
-    // order; products and sums in FP64, as lbs_diagnostics forms them (one
-    // pass a step), so that the rescale holds the total the diagnostics report
-    double val[SURF_STRIP];
+    // order: each product exact as hi + lo and the strip's sum compensated,
+    // the total lbs_diagnostics forms in FP64 to rounding of the sum alone
+    R va[SURF_STRIP], vp[SURF_STRIP], vb[SURF_STRIP], vc[SURF_STRIP];
 #pragma unroll
     for (int k = 0; k < SURF_STRIP; k++) {
         const int y = y0 + k;
-        val[k] = 0.0;
+        va[k] = vp[k] = vb[k] = vc[k] = R(0);
         if (x < I.nx && y < rows) {
             const long long c = (long long)y * I.pitch + x;
-            val[k] = double(I.a[c] + I.eps_w) * double(P[c]) +
-                     double(I.chi[c] + I.eps_w) * double(Cc[c]);
+            va[k] = I.a[c] + I.eps_w;
+            vp[k] = P[c];
+            vb[k] = I.chi[c] + I.eps_w;
+            vc[k] = Cc[c];
         }
     }
-    double sum = 0.0;
+    R hi = R(0), lo = R(0);
 #pragma unroll
-    for (int k = 0; k < SURF_STRIP; k++) sum += val[k];
-    double v[1] = {sum};
+    for (int k = 0; k < SURF_STRIP; k++) {
+        comp_add_prod(hi, lo, va[k], vp[k]);
+        comp_add_prod(hi, lo, vb[k], vc[k]);
+    }
+    double v[1] = {double(hi) + double(lo)};
     int b = bx + by * gdx;
     block_sum<BS, 1>(v, I.part + b);
     if (!last_block(&I.ctl->ticket, nblocks)) return;
@@ -1431,17 +1436,18 @@ template <typename R>
 __device__ __forceinline__ void scale2_cell(const Inst<R> &I, int x, int y, int z) {
     if (x >= I.nx || y >= I.ny) return;
     long long c = ((long long)z * I.ny + y) * I.pitch + x;
-    // x (1 + d) with d = s - 1 formed in double, rounded without bias
+    // x (1 + d) with d = s - 1, rounded without bias
     // (rescale_one); the step counter has already advanced
     const double d = I.ctl->dscale;
+    const float df = I.ctl->dscale_f;
     const long long n = I.ctl->step - 1;
     // the blocked SOR leaves its result in the second buffer after an odd
     // number of rounds
     const bool alt = I.ctl->sor_iters_parity != 0;
     const R p = alt ? I.psi2[c] : I.psi[c];
     const R q = alt ? I.C2[c] : I.C[c];
-    I.psi[c] = rescale_one(p, d, rescale_key(c, 0, n));
-    I.C[c] = rescale_one(q, d, rescale_key(c, 1, n));
+    I.psi[c] = rescale_one(p, d, df, rescale_key(c, 0, n));
+    I.C[c] = rescale_one(q, d, df, rescale_key(c, 1, n));
 }
 
 template <typename R>
