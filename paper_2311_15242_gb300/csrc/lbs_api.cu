@@ -126,7 +126,7 @@ constexpr int kScal2 = 21, kScal3 = 25, kRest = 6;
 constexpr int kCoef2 = 6;  // 2D SOR coefficient planes (faces and inverse diagonals)
 constexpr int kNext2 = 5;  // 2D moments of t+1 written by the fused step (rho^R, rho^B, rho^N, j)
 // tile of the fused 2D step (k_lbfd2): TX x TY cells, one thread a cell
-constexpr int FTX = 32, FTY = 8;
+constexpr int FTX = 32, FTY = 16;
 
 template <typename R, typename P>
 Layout layout_of(const lbs_params *p) {

@@ -578,7 +578,7 @@ __device__ __forceinline__ void lbfd2_tile(const Inst<R> &I, const PopSets<R> &p
 }
 
 template <typename R, typename P, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, sizeof(R) == 4 ? 4 : 2) k_lbfd2(Inst<R> I) {
+__global__ void __launch_bounds__(TX * TY, (sizeof(R) == 4 ? 1024 : 512) / (TX * TY)) k_lbfd2(Inst<R> I) {
     using F = Fuse2<R, TX, TY>;
     constexpr int W3 = F::W3, N3 = F::N3, N2 = F::N2, N1 = F::N1;
     constexpr int NT = F::NT;
@@ -668,7 +668,7 @@ __global__ void k_grad2n(Inst<R> I) {
 //      b, b + nblocks, ...), a grid barrier after each round, the same stop
 //      decision in every block;
 //   3. the total surfactant sum (a + eps) psi + (chi + eps) C of the result
-//      (products and sums in FP64),
+//      (exact products, compensated sums),
 //      grid barrier, every block adds the block partials in the same order;
 //   4. rescale psi, C by M0 / total (Sec. 2.2) into the canonical buffers.
 // Every barrier waits at most max_polls polls, then reports ST_TIMEOUT.
