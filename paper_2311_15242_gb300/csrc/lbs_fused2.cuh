@@ -704,8 +704,12 @@ __global__ void __launch_bounds__(BS) k_sorfuse2(Inst<R> I, int max_rounds, long
     bool conv = false;
     if (I.transport) {
         for (;; round++) {
-            for (int t = blockIdx.x; t < nt; t += nb)
+            for (int t = blockIdx.x; t < nt; t += nb) {
+                if (t + (int)nb < nt)
+                    sor_prefetch_tile<R, TX, TY, K, BS>(I, round, (t + nb) % tiles_x,
+                                                        (t + nb) / tiles_x);
                 sor_tile2<R, TX, TY, K, BS>(I, round, t % tiles_x, t / tiles_x, smem_raw);
+            }
             if (!grid_barrier(ctl, nb, max_polls)) return;
             conv = round_converged<R>(ctl, round, double(I.sor_tol));
             if (conv || round + 1 >= max_rounds) break;

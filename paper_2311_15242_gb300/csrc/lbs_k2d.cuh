@@ -1198,6 +1198,43 @@ __device__ __forceinline__ void sor_tile2_list(const Inst<R> &I, int round, int 
     sor_fold_maxima<R, BS>(I, round, v);
 }
 
+// L2 prefetch of the lines tile (bx, by) of round `round` will load (the
+// region of the tile and its halo, rows and columns inside the grid): a
+// block that takes several tiles a round issues it for its next tile before
+// it works on the current one, so that the next tile's loads find L2 rather
+// than wait on DRAM one dependent round at a time.  The round's inputs are
+// not written during the round, so the lines stay valid.
+template <typename R, int TX, int TY, int K, int BS>
+__device__ __forceinline__ void sor_prefetch_tile(const Inst<R> &I, int round, int bx, int by) {
+    constexpr int H = SorTile<R, TX, TY, K, BS>::H;
+    const bool odd = ((round + I.sor_phase) & 1) != 0;
+    const int np = (round > 0 && I.sfx != nullptr) ? 10 : 6;
+    const int xlo = max(bx * TX - H, 0), xhi = min(bx * TX + TX + H, I.nx);
+    const int ylo = max(by * TY - H, 0), yhi = min(by * TY + TY + H, I.ny);
+    if (xhi <= xlo || yhi <= ylo) return;
+    const int lo = xlo * (int)sizeof(R), hi = xhi * (int)sizeof(R) - 1;  // bytes of a row
+    const int nl = (hi - lo) / 128 + 2;                                  // lines a row (one spare)
+    const int per = (yhi - ylo) * nl;
+    for (int it = threadIdx.x; it < np * per; it += BS) {
+        const int k = it / per, r0 = it - k * per, r = r0 / nl, l = r0 - r * nl;
+        const R *b;
+        switch (k) {
+        case 0: b = odd ? I.psi2 : I.psi; break;
+        case 1: b = odd ? I.C2 : I.C; break;
+        case 2: b = I.rpsi; break;
+        case 3: b = I.rC; break;
+        case 4: b = np == 10 ? I.sfx : I.a; break;
+        case 5: b = np == 10 ? I.scx : I.chi; break;
+        case 6: b = I.sfy; break;
+        case 7: b = I.scy; break;
+        case 8: b = I.sip; break;
+        default: b = I.sic; break;
+        }
+        const char *a = (const char *)(b + (size_t)(ylo + r) * I.pitch) + min(lo + 128 * l, hi);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    }
+}
+
 // one tile (bx, by) of round `round` of instance I, in smem_raw
 // (SorTile::smem_bytes()); folds the tile's maxima into the round's slot
 template <typename R, int TX, int TY, int K, int BS>
