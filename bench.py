@@ -45,24 +45,26 @@ UNIT = "MLUPS"
 #     chi, C, S, B, psi^(t-1), C^(t-1) (14 fields); write the next moments
 #     rho^R, rho^B, rho^N, j (2), the right-hand sides (2), S, B, the SOR
 #     guess (2) and psi^(t-1), C^(t-1) (13 fields)
-#   grad (k_grad2n): read the next moments (5), write g (2), a, chi and the
-#     current moments (9)
+#   grad (k_grad2n): read rho^R, rho^B, rho^N of t+1 (3), write g (2), a,
+#     chi (4); the moments alternate between two sets, nothing is copied
 #   surf (k_surf2 + k_scale2): read a, chi, psi, C; read psi, C, write psi, C
 #   sor: 32 B a sweep and cell in FP32 (psi, C, two right-hand sides, a, chi
 #     read; psi, C written: the count of a plain unblocked sweep), whatever
 #     the sweeps the blocked kernel runs in shared memory; the one-launch form
-#     (k_sorfuse2) also carries the grad and surf groups' fields
+#     (k_sorfuse2) also carries the grad group's fields and, of the surf
+#     group's, a and chi for the total (psi, C are the last sweep's) and the
+#     rescale's read and write of psi, C (7 + 2 + 4 fields)
 def alg_bytes_2d(group, storage, sweeps=0, fused_sor=False):
     rb = 8 if storage == "f64" else 4
     pb = POP_BYTES[storage]
     if group == "collide":
         return 2 * (16 * pb + 2 * rb + 1) + (14 + 13) * rb
     if group == "grad":
-        return 14 * rb
+        return 7 * rb
     if group == "surf":
         return 8 * rb
     if group == "sor":
-        return 8 * rb * sweeps + ((14 + 8) * rb if fused_sor else 0)
+        return 8 * rb * sweeps + (13 * rb if fused_sor else 0)
     raise KeyError(group)
 
 # D3Q19: fixed bytes per cell of each group (FP32 fields, flags) and the

@@ -723,8 +723,9 @@ struct Solver : Base {
             out[n++] = {(char *)T + (size_t)i * L.plane * sizeof(P), sizeof(P)};
         for (int i = 1; i < Q; i++)
             out[n++] = {(char *)M + (size_t)i * L.plane * sizeof(P), sizeof(P)};
-        R *const sc[] = {T0,    M0,    I.rhoR, I.rhoB, I.rhoN, I.jx, I.jy, I.gx, I.gy, I.a,
-                         I.chi, I.ux,  I.uy,   I.Fx,   I.Fy,   I.psi, I.C, I.S, I.B, I.psip, I.Cp};
+        const MomSet<R> m = mom_set(I, odd);
+        R *const sc[] = {T0,    M0,    m.rR, m.rB, m.rN, m.jx, m.jy, I.gx, I.gy, I.a,
+                         I.chi, I.ux,  I.uy, I.Fx, I.Fy, I.psi, I.C, I.S, I.B, I.psip, I.Cp};
         for (R *f : sc) out[n++] = {f, sizeof(R)};
         if (D == 3) {
             R *const s3[] = {I.jz, I.gz, I.uz, I.Fz};
@@ -854,6 +855,10 @@ struct Solver : Base {
 
     const void *inst() const override { return &I; }
     size_t inst_bytes() const override { return sizeof(I); }
+    void set_batch_member() override {
+        I.pop_pp = 0;
+        I.sor_phase = 0;
+    }
 
     int set_graph(int on) override {
         use_graph = bool(on);

@@ -330,11 +330,11 @@ struct Batch : lbs_batch {
                 berr(this, "internal: descriptor size mismatch");
                 return LBS_EINVAL;
             }
+            // the batch runs the separate per-cell kernels: populations and
+            // moments return to set 0 every step and the SOR starting guess
+            // sits in psi, C
+            c->impl->set_batch_member();
             std::memcpy(&h[k], c->impl->inst(), sizeof(Inst<R>));
-            // the batch runs the separate per-cell kernels: populations return
-            // to set f every step and the SOR starting guess sits in psi, C
-            h[k].pop_pp = 0;
-            h[k].sor_phase = 0;
             if (p[k].sor_max_iter > max_iter) max_iter = p[k].sor_max_iter;
         }
         BCK(cudaMalloc(&d_insts, n * sizeof(Inst<R>)));

@@ -91,8 +91,8 @@ struct Ctl {
     float dscale_f;         // the same in single precision
     int sor_active;         // batched sweep: 1 while this instance's solve iterates
     int dead;               // non-finite total seen: a batch skips this instance
-    unsigned int bar_count; // grid barrier of the one-launch SOR: arrivals,
-    unsigned int bar_gen;   // and generation (bumped by the last arrival)
+    unsigned int bar_count; // grid barrier of the one-launch SOR: arrivals
+    unsigned int bar_gen;   // (unused)
     // per sweep: max |d psi|, max |d C|, max |psi|, max |C| (bits of
     // non-negative doubles, compared as unsigned integers)
     unsigned long long sweep[KMAX_SWEEPS][4];
@@ -164,6 +164,24 @@ struct Inst {
     Ctl *ctl;
     double *part;             // per-block partial sums of reductions
 };
+
+// The moment planes rho^R, rho^B, rho^N, j of one set.  The fused 2D step
+// keeps those of step s in set s & 1, like its populations (it reads one set
+// and writes the other, so nothing is copied); the other forms use set 0.
+template <typename R>
+struct MomSet {
+    R *rR, *rB, *rN, *jx, *jy;
+};
+template <typename R>
+__host__ __device__ __forceinline__ MomSet<R> mom_set(const Inst<R> &I, bool second) {
+    return second ? MomSet<R>{I.rhoRn, I.rhoBn, I.rhoNn, I.jxn, I.jyn}
+                  : MomSet<R>{I.rhoR, I.rhoB, I.rhoN, I.jx, I.jy};
+}
+// the set that holds the moments of step s
+template <typename R>
+__host__ __device__ __forceinline__ MomSet<R> mom_of_step(const Inst<R> &I, long long s) {
+    return mom_set(I, I.pop_pp && (s & 1));
+}
 
 // ---------------------------------------------------------------------------
 // Population storage: arithmetic in R, storage in P.  The stored numbers are

@@ -16,11 +16,10 @@
 //
 // Populations ping-pong between the two sets of the workspace by the parity
 // of the step counter: the state at step s lives in set s & 1 (pull form
-// reads neighbours' values, so a step cannot write the set it reads).  The
-// moments rho^R, rho^B, rho^N, j of t+1 go to separate planes (the next
-// moments), since neighbouring tiles still read those of t; the SOR launch's
-// first phase, which reads them for the gradient, copies them over the
-// current ones.
+// reads neighbours' values, so a step cannot write the set it reads).  So do
+// the moments rho^R, rho^B, rho^N, j (mom_set): k_lbfd2 reads those of t and
+// writes those of t+1 to the other set, which the SOR launch's first phase
+// reads for the gradient of t+1.
 #pragma once
 
 #include "lbs_k2d.cuh"
@@ -61,7 +60,8 @@ __device__ __forceinline__ R round_pop(const Inst<R> &I, R v) {
     return PopCvt<P>::scaled ? back * I.pinv : back;
 }
 
-// the population sets of the current step (src) and of the next (dst)
+// the population sets of the current step (src) and of the next (dst), and
+// the moment planes of both
 template <typename R>
 struct PopSets {
     const void *sT, *sM;
@@ -70,6 +70,7 @@ struct PopSets {
     void *dT, *dM;
     R *dT0, *dM0;
     uint8_t *dflag;
+    MomSet<R> sm, dm;
 };
 template <typename R>
 __device__ __forceinline__ PopSets<R> pop_sets(const Inst<R> &I) {
@@ -85,6 +86,8 @@ __device__ __forceinline__ PopSets<R> pop_sets(const Inst<R> &I) {
     p.dT0 = odd ? I.fT0 : I.gT0;
     p.dM0 = odd ? I.fM0 : I.gM0;
     p.dflag = odd ? I.flag : I.gflag;
+    p.sm = mom_set(I, odd);
+    p.dm = mom_set(I, !odd);
     return p;
 }
 
@@ -486,11 +489,11 @@ __device__ __forceinline__ void lbfd2_tile(const Inst<R> &I, const PopSets<R> &p
             ps.dT0[c] = t[0];
             ps.dM0[c] = m[0];
             ps.dflag[c] = (uint8_t)flc;
-            I.rhoRn[c] = rR;
-            I.rhoBn[c] = rB;
-            I.rhoNn[c] = colour_fn(I, rR, rB);
-            I.jxn[c] = jx;
-            I.jyn[c] = jy;
+            ps.dm.rR[c] = rR;
+            ps.dm.rB[c] = rB;
+            ps.dm.rN[c] = colour_fn(I, rR, rB);
+            ps.dm.jx[c] = jx;
+            ps.dm.jy[c] = jy;
             return;
         }
     }
@@ -570,11 +573,11 @@ __device__ __forceinline__ void lbfd2_tile(const Inst<R> &I, const PopSets<R> &p
     ps.dM0[c] = fM[0];
     ps.dflag[c] = (uint8_t)fl;
     const Mom2<R> mo = moments9(I, fT, fM, fl);
-    I.rhoRn[c] = mo.rR;
-    I.rhoBn[c] = mo.rB;
-    I.rhoNn[c] = colour_fn(I, mo.rR, mo.rB);
-    I.jxn[c] = mo.jx;
-    I.jyn[c] = mo.jy;
+    ps.dm.rR[c] = mo.rR;
+    ps.dm.rB[c] = mo.rB;
+    ps.dm.rN[c] = colour_fn(I, mo.rR, mo.rB);
+    ps.dm.jx[c] = mo.jx;
+    ps.dm.jy[c] = mo.jy;
 }
 
 template <typename R, typename P, int TX, int TY>
@@ -618,10 +621,10 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(R) == 4 ? 1024 : 512) / (TX *
             gy3[q] = g1;
             ps3[q] = I.psi[c];
             if (h2) {
-                rR2[k] = I.rhoR[c];
-                rB2[k] = I.rhoB[c];
-                jx2[k] = I.jx[c];
-                jy2[k] = I.jy[c];
+                rR2[k] = ps.sm.rR[c];
+                rB2[k] = ps.sm.rB[c];
+                jx2[k] = ps.sm.jx[c];
+                jy2[k] = ps.sm.jy[c];
                 a2[k] = I.a[c];
                 ch2[k] = I.chi[c];
                 Cs2[k] = I.C[c];
@@ -637,18 +640,13 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(R) == 4 ? 1024 : 512) / (TX *
 }
 
 // ---------------------------------------------------------------------------
-// Colour gradient and weights at t+1 from the next moments, and the next
-// moments copied over the current ones (cell (x, y)).
+// Colour gradient and weights at t+1 from the moments of t+1 (set m), cell
+// (x, y).
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ void grad2_next_cell(const Inst<R> &I, int x, int y) {
-    const long long c = (long long)y * I.pitch + x;
-    grad2_cell_from(I, x, y, I.rhoRn, I.rhoBn, I.rhoNn);
-    I.rhoR[c] = I.rhoRn[c];
-    I.rhoB[c] = I.rhoBn[c];
-    I.rhoN[c] = I.rhoNn[c];
-    I.jx[c] = I.jxn[c];
-    I.jy[c] = I.jyn[c];
+__device__ __forceinline__ void grad2_next_cell(const Inst<R> &I, const MomSet<R> &m, int x,
+                                                int y) {
+    grad2_cell_from(I, x, y, m.rR, m.rB, m.rN);
 }
 
 // the same as its own launch (the SOR runs one launch a round), with the
@@ -657,8 +655,9 @@ template <typename R>
 __global__ void k_grad2n(Inst<R> I) {
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
         I.ctl->bar_count = 0;
+    const MomSet<R> m = mom_of_step(I, I.ctl->step + 1);
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x < I.nx && y < I.ny) grad2_next_cell(I, x, y);
+    if (x < I.nx && y < I.ny) grad2_next_cell(I, m, x, y);
 }
 
 // ---------------------------------------------------------------------------
@@ -666,10 +665,11 @@ __global__ void k_grad2n(Inst<R> I) {
 //   1. colour gradient and weights at t+1 (grad2_next_cell), grid barrier;
 //   2. SOR rounds: the blocked tiles of k_sor_tb2 (each block takes tiles
 //      b, b + nblocks, ...), a grid barrier after each round, the same stop
-//      decision in every block;
-//   3. the total surfactant sum (a + eps) psi + (chi + eps) C of the result
-//      (exact products, compensated sums),
-//      grid barrier, every block adds the block partials in the same order;
+//      decision in every block; a block also sums the surfactant of the
+//      cells it stores (exact products, compensated sums) into its partial;
+//   3. the total surfactant sum (a + eps) psi + (chi + eps) C of the result:
+//      the partials of the last round, added by every block in the same
+//      order;
 //   4. rescale psi, C by M0 / total (Sec. 2.2) into the canonical buffers.
 // Every barrier waits at most max_polls polls, then reports ST_TIMEOUT.
 // ---------------------------------------------------------------------------
@@ -680,6 +680,7 @@ __global__ void __launch_bounds__(BS) k_sorfuse2(Inst<R> I, int max_rounds, long
     const int tid = threadIdx.x;
     Ctl *ctl = I.ctl;
     const long long step0 = ctl->step;  // (block 0 advances it at the end)
+    unsigned int bt = 0;                // arrivals that end the next grid barrier
     // the cells of this thread: every (nb BS)-th cell in row order from
     // b BS + tid, walked as (x, y) with the stride split once into (sx, sy)
     const long long stride = (long long)nb * BS;
@@ -687,8 +688,9 @@ __global__ void __launch_bounds__(BS) k_sorfuse2(Inst<R> I, int max_rounds, long
     const long long q0 = (long long)blockIdx.x * BS + tid;
     const int x0 = int(q0 % I.nx), y0 = int(q0 / I.nx);
     // 1. gradient and weights of t+1
+    const MomSet<R> mnext = mom_of_step(I, step0 + 1);
     for (int x = x0, y = y0; y < I.ny;) {
-        grad2_next_cell(I, x, y);
+        grad2_next_cell(I, mnext, x, y);
         x += sx;
         y += sy;
         if (x >= I.nx) {
@@ -696,21 +698,28 @@ __global__ void __launch_bounds__(BS) k_sorfuse2(Inst<R> I, int max_rounds, long
             y++;
         }
     }
-    if (!grid_barrier(ctl, nb, max_polls)) return;
-    // 2. SOR rounds
+    if (!grid_barrier(ctl, nb, bt, max_polls)) return;
+    // 2. SOR rounds.  As a block stores its tiles' cells it also sums their
+    //    surfactant; the round that ends the solve thus leaves the block
+    //    partials of the total in I.part (3) with no pass of its own.
     const int tiles_x = (I.nx + TX - 1) / TX, tiles_y = (I.ny + TY - 1) / TY;
     const int nt = tiles_x * tiles_y;
     int round = 0;
     bool conv = false;
     if (I.transport) {
         for (;; round++) {
+            R tsum[2] = {R(0), R(0)};
             for (int t = blockIdx.x; t < nt; t += nb) {
                 if (t + (int)nb < nt)
                     sor_prefetch_tile<R, TX, TY, K, BS>(I, round, (t + nb) % tiles_x,
                                                         (t + nb) / tiles_x);
-                sor_tile2<R, TX, TY, K, BS>(I, round, t % tiles_x, t / tiles_x, smem_raw);
+                sor_tile2<R, TX, TY, K, BS>(I, round, t % tiles_x, t / tiles_x, smem_raw, tsum);
             }
-            if (!grid_barrier(ctl, nb, max_polls)) return;
+            double v[1] = {double(tsum[0]) + double(tsum[1])};
+            double bsum[1];
+            block_sum<BS, 1>(v, bsum);
+            if (tid == 0) I.part[blockIdx.x] = bsum[0];
+            if (!grid_barrier(ctl, nb, bt, max_polls)) return;
             conv = round_converged<R>(ctl, round, double(I.sor_tol));
             if (conv || round + 1 >= max_rounds) break;
         }
@@ -721,25 +730,28 @@ __global__ void __launch_bounds__(BS) k_sorfuse2(Inst<R> I, int max_rounds, long
     const bool alt = ((round + I.sor_phase) & 1) != 0;
     const R *P = alt ? I.psi2 : I.psi;
     const R *Cq = alt ? I.C2 : I.C;
-    // (each product exact as hi + lo, the thread's sum compensated: the
-    // total lbs_diagnostics forms in FP64, to rounding of the sum alone)
-    R hi = R(0), lo = R(0);
-    for (int x = x0, y = y0; y < I.ny;) {
-        const long long c = (long long)y * I.pitch + x;
-        comp_add_prod(hi, lo, __ldcg(&I.a[c]) + I.eps_w, __ldcg(&P[c]));
-        comp_add_prod(hi, lo, __ldcg(&I.chi[c]) + I.eps_w, __ldcg(&Cq[c]));
-        x += sx;
-        y += sy;
-        if (x >= I.nx) {
-            x -= I.nx;
-            y++;
+    if (!I.transport) {
+        // (no solve: the total of the current values in a pass of its own;
+        // each product exact as hi + lo, the thread's sum compensated)
+        R hi = R(0), lo = R(0);
+        for (int x = x0, y = y0; y < I.ny;) {
+            const long long c = (long long)y * I.pitch + x;
+            comp_add_prod(hi, lo, __ldcg(&I.a[c]) + I.eps_w, __ldcg(&P[c]));
+            comp_add_prod(hi, lo, __ldcg(&I.chi[c]) + I.eps_w, __ldcg(&Cq[c]));
+            x += sx;
+            y += sy;
+            if (x >= I.nx) {
+                x -= I.nx;
+                y++;
+            }
         }
+        double v[1] = {double(hi) + double(lo)};
+        double bsum[1];
+        block_sum<BS, 1>(v, bsum);
+        if (tid == 0) I.part[blockIdx.x] = bsum[0];
+        if (!grid_barrier(ctl, nb, bt, max_polls)) return;
     }
-    double v[1] = {double(hi) + double(lo)};
-    double bsum[1];
-    block_sum<BS, 1>(v, bsum);
-    if (tid == 0) I.part[blockIdx.x] = bsum[0];
-    if (!grid_barrier(ctl, nb, max_polls)) return;
+    // every block adds the block partials in the same order
     double acc[1] = {0.0};
     for (unsigned int k = tid; k < nb; k += BS) acc[0] += __ldcg(&I.part[k]);
     double tot[1];

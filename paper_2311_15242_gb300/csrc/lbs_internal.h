@@ -27,6 +27,10 @@ struct Base {
     // host copy of the device descriptor Inst<R> of this instance, and its size
     virtual const void *inst() const = 0;
     virtual size_t inst_bytes() const = 0;
+    // member of a batch (2D): the batch runs the per-cell kernels, which keep
+    // populations and moments in set 0 and start the solve from psi, C; the
+    // instance's own descriptor (fields, diagnostics) must say the same
+    virtual void set_batch_member() = 0;
     // blocked SOR tile variant (2D), see lbs_set_sor_tile
     virtual int set_sor_tile(int v) = 0;
     // all SOR rounds of a 2D solve in one launch where possible, see

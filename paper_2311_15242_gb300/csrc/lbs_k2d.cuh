@@ -323,7 +323,9 @@ __device__ __forceinline__ void force2_cell(const Inst<R> &I, int x, int y) {
         Fx = -R(0.5) * I.sigma_min * kappa * gx;
         Fy = -R(0.5) * I.sigma_min * kappa * gy;
     }
-    R rR = I.rhoR[c], rB = I.rhoB[c];
+    // (the moments of the current step: set 0 but in the fused step's form)
+    const MomSet<R> m = mom_of_step(I, I.ctl->step);
+    R rR = m.rR[c], rB = m.rB[c];
     R rho = rR + rB;
     // (rho - rhoB0) = rho^R + (rho^B - rhoB0)
     R drb = rR + (rB - I.rhoB0);
@@ -332,8 +334,8 @@ __device__ __forceinline__ void force2_cell(const Inst<R> &I, int x, int y) {
     I.Fx[c] = Fx;
     I.Fy[c] = Fy;
     const R irho = fdiv(R(1), rho);
-    I.ux[c] = (I.jx[c] + R(0.5) * Fx) * irho;
-    I.uy[c] = (I.jy[c] + R(0.5) * Fy) * irho;
+    I.ux[c] = (m.jx[c] + R(0.5) * Fx) * irho;
+    I.uy[c] = (m.jy[c] + R(0.5) * Fy) * irho;
 }
 
 template <typename R>
@@ -884,7 +886,7 @@ __device__ __forceinline__ void sor_fold_maxima(const Inst<R> &I, int round, R v
 // Iv = inverse diagonals, FX / FY = face coefficients towards +x / +y.
 template <typename R, int TX, int TY, int K, int BS>
 __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx, int by,
-                                             unsigned char *smem_raw) {
+                                             unsigned char *smem_raw, R *tot) {
     using T = SorTile<R, TX, TY, K, BS>;
     using V = typename Vec2<R>::T;
     constexpr int RX = T::RX, RY = T::RY, H = T::H, RXH = T::RXH, NH = T::NH, NHP = T::NHP;
@@ -1053,6 +1055,10 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
         const V xs = X[s];
         pout[c] = xs.x;
         cout[c] = xs.y;
+        if (tot) {
+            comp_add_prod(tot[0], tot[1], __ldcg(&I.a[c]) + I.eps_w, xs.x);
+            comp_add_prod(tot[0], tot[1], __ldcg(&I.chi[c]) + I.eps_w, xs.y);
+        }
         if (first && I.sfx) {
             const V fx = FX[s], fy = FY[s], iv = Iv[s];
             I.sfx[c] = fx.x;
@@ -1069,7 +1075,7 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
 // list form of a tile (see above)
 template <typename R, int TX, int TY, int K, int BS>
 __device__ __forceinline__ void sor_tile2_list(const Inst<R> &I, int round, int bx, int by,
-                                               unsigned char *smem_raw) {
+                                               unsigned char *smem_raw, R *tot) {
     using T = SorTile<R, TX, TY, K, BS>;
     constexpr int RX = T::RX, RY = T::RY, NR = T::NR, H = T::H;
     R *sp = (R *)smem_raw, *sc = sp + NR, *bp = sc + NR, *bc = bp + NR;
@@ -1194,6 +1200,10 @@ __device__ __forceinline__ void sor_tile2_list(const Inst<R> &I, int round, int 
         long long c = (long long)(y0 + ry) * I.pitch + (x0 + rx);
         pout[c] = sp[q];
         cout[c] = sc[q];
+        if (tot) {
+            comp_add_prod(tot[0], tot[1], __ldcg(&I.a[c]) + I.eps_w, sp[q]);
+            comp_add_prod(tot[0], tot[1], __ldcg(&I.chi[c]) + I.eps_w, sc[q]);
+        }
     }
     sor_fold_maxima<R, BS>(I, round, v);
 }
@@ -1236,14 +1246,17 @@ __device__ __forceinline__ void sor_prefetch_tile(const Inst<R> &I, int round, i
 }
 
 // one tile (bx, by) of round `round` of instance I, in smem_raw
-// (SorTile::smem_bytes()); folds the tile's maxima into the round's slot
+// (SorTile::smem_bytes()); folds the tile's maxima into the round's slot.
+// With tot (a thread's compensated sum hi, lo), the thread also adds the
+// surfactant (a + eps) psi + (chi + eps) C of the tile cells it stores, each
+// product exact as hi + lo.
 template <typename R, int TX, int TY, int K, int BS>
 __device__ __forceinline__ void sor_tile2(const Inst<R> &I, int round, int bx, int by,
-                                          unsigned char *smem_raw) {
+                                          unsigned char *smem_raw, R *tot = nullptr) {
     if ((I.wall[0] || !(I.nx & 1)) && (I.wall[1] || !(I.ny & 1)))
-        sor_tile2_cb<R, TX, TY, K, BS>(I, round, bx, by, smem_raw);
+        sor_tile2_cb<R, TX, TY, K, BS>(I, round, bx, by, smem_raw, tot);
     else
-        sor_tile2_list<R, TX, TY, K, BS>(I, round, bx, by, smem_raw);
+        sor_tile2_list<R, TX, TY, K, BS>(I, round, bx, by, smem_raw, tot);
 }
 
 // ---------------------------------------------------------------------------
@@ -1254,31 +1267,32 @@ __device__ __forceinline__ void sor_tile2(const Inst<R> &I, int round, int bx, i
 // ---------------------------------------------------------------------------
 constexpr long long kBarrierPolls = 1LL << 24;
 
-// true in every thread of the block once every block of the grid arrived;
-// false when the wait gave up
+// Grid barrier of a cooperative launch: every block adds one arrival to a
+// counter that the kernel before the launch cleared, and waits until the
+// count reaches nblocks times the barriers passed so far (target, kept by
+// the caller): no block resets or flips anything, so the last arrival is
+// seen after one write.  True in every thread of the block once every block
+// arrived; false when the wait gave up (ST_TIMEOUT: the count then stays
+// short of every later target, so the launch's later barriers give up too,
+// and the next launch starts from a cleared counter).
 __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned int nblocks,
-                                             long long max_polls) {
+                                             unsigned int &target, long long max_polls) {
     __shared__ int ok;
+    target += nblocks;
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
-        volatile unsigned int *gen = &ctl->bar_gen;
-        const unsigned int g = *gen;
         __threadfence();
-        if (atomicAdd(&ctl->bar_count, 1u) == nblocks - 1) {
-            ctl->bar_count = 0;
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            long long polls = 0;
-            while (*gen == g) {
-                if (++polls > max_polls) {
-                    ok = 0;
-                    atomicOr(&ctl->status, int(ST_TIMEOUT));
-                    break;
-                }
-                __nanosleep(64);
+        atomicAdd(&ctl->bar_count, 1u);
+        const volatile unsigned int *count = &ctl->bar_count;
+        long long polls = 0;
+        while (*count < target) {
+            if (++polls > max_polls) {
+                ok = 0;
+                atomicOr(&ctl->status, int(ST_TIMEOUT));
+                break;
             }
+            __nanosleep(32);
         }
         __threadfence();
     }
@@ -1516,6 +1530,7 @@ __global__ void k_diag(Inst<R> I, int nblocks) {
     // (every thread a strip of DIAG_STRIP cells along y)
     double v[NDIAG] = {0};
     double pmin = 1e300, pmax = -1e300;
+    const R *rhoN = mom_of_step(I, I.ctl->step).rN;
     double umax = 0.0;
     // the population set of the current step (the fused 2D step alternates
     // the two sets by the parity of the step counter)
@@ -1527,7 +1542,7 @@ __global__ void k_diag(Inst<R> I, int nblocks) {
         const int y = y0 + kk;
         if (y >= I.ny) break;
         long long c = ((long long)z * I.ny + y) * I.pitch + x;
-        double rN = I.rhoN[c];
+        double rN = rhoN[c];
         // colour masses: the exact FP64 sums of the stored populations
         // (minority as stored, majority = shift + total deviation - minority)
         const int fl = pfl[c];
@@ -1661,11 +1676,12 @@ __global__ void k_export2(Inst<R> I, double *rho, double *u, double *phi, double
     long long c = ((long long)z * I.ny + y) * I.pitch + x;
     long long d = ((long long)z * I.ny + y) * I.nx + x;
     long long N = (long long)I.nx * I.ny * I.nz;
-    rho[d] = double(I.rhoR[c]) + double(I.rhoB[c]);
+    const MomSet<R> m = mom_of_step(I, I.ctl->step);
+    rho[d] = double(m.rR[c]) + double(m.rB[c]);
     u[d] = I.ux[c];
     u[N + d] = I.uy[c];
     u[2 * N + d] = I.uz ? double(I.uz[c]) : 0.0;
-    phi[d] = I.rhoN[c];
+    phi[d] = m.rN[c];
     psi[d] = I.psi[c];
     C[d] = I.C[c];
 }

@@ -54,6 +54,12 @@ def test_batch_f64_matches_oracle():
         o.step(25)
         err = errors(o.fields(), b.fields(k))
         assert max(err.values()) < 1e-9, (k, err)
+        # the instance's diagnostics at an odd step read the batch's sets
+        # (populations and moments stay in set 0 in the batched form)
+        od, bd = o.diagnostics(), b.diagnostics()[k]
+        for key in ("mass_R", "mass_B", "surf_total", "U", "centroid", "psi_av"):
+            a, g = np.atleast_1d(od[key]), np.atleast_1d(bd[key])
+            assert np.allclose(a, g, rtol=1e-9, atol=1e-12), (k, key, a, g)
     d = b.diagnostics()
     assert all(x["step"] == 25 for x in d)
 

@@ -25,17 +25,17 @@ def bench():
 
 def test_fused_step_accounting(bench):
     """The fused 2D step: the SOR group is one launch carrying every sweep
-    (32 B a cell and sweep in FP32) plus the gradient, total and rescale
-    fields (22 fields); the fused LB-FD kernel moves its populations and 27
-    fields once."""
+    (32 B a cell and sweep in FP32) plus the gradient (7 fields), the total's
+    weights (2) and the rescale (4); the fused LB-FD kernel moves its
+    populations and 27 fields once."""
     km = {"force": 0.0, "collide": 0.030, "stream": 0.0, "grad": 0.0, "sor": 0.050,
           "surf": 0.0}
     cells, sweeps = 262144, 8
     r = bench.roofline2(km, cells, "f32", sweeps, 6780.0, "measured", sor_launches=1)
     assert r["kernel"] == "sor"
-    assert r["alg_bytes_per_cell"] == 32 * sweeps + 22 * 4
-    assert r["alg_bytes_per_launch"] == (32 * sweeps + 88) * cells
-    assert r["achieved"] == pytest.approx((32 * sweeps + 88) * cells / 0.050e-3 / 1e9)
+    assert r["alg_bytes_per_cell"] == 32 * sweeps + 13 * 4
+    assert r["alg_bytes_per_launch"] == (32 * sweeps + 52) * cells
+    assert r["achieved"] == pytest.approx((32 * sweeps + 52) * cells / 0.050e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6780.0)
     # FP64 fields double every field byte
     d = bench.roofline2(km, cells, "f64", sweeps, 6780.0, "measured", sor_launches=1)
