@@ -68,7 +68,14 @@ def test_traffic_table_shape(bench):
     # reports them only while that hash matches)
     t = bench.TRAFFIC
     assert len(t["kernel_sha"]) == 16 and int(t["kernel_sha"], 16) >= 0
-    for k, v in t["bytes_per_cell"].items():
-        assert k in ("collide", "sor") and v > 0
+    for table in ("bytes_per_cell", "bytes_per_cell_hbm"):
+        for k, v in t[table].items():
+            assert k in ("collide", "sor") and v > 0
+    assert isinstance(t["sor_variant"], int)
+    # valid only for the captured source, form and tile variant
+    ok = bench.src_hash(bench.FUSED2_FILES) == t["kernel_sha"]
+    assert bench.traffic_valid(1, t["sor_variant"]) == ok
+    assert not bench.traffic_valid(3, t["sor_variant"])
+    assert not bench.traffic_valid(1, t["sor_variant"] + 1)
     assert set(bench.FUSED2_FILES) == {"lbs_dev.cuh", "lbs_k2d.cuh", "lbs_fused2.cuh"}
     assert bench.src_hash(bench.FUSED2_FILES) != bench.src_hash()
