@@ -873,40 +873,73 @@ __global__ void __launch_bounds__(BS)
 // ---------------------------------------------------------------------------
 // k_sor_zm3: one full red-black SOR sweep per launch (Sec. 2.2) with the
 // planes of a z-chunk marched through shared memory.  A block owns a TX x TY
-// tile of (x, y) and ZC planes of z; it keeps a ring of 5 planes of the
+// tile of (x, y) and ZC planes of z; it keeps a ring of RING planes of the
 // (TX + 4) x (TY + 4) region (the tile and a 2-cell halo): psi, C, the two
-// right-hand sides and the two weights a + eps_w, chi + eps_w.  At step k it
-// prefetches plane k + 3, updates red on plane k + 1 over the tile and a
-// 1-cell ring (the values the neighbouring blocks compute for those cells,
-// from the same old black values) and black on plane k over the tile, then
-// writes plane k of the tile.  psi and C are read from one buffer and
-// written to the other (rounds alternate, as in 2D), so no block reads
-// values written in the same launch.  The red phase only reads black cells
-// and the black phase only red ones (every periodic axis has even length),
-// so the updates are made in place in shared memory.
+// right-hand sides and the weights a, chi.  The planes arrive by
+// asynchronous copies (cp.async) issued three steps before their first use,
+// so a plane's loads are in flight while the planes before it are swept.  At
+// step k the block issues plane k + 4, waits for plane k + 2, updates red on
+// plane k + 1 over the tile and a 1-cell ring (the values the neighbouring
+// blocks compute for those cells, from the same old black values) and black
+// on plane k over the tile, then writes plane k of the tile.  psi and C are
+// read from one buffer and written to the other (rounds alternate, as in
+// 2D), so no block reads values written in the same launch.  The red phase
+// only reads black cells and the black phase only red ones (every periodic
+// axis has even length), so the updates are made in place in shared memory.
+// The faces are summed in the order of k_sor_rb3, the weights formed as
+// there (a + eps_w), so the sweep's values are those of its two half-sweeps.
 // ---------------------------------------------------------------------------
 template <typename R, int TX, int TY, int ZC, int BS>
 struct SorZm {
-    static constexpr int RX = TX + 4, RY = TY + 4, NP = RX * RY, RING = 5;
-    // per ring slot and region cell: psi, C, rhs psi, rhs C, w psi, w C; one
-    // flag byte (bit0 in the domain)
-    static constexpr size_t smem_bytes() { return (size_t)RING * NP * (6 * sizeof(R) + 1) + 16; }
+    static_assert(TX % 2 == 0 && TY % 2 == 0, "z-marching tiles have even sides");
+    static constexpr int RX = TX + 4, RY = TY + 4, NP = RX * RY, RING = 6;
+    static constexpr int NPT = (NP + BS - 1) / BS;  // region cells a thread copies
+    // per ring slot and region cell three pairs: (psi, C), (rhs psi, rhs C),
+    // (a, chi); per region cell a flag byte (inside the domain in x and y),
+    // per slot one (the plane inside the domain)
+    static constexpr size_t smem_bytes() {
+        return (size_t)RING * NP * 6 * sizeof(R) + NP + RING + 16;
+    }
 };
+
+// asynchronous copy of one value from global to shared memory; zero when
+// `in` is false (no global read)
+template <typename R>
+__device__ __forceinline__ void cp_async_val(R *dst, const R *src, bool in) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    if (sizeof(R) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(src),
+                     "r"(in ? 4 : 0)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(s), "l"(src),
+                     "r"(in ? 8 : 0)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// wait until at most N of this thread's most recent groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 template <typename R, int TX, int TY, int ZC, int BS>
 __global__ void __launch_bounds__(BS)
     k_sor_zm3(Inst<R> I, cudaGraphConditionalHandle loop, int max_rounds, int eager_round) {
     using T = SorZm<R, TX, TY, ZC, BS>;
-    constexpr int RX = T::RX, NP = T::NP, RING = T::RING;
+    using V = typename Vec2<R>::T;
+    constexpr int RX = T::RX, NP = T::NP, RING = T::RING, NPT = T::NPT;
     if (eager_round > 0 && I.ctl->sor_exec < eager_round) return;  // loop already ended
     const int round = I.ctl->sor_exec;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *sp = (R *)smem_raw;              // [RING][NP] each
-    R *sc = sp + RING * NP, *bp = sc + RING * NP, *bc = bp + RING * NP;
-    R *wp = bc + RING * NP, *wc = wp + RING * NP;
-    uint8_t *fl = (uint8_t *)(wc + RING * NP);
+    V *X = (V *)smem_raw;  // [RING][NP] each
+    V *Bv = X + RING * NP, *Wv = Bv + RING * NP;
+    uint8_t *flxy = (uint8_t *)(Wv + RING * NP);
+    uint8_t *zok = flxy + NP;
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX - 2, y0 = blockIdx.y * TY - 2;
+    const int x0 = blockIdx.x * TX - 2, y0 = blockIdx.y * TY - 2;  // even
     const int zs = blockIdx.z * ZC, ze = min(zs + ZC, I.nz);
     const R *pin = (round & 1) ? I.psi2 : I.psi;
     const R *cin = (round & 1) ? I.C2 : I.C;
@@ -915,58 +948,84 @@ __global__ void __launch_bounds__(BS)
     const R hp = R(0.5) * I.Ds, hc = R(0.5) * I.Db;
     R v[4] = {R(0), R(0), R(0), R(0)};
 
-    // load plane z (any integer; mapped) into ring slot z mod RING
-    auto load_plane = [&](int z) {
+    // the region cells this thread copies: their offset in a plane and
+    // whether they lie inside the domain in x and y (else they stay zero)
+    long long off[NPT];
+    bool inxy[NPT];
+    int outside = 0;
+#pragma unroll
+    for (int u = 0; u < NPT; u++) {
+        const int q = tid + u * BS;
+        off[u] = 0;
+        inxy[u] = false;
+        if (q < NP) {
+            int refl = 0, sx, sy;
+            const int Xc = map_axis(x0 + q % RX, I.nx, I.wall[0], 1, refl, sx);
+            const int Yc = map_axis(y0 + q / RX, I.ny, I.wall[1], 2, refl, sy);
+            inxy[u] = !refl;
+            outside |= refl;
+            off[u] = (long long)Yc * I.pitch + Xc;
+            flxy[q] = (uint8_t)inxy[u];
+        }
+    }
+    // (no region cell beyond a wall or mirror plane in x or y: every face
+    // in the plane is taken without reading its flag; block-uniform)
+    const bool edge = __syncthreads_or(outside) != 0;
+    // issue the copies of plane z (any integer; mapped) into ring slot z mod RING
+    auto issue = [&](int z) {
         const int slot = ((z % RING) + RING) % RING;
         int zr = 0, zside;
         const int Z = map_axis(z, I.nz, I.wall[2], 4, zr, zside);
-        for (int q = tid; q < NP; q += BS) {
-            const int rx = q % RX, ry = q / RX;
-            int refl = zr, sx, sy;
-            const int X = map_axis(x0 + rx, I.nx, I.wall[0], 1, refl, sx);
-            const int Y = map_axis(y0 + ry, I.ny, I.wall[1], 2, refl, sy);
+        if (tid == 0) zok[slot] = (uint8_t)!zr;
+        const long long base = (long long)Z * I.ny * I.pitch;
+#pragma unroll
+        for (int u = 0; u < NPT; u++) {
+            const int q = tid + u * BS;
+            if (q >= NP) continue;
+            const bool in = inxy[u] && !zr;
+            const long long c = in ? base + off[u] : 0;
             const int k = slot * NP + q;
-            if (!refl) {
-                const long long c = ((long long)Z * I.ny + Y) * I.pitch + X;
-                sp[k] = pin[c];
-                sc[k] = cin[c];
-                bp[k] = I.rpsi[c];
-                bc[k] = I.rC[c];
-                wp[k] = I.a[c] + I.eps_w;
-                wc[k] = I.chi[c] + I.eps_w;
-                fl[k] = 1;
-            } else {
-                sp[k] = sc[k] = bp[k] = bc[k] = wp[k] = wc[k] = R(0);
-                fl[k] = 0;
-            }
+            cp_async_val((R *)&X[k], pin + c, in);
+            cp_async_val((R *)&X[k] + 1, cin + c, in);
+            cp_async_val((R *)&Bv[k], I.rpsi + c, in);
+            cp_async_val((R *)&Bv[k] + 1, I.rC + c, in);
+            cp_async_val((R *)&Wv[k], I.a + c, in);
+            cp_async_val((R *)&Wv[k] + 1, I.chi + c, in);
         }
     };
-    // one cell update at region index q of plane z (slot s); the six faces:
-    // +-x, +-y in the plane, the planes z - 1 and z + 1; no flux across a
-    // wall or outside the domain (flag 0)
-    auto update = [&](int z, int q, bool track) {
-        const int s0 = ((z % RING) + RING) % RING;
-        const int sm = (s0 + RING - 1) % RING, spl = (s0 + 1) % RING;
+    // one cell update at region index q of ring slot s0 (neighbour planes in
+    // slots sm, spl, inside the domain when zm, zp); the six faces in the
+    // order -x, +x, -y, +y, plane below, plane above; no flux across a wall
+    // or out of the domain
+    auto update = [&](int s0, int sm, int spl, bool zm, bool zp, int q, bool track) {
         const int k = s0 * NP + q;
-        const R w0p = wp[k], w0c = wc[k];
-        R dp = w0p, dc = w0c, op = bp[k], oc = bc[k];
+        const V w0 = Wv[k], b0 = Bv[k];
+        const R w0p = w0.x + I.eps_w, w0c = w0.y + I.eps_w;
+        R dp = w0p, dc = w0c, op = b0.x, oc = b0.y;
         const int nbk[6] = {k - 1, k + 1, k - RX, k + RX, sm * NP + q, spl * NP + q};
+        bool nin[6] = {true, true, true, true, zm, zp};
+        if (edge) {
+            nin[0] = flxy[q - 1] != 0;
+            nin[1] = flxy[q + 1] != 0;
+            nin[2] = flxy[q - RX] != 0;
+            nin[3] = flxy[q + RX] != 0;
+        }
 #pragma unroll
         for (int f = 0; f < 6; f++) {
+            if (!nin[f]) continue;
             const int j = nbk[f];
-            if (!fl[j]) continue;
-            const R fp = hp * (R(0.5) * (w0p + wp[j]));
-            const R fc = hc * (R(0.5) * (w0c + wc[j]));
+            const V wj = Wv[j], xj = X[j];
+            const R fp = hp * (R(0.5) * (w0p + (wj.x + I.eps_w)));
+            const R fc = hc * (R(0.5) * (w0c + (wj.y + I.eps_w)));
             dp += fp;
             dc += fc;
-            op += fp * sp[j];
-            oc += fc * sc[j];
+            op += fp * xj.x;
+            oc += fc * xj.y;
         }
-        const R p0 = sp[k], c0 = sc[k];
-        const R d1 = I.omega * (fdiv(op, dp) - p0), d2 = I.omega * (fdiv(oc, dc) - c0);
-        const R p1 = p0 + d1, c1 = c0 + d2;
-        sp[k] = p1;
-        sc[k] = c1;
+        const V x0v = X[k];
+        const R d1 = I.omega * (fdiv(op, dp) - x0v.x), d2 = I.omega * (fdiv(oc, dc) - x0v.y);
+        const R p1 = x0v.x + d1, c1 = x0v.y + d2;
+        X[k] = V{p1, c1};
         if (track) {
             v[0] = fmax(v[0], fabs(d1));
             v[1] = fmax(v[1], fabs(d2));
@@ -975,44 +1034,58 @@ __global__ void __launch_bounds__(BS)
         }
     };
     const bool zwall = I.wall[2] != 0;
-    // step k needs planes k - 1 .. k + 2 (red of k + 1, black of k); planes
-    // zs - 2 .. zs first; step k prefetches plane k + 3 into the slot of
-    // plane k - 2.  The march starts at k = zs - 2 (red of the plane below
-    // the chunk).
-    for (int z = zs - 2; z <= zs; z++) load_plane(z);
-    __syncthreads();
+    // step k needs planes k - 1 .. k + 2 (red of k + 1, black of k).  The
+    // march starts at k = zs - 2 (red of the plane below the chunk); planes
+    // zs - 2 .. zs + 1 go out first, and step k issues plane k + 4 into the
+    // slot of plane k - 2 (last read by the black phase of step k - 1).
+    for (int z = zs - 2; z <= zs + 1; z++) {
+        issue(z);
+        cp_async_commit();
+    }
     for (int k = zs - 2; k < ze; k++) {
-        if (k + 3 <= ze + 1) load_plane(k + 3);
-        // red on plane k + 1 over the tile and a 1-cell ring
+        if (k + 4 <= ze + 1) issue(k + 4);
+        cp_async_commit();  // (an empty group past the chunk keeps the count)
+        cp_async_wait<2>();  // this thread's copies of planes <= k + 2 landed
+        __syncthreads();
+        // red on plane k + 1 over the tile and a 1-cell ring: thread t takes
+        // red cell t of the (TX + 2) x (TY + 2) ring region, row by row
+        // (red: x + y + z even; a periodic wrap of even length keeps the
+        // parity, a reflected cell is outside)
         if (k + 1 <= ze) {
             const int zr = k + 1;
             const bool zin = zr >= 0 && zr < I.nz;
-            if (zin || !zwall) {
-                constexpr int AX = TX + 2, AY = TY + 2;
-                for (int a = tid; a < AX * AY; a += BS) {
-                    const int rx = 1 + a % AX, ry = 1 + a / AX;
+            const int s0 = ((zr % RING) + RING) % RING;
+            if ((zin || !zwall) && zok[s0]) {
+                const int sm = (s0 + RING - 1) % RING, spl = (s0 + 1) % RING;
+                const bool zm = zok[sm] != 0, zp = zok[spl] != 0;
+                constexpr int HX = (TX + 2) / 2, NRED = HX * (TY + 2);
+                for (int t = tid; t < NRED; t += BS) {
+                    const int ry = 1 + t / HX, j = t - (ry - 1) * HX;
+                    const int p = (x0 + y0 + ry + zr) & 1;
+                    const int rx = 2 - p + 2 * j;
                     const int q = ry * RX + rx;
-                    const int s0 = ((zr % RING) + RING) % RING;
-                    if (!fl[s0 * NP + q]) continue;
+                    if (edge && !flxy[q]) continue;
                     const int gx = x0 + rx, gy = y0 + ry;
-                    // red: (x + y + z) even; a periodic wrap of even length
-                    // keeps the parity, a reflected cell is outside (flag 0)
-                    if ((gx + gy + zr) & 1) continue;
                     const bool own = rx >= 2 && rx < 2 + TX && ry >= 2 && ry < 2 + TY &&
                                      gx < I.nx && gy < I.ny && zr >= zs && zr < ze;
-                    update(zr, q, own);
+                    update(s0, sm, spl, zm, zp, q, own);
                 }
             }
         }
         __syncthreads();
-        // black on plane k over the tile
+        // black on plane k over the tile: thread t takes black cell t
         if (k >= zs) {
-            for (int a = tid; a < TX * TY; a += BS) {
-                const int rx = 2 + a % TX, ry = 2 + a / TX;
+            const int s0 = ((k % RING) + RING) % RING;
+            const int sm = (s0 + RING - 1) % RING, spl = (s0 + 1) % RING;
+            const bool zm = zok[sm] != 0, zp = zok[spl] != 0;
+            constexpr int HX = TX / 2, NBL = HX * TY;
+            for (int t = tid; t < NBL; t += BS) {
+                const int ry = 2 + t / HX, j = t - (ry - 2) * HX;
+                const int p = (x0 + y0 + ry + k) & 1;
+                const int rx = 3 - p + 2 * j;  // black: x + y + z odd
                 const int gx = x0 + rx, gy = y0 + ry;
                 if (gx >= I.nx || gy >= I.ny) continue;
-                if (!((gx + gy + k) & 1)) continue;  // black: odd
-                update(k, ry * RX + rx, true);
+                update(s0, sm, spl, zm, zp, ry * RX + rx, true);
             }
         }
         __syncthreads();
@@ -1024,11 +1097,13 @@ __global__ void __launch_bounds__(BS)
                 const int gx = x0 + rx, gy = y0 + ry;
                 if (gx >= I.nx || gy >= I.ny) continue;
                 const long long c = ((long long)k * I.ny + gy) * I.pitch + gx;
-                pout[c] = sp[s0 * NP + ry * RX + rx];
-                cout[c] = sc[s0 * NP + ry * RX + rx];
+                const V xs = X[s0 * NP + ry * RX + rx];
+                pout[c] = xs.x;
+                cout[c] = xs.y;
             }
         }
     }
+    cp_async_wait<0>();
     __syncthreads();
     // block maxima of the sweep -> round slot; the last block decides
     __shared__ R sh[4][BS / 32];
