@@ -76,7 +76,23 @@ def test_accuracy_against_plain_solves(trained):
                                   steady.sum(), np.median(rel[steady, 0]),
                                   np.median(rel[steady, 1]), np.quantile(rel[steady].max(1), 0.9)))
     assert np.median(rel[steady, 1]) < 0.03
-    assert np.median(rel[steady, 0]) < 0.08
+    # regression bound at the measured level (3.8 %); the stated 3 % target
+    # is the expected failure below
+    assert np.median(rel[steady, 0]) < 0.045
+
+
+@pytest.mark.xfail(reason="the stated target, median held-out Re error <= 3 %, is not met: "
+                          "measured 3.8 % (MLP ensemble; 5.3 % with a Gaussian-process fit of "
+                          "the same data); the labels' own spread over the averaging window "
+                          "(up to 5 % for the steady solves kept) bounds what a fit can reach",
+                   strict=False)
+def test_terminal_re_within_stated_target(trained):
+    sg, _, _ = trained
+    Xte, Yte, d = load("bubble_sweep_heldout.npz")
+    steady = d["S"][d["ok"]].max(axis=1) <= STEADY
+    mean, _ = sg.predict(Xte)
+    rel = np.abs(mean - Yte) / np.abs(Yte)
+    assert np.median(rel[steady, 0]) <= TOL
 
 
 def test_gate_and_calibration(trained, plain_solve):
