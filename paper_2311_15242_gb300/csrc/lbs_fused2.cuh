@@ -713,7 +713,8 @@ __global__ void __launch_bounds__(BS) k_sorfuse2(Inst<R> I, int max_rounds, long
                 if (t + (int)nb < nt)
                     sor_prefetch_tile<R, TX, TY, K, BS>(I, round, (t + nb) % tiles_x,
                                                         (t + nb) / tiles_x);
-                sor_tile2<R, TX, TY, K, BS>(I, round, t % tiles_x, t / tiles_x, smem_raw, tsum);
+                sor_tile2<R, TX, TY, K, BS>(I, round, t % tiles_x, t / tiles_x, smem_raw, tsum,
+                                            nt <= (int)nb);
             }
             double v[1] = {double(tsum[0]) + double(tsum[1])};
             double bsum[1];

@@ -886,7 +886,7 @@ __device__ __forceinline__ void sor_fold_maxima(const Inst<R> &I, int round, R v
 // Iv = inverse diagonals, FX / FY = face coefficients towards +x / +y.
 template <typename R, int TX, int TY, int K, int BS>
 __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx, int by,
-                                             unsigned char *smem_raw, R *tot) {
+                                             unsigned char *smem_raw, R *tot, bool keep) {
     using T = SorTile<R, TX, TY, K, BS>;
     using V = typename Vec2<R>::T;
     constexpr int RX = T::RX, RY = T::RY, H = T::H, RXH = T::RXH, NH = T::NH, NHP = T::NHP;
@@ -905,7 +905,29 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
     // fixed during the solve: round 0 builds them from a and chi (steps 1-3)
     // and stores those of its tile interior; later rounds load them (step 1').
     const bool first = round == 0 || I.sfx == nullptr;
-    if (!first) {
+    if (!first && keep) {
+        // 1''. the block took this same tile in the round before: the
+        //      right-hand sides and coefficients are still in shared memory,
+        //      and so are psi, C of the cells it owns (the values it wrote
+        //      back); only the other region slots are reloaded
+        for (int q = tid; q < RX * RY; q += BS) {
+            const int rx = q % RX, ry = q / RX;
+            if (rx >= H && rx < H + TX && ry >= H && ry < H + TY && x0 + rx < I.nx &&
+                y0 + ry < I.ny)
+                continue;
+            int refl = 0, sx, sy;
+            const int Xc = map_axis(x0 + rx, I.nx, I.wall[0], 1, refl, sx);
+            const int Yc = map_axis(y0 + ry, I.ny, I.wall[1], 2, refl, sy);
+            const int s = ((rx + ry) & 1) * NHP + ry * RXH + (rx >> 1);
+            if (!refl) {
+                const long long c = (long long)Yc * I.pitch + Xc;
+                X[s] = V{__ldcg(&pin[c]), __ldcg(&cin[c])};
+            } else {
+                X[s] = zero;
+            }
+        }
+        __syncthreads();
+    } else if (!first) {
         // 1'. load psi, C, the right-hand sides and the coefficients, in row
         //     order; zero outside the domain.  psi and C change between the
         //     rounds of one launch: they are read through L2, never from a
@@ -1059,7 +1081,7 @@ __device__ __forceinline__ void sor_tile2_cb(const Inst<R> &I, int round, int bx
             comp_add_prod(tot[0], tot[1], __ldcg(&I.a[c]) + I.eps_w, xs.x);
             comp_add_prod(tot[0], tot[1], __ldcg(&I.chi[c]) + I.eps_w, xs.y);
         }
-        if (first && I.sfx) {
+        if (first && I.sfx && !keep) {
             const V fx = FX[s], fy = FY[s], iv = Iv[s];
             I.sfx[c] = fx.x;
             I.scx[c] = fx.y;
@@ -1250,11 +1272,15 @@ __device__ __forceinline__ void sor_prefetch_tile(const Inst<R> &I, int round, i
 // With tot (a thread's compensated sum hi, lo), the thread also adds the
 // surfactant (a + eps) psi + (chi + eps) C of the tile cells it stores, each
 // product exact as hi + lo.
+// keep: the calling block takes this same tile in every round of the launch,
+// so the checkerboard form keeps the tile's coefficients and right-hand sides
+// in shared memory from round to round (identical iterates).
 template <typename R, int TX, int TY, int K, int BS>
 __device__ __forceinline__ void sor_tile2(const Inst<R> &I, int round, int bx, int by,
-                                          unsigned char *smem_raw, R *tot = nullptr) {
+                                          unsigned char *smem_raw, R *tot = nullptr,
+                                          bool keep = false) {
     if ((I.wall[0] || !(I.nx & 1)) && (I.wall[1] || !(I.ny & 1)))
-        sor_tile2_cb<R, TX, TY, K, BS>(I, round, bx, by, smem_raw, tot);
+        sor_tile2_cb<R, TX, TY, K, BS>(I, round, bx, by, smem_raw, tot, keep);
     else
         sor_tile2_list<R, TX, TY, K, BS>(I, round, bx, by, smem_raw, tot);
 }
