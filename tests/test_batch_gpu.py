@@ -82,7 +82,13 @@ def test_batch_equals_single_instances(tiles):
         assert within(err, F32_IMPL_TOL), (tiles, k, err)
         ds = s.diagnostics()
         assert ds["sor_rounds"] == db[k]["sor_rounds"]
-        assert ds["mass_R"] == pytest.approx(db[k]["mass_R"], rel=1e-7)
+        # two trajectories whose FP32 roundings differ (the batch's per-cell
+        # kernels, the single context's fused step): each cell's colour mass
+        # moves by one FP32 rounding of its rest population a step, a random
+        # walk of about 3e-7 a step on these 5000-cell light-bubble instances
+        # (measured on instance 0), so after 20 steps the two totals may
+        # differ by ~1.5e-6 (1.1e-7 relative seen)
+        assert ds["mass_R"] == pytest.approx(db[k]["mass_R"], rel=5e-7)
         s.close()
     b.close()
 
