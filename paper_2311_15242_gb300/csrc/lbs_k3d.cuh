@@ -296,7 +296,7 @@ __global__ void k_fd3(Inst<R> I, double *Sout = nullptr, double *Bout = nullptr)
 //   then give F.
 // ---------------------------------------------------------------------------
 template <typename R, typename P>
-__global__ void __launch_bounds__(256) k_collide3(Inst<R> I) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_collide3(Inst<R> I) {
     LBS_CELL3
     R fT[Q19], fM[Q19];
     const int fl = I.flag[c];
