@@ -219,7 +219,8 @@ __global__ void k_force3(Inst<R> I) {
 // explicit surfactant terms (Eqs. 22-27) and Crank-Nicolson right-hand sides
 // with the six-face operator of Eq. 28; Sout / Bout: export only (see k_fd2)
 template <typename R>
-__global__ void k_fd3(Inst<R> I, double *Sout = nullptr, double *Bout = nullptr) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2)
+    k_fd3(Inst<R> I, double *Sout = nullptr, double *Bout = nullptr) {
     LBS_CELL3
     const R u[3] = {I.ux[c], I.uy[c], I.uz[c]};
     const R *uax[3] = {I.ux, I.uy, I.uz};
