@@ -158,7 +158,7 @@ __global__ void k_grad3(Inst<R> I, int guess = 1) {
 // normal, curvature (Eq. 7), grad psi, sigma (Eq. 8), interfacial force
 // (Eq. 9) plus buoyancy, velocity (Eq. 10)
 template <typename R>
-__global__ void k_force3(Inst<R> I) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 2) k_force3(Inst<R> I) {
     LBS_CELL3
     const R e2 = I.eps_n * I.eps_n;
     const Ax X = make_ax(x, I.nx, I.wall[0], 1), Y = make_ax(y, I.ny, I.wall[1], 2),
