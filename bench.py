@@ -78,15 +78,17 @@ POP_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 
 # DRAM bytes (read + write) a cell of one launch of each fused 2D kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum over cells), from ncu
-# captures with the SOR tile variant below: "bytes_per_cell" on the bench
-# workload itself (256 x 1024; ncu empties the caches before the launch),
+# captures, per SOR tile variant: "bytes_per_cell" on the bench workload
+# itself (256 x 1024; ncu empties the caches before the launch),
 # "bytes_per_cell_hbm" on the 2048 x 2048 bubble array (4.2 M cells, about
 # six times the L2), which the 4096 x 4096 array's roofline scales by its
 # cells (the kernels' traffic grows with the cells).  Reported only while the
 # files that hold their device code (FUSED2_FILES) hash as below.
-TRAFFIC = {"kernel_sha": "e881979bab806c7d", "sor_variant": 6,
-           "bytes_per_cell": {"collide": 129.8, "sor": 28.3},
-           "bytes_per_cell_hbm": {"collide": 243.8, "sor": 200.4}}
+TRAFFIC = {"kernel_sha": "b95ed7afb5a3214c",
+           "bytes_per_cell": {"4": {"collide": 129.8, "sor": 30.3},
+                              "6": {"collide": 129.8, "sor": 28.3}},
+           "bytes_per_cell_hbm": {"4": {"collide": 243.8, "sor": 200.1},
+                                  "6": {"collide": 243.8, "sor": 200.3}}}
 
 def src_hash(files=None):
     """Hash of the CUDA sources (every .cu/.cuh file, or the named ones)."""
@@ -102,11 +104,11 @@ def src_hash(files=None):
 FUSED2_FILES = ("lbs_dev.cuh", "lbs_k2d.cuh", "lbs_fused2.cuh")
 
 
-def traffic_valid(sor_launches, sor_variant):
+def traffic_valid(sor_launches, sor_variant, table="bytes_per_cell"):
     """The captured DRAM traffic applies: same kernel source, the fused
-    two-launch step, the captured SOR tile variant."""
+    two-launch step, a captured SOR tile variant."""
     return (TRAFFIC["kernel_sha"] == src_hash(FUSED2_FILES) and sor_launches == 1
-            and sor_variant == TRAFFIC["sor_variant"])
+            and str(sor_variant) in TRAFFIC[table])
 
 
 def peaks():
@@ -632,7 +634,7 @@ def main():
     roof = roofline2(kmean, cells, args.storage, sweeps, hbm, src, sor_launches=sor_launches)
     roof["sor_launches_per_step"] = sor_launches
     if traffic_valid(sor_launches, tuned["sor"]):
-        roof["traffic"] = TRAFFIC["bytes_per_cell"][roof["kernel"]] * cells
+        roof["traffic"] = TRAFFIC["bytes_per_cell"][str(tuned["sor"])][roof["kernel"]] * cells
     steproof = {"2d_" + args.storage: step_roofline(value / world, "d2q9", args.storage, hbm,
                                                    "L2 (46 MB of state)")}
 
@@ -812,9 +814,10 @@ def main():
                 sl = 1 if nkb == 2 else nkb - 4
                 big["roofline"] = roofline2(km, cellsb, st, dgb["sor_iters_psi"], hbm, src,
                                             sor_launches=sl)
-                if traffic_valid(sl, tb["sor"]):
+                if traffic_valid(sl, tb["sor"], "bytes_per_cell_hbm"):
                     big["roofline"]["traffic"] = (
-                        TRAFFIC["bytes_per_cell_hbm"][big["roofline"]["kernel"]] * cellsb)
+                        TRAFFIC["bytes_per_cell_hbm"][str(tb["sor"])][big["roofline"]["kernel"]]
+                        * cellsb)
                     big["roofline"]["traffic_source"] = (
                         "ncu on the 2048 x 2048 bubble array, scaled by cells")
             steproof["big2d_" + st] = step_roofline(big["mlups"][st], "d2q9", st, hbm,

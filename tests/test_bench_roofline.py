@@ -69,13 +69,16 @@ def test_traffic_table_shape(bench):
     t = bench.TRAFFIC
     assert len(t["kernel_sha"]) == 16 and int(t["kernel_sha"], 16) >= 0
     for table in ("bytes_per_cell", "bytes_per_cell_hbm"):
-        for k, v in t[table].items():
-            assert k in ("collide", "sor") and v > 0
-    assert isinstance(t["sor_variant"], int)
-    # valid only for the captured source, form and tile variant
+        for variant, per in t[table].items():
+            assert 0 <= int(variant) <= 8
+            for k, v in per.items():
+                assert k in ("collide", "sor") and v > 0
+    # valid only for the captured source, form and tile variants
     ok = bench.src_hash(bench.FUSED2_FILES) == t["kernel_sha"]
-    assert bench.traffic_valid(1, t["sor_variant"]) == ok
-    assert not bench.traffic_valid(3, t["sor_variant"])
-    assert not bench.traffic_valid(1, t["sor_variant"] + 1)
+    v = int(next(iter(t["bytes_per_cell"])))
+    assert bench.traffic_valid(1, v) == ok
+    assert not bench.traffic_valid(3, v)
+    missing = next(k for k in range(9) if str(k) not in t["bytes_per_cell"])
+    assert not bench.traffic_valid(1, missing)
     assert set(bench.FUSED2_FILES) == {"lbs_dev.cuh", "lbs_k2d.cuh", "lbs_fused2.cuh"}
     assert bench.src_hash(bench.FUSED2_FILES) != bench.src_hash()
