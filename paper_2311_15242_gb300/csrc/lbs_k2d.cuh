@@ -116,14 +116,21 @@ __device__ __forceinline__ void meq9(R rho, R ux, R uy, R al, R *m) {
     m[8] = rho * ux * uy;
 }
 
+// f = M^{-1} m = M^T diag(1 / |row j|^2) m.  Each moment is divided by its
+// row norm once; the entries of M are 0, +-1, +-2 or +-4, so a (m_j / n_j)
+// equals (a m_j) / n_j exactly (nine divisions instead of one a term: this
+// runs in FP64, on GB300's narrow FP64 pipe)
 template <typename R>
 __device__ __forceinline__ void minv9(const R *m, R *f) {
+    R mn[Q9];
+#pragma unroll
+    for (int j = 0; j < Q9; j++) mn[j] = m[j] / R(mnorm9(j));
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         R s = R(0);
 #pragma unroll
         for (int j = 0; j < Q9; j++)
-            if (m9(j, i) != 0) s += R(m9(j, i)) * m[j] / R(mnorm9(j));
+            if (m9(j, i) != 0) s += R(m9(j, i)) * mn[j];
         f[i] = s;
     }
 }

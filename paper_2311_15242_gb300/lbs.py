@@ -245,12 +245,23 @@ class Solver:
     def sync(self):
         self._check(self.L.lbs_sync(self.h))
 
-    def fields(self):
-        rho = np.empty(self.shape)
-        u = np.empty((3,) + self.shape)
-        phi, psi, C_ = (np.empty(self.shape) for _ in range(3))
-        self._check(self.L.lbs_get_fields(self.h, _dp(rho), _dp(u), _dp(phi), _dp(psi), _dp(C_)))
-        return dict(rho=rho, u=u, phi=phi, psi=psi, C=C_)
+    def fields(self, out=None):
+        """rho, u (3 components), phi, psi, C as float64 arrays of the grid's
+        shape; into the caller's arrays when `out` holds them (page-locked
+        ones make the copy faster), else into new ones."""
+        if out is None:
+            out = dict(rho=np.empty(self.shape), u=np.empty((3,) + self.shape),
+                       phi=np.empty(self.shape), psi=np.empty(self.shape),
+                       C=np.empty(self.shape))
+        for k in ("rho", "phi", "psi", "C"):
+            a = out[k]
+            if a.dtype != np.float64 or a.shape != self.shape or not a.flags.c_contiguous:
+                raise ValueError(f"fields: {k} must be a C-contiguous float64 array of {self.shape}")
+        a = out["u"]
+        if a.dtype != np.float64 or a.shape != (3,) + self.shape or not a.flags.c_contiguous:
+            raise ValueError(f"fields: u must be a C-contiguous float64 array of {(3,) + self.shape}")
+        self._check(self.L.lbs_get_fields(self.h, *[_dp(out[k]) for k in ("rho", "u", "phi", "psi", "C")]))
+        return out
 
     def profile(self, on=True):
         self._check(self.L.lbs_profile(self.h, int(bool(on))))

@@ -440,3 +440,24 @@ def test_wide_halo_sor_variants(variant):
     assert within(err, F32_TOL), (variant, err)
     err = errors(out[4], out[variant])
     assert max(err.values()) < 1e-5, (variant, err)
+
+
+def test_fields_into_caller_arrays():
+    """lbs_get_fields through the binding into arrays the caller owns (the
+    bench passes page-locked ones): the same values as fresh arrays; arrays of
+    the wrong shape or type are refused before any copy."""
+    cfg = bubble()
+    f = W.initial_fields(cfg, seed=3, noise=0.02)
+    s = solver(cfg, "f32")
+    s.init_fields(f["phi"], f["psi"], f["C"], f["u"])
+    s.step(3)
+    a = s.fields()
+    out = {k: np.empty_like(v) for k, v in a.items()}
+    b = s.fields(out=out)
+    assert b is out
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    bad = dict(out, psi=np.empty(out["psi"].shape, dtype=np.float32))
+    with pytest.raises(ValueError):
+        s.fields(out=bad)
+    s.close()
