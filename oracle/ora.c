@@ -20,9 +20,10 @@
  * Readings of points the paper leaves open (numbered R1..R28) are marked
  * "reading:" where they are used.
  *
- * Parity unpinned: the D3Q19 equilibrium rows 17-19 (Eq. 40, taken as
- * printed) have no independent check; the 3D correction coefficient is
- * checked only where it vanishes (standard alpha).
+ * Parity unpinned: the velocity terms of the D3Q19 equilibrium rows 17-19
+ * (Eq. 40, taken as printed) have no independent check (their rest value
+ * is checked against the alpha-model's rest state); the 3D correction
+ * coefficient is checked only where it vanishes (standard alpha).
  */
 #include "ora.h"
 

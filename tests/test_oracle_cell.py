@@ -101,6 +101,31 @@ def test_meq_moments_for_any_alpha(D):
     assert np.isclose(ora.cs2(2, 0.2), 0.6 * 0.8)
 
 
+def test_d3q19_equilibrium_at_rest_is_the_alpha_model_rest_state():
+    """The rest state of the alpha-model on D3Q19, for any alpha^k: the rest
+    particle carries rho alpha, and the moving directions share rho (1 -
+    alpha) in the proportion of the standard weights, 1/18 : 1/36 over their
+    total 2/3, i.e. rho (1 - alpha)/12 on the axes and rho (1 - alpha)/24 on
+    the diagonals.  It pins every row of Eq. 40 at u = 0, rows 17-19 included
+    (their rest value rho (1 - alpha)/6; rho/9 at the standard alpha 1/3,
+    the fourth moment sum w_i e_a^2 e_b^2 of the standard lattice); only
+    their velocity terms stay unpinned."""
+    e, w, _, Minv = lat(3)
+    axis = np.abs(e).sum(axis=1) == 1
+    diag = np.abs(e).sum(axis=1) == 2
+    rng = np.random.default_rng(4)
+    for alpha in (0.2, 1 / 3, 0.6, 0.9444444444444444):
+        rho = rng.uniform(0.1, 2)
+        f = Minv @ ora.meq(3, rho, np.zeros(3), alpha)
+        ref = np.where(axis, rho * (1 - alpha) / 12, np.where(diag, rho * (1 - alpha) / 24,
+                                                              rho * alpha))
+        assert np.allclose(f, ref, atol=1e-15), alpha
+    # the standard alpha gives the standard weights
+    f = Minv @ ora.meq(3, 1.0, np.zeros(3), 1 / 3)
+    assert np.allclose(f, w, atol=1e-15)
+    assert np.isclose(np.sum(w * e[:, 0] ** 2 * e[:, 1] ** 2), 1 / 9)
+
+
 def test_correction_coefficient_is_the_lattice_third_moment_deficit():
     """App. A: 1.8 alpha - 0.8 = 1 - 3 (c_s^k)^2 (D2Q9 has sum f e_x^3 =
     sum f e_x, so the equilibrium third moment misses 3 c_s^2 - 1)."""
