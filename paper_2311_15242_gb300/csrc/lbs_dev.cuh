@@ -357,17 +357,62 @@ __device__ __forceinline__ unsigned int fmix32(unsigned int h) {
 __device__ __forceinline__ unsigned int rescale_key(long long c, int k, long long n) {
     return fmix32((unsigned int)c ^ fmix32((unsigned int)(2 * n + k)));
 }
+// the exact s + e (s = fl(s + e), |e| <= ulp/2) rounded without bias: s, or
+// its neighbour on the side of e with probability |e| / (distance to it)
+__device__ __forceinline__ float pick_unbiased(float s, float e, unsigned int key) {
+    if (e == 0.0f) return s;
+    const float nb = nextafterf(s, e > 0.0f ? INFINITY : -INFINITY);
+    const float frac = __fdividef(e, nb - s);  // in (0, 1/2]
+    const float u = float(key >> 8) * 0x1.0p-24f;
+    return u < frac ? nb : s;
+}
 __device__ __forceinline__ double rescale_one(double x, double d, float, unsigned int) {
     return fma(x, d, x);
 }
 __device__ __forceinline__ float rescale_one(float x, double, float d, unsigned int key) {
     float e;
     const float s = two_sum(x, x * d, e);
-    if (e == 0.0f) return s;
-    const float nb = nextafterf(s, e > 0.0f ? INFINITY : -INFINITY);
-    const float frac = __fdividef(e, nb - s);  // in (0, 1/2]
-    const float u = float(key >> 8) * 0x1.0p-24f;
-    return u < frac ? nb : s;
+    return pick_unbiased(s, e, key);
+}
+
+// ---------------------------------------------------------------------------
+// A cell's rest population closes its mass: (a_s + a_c) - (b_s + b_c) + lo,
+// the difference of two compensated sums (the mass the cell holds, the mass
+// its stored moving populations carry) plus a small term.  The hi parts are
+// subtracted exactly (TwoSum), so the value is exact before the one rounding
+// to the storage; in single precision that rounding is unbiased (as the
+// rescale's above).  Rounding to nearest erred the same way step after step:
+// on a steady interface a cell receives the same sub-ulp residual of its
+// 16-bit moving populations every step, and rounding dropped it every time,
+// moving about 1e-9 of one colour's mass into the other's a cell and step.
+// The draws: one 32-bit hash of the cell and a salt of the kernel and step
+// (rest_salt, the same for every cell of a launch) gives the cell's two
+// closures (total, minority) a 16-bit uniform each (rest_u).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned int rest_salt(int tag, long long n) {
+    return fmix32((unsigned int)(4 * n + tag) ^ 0x9E3779B9u);
+}
+__device__ __forceinline__ unsigned int rest_key(long long c, unsigned int salt) {
+    return fmix32((unsigned int)c ^ salt);
+}
+// uniform in [0, 1) of half h (0: total, 1: minority) of a cell's key
+__device__ __forceinline__ float rest_u(unsigned int key, int h) {
+    return float(h ? key >> 16 : key & 0xFFFFu) * 0x1.0p-16f;
+}
+__device__ __forceinline__ double rest_close(double as, double ac, double bs, double bc,
+                                             double lo, float) {
+    double e;
+    const double d = two_sum(as, -bs, e);
+    return d + ((e + (ac - bc)) + lo);
+}
+__device__ __forceinline__ float rest_close(float as, float ac, float bs, float bc, float lo,
+                                            float u) {
+    float e1, e2;
+    const float d = two_sum(as, -bs, e1);
+    const float s = two_sum(d, (e1 + (ac - bc)) + lo, e2);
+    if (e2 == 0.0f) return s;
+    const float nb = nextafterf(s, e2 > 0.0f ? INFINITY : -INFINITY);
+    return u < __fdividef(e2, nb - s) ? nb : s;
 }
 
 // the product a b exactly as hi + lo (lo by one FMA), added to a compensated

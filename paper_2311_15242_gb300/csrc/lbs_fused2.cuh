@@ -435,8 +435,9 @@ __device__ __forceinline__ void lbfd2_tile(const Inst<R> &I, const PopSets<R> &p
             sT.add(vT);
             sM.add(vM);
         }
-        pT01[p1] = (mo.dr_s - sT.s) + (mo.dr_c - sT.c);
-        pM01[p1] = (mo.rm_s - sM.s) + (mo.rm_c - sM.c);
+        const unsigned int rk = rest_key(cc, rest_salt(0, I.ctl->step));
+        pT01[p1] = rest_close(mo.dr_s, mo.dr_c, sT.s, sT.c, R(0), rest_u(rk, 0));
+        pM01[p1] = rest_close(mo.rm_s, mo.rm_c, sM.s, sM.c, R(0), rest_u(rk, 1));
         flag1[p1] = (uint8_t)fl;
     }
     __syncthreads();
@@ -567,8 +568,9 @@ __device__ __forceinline__ void lbfd2_tile(const Inst<R> &I, const PopSets<R> &p
             sM.add(fM[i]);
         }
     }
-    fT[0] = ((gT.s - sT.s) + (gT.c - sT.c)) + loT;
-    fM[0] = ((gM.s - sM.s) + (gM.c - sM.c)) + loM;
+    const unsigned int rk = rest_key(c, rest_salt(1, I.ctl->step));
+    fT[0] = rest_close(gT.s, gT.c, sT.s, sT.c, loT, rest_u(rk, 0));
+    fM[0] = rest_close(gM.s, gM.c, sM.s, sM.c, loM, rest_u(rk, 1));
     ps.dT0[c] = fT[0];
     ps.dM0[c] = fM[0];
     ps.dflag[c] = (uint8_t)fl;

@@ -436,8 +436,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_collide3(Inst<R
         sT.add(stq<R, P>(I, I.gT, i, c, post[i]));
         sM.add(stq<R, P>(I, I.gM, i, c, fr * (I.shift[i] + post[i]) + sg * segi));
     }
-    I.gT0[c] = (mo.dr_s - sT.s) + (mo.dr_c - sT.c);
-    I.gM0[c] = (mo.rm_s - sM.s) + (mo.rm_c - sM.c);
+    const unsigned int rk = rest_key(c, rest_salt(0, I.ctl->step));
+    I.gT0[c] = rest_close(mo.dr_s, mo.dr_c, sT.s, sT.c, R(0), rest_u(rk, 0));
+    I.gM0[c] = rest_close(mo.rm_s, mo.rm_c, sM.s, sM.c, R(0), rest_u(rk, 1));
     I.gflag[c] = (uint8_t)fl;
 }
 
@@ -586,8 +587,9 @@ __global__ void __launch_bounds__(256, 3) k_stream3(Inst<R> I) {
             sM.add(fM[i]);
         }
     }
-    fT[0] = ((gT.s - sT.s) + (gT.c - sT.c)) + loT;
-    fM[0] = ((gM.s - sM.s) + (gM.c - sM.c)) + loM;
+    const unsigned int rk = rest_key(c, rest_salt(1, I.ctl->step));
+    fT[0] = rest_close(gT.s, gT.c, sT.s, sT.c, loT, rest_u(rk, 0));
+    fM[0] = rest_close(gM.s, gM.c, sM.s, sM.c, loM, rest_u(rk, 1));
     I.fT0[c] = fT[0];
     I.fM0[c] = fM[0];
     I.flag[c] = (uint8_t)fl;

@@ -3,17 +3,18 @@ D = 64, density ratio 10, Eo = 10, Bi = 1: 50,000 steps), every storage form
 against the FP64 storage of the same GPU path (itself matched to the FP64
 oracle to 1e-9 stage by stage; the oracle would need hours for this run).
 
-Measured (the diagnostics' terminal values, relative to FP64):
+Measured (the diagnostics' terminal values, relative to FP64; drifts a
+step of the colour masses and the total surfactant):
   FP32: Re 2.5e-4, aspect ratio 4.3e-4, rise velocity 6e-5, centroid 2e-5,
-        psi_av 3e-3; colour masses drift 1.5e-11 a step, the total
-        surfactant 7.5e-17;
-  FP16: Re 7.3 %, aspect ratio 2.4 %, centroid 2.4 %; red mass -5e-9 a step;
-  BF16: Re 26 %, aspect ratio 22 %, centroid 13 %; red mass -5.7e-9 a step.
-FP32 keeps the physics of the run; the 16-bit forms do not (their rounding
-of the light phase's populations speeds the bubble up), and their red-mass
-drift is 50 times the stated 1e-10 a step.  The FP32 bounds below are the
-run's claims; the 16-bit bounds are regression bounds at the measured
-level."""
+        psi_av 3e-3; red mass 6e-13, total surfactant 2e-16;
+  FP16: Re 7.4 %, aspect ratio 2.2 %, centroid 2.4 %; red mass 4.5e-14;
+  BF16: Re 26 %, aspect ratio 21 %, centroid 13 %; red mass 1.5e-12.
+FP32 keeps the physics of the run; the 16-bit forms conserve as well but do
+not keep the physics (their rounding of the light phase's populations
+speeds the bubble up).  (Before the rest populations were rounded without
+bias, the 16-bit forms moved red mass into blue at about 5e-9 a step.)  The
+FP32 bounds and every form's conservation bound are the run's claims; the
+16-bit physics bounds are regression bounds at the measured level."""
 import numpy as np
 import pytest
 
@@ -61,6 +62,11 @@ def test_fp32_keeps_the_physics_of_the_full_run(runs):
     assert rel(d["U"][1], ref["U"][1]) < 1e-3
     assert rel(d["centroid"][1], ref["centroid"][1]) < 1e-4
     assert rel(d["psi_av"], ref["psi_av"]) < 1e-2
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_every_form_conserves_to_the_stated_bound(runs, storage):
+    d0, d = runs[storage]
     for k in ("mass_R", "mass_B", "surf_total"):
         assert abs(drift(d0, d, k)) <= 1e-10, (k, drift(d0, d, k))
 
@@ -80,15 +86,3 @@ def test_16bit_forms_at_their_measured_level(runs, storage, bound):
     print(storage, {k: "%.3g" % v for k, v in errs.items()},
           "red mass drift a step %.2e" % drift(d0, d, "mass_R"))
     assert max(errs.values()) < bound, errs
-    assert abs(drift(d0, d, "mass_R")) < 1e-8
-    assert abs(drift(d0, d, "surf_total")) < 1e-13
-
-
-@pytest.mark.xfail(strict=False, reason="16-bit storage: the red (light) mass drifts -5e-9 (FP16) "
-                   "and -5.7e-9 (BF16) a step over the full run, 50 times the stated 1e-10; the "
-                   "dense phase and the total surfactant stay within it")
-@pytest.mark.parametrize("storage", ["f16", "bf16"])
-def test_16bit_forms_conserve_to_the_stated_bound(runs, storage):
-    d0, d = runs[storage]
-    for k in ("mass_R", "mass_B", "surf_total"):
-        assert abs(drift(d0, d, k)) <= 1e-10, (k, drift(d0, d, k))
