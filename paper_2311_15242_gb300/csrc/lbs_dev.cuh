@@ -199,24 +199,40 @@ struct PopCvt<float> {
     static constexpr bool scaled = false;
     static __device__ __forceinline__ float to(float v) { return v; }
     static __device__ __forceinline__ float from(float v) { return v; }
+    static __device__ __forceinline__ float from_sr(float v, float) { return v; }
 };
 template <>
 struct PopCvt<double> {
     static constexpr bool scaled = false;
     static __device__ __forceinline__ double to(double v) { return v; }
     static __device__ __forceinline__ double from(double v) { return v; }
+    static __device__ __forceinline__ double from_sr(double v, float) { return v; }
 };
 template <>
 struct PopCvt<__half> {
     static constexpr bool scaled = true;
     static __device__ __forceinline__ float to(__half v) { return __half2float(v); }
     static __device__ __forceinline__ __half from(float v) { return __float2half_rn(v); }
+    // one of the two neighbouring values, the upper with probability by
+    // distance (u uniform in [0, 1)); u < 0: to nearest
+    static __device__ __forceinline__ __half from_sr(float v, float u) {
+        if (u < 0.0f) return from(v);
+        const __half lo = __float2half_rd(v), hi = __float2half_ru(v);
+        const float a = __half2float(lo), b = __half2float(hi);
+        return (b > a && u * (b - a) < v - a) ? hi : lo;
+    }
 };
 template <>
 struct PopCvt<__nv_bfloat16> {
     static constexpr bool scaled = false;
     static __device__ __forceinline__ float to(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ __nv_bfloat16 from_sr(float v, float u) {
+        if (u < 0.0f) return from(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rd(v), hi = __float2bfloat16_ru(v);
+        const float a = __bfloat162float(lo), b = __bfloat162float(hi);
+        return (b > a && u * (b - a) < v - a) ? hi : lo;
+    }
 };
 
 template <typename R, typename P>
@@ -236,9 +252,12 @@ __device__ __forceinline__ R ldq(const Inst<R> &I, const void *mov, const R *res
     return i == 0 ? rest[c] : ldp<R, P>(I, mov, (long long)i * I.plane + c);
 }
 // store moving population i (i >= 1); returns the value actually stored
+// (u: the draw of an unbiased rounding to a 16-bit storage, pop_u; negative:
+// to nearest; FP32 and FP64 storage store v itself)
 template <typename R, typename P>
-__device__ __forceinline__ R stq(const Inst<R> &I, void *mov, int i, long long c, R v) {
-    const P s = PopCvt<P>::from(PopCvt<P>::scaled ? v * I.pscale : v);
+__device__ __forceinline__ R stq(const Inst<R> &I, void *mov, int i, long long c, R v,
+                                 float u = -1.0f) {
+    const P s = PopCvt<P>::from_sr(PopCvt<P>::scaled ? v * I.pscale : v, u);
     ((P *)mov)[(long long)i * I.plane + c] = s;
     const R back = R(PopCvt<P>::to(s));
     return PopCvt<P>::scaled ? back * I.pinv : back;
@@ -398,6 +417,12 @@ __device__ __forceinline__ unsigned int rest_key(long long c, unsigned int salt)
 // uniform in [0, 1) of half h (0: total, 1: minority) of a cell's key
 __device__ __forceinline__ float rest_u(unsigned int key, int h) {
     return float(h ? key >> 16 : key & 0xFFFFu) * 0x1.0p-16f;
+}
+// the draw of moving population j (2 i for the total, 2 i + 1 for the
+// minority) of a cell: its 16-bit storage is rounded without bias too, since
+// at a steady interface rounding to nearest errs the same way every step
+__device__ __forceinline__ float pop_u(unsigned int key, int j) {
+    return float(fmix32(key ^ (0x9E3779B9u * (unsigned int)(j + 1))) >> 8) * 0x1.0p-24f;
 }
 __device__ __forceinline__ double rest_close(double as, double ac, double bs, double bc,
                                              double lo, float) {

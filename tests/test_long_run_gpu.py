@@ -6,15 +6,17 @@ oracle to 1e-9 stage by stage; the oracle would need hours for this run).
 Measured (the diagnostics' terminal values, relative to FP64; drifts a
 step of the colour masses and the total surfactant):
   FP32: Re 2.5e-4, aspect ratio 4.3e-4, rise velocity 6e-5, centroid 2e-5,
-        psi_av 3e-3; red mass 6e-13, total surfactant 2e-16;
-  FP16: Re 7.4 %, aspect ratio 2.2 %, centroid 2.4 %; red mass 4.5e-14;
-  BF16: Re 26 %, aspect ratio 21 %, centroid 13 %; red mass 1.5e-12.
-FP32 keeps the physics of the run; the 16-bit forms conserve as well but do
-not keep the physics (their rounding of the light phase's populations
-speeds the bubble up).  (Before the rest populations were rounded without
-bias, the 16-bit forms moved red mass into blue at about 5e-9 a step.)  The
-FP32 bounds and every form's conservation bound are the run's claims; the
-16-bit physics bounds are regression bounds at the measured level."""
+        psi_av 3e-3; red mass 6e-12, total surfactant 1e-16;
+  FP16: Re 1.6e-4, aspect ratio 3.4e-4, rise velocity 1.4e-4, centroid
+        5.5e-5, psi_av 1e-3; red mass 3e-12;
+  BF16: Re 8.2e-4, aspect ratio 1.1e-3, rise velocity 3.6e-4, centroid
+        1.8e-4, psi_av 5.7e-3; red mass 2.2e-12.
+Every form keeps the physics of the run and conserves within the stated
+1e-10 a step.  The 16-bit forms do so because both their moving and their
+rest populations are rounded without bias: rounded to nearest, the same
+residual at a steady interface errs the same way step after step, which
+sped the bubble up (Re +7 % FP16, +26 % BF16) and moved red mass into blue
+(-5e-9 a step)."""
 import numpy as np
 import pytest
 
@@ -77,12 +79,14 @@ def test_fp64_conserves_to_round_off(runs):
         assert abs(drift(d0, d, k)) <= 1e-15, (k, drift(d0, d, k))
 
 
-@pytest.mark.parametrize("storage,bound", [("f16", 0.12), ("bf16", 0.4)])
-def test_16bit_forms_at_their_measured_level(runs, storage, bound):
+@pytest.mark.parametrize("storage,bound", [("f16", 1e-3), ("bf16", 3e-3)])
+def test_16bit_forms_keep_the_physics_of_the_full_run(runs, storage, bound):
     _, ref = runs["f64"]
     d0, d = runs[storage]
     errs = {k: rel(d[k], ref[k]) for k in ("Re", "aspect_ratio")}
+    errs["U"] = rel(d["U"][1], ref["U"][1])
     errs["centroid"] = rel(d["centroid"][1], ref["centroid"][1])
     print(storage, {k: "%.3g" % v for k, v in errs.items()},
           "red mass drift a step %.2e" % drift(d0, d, "mass_R"))
     assert max(errs.values()) < bound, errs
+    assert rel(d["psi_av"], ref["psi_av"]) < 2e-2
