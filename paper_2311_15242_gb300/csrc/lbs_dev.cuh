@@ -186,7 +186,7 @@ __host__ __device__ __forceinline__ MomSet<R> mom_of_step(const Inst<R> &I, long
 // ---------------------------------------------------------------------------
 // Population storage: arithmetic in R, storage in P.  The stored numbers are
 // deviations from a rest state or minority-colour populations, all small,
-// which is what makes 16-bit storage usable (rounded to nearest).
+// which is what makes 16-bit storage usable.
 // ---------------------------------------------------------------------------
 // FP16 populations are stored multiplied by a power of two (2^14 for pure-
 // phase densities <= 1, lower for heavier phases, set on the host): the
@@ -199,27 +199,40 @@ struct PopCvt<float> {
     static constexpr bool scaled = false;
     static __device__ __forceinline__ float to(float v) { return v; }
     static __device__ __forceinline__ float from(float v) { return v; }
-    static __device__ __forceinline__ float from_sr(float v, float) { return v; }
+    static __device__ __forceinline__ float from_r(float v, unsigned int) { return v; }
 };
 template <>
 struct PopCvt<double> {
     static constexpr bool scaled = false;
     static __device__ __forceinline__ double to(double v) { return v; }
     static __device__ __forceinline__ double from(double v) { return v; }
-    static __device__ __forceinline__ double from_sr(double v, float) { return v; }
+    static __device__ __forceinline__ double from_r(double v, unsigned int) { return v; }
 };
 template <>
 struct PopCvt<__half> {
     static constexpr bool scaled = true;
     static __device__ __forceinline__ float to(__half v) { return __half2float(v); }
     static __device__ __forceinline__ __half from(float v) { return __float2half_rn(v); }
-    // one of the two neighbouring values, the upper with probability by
-    // distance (u uniform in [0, 1)); u < 0: to nearest
-    static __device__ __forceinline__ __half from_sr(float v, float u) {
-        if (u < 0.0f) return from(v);
-        const __half lo = __float2half_rd(v), hi = __float2half_ru(v);
-        const float a = __half2float(lo), b = __half2float(hi);
-        return (b > a && u * (b - a) < v - a) ? hi : lo;
+    // one of the two neighbouring values, the far one with probability by
+    // distance (r: 32 uniform bits): the top bits of r are added to the bits
+    // of v that the rounding drops, and their carry decides, so the
+    // probability is exactly the dropped fraction.  Integer instructions
+    // only, no branch: v's significand m (leading one included) counts
+    // steps of 2^(e - 150) for its exponent field e; FP16's step is
+    // 2^(max(e, 113) - 137), t = 126 - min(e, 113) bits coarser (13 in
+    // FP16's normal range, more in its subnormal range below 2^-14).  The
+    // rounded count k is the FP16 significand (1024..2048, a carry being the
+    // next binade's first value) or, below 2^-14, the whole FP16 number.
+    // Exact for t <= 31 (|v| >= 2^-32); below, m is first shifted down to 31
+    // bits, which lowers the probability by less than 2^-31.
+    static __device__ __forceinline__ __half from_r(float v, unsigned int r) {
+        const unsigned int b = __float_as_uint(v), a = b & 0x7FFFFFFFu;
+        const unsigned int e = max(a >> 23, 1u);
+        const unsigned int m = (a & 0x7FFFFFu) | (a >= 0x800000u ? 0x800000u : 0u);
+        const unsigned int t = 126u - min(e, 113u), tt = min(t, 31u);
+        const unsigned int k = ((m >> min(t - tt, 31u)) + (r >> (32u - tt))) >> tt;
+        const unsigned int h = ((max(e, 113u) - 113u) << 10) + k;
+        return __ushort_as_half((unsigned short)(h | ((b >> 16) & 0x8000u)));
     }
 };
 template <>
@@ -227,11 +240,9 @@ struct PopCvt<__nv_bfloat16> {
     static constexpr bool scaled = false;
     static __device__ __forceinline__ float to(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
-    static __device__ __forceinline__ __nv_bfloat16 from_sr(float v, float u) {
-        if (u < 0.0f) return from(v);
-        const __nv_bfloat16 lo = __float2bfloat16_rd(v), hi = __float2bfloat16_ru(v);
-        const float a = __bfloat162float(lo), b = __bfloat162float(hi);
-        return (b > a && u * (b - a) < v - a) ? hi : lo;
+    // as FP16's: BF16 is FP32 without the low 16 bits, at every magnitude
+    static __device__ __forceinline__ __nv_bfloat16 from_r(float v, unsigned int r) {
+        return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r >> 16)) >> 16));
     }
 };
 
@@ -252,12 +263,19 @@ __device__ __forceinline__ R ldq(const Inst<R> &I, const void *mov, const R *res
     return i == 0 ? rest[c] : ldp<R, P>(I, mov, (long long)i * I.plane + c);
 }
 // store moving population i (i >= 1); returns the value actually stored
-// (u: the draw of an unbiased rounding to a 16-bit storage, pop_u; negative:
-// to nearest; FP32 and FP64 storage store v itself)
 template <typename R, typename P>
-__device__ __forceinline__ R stq(const Inst<R> &I, void *mov, int i, long long c, R v,
-                                 float u = -1.0f) {
-    const P s = PopCvt<P>::from_sr(PopCvt<P>::scaled ? v * I.pscale : v, u);
+__device__ __forceinline__ R stq(const Inst<R> &I, void *mov, int i, long long c, R v) {
+    const P s = PopCvt<P>::from(PopCvt<P>::scaled ? v * I.pscale : v);
+    ((P *)mov)[(long long)i * I.plane + c] = s;
+    const R back = R(PopCvt<P>::to(s));
+    return PopCvt<P>::scaled ? back * I.pinv : back;
+}
+// the same, rounded to a 16-bit storage without bias (r: the population's
+// draw, pop_r); FP32 and FP64 storage store v itself
+template <typename R, typename P>
+__device__ __forceinline__ R stq_r(const Inst<R> &I, void *mov, int i, long long c, R v,
+                                   unsigned int r) {
+    const P s = PopCvt<P>::from_r(PopCvt<P>::scaled ? v * I.pscale : v, r);
     ((P *)mov)[(long long)i * I.plane + c] = s;
     const R back = R(PopCvt<P>::to(s));
     return PopCvt<P>::scaled ? back * I.pinv : back;
@@ -418,11 +436,17 @@ __device__ __forceinline__ unsigned int rest_key(long long c, unsigned int salt)
 __device__ __forceinline__ float rest_u(unsigned int key, int h) {
     return float(h ? key >> 16 : key & 0xFFFFu) * 0x1.0p-16f;
 }
-// the draw of moving population j (2 i for the total, 2 i + 1 for the
-// minority) of a cell: its 16-bit storage is rounded without bias too, since
-// at a steady interface rounding to nearest errs the same way every step
-__device__ __forceinline__ float pop_u(unsigned int key, int j) {
-    return float(fmix32(key ^ (0x9E3779B9u * (unsigned int)(j + 1))) >> 8) * 0x1.0p-24f;
+// The moving populations' 16-bit storage is rounded without bias too, since
+// at a steady interface rounding to nearest errs the same way every step.
+// Their draws: a second hash of the cell's key (pop_seed, mixed apart from
+// the closures' draws), times an odd constant for population j (2 i for the
+// total, 2 i + 1 for the minority): a bijection of 32-bit words, so each
+// draw is uniform, at one multiply a population.
+__device__ __forceinline__ unsigned int pop_seed(unsigned int key) {
+    return fmix32(key ^ 0x85EBCA6Bu);
+}
+__device__ __forceinline__ unsigned int pop_r(unsigned int seed, int j) {
+    return seed * (0x9E3779B9u * (2u * (unsigned int)j + 1u));
 }
 __device__ __forceinline__ double rest_close(double as, double ac, double bs, double bc,
                                              double lo, float) {

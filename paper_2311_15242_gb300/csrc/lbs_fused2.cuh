@@ -54,8 +54,8 @@ struct Fuse2 {
 
 // the value stq would store and return, without storing it
 template <typename R, typename P>
-__device__ __forceinline__ R round_pop(const Inst<R> &I, R v, float u) {
-    const P s = PopCvt<P>::from_sr(PopCvt<P>::scaled ? v * I.pscale : v, u);
+__device__ __forceinline__ R round_pop(const Inst<R> &I, R v, unsigned int r) {
+    const P s = PopCvt<P>::from_r(PopCvt<P>::scaled ? v * I.pscale : v, r);
     const R back = R(PopCvt<P>::to(s));
     return PopCvt<P>::scaled ? back * I.pinv : back;
 }
@@ -425,13 +425,13 @@ __device__ __forceinline__ void lbfd2_tile(const Inst<R> &I, const PopSets<R> &p
         const R fr = fdiv(rmin, rdag);
         const R sg = fl ? R(-1) : R(1);
         CSum<R> sT, sM;
-        const unsigned int rk = rest_key(cc, rest_salt(0, I.ctl->step));
+        const unsigned int rk = rest_key(cc, rest_salt(0, I.ctl->step)), rs = pop_seed(rk);
 #pragma unroll
         for (int i = 1; i < Q9; i++) {
             const R segi = seg * w9<R>(i) * (R(ex9(i)) * ggx + R(ey9(i)) * ggy);
-            const R vT = round_pop<R, P>(I, post[i], pop_u(rk, 2 * i));
+            const R vT = round_pop<R, P>(I, post[i], pop_r(rs, 2 * i));
             const R vM = round_pop<R, P>(I, fr * (I.shift[i] + post[i]) + sg * segi,
-                                         pop_u(rk, 2 * i + 1));
+                                         pop_r(rs, 2 * i + 1));
             pT1[(i - 1) * N1 + p1] = vT;
             pM1[(i - 1) * N1 + p1] = vM;
             sT.add(vT);
@@ -557,15 +557,15 @@ __device__ __forceinline__ void lbfd2_tile(const Inst<R> &I, const PopSets<R> &p
     R fT[Q9], fM[Q9];
     CSum<R> gT, gM, sT, sM;
     const R loM = fl ? loB : loR;
-    const unsigned int rk = rest_key(c, rest_salt(1, I.ctl->step));
+    const unsigned int rk = rest_key(c, rest_salt(1, I.ctl->step)), rs = pop_seed(rk);
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         const R mh = fl ? fB[i] : fR[i];
         gT.add(t[i]);
         gM.add(mh);
         if (i) {
-            fT[i] = stq<R, P>(I, ps.dT, i, c, t[i], pop_u(rk, 2 * i));
-            fM[i] = stq<R, P>(I, ps.dM, i, c, mh, pop_u(rk, 2 * i + 1));
+            fT[i] = stq_r<R, P>(I, ps.dT, i, c, t[i], pop_r(rs, 2 * i));
+            fM[i] = stq_r<R, P>(I, ps.dM, i, c, mh, pop_r(rs, 2 * i + 1));
             sT.add(fT[i]);
             sM.add(fM[i]);
         }

@@ -580,13 +580,13 @@ __device__ __forceinline__ void collide2_cell(const Inst<R> &I, int x, int y) {
     // the total, recolouring each colour): every rounding residual of the
     // step stays in the cell
     CSum<R> sT, sM;
-    const unsigned int rk = rest_key(c, rest_salt(0, I.ctl->step));
+    const unsigned int rk = rest_key(c, rest_salt(0, I.ctl->step)), rs = pop_seed(rk);
 #pragma unroll
     for (int i = 1; i < Q9; i++) {
         const R segi = seg * w9<R>(i) * (R(ex9(i)) * ggx + R(ey9(i)) * ggy);
-        sT.add(stq<R, P>(I, I.gT, i, c, post[i], pop_u(rk, 2 * i)));
-        sM.add(stq<R, P>(I, I.gM, i, c, fr * (I.shift[i] + post[i]) + sg * segi,
-                         pop_u(rk, 2 * i + 1)));
+        sT.add(stq_r<R, P>(I, I.gT, i, c, post[i], pop_r(rs, 2 * i)));
+        sM.add(stq_r<R, P>(I, I.gM, i, c, fr * (I.shift[i] + post[i]) + sg * segi,
+                           pop_r(rs, 2 * i + 1)));
     }
     I.gT0[c] = rest_close(mo.dr_s, mo.dr_c, sT.s, sT.c, R(0), rest_u(rk, 0));
     I.gM0[c] = rest_close(mo.rm_s, mo.rm_c, sM.s, sM.c, R(0), rest_u(rk, 1));
@@ -750,15 +750,15 @@ __device__ __forceinline__ void stream2_cell(const Inst<R> &I, int x, int y) {
     R fT[Q9], fM[Q9];
     CSum<R> gT, gM, sT, sM;
     const R loM = fl ? loB : loR;
-    const unsigned int rk = rest_key(c, rest_salt(1, I.ctl->step));
+    const unsigned int rk = rest_key(c, rest_salt(1, I.ctl->step)), rs = pop_seed(rk);
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
         const R mh = fl ? fB[i] : fR[i];
         gT.add(t[i]);
         gM.add(mh);
         if (i) {
-            fT[i] = stq<R, P>(I, I.fT, i, c, t[i], pop_u(rk, 2 * i));
-            fM[i] = stq<R, P>(I, I.fM, i, c, mh, pop_u(rk, 2 * i + 1));
+            fT[i] = stq_r<R, P>(I, I.fT, i, c, t[i], pop_r(rs, 2 * i));
+            fM[i] = stq_r<R, P>(I, I.fM, i, c, mh, pop_r(rs, 2 * i + 1));
             sT.add(fT[i]);
             sM.add(fM[i]);
         }

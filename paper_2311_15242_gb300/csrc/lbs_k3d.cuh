@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_collide3(Inst<R
     // moving populations as stored; the rest populations close the cell's
     // total and minority mass on the pre-collision values (see k_collide2)
     CSum<R> sT, sM;
-    const unsigned int rk = rest_key(c, rest_salt(0, I.ctl->step));
+    const unsigned int rk = rest_key(c, rest_salt(0, I.ctl->step)), rs = pop_seed(rk);
 #pragma unroll
     for (int i = 1; i < Q19; i++) {
         R eg = R(0);
@@ -434,9 +434,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_collide3(Inst<R
         if (ey19(i)) eg += R(ey19(i)) * ggy;
         if (ez19(i)) eg += R(ez19(i)) * ggz;
         const R segi = seg * w19<R>(i) * eg;
-        sT.add(stq<R, P>(I, I.gT, i, c, post[i], pop_u(rk, 2 * i)));
-        sM.add(stq<R, P>(I, I.gM, i, c, fr * (I.shift[i] + post[i]) + sg * segi,
-                         pop_u(rk, 2 * i + 1)));
+        sT.add(stq_r<R, P>(I, I.gT, i, c, post[i], pop_r(rs, 2 * i)));
+        sM.add(stq_r<R, P>(I, I.gM, i, c, fr * (I.shift[i] + post[i]) + sg * segi,
+                           pop_r(rs, 2 * i + 1)));
     }
     I.gT0[c] = rest_close(mo.dr_s, mo.dr_c, sT.s, sT.c, R(0), rest_u(rk, 0));
     I.gM0[c] = rest_close(mo.rm_s, mo.rm_c, sM.s, sM.c, R(0), rest_u(rk, 1));
@@ -576,15 +576,15 @@ __global__ void __launch_bounds__(256, 3) k_stream3(Inst<R> I) {
     R fT[Q19], fM[Q19];
     CSum<R> gT, gM, sT, sM;
     const R loM = fl ? loB : loR;
-    const unsigned int rk = rest_key(c, rest_salt(1, I.ctl->step));
+    const unsigned int rk = rest_key(c, rest_salt(1, I.ctl->step)), rs = pop_seed(rk);
 #pragma unroll
     for (int i = 0; i < Q19; i++) {
         const R mh = fl ? fB[i] : fR[i];
         gT.add(t[i]);
         gM.add(mh);
         if (i) {
-            fT[i] = stq<R, P>(I, I.fT, i, c, t[i], pop_u(rk, 2 * i));
-            fM[i] = stq<R, P>(I, I.fM, i, c, mh, pop_u(rk, 2 * i + 1));
+            fT[i] = stq_r<R, P>(I, I.fT, i, c, t[i], pop_r(rs, 2 * i));
+            fM[i] = stq_r<R, P>(I, I.fM, i, c, mh, pop_r(rs, 2 * i + 1));
             sT.add(fT[i]);
             sM.add(fM[i]);
         }
