@@ -84,9 +84,9 @@ POP_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 # six times the L2), which the 4096 x 4096 array's roofline scales by its
 # cells (the kernels' traffic grows with the cells).  Reported only while the
 # files that hold their device code (FUSED2_FILES) hash as below.
-TRAFFIC = {"kernel_sha": "b95ed7afb5a3214c",
-           "bytes_per_cell": {"4": {"collide": 129.8, "sor": 30.3},
-                              "6": {"collide": 129.8, "sor": 28.3}},
+TRAFFIC = {"kernel_sha": "76d859fe8b6be644",
+           "bytes_per_cell": {"4": {"collide": 130.0, "sor": 30.3},
+                              "6": {"collide": 129.9, "sor": 28.3}},
            "bytes_per_cell_hbm": {"4": {"collide": 243.8, "sor": 200.1},
                                   "6": {"collide": 243.8, "sor": 200.3}}}
 
