@@ -57,8 +57,12 @@ typedef enum {
 typedef enum {
     LBS_F64 = 0,  /* everything in double (reference-grade, slow on GB300) */
     LBS_F32 = 1,  /* FP32 storage and arithmetic, FP64 conservation sums */
-    LBS_F16 = 2,  /* populations stored as IEEE FP16 in shifted form (total
-                     minus a rest state, and the minority colour), FP32
+    LBS_F16 = 2,  /* moving populations stored as IEEE FP16 in shifted form
+                     (total minus a rest state, and the minority colour),
+                     rounded without bias (to a neighbouring value with
+                     probability by distance, drawn from a hash of cell,
+                     step and population: reproducible); rest populations in
+                     FP32 close each cell's total and minority mass; FP32
                      arithmetic and fields, FP64 totals */
     LBS_BF16 = 3  /* the same with bfloat16 population storage */
 } lbs_storage;
