@@ -11,8 +11,9 @@ step of the colour masses and the total surfactant):
         3.9e-5; red mass 1.1e-12;
   BF16: Re 2.4e-4, aspect ratio 1.5e-4, rise velocity 7e-5, centroid
         1.4e-4; red mass 1.5e-12.
-(The 16-bit figures are one realisation of the rounding's draws: another
-realisation of the same rounding gave up to 1.1e-3 in BF16.)
+(The 16-bit figures are one realisation of the rounding's draws: an
+earlier implementation of the same unbiased rounding, drawing other random
+numbers, gave up to 1.1e-3 in BF16.)
 Every form keeps the physics of the run and conserves within the stated
 1e-10 a step.  The 16-bit forms do so because both their moving and their
 rest populations are rounded without bias: rounded to nearest, the same
