@@ -91,9 +91,9 @@ def test_confinement_and_retardation(runs):
     assert runs["surf04"].max() > 1.01 * s04, (runs["surf04"].max(), s04)
 
 
-def test_resolution_trend_towards_the_paper(runs):
+def test_resolution_trend_towards_the_paper(runs, printed):
     r10, r15 = terminal(runs["clean04"]), terminal(runs["clean04_R15"])
-    assert 0.552 < r15 < r10, (r10, r15)
+    assert printed["bubble_clean_2R/Lx=0.4"] < r15 < r10, (r10, r15)
 
 
 def test_liquid_drift_and_relative_velocity(runs):

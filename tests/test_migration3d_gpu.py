@@ -65,7 +65,8 @@ def test_terminal_velocity_against_ygb(terminal):
         assert 0.9 <= v <= 1.1, (k, v)
 
 
-def test_wall_confinement_and_resolution(terminal):
+def test_wall_confinement_and_resolution(terminal, printed):
     ratio = terminal["box10"] / terminal["cube10"]
     assert 0.90 <= ratio <= 0.99, ratio
-    assert abs(terminal["box15"] - 0.958) < abs(terminal["box10"] - 0.958), terminal
+    box = printed["migration_5Rx5Rx10R"]
+    assert abs(terminal["box15"] - box) < abs(terminal["box10"] - box), terminal
